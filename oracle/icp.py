@@ -1,0 +1,123 @@
+"""Differentiable projective point-to-plane ICP (X-SLAM Sec. 4.1, "Differentiable ICP" paragraph).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Energy (Eq. icp): E = sum_u ((T_j V_k(u) - V_g(u_hat))^T N_g(u_hat))^2 with
+u_hat = pi(K T_{k-1}^-1 T_j V_k(u)); V_g, N_g are the model maps ray-cast at the previous pose T_{k-1},
+sampled at the real-valued u_hat by bilinear interpolation (Sec. 4.1, "we generalize the domain of
+integer-value pixel index to R^2 by bilinear interpolation"). Linearising the pose update (Eq. "icp
+approx") turns each iteration into the linear least-squares problem A x = b, solved through its
+normal equations; complex inputs give a complex A and b and the complex solve carries the derivative.
+
+Readings of the paper used here:
+  * the norm in Eq. icp is the squared residual (Gauss-Newton / normal equations);
+  * u_hat's lost pi(.) is restored: u_hat = pi(K_l T_{k-1}^-1 T_j V_k(u));
+  * the update is a left-multiplied twist x = (omega, v): T_{j+1} = exp(x) T_j, with residual
+    r = (p' - q).n and Jacobian J = [(p' x n)^T, n^T] at p' = T_j V_k(u);
+  * pyramid level l reads the level-0 model maps at pixel 2^l u (K_l = K / 2^l);
+  * a correspondence needs: p' in front of the previous camera, the bilinear cell inside the level
+    image (0 <= cell <= size - 2), its 4 model taps valid with |d10-d00|+|d01-d00|+|d11-d00| < disc_gate on the model
+    depth, |p' - q| <= dist_gate, and |(R_j N_k(u)) . n| >= cos(normal_gate) |n| (orientation-free,
+    because the measured and the ray-cast normals point opposite ways); all decided on real parts;
+  * the bilinear normal is not re-normalised;
+  * the bilinear cell of u_hat is chosen as floor(u_hat + CELL_BIAS) with CELL_BIAS = 2^-6 pixel
+    (the weights a = u_hat - cell then lie in [-2^-6, 1 - 2^-6)): at the first iteration
+    T_j = T_{k-1}, so u_hat equals the integer pixel u up to rounding, and an unbiased floor would
+    pick the cell on either side of u depending on the last bit; the bias removes that tie;
+  * iterations run coarse to fine, a fixed number per level (no early exit); an iteration with fewer
+    than min_corr_frac of the level's pixels as correspondences, or whose real A is not positive
+    definite, fails the frame: the pose falls back to the initial guess T_{k-1}.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import measure, se3
+
+CELL_BIAS = 2.0 ** -6
+
+
+def correspondences(D, lintr, level, Tj, Tprev, model, dist_gate=0.1, normal_gate_deg=20.0,
+                    disc_gate=0.1, log=None):
+    """Per-pixel residual r, Jacobian J (N, 6) and validity mask at one pyramid level.
+    ``log``, if a list, receives the discrete decisions (validity, bilinear cells)."""
+    fx, fy, cx, cy, W, H = lintr
+    V = measure.vertex_map(D, lintr)
+    Nm, vvalid = measure.normal_map(D, V)
+    V = V.reshape(-1, 3)
+    Nm = Nm.reshape(-1, 3)
+    valid = vvalid.reshape(-1)
+    Tj = np.asarray(Tj)
+    pp = se3.transform(Tj, V)                          # p' = T_j V_k(u)
+    pc = se3.transform(se3.inverse(Tprev), pp)         # previous camera frame
+    z = pc[:, 2]
+    valid &= np.real(z) > 0
+    zs = np.where(valid, z, 1.0)
+    ux = fx * pc[:, 0] / zs + cx
+    uy = fy * pc[:, 1] / zs + cy
+    ci = np.floor(np.real(ux) + CELL_BIAS)
+    cj = np.floor(np.real(uy) + CELL_BIAS)
+    valid &= (ci >= 0) & (ci <= W - 2) & (cj >= 0) & (cj <= H - 2)
+    i0 = np.where(valid, ci, 0).astype(np.int64)
+    j0 = np.where(valid, cj, 0).astype(np.int64)
+    a = ux - i0
+    b = uy - j0
+    s = 2 ** level
+    dg = model["depth"]
+    taps = [(j0 * s, i0 * s), (j0 * s, (i0 + 1) * s), ((j0 + 1) * s, i0 * s), ((j0 + 1) * s, (i0 + 1) * s)]
+    d = [dg[r, c] for r, c in taps]
+    valid &= (d[0] > 0) & (d[1] > 0) & (d[2] > 0) & (d[3] > 0)
+    valid &= (np.abs(d[1] - d[0]) + np.abs(d[2] - d[0]) + np.abs(d[3] - d[0])) < disc_gate
+    w = [(1 - a) * (1 - b), a * (1 - b), (1 - a) * b, a * b]
+    q = sum(w[i][:, None] * model["V"][taps[i]] for i in range(4))
+    n = sum(w[i][:, None] * model["N"][taps[i]] for i in range(4))
+    diff = pp - q
+    dre = np.real(diff)
+    valid &= np.sum(dre * dre, -1) <= dist_gate ** 2
+    nw = np.real(Nm) @ np.real(Tj[:, :3]).T
+    nre = np.real(n)
+    cosang = np.abs(np.sum(nw * nre, -1))
+    valid &= cosang >= math.cos(math.radians(normal_gate_deg)) * np.sqrt(np.sum(nre * nre, -1))
+    r = np.sum(diff * n, -1)
+    J = np.concatenate([np.cross(pp, n), n], -1)
+    if log is not None:
+        log += [valid, np.where(valid, i0, -1), np.where(valid, j0, -1)]
+    return r, J, valid
+
+
+def normal_equations(r, J, valid):
+    """A = sum J J^T, b = -sum J r over valid pixels (Eq. "icp approx" posed as A x = b)."""
+    Jv = J[valid]
+    rv = r[valid]
+    A = Jv.T @ Jv
+    b = -(Jv.T @ rv)
+    return A, b, int(valid.sum())
+
+
+def solve(A, b):
+    """x = A^-1 b (complex LU; the real part decides positive definiteness)."""
+    try:
+        np.linalg.cholesky(np.real(A))
+    except np.linalg.LinAlgError:
+        return None
+    return np.linalg.solve(A, b)
+
+
+def track(pyr, intr, T_init, T_prev, model, iters=(10, 5, 4), min_corr_frac=0.1, log=None, **gates):
+    """Multi-level ICP from coarse to fine; returns (T_k, ok)."""
+    T = np.asarray(T_init)
+    for level in range(len(iters) - 1, -1, -1):
+        lintr = measure.level_intrinsics(intr, level)
+        npx = lintr[4] * lintr[5]
+        for _ in range(iters[level]):
+            r, J, valid = correspondences(pyr[level], lintr, level, T, T_prev, model, log=log, **gates)
+            A, b, nv = normal_equations(r, J, valid)
+            if nv < min_corr_frac * npx:
+                return np.asarray(T_init), False
+            x = solve(A, b)
+            if x is None:
+                return np.asarray(T_init), False
+            T = se3.compose(se3.se3_exp(x), T)
+    return T, True

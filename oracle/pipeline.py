@@ -1,0 +1,135 @@
+"""The per-frame X-KinectFusion step in CSFD arithmetic (X-SLAM Sec. 4.1) and whole-sequence runs.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Frame k (Sec. 4.1, in the paper's order): surface measurement of D_k (range gate, pyramid, vertex
+and normal maps), camera pose estimation by multi-level ICP against the model maps ray-cast at
+T_{k-1} (frame 0 keeps its given pose), surface update of the TSDF at T_k, and ray casting at T_k
+for the next frame.
+
+Seeds (which input carries the imaginary perturbation h i; one complex run per seed):
+  POSE0 (kind 0, index 0..5): T_0* = exp(h i e_index) T_0 (Eq. lie), a left twist of frame 0's pose;
+  TRUNC (kind 2): mu* = mu + h i;
+  DEPTH (kind 3, index -1 for every pixel, else one linear pixel index): D_k* = D_k + h i at every
+    frame (Eq. csfd_depth).
+The derivative of any result X is Im(X*) / h (Eq. csfd).
+
+Readings: ICP starts each frame from the previous pose T_{k-1} (Sec. 4.1, "initialized with the
+previous frame pose"); on an ICP failure the frame is fused at T_{k-1} and the step reports it.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import fusion, icp, measure, raycast, se3
+from .csfd import H_ORACLE
+
+POSE0, POSE, TRUNC, DEPTH = 0, 1, 2, 3
+
+
+@dataclasses.dataclass
+class Config:
+    icp_iters: tuple = (10, 5, 4)  # finest level first, run coarse to fine
+    dist_gate: float = 0.1
+    normal_gate_deg: float = 20.0
+    disc_gate: float = 0.1
+    min_corr_frac: float = 0.1
+    ray_step_vox: float = 1.0
+    depth_min: float = 0.2
+    depth_max: float = 4.0
+    pyr_range: float = 0.09
+    w_max: float = np.inf
+
+
+@dataclasses.dataclass
+class Seed:
+    """A perturbed input. ``imag`` True: the CSFD perturbation h i; False: a real shift by h (used
+    only to evaluate central finite differences of the real pipeline)."""
+    kind: int
+    index: int = 0
+    h: float = H_ORACLE
+    imag: bool = True
+
+    @property
+    def delta(self):
+        return 1j * self.h if self.imag else self.h
+
+
+class XKinectFusion:
+    """One run of the pipeline: real (seed None) or with one complex perturbation direction."""
+
+    def __init__(self, dims, voxel, mu, origin, intr, T0, cfg: Config = None, seed: Seed = None):
+        self.dims, self.voxel, self.origin, self.intr = tuple(dims), voxel, tuple(origin), intr
+        self.cfg = cfg or Config()
+        self.seed = seed
+        self.cplx = seed is not None and seed.imag
+        self.pert = seed is not None
+        dt = np.complex128 if self.cplx else np.float64
+        n = int(np.prod(dims))
+        self.F = np.ones(n, dt)
+        self.W = np.zeros(n)
+        self.mu = mu + (seed.delta if self.pert and seed.kind == TRUNC else 0)
+        T0 = np.asarray(T0, np.float64)
+        if self.pert and seed.kind == POSE0:
+            self.T = se3.perturb_pose(T0, seed.index, seed.delta)
+        else:
+            self.T = T0.astype(dt)
+        self.k = 0
+        self.model = None
+        self.decisions = []  # every discrete branch taken, for mask-identity checks
+
+    def measure(self, depth):
+        D = np.asarray(depth, np.float64)
+        if self.pert and self.seed.kind == DEPTH:
+            pert = np.zeros(D.shape, type(self.seed.delta))
+            if self.seed.index < 0:
+                pert[:] = self.seed.delta
+            else:
+                pert.reshape(-1)[self.seed.index] = self.seed.delta
+            D = np.where(D > 0, D + pert, 0)
+        D = measure.range_gate(D, self.cfg.depth_min, self.cfg.depth_max)
+        return measure.pyramid(D, len(self.cfg.icp_iters), self.cfg.pyr_range)
+
+    def frame(self, depth):
+        c = self.cfg
+        pyr = self.measure(depth)
+        ok = True
+        if self.k > 0:
+            gates = dict(dist_gate=c.dist_gate, normal_gate_deg=c.normal_gate_deg, disc_gate=c.disc_gate)
+            self.T, ok = icp.track(pyr, self.intr, self.T, self.T, self.model, c.icp_iters,
+                                   c.min_corr_frac, log=self.decisions, **gates)
+        fusion.integrate(self.F, self.W, pyr[0], self.T, self.intr, self.dims, self.origin,
+                         self.voxel, self.mu, c.disc_gate, c.w_max, log=self.decisions)
+        d, V, N = raycast.raycast(self.F, self.W, self.T, self.intr, self.dims, self.origin, self.voxel,
+                                  c.depth_min, c.depth_max, c.ray_step_vox, log=self.decisions)
+        self.model = dict(depth=d, V=V, N=N)
+        self.k += 1
+        return self.T, ok
+
+
+def run(wl, seeds=(), frames=None, cfg: Config = None):
+    """Run the real pipeline and one complex run per seed over ``frames`` frames of workload ``wl``.
+
+    Returns dict: pose (F, 3, 4) real trajectory; ok (F,); per seed j: dpose[j] (F, 3, 4) = Im T / h,
+    dtwist[j] (F, 6) as left twists; real_match[j] = max |Re(T*) - T| over the run."""
+    cfg = cfg or Config(icp_iters=tuple(wl.icp_iters), depth_min=wl.depth_min, depth_max=wl.depth_max)
+    nf = wl.depth.shape[0] if frames is None else frames
+    runs = [XKinectFusion(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, wl.poses[0], cfg, None)]
+    runs += [XKinectFusion(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, wl.poses[0], cfg, s) for s in seeds]
+    pose = np.zeros((nf, 3, 4))
+    ok = np.zeros(nf, bool)
+    dpose = np.zeros((len(seeds), nf, 3, 4))
+    dtwist = np.zeros((len(seeds), nf, 6))
+    real_match = np.zeros(len(seeds))
+    for k in range(nf):
+        T, ok[k] = runs[0].frame(wl.depth[k])
+        pose[k] = T
+        for j, s in enumerate(seeds):
+            Tc, _ = runs[j + 1].frame(wl.depth[k])
+            _, dT, tw = se3.readout(Tc, s.h) if s.h != 0 else (None, np.zeros((3, 4)), np.zeros(6))
+            dpose[j, k] = dT
+            dtwist[j, k] = tw
+            real_match[j] = max(real_match[j], np.abs(Tc.real - T).max())
+    return dict(pose=pose, ok=ok, dpose=dpose, dtwist=dtwist, real_match=real_match, runs=runs)
