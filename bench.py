@@ -1,0 +1,458 @@
+#!/usr/bin/env python3
+"""Throughput of the X-SLAM complex-step X-KinectFusion step (X-SLAM Sec. 3-4.1) on one GB300.
+
+A step is one frame of the whole hot path (range gate, bilateral filter, pyramid, 19 ICP iterations
+with the FP64 6x6 solve, TSDF update, ray cast, derivative read-out) on 1 real + K FP32 imaginary
+lanes, over a seeded synthetic 640x480 depth sequence through a 256^3 x 1 cm room (K = 6: the left
+twist of the first pose). Prints one JSON line (rank 0):
+
+  value        frames/s with the depth frames resident in HBM (CUDA events on the caller's stream,
+               which the library's stream is ordered against), summed over ranks;
+  e2e          frames/s through the public call with pinned host depth in and the pose + derivative
+               block out every frame (host<->device copies inside the timed region);
+  roofline     the dominant kernel (largest device time per frame in a profiled pass over the same
+               frames): algorithmic bytes per launch / its mean launch time, against the measured HBM
+               copy bandwidth;
+  cpu_baseline the CPU oracle (complex128, one process per lane) timed on the machine's host cores on
+               frame 1 of the same sequence, which also gives the derivative error of the GPU lanes.
+
+--impl reference times the oracle alone on sampled steps of the same workload (see _reference).
+Multi-GPU (torchrun): every rank runs its own independent sequence (replicas, no collective in the
+data path; weak scaling); the timed region is bracketed by barriers and the max over ranks is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CSFD frames/s (640x480, 256³, K=6) FP32-batched vs plain FP64 at 1e-3 grad err"
+H_GPU = 1e-10
+
+
+# ------------------------------------------------------------------------------------------------
+# workloads
+# ------------------------------------------------------------------------------------------------
+def make_workload(name, seed, frames, device):
+    from paper_2405_02187_gb300 import synth
+    if name == "room256":
+        return synth.room_walk(seed=seed, frames=frames, device=device)
+    if name == "orbit64":
+        return synth.small_orbit(seed=seed, frames=frames, device=device)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def wl_desc(wl, K):
+    return dict(workload=f"{wl.name}_K{K}", volume=f"{wl.dims[0]}^3 x {wl.voxel * 100:g} cm",
+                image=f"{wl.intr.width}x{wl.intr.height}", lanes=K, seeds=f"POSE0 twist components 0..{K - 1}",
+                icp_iters="/".join(str(i) for i in wl.icp_iters), bilateral=bool(wl.bilateral))
+
+
+def xslam_cfg(wl):
+    from paper_2405_02187_gb300 import xslam
+    c = xslam.default_config()
+    c.icp_levels = len(wl.icp_iters)
+    for i, n in enumerate(wl.icp_iters):
+        c.icp_iters[i] = n
+    c.depth_min_m, c.depth_max_m, c.bilateral = wl.depth_min, wl.depth_max, int(wl.bilateral)
+    return c
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle legs (run in spawned processes: no CUDA state is inherited)
+# ------------------------------------------------------------------------------------------------
+def _oracle_frames(task):
+    """One complex lane of the oracle: frame 0 untimed, frame 1 timed. Returns (seconds, dtwist)."""
+    import os as _os
+    _os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import pipeline as P
+    from oracle import se3
+    wl, seed = task
+    cfg = P.Config(icp_iters=tuple(wl["icp_iters"]), depth_min=wl["depth_min"], depth_max=wl["depth_max"],
+                   bilateral=wl["bilateral"])
+    run = P.XKinectFusion(wl["dims"], wl["voxel"], wl["trunc"], wl["origin"], wl["intr"], wl["pose0"], cfg,
+                          P.Seed(seed[0], seed[1]))
+    run.frame(wl["depth"][0])
+    t = time.perf_counter()
+    T, ok = run.frame(wl["depth"][1])
+    dt = time.perf_counter() - t
+    return dt, se3.readout(T, run.seed.h)[2], bool(ok)
+
+
+def _oracle_shard_steps(task):
+    """One complex lane of the oracle over sampled steps: after an untimed full frame 0, each step
+    processes shard s = i mod R of frame 1 (1/R of the voxels, of the ray-cast pixels and of the ICP
+    pixels at every level, with all 19 iterations). Returns the timed step durations."""
+    from oracle import fusion, icp, measure, raycast, se3
+    from oracle import pipeline as P
+    wl, seed, R, warm, steps = task
+    cfg = P.Config(icp_iters=tuple(wl["icp_iters"]), depth_min=wl["depth_min"], depth_max=wl["depth_max"],
+                   bilateral=wl["bilateral"])
+    run = P.XKinectFusion(wl["dims"], wl["voxel"], wl["trunc"], wl["origin"], wl["intr"], wl["pose0"], cfg,
+                          P.Seed(seed[0], seed[1]))
+    run.frame(wl["depth"][0])
+    intr = wl["intr"]
+    n = int(np.prod(wl["dims"]))
+    out = []
+    for i in range(warm + steps):
+        s = i % R
+        t = time.perf_counter()
+        pyr = run.measure(wl["depth"][1])
+        T = run.T
+        for level in range(len(cfg.icp_iters) - 1, -1, -1):
+            li = measure.level_intrinsics(intr, level)
+            pix = np.arange(s, li[4] * li[5], R)
+            for _ in range(cfg.icp_iters[level]):
+                r, J, v = icp.correspondences(pyr[level], li, level, T, run.T, run.model, pix=pix)
+                A, b, nv = icp.normal_equations(r, J, v)
+                x = icp.solve(A, b) if nv >= 6 else None
+                if x is not None:
+                    T = se3.compose(se3.se3_exp(x), T)
+        fusion.integrate(run.F, run.W, pyr[0], T, intr, run.dims, run.origin, run.voxel, run.mu,
+                         idx=np.arange(s, n, R))
+        raycast.raycast(run.F, run.W, T, intr, run.dims, run.origin, run.voxel, cfg.depth_min, cfg.depth_max,
+                        pix=np.arange(s, intr.width * intr.height, R))
+        if i >= warm:
+            out.append(time.perf_counter() - t)
+    return out
+
+
+def _wl_payload(wl, frames=2):
+    return dict(dims=wl.dims, voxel=wl.voxel, trunc=wl.trunc, origin=wl.origin, intr=wl.intr,
+                pose0=wl.poses[0], depth=wl.depth[:frames], icp_iters=wl.icp_iters, depth_min=wl.depth_min,
+                depth_max=wl.depth_max, bilateral=wl.bilateral)
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# ------------------------------------------------------------------------------------------------
+# roofline bookkeeping
+# ------------------------------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+KERNEL_SRC = {"integrate": "fuse.cu", "raycast": "raycast.cu", "icp": "icp.cu"}
+KERNEL_NAME = {"integrate": "k_integrate", "raycast": "k_raycast", "icp": "k_icp"}
+
+
+def _src_hash(stage):
+    p = os.path.join(ROOT, "paper_2405_02187_gb300", "csrc", KERNEL_SRC[stage])
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def ncu_traffic(stage, workload):
+    """DRAM bytes per launch of the stage's kernel from the committed ncu summary, if that summary was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(f"{workload}:{stage}")
+    if not e or e.get("src_sha256_16") != _src_hash(stage):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(stage, wl, K, per_frame):
+    """Bytes a launch of the stage must move (see the kernels' headers):
+    integrate: read + write of F (1 + K lanes) and W for every updated voxel, plus the depth map;
+    raycast:   the model outputs (depth + vertex and normal on 1 + K lanes) plus F and W of the
+               voxels in front of the surface that the rays cross (counted as the voxels the update
+               of the same pose touched) plus the K imaginary planes at the 8 cells of every hit;
+    icp:       per pixel of the level: its depth, and the model depth, vertex and normal (1 + K lanes)
+               at its correspondence."""
+    L = 1 + K
+    hw = wl.intr.width * wl.intr.height
+    if stage == "integrate":
+        return per_frame["fused"] * 2 * 4 * (L + 1) + 4 * hw
+    if stage == "raycast":
+        return hw * 4 * (1 + 6 * L) + per_frame["fused"] * 8 + per_frame["hits"] * 8 * 8 * 4 * K
+    if stage == "icp":
+        tot, launches = 0.0, 0
+        for level, iters in enumerate(wl.icp_iters):
+            tot += iters * (hw >> (2 * level)) * (4 + 4 + 24 * L)
+            launches += iters
+        return tot / launches
+    raise ValueError(stage)
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2405_02187_gb300 import xslam
+
+    # the CPU oracle processes are spawned (fresh interpreters) before any GPU call
+    pool = None
+    cpu_lanes = min(args.lanes, 6)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = mp.get_context("spawn").Pool(cpu_lanes)
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    W, K, L = args.warmup, args.steps, args.lanes
+    nf = W + K + 1
+    wl = make_workload(args.workload, 2 + rank, nf, dev)
+    if args.workload == "room256" and nf > 300:
+        print("note: more frames than the 300-frame sequence were generated", file=sys.stderr)
+    cfg = xslam_cfg(wl)
+    seeds = [(xslam.POSE0, j % 6, H_GPU) for j in range(L)]
+    depth_dev = torch.tensor(wl.depth, device=dev)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+
+    def handle():
+        x = xslam.XSlam(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, cfg, max_lanes=L)
+        x.set_pose(wl.poses[0])
+        return x
+
+    # ---- timed region: device-resident depth, graphs, no host sync per frame ----
+    x = handle()
+    for k in range(W):
+        x.frame(depth_dev[k], seeds, outputs=False)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(W, W + K):
+        x.frame(depth_dev[k], seeds, outputs=False)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    _, n_fail = x.sync()
+    x.close()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = K * world / (ms / 1000.0)
+
+    # ---- profiled pass over the same frames: per-stage device time (no graphs) ----
+    x = handle()
+    for k in range(W):
+        x.frame(depth_dev[k], seeds, outputs=False)
+    x.profile(True)
+    for k in range(W, W + K):
+        x.frame(depth_dev[k], seeds, outputs=False)
+    stages, counters = x.profile_read()
+    x.profile(False)
+    x.close()
+    nprof = counters["frames"]
+    per_frame = dict(fused=counters["fused"] / nprof, hits=counters["hits"] / nprof)
+    launches_per_frame = sum(v[1] for v in stages.values()) / nprof
+    cand = {s: stages[s][0] / nprof for s in ("integrate", "raycast", "icp")}
+    dom = max(cand, key=cand.get)
+    ms_launch = stages[dom][0] / stages[dom][1]
+    bytes_launch = algorithmic_bytes(dom, wl, L, per_frame)
+    peak, peak_src = measured_peaks()
+    achieved = bytes_launch / (ms_launch * 1e-3) / 1e9
+    traffic = ncu_traffic(dom, wl.name)
+    roofline = dict(bound="hbm", achieved=round(achieved, 1), peak=peak, unit="GB/s",
+                    frac=round(achieved / peak, 4), traffic=traffic, kernel=KERNEL_NAME[dom],
+                    peak_source=f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                    bytes_per_launch=round(bytes_launch), ms_per_launch=round(ms_launch, 5))
+    stage_ms = {s: round(v[0] / nprof, 4) for s, v in stages.items()}
+
+    # ---- end to end: pinned host depth in, pose + derivative block out, every frame ----
+    host = torch.empty((nf,) + tuple(wl.depth.shape[1:]), dtype=torch.float32, pin_memory=True)
+    host.copy_(torch.from_numpy(wl.depth))
+    x = handle()
+    dtw_frame1 = None
+    for k in range(W):
+        pose, dpose, dtw, st = x.frame(host[k], seeds)
+        if k == 1:
+            dtw_frame1 = dtw.copy()
+    torch.cuda.synchronize()
+    barrier()
+    e0.record()
+    for k in range(W, W + K):
+        pose, dpose, dtw, st = x.frame(host[k], seeds)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    x.close()
+    if dist:
+        t = torch.tensor([ms_e2e], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = dict(value=round(K * world / (ms_e2e / 1000.0), 2), unit="frames/s",
+               h2d_bytes_per_step=int(4 * wl.intr.width * wl.intr.height), d2h_bytes_per_step=int(8 * (12 + 18 * L)))
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1): frame 1 of the same sequence ----
+    cpu = None
+    grad_err = None
+    if pool is not None:
+        payload = _wl_payload(wl, 2)
+        lanes = [(0, j % 6) for j in range(cpu_lanes)]
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_frames, [(payload, s) for s in lanes])
+        wall = time.perf_counter() - t0
+        pool.close()
+        lane_s = max(r[0] for r in res)
+        cpu = dict(value=round(1.0 / lane_s * cpu_lanes / L, 5), unit="frames/s", cores=cpu_lanes, kind="oracle",
+                   sample=f"frame 1 (ICP 19 iterations, fusion, ray cast) of the same {wl.name} sequence after an "
+                          f"untimed frame 0; {cpu_lanes} complex128 lanes, one process per lane, slowest lane "
+                          f"{lane_s:.1f} s (wall incl. frame 0: {wall:.0f} s)")
+        if dtw_frame1 is not None and W > 1:
+            ref = np.stack([r[1] for r in res])
+            gpu = dtw_frame1[:cpu_lanes]
+            grad_err = float(np.linalg.norm(gpu - ref) / np.linalg.norm(ref))
+
+    line = dict(metric=METRIC, value=round(value, 2), unit="frames/s", n_gpus=world, steps=K, warmup=W,
+                ms_per_step=round(ms / K, 4), higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32", data="synthetic",
+                config=dict(wl_desc(wl, L), parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                            l2="inputs larger than L2: the TSDF state alone is "
+                               f"{np.prod(wl.dims) * 4 * (L + 1) / 1e6:.0f} MB",
+                            tracking_failures=int(n_fail)),
+                roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(round(launches_per_frame * K)),
+                clocks=clk, stage_ms_per_frame=stage_ms, grad_rel_err_vs_oracle=grad_err,
+                per_frame=dict(fused_voxels=round(per_frame["fused"]), surface_pixels=round(per_frame["hits"])))
+    if rank == 0:
+        print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# ------------------------------------------------------------------------------------------------
+def _reference(args, rank):
+    if rank != 0:
+        return
+    R = args.ref_shards
+    L = args.lanes
+    procs = min(L, 6)
+    wl = make_workload(args.workload, 2, 2, "cpu")
+    payload = _wl_payload(wl, 2)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_oracle_shard_steps, [(payload, (0, j % 6), R, args.warmup, args.steps) for j in range(procs)])
+    step_s = np.max(np.stack([np.asarray(r) for r in res]), 0)  # the slowest lane per step
+    frame_s = step_s.mean() * R * L / procs
+    value = 1.0 / frame_s
+    line = dict(impl="reference", metric=METRIC, value=round(value, 6), unit="frames/s", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=round(step_s.mean() * 1000, 2),
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="c128", data="synthetic",
+                config=dict(wl_desc(wl, L), parallelism="host cores"),
+                cpu_baseline=dict(kind="oracle", cores=procs, value=round(value, 6), unit="frames/s",
+                                  sample=f"each step is shard s = step mod {R} of frame 1 of {wl.name}: 1/{R} of the "
+                                         f"voxels, ray-cast pixels and ICP pixels (19 iterations), on {procs} "
+                                         f"complex128 lanes in parallel processes; frames/s = 1 / ({R} x mean step)"),
+                e2e=dict(value=round(value, 6), unit="frames/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=280)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("room256", "orbit64"), default="room256")
+    ap.add_argument("--lanes", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-shards", type=int, default=64)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        _reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

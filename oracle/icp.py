@@ -40,15 +40,18 @@ CELL_BIAS = 2.0 ** -6
 
 
 def correspondences(D, lintr, level, Tj, Tprev, model, dist_gate=0.1, normal_gate_deg=20.0,
-                    disc_gate=0.1, log=None):
+                    disc_gate=0.1, log=None, pix=None):
     """Per-pixel residual r, Jacobian J (N, 6) and validity mask at one pyramid level.
-    ``log``, if a list, receives the discrete decisions (validity, bilinear cells)."""
+    ``log``, if a list, receives the discrete decisions (validity, bilinear cells); ``pix`` restricts
+    the result to those linear pixel indices (each pixel is independent)."""
     fx, fy, cx, cy, W, H = lintr
     V = measure.vertex_map(D, lintr)
     Nm, vvalid = measure.normal_map(D, V)
     V = V.reshape(-1, 3)
     Nm = Nm.reshape(-1, 3)
     valid = vvalid.reshape(-1)
+    if pix is not None:
+        V, Nm, valid = V[pix], Nm[pix], valid[pix]
     Tj = np.asarray(Tj)
     pp = se3.transform(Tj, V)                          # p' = T_j V_k(u)
     pc = se3.transform(se3.inverse(Tprev), pp)         # previous camera frame

@@ -6,8 +6,11 @@ Functions accept real (float64) or complex (complex128) depth; every validity de
 real parts, the imaginary part follows the chosen branch.
 
 Readings of the paper used here (it names the operations but not their parameters):
-  * the bilateral filter of the raw depth is off (all workloads are synthetic);
-  * depth outside [depth_min, depth_max] counts as invalid (0);
+  * depth outside [depth_min, depth_max] counts as invalid (0), before any filtering;
+  * the bilateral filter of the raw depth (Sec. 4.1, "applying a bilateral filter to the raw depth map
+    for noise reduction") is optional: a 7x7 window, spatial sigma 4.5 pixels, range sigma 0.03 m,
+    over valid taps only, invalid where the centre is invalid; it is on where the depth noise exceeds
+    the pixel footprint (the 640x480 workload), off otherwise;
   * the pyramid has 3 levels; level l+1 at pixel u is the 5x5 binomial ([1 4 6 4 1]/16 per axis)
     average of level l around pixel 2u over the taps that are valid and within ``range_m`` of the
     centre depth, and is invalid where the centre is invalid; the perturbation is averaged with the
@@ -34,6 +37,27 @@ def range_gate(D, depth_min: float, depth_max: float):
     """Depth outside the sensor range becomes invalid (0)."""
     Dr = np.real(D)
     return np.where((Dr >= depth_min) & (Dr <= depth_max), D, 0)
+
+
+def bilateral(D, sigma_s: float = 4.5, sigma_r: float = 0.03, radius: int = 3):
+    """Edge-preserving smoothing of the raw depth (Sec. 4.1, surface measurement): the normalised sum
+    of w_s(u - u') w_r(D(u) - D(u')) D(u') over the valid taps u' of the (2 radius + 1)^2 window, with
+    Gaussian w_s and w_r; tap validity is decided on real parts, the range weight is evaluated on the
+    complex depths (it is a smooth function of them)."""
+    H, W = D.shape
+    P = np.zeros((H + 2 * radius, W + 2 * radius), D.dtype)
+    P[radius:-radius, radius:-radius] = D
+    Cr = np.real(D)
+    acc = np.zeros((H, W), D.dtype)
+    wsum = np.zeros((H, W), D.dtype)
+    for dy in range(-radius, radius + 1):
+        for dx in range(-radius, radius + 1):
+            tap = P[radius + dy:radius + dy + H, radius + dx:radius + dx + W]
+            tr = np.real(tap)
+            w = np.exp(-(dx * dx + dy * dy) / (2 * sigma_s ** 2) - (tap - D) ** 2 / (2 * sigma_r ** 2)) * (tr > 0)
+            acc = acc + w * tap
+            wsum = wsum + w
+    return np.where(Cr > 0, acc / np.where(np.real(wsum) > 0, wsum, 1.0), 0).astype(D.dtype)
 
 
 def pyramid_down(D, range_m: float):

@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Frame k (Sec. 4.1, in the paper's order): surface measurement of D_k (range gate, pyramid, vertex
+Frame k (Sec. 4.1, in the paper's order): surface measurement of D_k (range gate, optional bilateral
+filter, pyramid, vertex
 and normal maps), camera pose estimation by multi-level ICP against the model maps ray-cast at
 T_{k-1} (frame 0 keeps its given pose), surface update of the TSDF at T_k, and ray casting at T_k
 for the next frame.
@@ -41,6 +42,7 @@ class Config:
     depth_max: float = 4.0
     pyr_range: float = 0.09
     w_max: float = np.inf
+    bilateral: bool = False
 
 
 @dataclasses.dataclass
@@ -90,6 +92,8 @@ class XKinectFusion:
                 pert.reshape(-1)[self.seed.index] = self.seed.delta
             D = np.where(D > 0, D + pert, 0)
         D = measure.range_gate(D, self.cfg.depth_min, self.cfg.depth_max)
+        if self.cfg.bilateral:
+            D = measure.bilateral(D)
         return measure.pyramid(D, len(self.cfg.icp_iters), self.cfg.pyr_range)
 
     def frame(self, depth):
@@ -114,7 +118,8 @@ def run(wl, seeds=(), frames=None, cfg: Config = None):
 
     Returns dict: pose (F, 3, 4) real trajectory; ok (F,); per seed j: dpose[j] (F, 3, 4) = Im T / h,
     dtwist[j] (F, 6) as left twists; real_match[j] = max |Re(T*) - T| over the run."""
-    cfg = cfg or Config(icp_iters=tuple(wl.icp_iters), depth_min=wl.depth_min, depth_max=wl.depth_max)
+    cfg = cfg or Config(icp_iters=tuple(wl.icp_iters), depth_min=wl.depth_min, depth_max=wl.depth_max,
+                        bilateral=wl.bilateral)
     nf = wl.depth.shape[0] if frames is None else frames
     runs = [XKinectFusion(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, wl.poses[0], cfg, None)]
     runs += [XKinectFusion(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, wl.poses[0], cfg, s) for s in seeds]

@@ -54,22 +54,26 @@ def trilinear(F, Wt, g, i0, inside, dims):
     return val, ok
 
 
-def raycast(F, Wt, T, intr, dims, origin, voxel, depth_min=0.2, depth_max=4.0, ray_step_vox=1.0, log=None):
-    """Predict (depth, V_g, N_g) at pose T from the volume (F, Wt). Shapes (H, W), (H, W, 3) x2.
+def raycast(F, Wt, T, intr, dims, origin, voxel, depth_min=0.2, depth_max=4.0, ray_step_vox=1.0, log=None,
+            pix=None):
+    """Predict (depth, V_g, N_g) at pose T from the volume (F, Wt). Shapes (H, W), (H, W, 3) x2, or
+    (P,), (P, 3), (P, 3) for the linear pixel indices ``pix`` if given (each ray is independent).
     ``log``, if a list, receives the discrete decisions (hit sample, pixel validity, trilinear cells)."""
     H, W = intr.height, intr.width
     T = np.asarray(T)
     origin = np.asarray(origin, np.float64)
     uu, vv = np.meshgrid(np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64))
     ray = np.stack([(uu - intr.cx) / intr.fx, (vv - intr.cy) / intr.fy, np.ones_like(uu)], -1).reshape(-1, 3)
+    if pix is not None:
+        ray = ray[np.asarray(pix)]
     n = ray.shape[0]
     dirs = ray @ T[:, :3].T          # complex if T is
     t = T[:, 3]
     dir_re, t_re = np.real(dirs), np.real(t)
     Fre = np.real(F)
     step = ray_step_vox * voxel
-    m0 = math.ceil(depth_min / step - 1e-9)
-    m1 = math.floor(depth_max / step + 1e-9)
+    m0 = math.ceil(depth_min / step - 1e-4)
+    m1 = math.floor(depth_max / step + 1e-4)
 
     prev_valid = np.zeros(n, bool)
     prev_pos = np.zeros(n, bool)
@@ -139,4 +143,6 @@ def raycast(F, Wt, T, intr, dims, origin, voxel, depth_min=0.2, depth_max=4.0, r
         N[good] = (grad / norm[:, None])[ok]
     if log is not None:
         log += [np.where(hit, m_hit, -1), depth > 0] + (cells if idx.size else [])
+    if pix is not None:
+        return depth, V, N
     return depth.reshape(H, W), V.reshape(H, W, 3), N.reshape(H, W, 3)

@@ -1,0 +1,721 @@
+// C ABI of libxslam (declared in include/xslam.h): handle, device memory, frame driver, stage calls.
+//
+// The frame step of X-SLAM Sec. 4.1 is a fixed chain of launches on the handle's own stream:
+//   frame 0:  range gate -> seed pose lanes -> TSDF update -> ray cast -> read-out
+//   frame k:  range gate + pyramid -> ICP iterations (one launch each, coarse to fine) -> TSDF
+//             update -> ray cast -> read-out
+// Each chain is captured once into a CUDA graph and replayed per frame (kernel arguments only point at
+// handle-owned buffers, so a replay needs nothing but the new depth copied into the input buffer).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "../../include/xslam.h"
+#include "internal.cuh"
+
+using namespace xslam;
+
+static constexpr int kProfRing = 256;
+
+struct xslam_s {
+  Params p;
+  Buffers b;
+  xslam_config cfg;
+  int max_lanes = 0;
+  int nsm = 148;
+  cudaStream_t s = nullptr;     // internal stream
+  cudaStream_t user = nullptr;  // caller's stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int frame = 0;
+  int K = 0;
+  xslam_seed seeds[kMaxLanes];
+  int* d_kinds = nullptr;   // device copies of lane kinds / indices
+  int* d_index = nullptr;
+  double* pose_tmp = nullptr;  // scratch pose lanes (raycast / grad)
+  float* model_q = nullptr;    // scratch model maps of xslam_grad (7 lanes)
+  double* h_result = nullptr;  // pinned host staging
+  int* h_status = nullptr;
+  int nblk[3] = {1, 1, 1};
+  cudaGraphExec_t g_first = nullptr, g_track = nullptr;
+  bool use_graphs = true;
+  // stage profiling (xslam_profile): one event pair per stage and frame, accumulated on read
+  bool profiling = false;
+  cudaEvent_t pev[XSLAM_NSTAGE][kProfRing][2] = {};
+  int pcount[XSLAM_NSTAGE] = {};      // pairs recorded and not yet accumulated
+  double pms[XSLAM_NSTAGE] = {};      // accumulated milliseconds
+  long long plaunch[XSLAM_NSTAGE] = {};
+  long long pframes = 0;
+  std::string err;
+};
+
+static std::string g_create_err;
+
+static xslam_status fail(xslam_t h, xslam_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return st;
+}
+
+#define CU(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(h, XSLAM_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" void xslam_default_config(xslam_config* c) {
+  if (!c) return;
+  c->icp_levels = 3;
+  c->icp_iters[0] = 10;
+  c->icp_iters[1] = 5;
+  c->icp_iters[2] = 4;
+  c->icp_iters[3] = 0;
+  c->dist_gate_m = 0.1f;
+  c->normal_gate_deg = 20.f;
+  c->disc_gate_m = 0.1f;
+  c->min_corr_frac = 0.1f;
+  c->ray_step_vox = 1.f;
+  c->depth_min_m = 0.2f;
+  c->depth_max_m = 4.f;
+  c->pyr_range_m = 0.09f;
+  c->bilateral = 0;
+  c->w_max = 0.f;
+}
+
+static void drop_graphs(xslam_t h) {
+  if (h->g_first) cudaGraphExecDestroy(h->g_first);
+  if (h->g_track) cudaGraphExecDestroy(h->g_track);
+  h->g_first = h->g_track = nullptr;
+}
+
+static xslam_status enter(xslam_t h) {
+  CU(cudaEventRecord(h->ev_in, h->user));
+  CU(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+  return XSLAM_OK;
+}
+
+static xslam_status leave(xslam_t h) {
+  CU(cudaEventRecord(h->ev_out, h->s));
+  CU(cudaStreamWaitEvent(h->user, h->ev_out, 0));
+  return XSLAM_OK;
+}
+
+static int ray_m0(double dmin, double step) { return (int)std::ceil(dmin / step - 1e-4); }
+static int ray_m1(double dmax, double step) { return (int)std::floor(dmax / step + 1e-4); }
+
+extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float voxel_m, float trunc_m,
+                                     const float origin_m[3], const xslam_intrinsics* K, const xslam_config* cfg,
+                                     int max_lanes, void* cuda_stream) {
+  xslam_t h = nullptr;
+  if (!out) return fail(h, XSLAM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nx < 2 || ny < 2 || nz < 2 || (size_t)nx * ny * nz > (size_t)1 << 34)
+    return fail(h, XSLAM_EINVAL, "volume dimensions must be >= 2 and at most 2^34 voxels");
+  if (!(voxel_m > 0.f) || !(trunc_m > 0.f)) return fail(h, XSLAM_EINVAL, "voxel and truncation must be > 0");
+  if (!origin_m || !K) return fail(h, XSLAM_EINVAL, "origin and intrinsics are required");
+  if (max_lanes < 0 || max_lanes > kMaxLanes - 1) return fail(h, XSLAM_EINVAL, "max_lanes must be in 0..15");
+  xslam_config c;
+  if (cfg) c = *cfg;
+  else xslam_default_config(&c);
+  if (c.icp_levels < 1 || c.icp_levels > 3) return fail(h, XSLAM_EINVAL, "icp_levels must be 1..3");
+  for (int l = 0; l < c.icp_levels; ++l)
+    if (c.icp_iters[l] < 0 || c.icp_iters[l] > 100) return fail(h, XSLAM_EINVAL, "icp_iters must be 0..100");
+  if (c.bilateral != 0 && c.bilateral != 1) return fail(h, XSLAM_EINVAL, "bilateral must be 0 or 1");
+  const int div = 1 << (c.icp_levels - 1);
+  if (K->width < 4 * div || K->height < 4 * div || K->width % div || K->height % div)
+    return fail(h, XSLAM_EINVAL, "image size must be divisible by 2^(icp_levels-1) and at least 4 pixels per level");
+  if (!(K->fx > 0.f) || !(K->fy > 0.f)) return fail(h, XSLAM_EINVAL, "focal lengths must be > 0");
+  if (!(c.depth_max_m > c.depth_min_m) || !(c.depth_min_m >= 0.f) || !(c.ray_step_vox > 0.f))
+    return fail(h, XSLAM_EINVAL, "bad depth range or ray step");
+
+  h = new (std::nothrow) xslam_s();
+  if (!h) return fail(nullptr, XSLAM_ENOMEM, "host allocation failed");
+  h->cfg = c;
+  h->max_lanes = max_lanes;
+  h->user = (cudaStream_t)cuda_stream;
+  const char* env = getenv("XSLAM_GRAPHS");
+  h->use_graphs = !(env && env[0] == '0');
+  Params& p = h->p;
+  memset(&p, 0, sizeof(p));
+  p.nx = nx; p.ny = ny; p.nz = nz;
+  p.voxel = voxel_m; p.mu = trunc_m;
+  p.ox = origin_m[0]; p.oy = origin_m[1]; p.oz = origin_m[2];
+  p.w_max = c.w_max;
+  p.fx = K->fx; p.fy = K->fy; p.cx = K->cx; p.cy = K->cy;
+  p.W = K->width; p.H = K->height;
+  p.L = 1;
+  p.dist_gate2 = c.dist_gate_m * c.dist_gate_m;
+  p.cos_normal_gate = (float)std::cos(c.normal_gate_deg * M_PI / 180.0);
+  p.disc_gate = c.disc_gate_m;
+  p.min_corr_frac = c.min_corr_frac;
+  p.depth_min = c.depth_min_m;
+  p.depth_max = c.depth_max_m;
+  p.pyr_range = c.pyr_range_m;
+  p.bilateral = c.bilateral;
+  const double step = (double)c.ray_step_vox * (double)voxel_m;
+  p.ray_step = (float)step;
+  p.m0 = ray_m0(c.depth_min_m, step);
+  p.m1 = ray_m1(c.depth_max_m, step);
+
+  auto cleanup = [&](xslam_status st, const std::string& m) {
+    xslam_destroy(h);
+    return fail(nullptr, st, m);
+  };
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cleanup(XSLAM_ECUDA, "no CUDA device");
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(XSLAM_ECUDA, "stream/event creation failed");
+
+  const size_t n = (size_t)nx * ny * nz, hw = (size_t)p.W * p.H;
+  const int Lmax = 1 + max_lanes;
+  Buffers& b = h->b;
+  memset(&b, 0, sizeof(b));
+  int nblk_max = 1;
+  for (int l = 0; l < 3; ++l) {
+    const int np = (p.W >> l) * (p.H >> l);
+    h->nblk[l] = icp_blocks(np, Lmax);
+    nblk_max = std::max(nblk_max, h->nblk[l]);
+  }
+  nblk_max = std::max(nblk_max, 4 * h->nsm);  // k_loss grid
+  bool ok = true;
+  ok &= cudaMalloc(&b.F, sizeof(float) * n * Lmax) == cudaSuccess;
+  ok &= cudaMalloc(&b.Wt, sizeof(float) * n) == cudaSuccess;
+  ok &= cudaMalloc(&b.depth_in, sizeof(float) * hw) == cudaSuccess;
+  ok &= cudaMalloc(&b.gated, sizeof(float) * hw) == cudaSuccess;
+  for (int l = 0; l < 3; ++l) ok &= cudaMalloc(&b.pyr[l], sizeof(float) * (hw >> (2 * l))) == cudaSuccess;
+  ok &= cudaMalloc(&b.model, sizeof(float) * hw * (1 + 6 * Lmax)) == cudaSuccess;
+  ok &= cudaMalloc(&b.pose, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
+  ok &= cudaMalloc(&b.pose_prev, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
+  ok &= cudaMalloc(&h->pose_tmp, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
+  ok &= cudaMalloc(&b.partial, sizeof(float) * (size_t)nblk_max * kNT * kMaxLanes) == cudaSuccess;
+  ok &= cudaMalloc(&b.partial_n, sizeof(int) * nblk_max) == cudaSuccess;
+  ok &= cudaMalloc(&b.ticket, sizeof(unsigned)) == cudaSuccess;
+  ok &= cudaMalloc(&b.status, sizeof(int) * 4) == cudaSuccess;
+  ok &= cudaMalloc(&b.result, sizeof(double) * kResLen) == cudaSuccess;
+  ok &= cudaMalloc(&b.stats, sizeof(unsigned long long) * 2) == cudaSuccess;
+  ok &= cudaMalloc(&h->d_kinds, sizeof(int) * kMaxLanes) == cudaSuccess;
+  ok &= cudaMalloc(&h->d_index, sizeof(int) * kMaxLanes) == cudaSuccess;
+  if (max_lanes >= 6) ok &= cudaMalloc(&h->model_q, sizeof(float) * hw * (1 + 6 * 7)) == cudaSuccess;
+  ok &= cudaMallocHost(&h->h_result, sizeof(double) * kResLen) == cudaSuccess;
+  ok &= cudaMallocHost(&h->h_status, sizeof(int) * 4) == cudaSuccess;
+  if (!ok) return cleanup(XSLAM_ENOMEM, "device or pinned allocation failed");
+  *out = h;
+  xslam_status st = xslam_reset(h);
+  if (st != XSLAM_OK) {
+    std::string m = h->err;
+    *out = nullptr;
+    return cleanup(st, m);
+  }
+  double I[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+  cudaMemcpyAsync(b.pose, I, sizeof(I), cudaMemcpyHostToDevice, h->s);
+  if (cudaStreamSynchronize(h->s) != cudaSuccess) {
+    *out = nullptr;
+    return cleanup(XSLAM_ECUDA, "initialisation failed");
+  }
+  return XSLAM_OK;
+}
+
+extern "C" xslam_status xslam_destroy(xslam_t h) {
+  if (!h) return XSLAM_OK;
+  if (h->s) cudaStreamSynchronize(h->s);
+  drop_graphs(h);
+  Buffers& b = h->b;
+  cudaFree(b.F); cudaFree(b.Wt); cudaFree(b.depth_in); cudaFree(b.gated);
+  for (int l = 0; l < 3; ++l) cudaFree(b.pyr[l]);
+  cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp);
+  cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats);
+  for (int st = 0; st < XSLAM_NSTAGE; ++st)
+    for (int i = 0; i < kProfRing; ++i)
+      for (int k = 0; k < 2; ++k)
+        if (h->pev[st][i][k]) cudaEventDestroy(h->pev[st][i][k]);
+  cudaFree(h->d_kinds); cudaFree(h->d_index); cudaFree(h->model_q);
+  if (h->h_result) cudaFreeHost(h->h_result);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->s) cudaStreamDestroy(h->s);
+  delete h;
+  return XSLAM_OK;
+}
+
+// volume: F = 1 (all lanes: lane 0 = 1, lanes >= 1 = 0), W = 0
+__global__ void k_fill(float* a, size_t n, float v) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] = v;
+}
+__global__ void k_scale(const float* a, float* o, size_t n, double s) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    o[i] = (float)((double)a[i] * s);
+}
+
+extern "C" xslam_status xslam_reset(xslam_t h) {
+  if (!h) return XSLAM_EINVAL;
+  const size_t n = vox_count(h->p);
+  const int Lmax = 1 + h->max_lanes;
+  const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
+  k_fill<<<g, 256, 0, h->s>>>(h->b.F, n, 1.f);
+  CU(cudaGetLastError());
+  if (Lmax > 1) CU(cudaMemsetAsync(h->b.F + n, 0, sizeof(float) * n * (Lmax - 1), h->s));
+  CU(cudaMemsetAsync(h->b.Wt, 0, sizeof(float) * n, h->s));
+  CU(cudaMemsetAsync(h->b.model, 0, sizeof(float) * (size_t)h->p.W * h->p.H * (1 + 6 * Lmax), h->s));
+  CU(cudaMemsetAsync(h->b.ticket, 0, sizeof(unsigned), h->s));
+  CU(cudaMemsetAsync(h->b.status, 0, sizeof(int) * 4, h->s));
+  CU(cudaMemsetAsync(h->b.pose + 12, 0, sizeof(double) * 12 * (kMaxLanes - 1), h->s));
+  CU(cudaMemsetAsync(h->b.result, 0, sizeof(double) * kResLen, h->s));
+  CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * 2, h->s));
+  h->frame = 0;
+  h->K = 0;
+  h->p.L = 1;
+  drop_graphs(h);
+  CU(cudaStreamSynchronize(h->s));
+  return XSLAM_OK;
+}
+
+extern "C" xslam_status xslam_set_pose(xslam_t h, const double* T) {
+  if (!h || !T) return fail(h, XSLAM_EINVAL, "NULL argument");
+  if (h->frame > 0) return fail(h, XSLAM_ESTATE, "the pose can only be set before the first frame");
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(T[i])) return fail(h, XSLAM_EINVAL, "pose has a non-finite entry");
+  CU(cudaMemcpyAsync(h->b.pose, T, sizeof(double) * 12, cudaMemcpyHostToDevice, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  return XSLAM_OK;
+}
+
+static bool same_seeds(xslam_t h, const xslam_seed* s, int K) {
+  if (K != h->K) return false;
+  for (int j = 0; j < K; ++j)
+    if (s[j].kind != h->seeds[j].kind || s[j].index != h->seeds[j].index || s[j].h != h->seeds[j].h) return false;
+  return true;
+}
+
+extern "C" xslam_status xslam_set_lanes(xslam_t h, const xslam_seed* seeds, int K) {
+  if (!h) return XSLAM_EINVAL;
+  if (K < 0 || K > h->max_lanes) return fail(h, XSLAM_EINVAL, "K must be in 0..max_lanes");
+  if (K > 0 && !seeds) return fail(h, XSLAM_EINVAL, "seeds is NULL");
+  int kinds[kMaxLanes] = {0}, index[kMaxLanes] = {0};
+  Params p = h->p;
+  p.L = 1 + K;
+  for (int l = 0; l < kMaxLanes; ++l) {
+    p.dmu[l] = 0.f;
+    p.dD[l] = 0.f;
+    p.h[l] = 1.0;
+  }
+  for (int j = 0; j < K; ++j) {
+    const xslam_seed& s = seeds[j];
+    if (!std::isfinite(s.h) || s.h == 0.0 || std::fabs(s.h) > 1e-3 || std::fabs(s.h) < 1e-30)
+      return fail(h, XSLAM_EINVAL, "seed h must satisfy 1e-30 <= |h| <= 1e-3");
+    switch (s.kind) {
+      case XSLAM_SEED_POSE0:
+        if (s.index < 0 || s.index > 5) return fail(h, XSLAM_EINVAL, "POSE0 index must be 0..5");
+        break;
+      case XSLAM_SEED_TRUNC:
+        p.dmu[j + 1] = (float)s.h;
+        break;
+      case XSLAM_SEED_DEPTH:
+        if (s.index != -1) return fail(h, XSLAM_EINVAL, "only DEPTH seeds on every pixel (index -1) are built");
+        p.dD[j + 1] = (float)s.h;
+        break;
+      default:
+        return fail(h, XSLAM_EINVAL, "seed kind not built (POSE0, TRUNC and DEPTH are)");
+    }
+    kinds[j + 1] = s.kind;
+    index[j + 1] = s.index;
+    p.h[j + 1] = s.h;
+  }
+  CU(cudaMemcpyAsync(h->d_kinds, kinds, sizeof(kinds), cudaMemcpyHostToDevice, h->s));
+  CU(cudaMemcpyAsync(h->d_index, index, sizeof(index), cudaMemcpyHostToDevice, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  h->p = p;
+  h->K = K;
+  for (int j = 0; j < K; ++j) h->seeds[j] = seeds[j];
+  drop_graphs(h);
+  return XSLAM_OK;
+}
+
+static xslam_status copy_depth(xslam_t h, const float* depth, int on_device) {
+  const size_t bytes = sizeof(float) * h->p.W * h->p.H;
+  CU(cudaMemcpyAsync(h->b.depth_in, depth, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
+  return XSLAM_OK;
+}
+
+static void stage_begin(xslam_t h, int st) {
+  if (h->profiling) cudaEventRecord(h->pev[st][h->pcount[st] % kProfRing][0], h->s);
+}
+static void stage_end(xslam_t h, int st, int launches) {
+  if (!h->profiling) return;
+  cudaEventRecord(h->pev[st][h->pcount[st] % kProfRing][1], h->s);
+  h->pcount[st] += 1;
+  h->plaunch[st] += launches;
+}
+
+static cudaError_t enqueue_first(xslam_t h) {
+  cudaError_t e;
+  const size_t hw = (size_t)h->p.W * h->p.H;
+  stage_begin(h, XSLAM_STAGE_PREPARE);
+  if ((e = launch_prepare(h->p, h->b, 1, h->s)) != cudaSuccess) return e;
+  stage_end(h, XSLAM_STAGE_PREPARE, 1 + h->p.bilateral);
+  stage_begin(h, XSLAM_STAGE_OTHER);
+  if ((e = launch_seed_pose(h->p, h->b, h->d_kinds, h->d_index, h->s)) != cudaSuccess) return e;
+  stage_end(h, XSLAM_STAGE_OTHER, 1);
+  stage_begin(h, XSLAM_STAGE_INTEGRATE);
+  if ((e = launch_integrate(h->p, h->b, h->s)) != cudaSuccess) return e;
+  stage_end(h, XSLAM_STAGE_INTEGRATE, 1);
+  stage_begin(h, XSLAM_STAGE_RAYCAST);
+  if ((e = launch_raycast(h->p, h->b, h->b.pose, h->b.model, h->b.model + hw, h->b.model + hw * (1 + 3 * h->p.L),
+                          false, true, h->s)) != cudaSuccess)
+    return e;
+  stage_end(h, XSLAM_STAGE_RAYCAST, 1);
+  stage_begin(h, XSLAM_STAGE_OTHER);
+  e = launch_readout(h->p, h->b, h->s);
+  stage_end(h, XSLAM_STAGE_OTHER, 1);
+  return e;
+}
+
+static cudaError_t enqueue_track(xslam_t h) {
+  cudaError_t e;
+  const int levels = h->cfg.icp_levels;
+  stage_begin(h, XSLAM_STAGE_PREPARE);
+  if ((e = launch_prepare(h->p, h->b, levels, h->s)) != cudaSuccess) return e;
+  stage_end(h, XSLAM_STAGE_PREPARE, levels + h->p.bilateral);
+  int last_level = -1, n_icp = 0;
+  for (int l = levels - 1; l >= 0; --l)
+    if (h->cfg.icp_iters[l] > 0) last_level = l;
+  stage_begin(h, XSLAM_STAGE_ICP);
+  for (int l = levels - 1; l >= 0; --l) {
+    for (int it = 0; it < h->cfg.icp_iters[l]; ++it) {
+      int flags = 0;
+      if (l == last_level && it == h->cfg.icp_iters[l] - 1) flags |= kIcpLast;
+      if ((e = launch_icp(h->p, h->b, l, flags, h->nblk[l], h->s)) != cudaSuccess) return e;
+      ++n_icp;
+    }
+  }
+  stage_end(h, XSLAM_STAGE_ICP, n_icp);
+  stage_begin(h, XSLAM_STAGE_INTEGRATE);
+  if ((e = launch_integrate(h->p, h->b, h->s)) != cudaSuccess) return e;
+  stage_end(h, XSLAM_STAGE_INTEGRATE, 1);
+  const size_t hw = (size_t)h->p.W * h->p.H;
+  stage_begin(h, XSLAM_STAGE_RAYCAST);
+  if ((e = launch_raycast(h->p, h->b, h->b.pose, h->b.model, h->b.model + hw, h->b.model + hw * (1 + 3 * h->p.L),
+                          false, true, h->s)) != cudaSuccess)
+    return e;
+  stage_end(h, XSLAM_STAGE_RAYCAST, 1);
+  stage_begin(h, XSLAM_STAGE_OTHER);
+  e = launch_readout(h->p, h->b, h->s);
+  stage_end(h, XSLAM_STAGE_OTHER, 1);
+  return e;
+}
+
+// Fold the recorded event pairs into the per-stage totals (synchronises the stream).
+static xslam_status prof_accumulate(xslam_t h) {
+  CU(cudaStreamSynchronize(h->s));
+  for (int st = 0; st < XSLAM_NSTAGE; ++st) {
+    const int n = h->pcount[st] < kProfRing ? h->pcount[st] : kProfRing;
+    for (int i = 0; i < n; ++i) {
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, h->pev[st][i][0], h->pev[st][i][1]));
+      h->pms[st] += ms;
+    }
+    h->pcount[st] = 0;
+  }
+  return XSLAM_OK;
+}
+
+static xslam_status run_chain(xslam_t h, bool first) {
+  cudaGraphExec_t* ge = first ? &h->g_first : &h->g_track;
+  if (h->profiling) {
+    for (int st = 0; st < XSLAM_NSTAGE; ++st)
+      if (h->pcount[st] + 2 > kProfRing) {
+        xslam_status s2 = prof_accumulate(h);
+        if (s2 != XSLAM_OK) return s2;
+        break;
+      }
+    CU(first ? enqueue_first(h) : enqueue_track(h));
+    h->pframes += 1;
+    return XSLAM_OK;
+  }
+  if (!h->use_graphs) {
+    CU(first ? enqueue_first(h) : enqueue_track(h));
+    return XSLAM_OK;
+  }
+  if (!*ge) {
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = first ? enqueue_first(h) : enqueue_track(h);
+    cudaError_t e2 = cudaStreamEndCapture(h->s, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return fail(h, XSLAM_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaError_t e3 = cudaGraphInstantiate(ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+      *ge = nullptr;
+      return fail(h, XSLAM_ECUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e3));
+    }
+  }
+  CU(cudaGraphLaunch(*ge, h->s));
+  return XSLAM_OK;
+}
+
+extern "C" xslam_status xslam_frame(xslam_t h, const float* depth, int depth_on_device, const xslam_seed* seeds, int K,
+                                    double* pose_out, double* dpose_out, double* dtwist_out) {
+  if (!h) return XSLAM_EINVAL;
+  if (!depth) return fail(h, XSLAM_EINVAL, "depth is NULL");
+  if (K < 0 || K > h->max_lanes) return fail(h, XSLAM_EINVAL, "K must be in 0..max_lanes");
+  if (h->frame == 0) {
+    xslam_status st = xslam_set_lanes(h, seeds, K);
+    if (st != XSLAM_OK) return st;
+  } else if (!same_seeds(h, seeds, K)) {
+    return fail(h, XSLAM_ESTATE, "seeds must not change after the first frame (xslam_reset first)");
+  }
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  if ((st = copy_depth(h, depth, depth_on_device)) != XSLAM_OK) return st;
+  if ((st = run_chain(h, h->frame == 0)) != XSLAM_OK) return st;
+  h->frame += 1;
+  const bool want = pose_out || dpose_out || dtwist_out;
+  if (!want && depth_on_device) return leave(h);
+  CU(cudaMemcpyAsync(h->h_result, h->b.result, sizeof(double) * kResSys, cudaMemcpyDeviceToHost, h->s));
+  CU(cudaMemcpyAsync(h->h_status, h->b.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->s));
+  if ((st = leave(h)) != XSLAM_OK) return st;
+  CU(cudaStreamSynchronize(h->s));
+  if (pose_out) memcpy(pose_out, h->h_result, sizeof(double) * 12);
+  if (dpose_out) memcpy(dpose_out, h->h_result + 12, sizeof(double) * 12 * h->K);
+  if (dtwist_out) memcpy(dtwist_out, h->h_result + 12 + 12 * (kMaxLanes - 1), sizeof(double) * 6 * h->K);
+  if (h->h_status[1] > 0) {
+    CU(cudaMemsetAsync(h->b.status + 1, 0, sizeof(int), h->s));
+    CU(cudaStreamSynchronize(h->s));
+    h->err = "ICP failed to track (too few correspondences or singular normal equations)";
+    return XSLAM_ENOTRACK;
+  }
+  return XSLAM_OK;
+}
+
+extern "C" xslam_status xslam_sync(xslam_t h, int* n_failed) {
+  if (!h) return XSLAM_EINVAL;
+  CU(cudaMemcpyAsync(h->h_status, h->b.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->s));
+  CU(cudaMemsetAsync(h->b.status + 1, 0, sizeof(int), h->s));
+  CU(cudaStreamSynchronize(h->s));
+  if (n_failed) *n_failed = h->h_status[1];
+  if (h->h_status[1] > 0) {
+    h->err = "ICP failed to track on some frames";
+    return XSLAM_ENOTRACK;
+  }
+  return XSLAM_OK;
+}
+
+static xslam_status upload_pose_lanes(xslam_t h, double* dst, const double* T) {
+  const int L = h->p.L;
+  for (int i = 0; i < 12 * L; ++i)
+    if (!std::isfinite(T[i])) return fail(h, XSLAM_EINVAL, "pose lanes have a non-finite entry");
+  CU(cudaMemcpyAsync(dst, T, sizeof(double) * 12 * L, cudaMemcpyHostToDevice, h->s));
+  return XSLAM_OK;
+}
+
+extern "C" xslam_status xslam_raycast(xslam_t h, const double* T, float* depth, float* vmap, float* nmap) {
+  if (!h) return XSLAM_EINVAL;
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  const double* pose = h->b.pose;
+  if (T) {
+    if ((st = upload_pose_lanes(h, h->pose_tmp, T)) != XSLAM_OK) return st;
+    pose = h->pose_tmp;
+  }
+  CU(launch_raycast(h->p, h->b, pose, depth, vmap, nmap, false, false, h->s));
+  st = leave(h);
+  CU(cudaStreamSynchronize(h->s));
+  return st;
+}
+
+extern "C" xslam_status xslam_read_tsdf(xslam_t h, int lane, float* out) {
+  if (!h || !out) return fail(h, XSLAM_EINVAL, "NULL argument");
+  if (lane < -1 || lane > h->K) return fail(h, XSLAM_EINVAL, "lane must be -1..K");
+  const size_t n = vox_count(h->p);
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  if (lane == -1) {
+    CU(cudaMemcpyAsync(out, h->b.Wt, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->s));
+  } else if (lane == 0) {
+    CU(cudaMemcpyAsync(out, h->b.F, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->s));
+  } else {
+    const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
+    k_scale<<<g, 256, 0, h->s>>>(h->b.F + (size_t)lane * n, out, n, 1.0 / h->p.h[lane]);
+    CU(cudaGetLastError());
+  }
+  st = leave(h);
+  CU(cudaStreamSynchronize(h->s));
+  return st;
+}
+
+extern "C" xslam_status xslam_write_tsdf(xslam_t h, int lane, const float* in) {
+  if (!h || !in) return fail(h, XSLAM_EINVAL, "NULL argument");
+  if (lane < -1 || lane > h->K) return fail(h, XSLAM_EINVAL, "lane must be -1..K");
+  const size_t n = vox_count(h->p);
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  float* dst = lane == -1 ? h->b.Wt : h->b.F + (size_t)lane * n;
+  CU(cudaMemcpyAsync(dst, in, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->s));
+  st = leave(h);
+  CU(cudaStreamSynchronize(h->s));
+  return st;
+}
+
+extern "C" xslam_status xslam_set_pose_lanes(xslam_t h, const double* T) {
+  if (!h || !T) return fail(h, XSLAM_EINVAL, "NULL argument");
+  xslam_status st = upload_pose_lanes(h, h->b.pose, T);
+  if (st != XSLAM_OK) return st;
+  CU(cudaStreamSynchronize(h->s));
+  return XSLAM_OK;
+}
+
+extern "C" xslam_status xslam_get_pose_lanes(xslam_t h, double* T) {
+  if (!h || !T) return fail(h, XSLAM_EINVAL, "NULL argument");
+  CU(cudaMemcpyAsync(T, h->b.pose, sizeof(double) * 12 * h->p.L, cudaMemcpyDeviceToHost, h->s));
+  CU(cudaStreamSynchronize(h->s));
+  return XSLAM_OK;
+}
+
+extern "C" xslam_status xslam_measure(xslam_t h, const float* depth, int level, float* out) {
+  if (!h || !depth) return fail(h, XSLAM_EINVAL, "NULL argument");
+  if (level < 0 || level >= h->cfg.icp_levels) return fail(h, XSLAM_EINVAL, "level out of range");
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  if ((st = copy_depth(h, depth, 1)) != XSLAM_OK) return st;
+  CU(launch_prepare(h->p, h->b, h->cfg.icp_levels, h->s));
+  if (out) {
+    const size_t npx = (size_t)(h->p.W >> level) * (h->p.H >> level);
+    CU(cudaMemcpyAsync(out, h->b.pyr[level], sizeof(float) * npx, cudaMemcpyDeviceToDevice, h->s));
+  }
+  st = leave(h);
+  CU(cudaStreamSynchronize(h->s));
+  return st;
+}
+
+extern "C" xslam_status xslam_integrate(xslam_t h, const float* depth) {
+  if (!h || !depth) return fail(h, XSLAM_EINVAL, "NULL argument");
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  if ((st = copy_depth(h, depth, 1)) != XSLAM_OK) return st;
+  CU(launch_prepare(h->p, h->b, 1, h->s));
+  CU(launch_integrate(h->p, h->b, h->s));
+  st = leave(h);
+  CU(cudaStreamSynchronize(h->s));
+  return st;
+}
+
+extern "C" xslam_status xslam_set_model(xslam_t h, const float* depth, const float* vmap, const float* nmap,
+                                        const double* T_prev) {
+  if (!h || !depth || !vmap || !nmap || !T_prev) return fail(h, XSLAM_EINVAL, "NULL argument");
+  const size_t hw = (size_t)h->p.W * h->p.H;
+  const int L = h->p.L;
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  CU(cudaMemcpyAsync(h->b.model, depth, sizeof(float) * hw, cudaMemcpyDeviceToDevice, h->s));
+  CU(cudaMemcpyAsync(h->b.model + hw, vmap, sizeof(float) * hw * 3 * L, cudaMemcpyDeviceToDevice, h->s));
+  CU(cudaMemcpyAsync(h->b.model + hw * (1 + 3 * L), nmap, sizeof(float) * hw * 3 * L, cudaMemcpyDeviceToDevice, h->s));
+  if ((st = upload_pose_lanes(h, h->b.pose_prev, T_prev)) != XSLAM_OK) return st;
+  st = leave(h);
+  CU(cudaStreamSynchronize(h->s));
+  return st;
+}
+
+extern "C" xslam_status xslam_icp_system(xslam_t h, int level, const double* Tj, double* out, int* n_valid) {
+  if (!h || !Tj || !out) return fail(h, XSLAM_EINVAL, "NULL argument");
+  if (level < 0 || level >= h->cfg.icp_levels) return fail(h, XSLAM_EINVAL, "level out of range");
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  if ((st = upload_pose_lanes(h, h->b.pose, Tj)) != XSLAM_OK) return st;
+  CU(launch_icp(h->p, h->b, level, kIcpNoUpdate, h->nblk[level], h->s));
+  CU(cudaMemcpyAsync(h->h_result, h->b.result, sizeof(double) * kResLen, cudaMemcpyDeviceToHost, h->s));
+  CU(cudaMemcpyAsync(h->h_status, h->b.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->s));
+  st = leave(h);
+  CU(cudaStreamSynchronize(h->s));
+  memcpy(out, h->h_result + kResSys, sizeof(double) * kNT * h->p.L);
+  if (n_valid) *n_valid = h->h_status[2];
+  return st;
+}
+
+extern "C" xslam_status xslam_grad(xslam_t h, const float* query_depth, const double* T_q, int order, double* loss,
+                                   double* grad, double* hess) {
+  (void)hess;
+  if (!h || !query_depth || !T_q) return fail(h, XSLAM_EINVAL, "NULL argument");
+  if (order != 1) return fail(h, XSLAM_EINVAL, "only order 1 is built");
+  if (h->max_lanes < 6 || !h->model_q) return fail(h, XSLAM_EINVAL, "xslam_grad needs max_lanes >= 6");
+  if (h->K != 0) return fail(h, XSLAM_ESTATE, "xslam_grad needs a handle without sequence lanes (reset first)");
+  Params p = h->p;
+  p.L = 7;
+  for (int l = 1; l < 7; ++l) {
+    p.dmu[l] = 0.f;
+    p.dD[l] = 0.f;
+    p.h[l] = 1e-10;
+  }
+  int kinds[kMaxLanes] = {0}, index[kMaxLanes] = {0};
+  for (int l = 1; l < 7; ++l) index[l] = l - 1;
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  CU(cudaMemcpyAsync(h->d_kinds, kinds, sizeof(kinds), cudaMemcpyHostToDevice, h->s));
+  CU(cudaMemcpyAsync(h->d_index, index, sizeof(index), cudaMemcpyHostToDevice, h->s));
+  CU(cudaMemcpyAsync(h->pose_tmp, T_q, sizeof(double) * 12, cudaMemcpyHostToDevice, h->s));
+  Buffers bq = h->b;
+  bq.pose = h->pose_tmp;
+  CU(launch_seed_pose(p, bq, h->d_kinds, h->d_index, h->s));
+  const size_t hw = (size_t)p.W * p.H;
+  CU(launch_raycast(p, bq, h->pose_tmp, h->model_q, h->model_q + hw, h->model_q + hw * (1 + 3 * 7), true, false, h->s));
+  if ((st = copy_depth(h, query_depth, 1)) != XSLAM_OK) return st;
+  CU(launch_prepare(p, h->b, 1, h->s));
+  CU(launch_loss(p, h->b, h->b.pyr[0], h->model_q, h->pose_tmp, h->b.result + kResSys, 4 * h->nsm, h->s));
+  CU(cudaMemcpyAsync(h->h_result, h->b.result, sizeof(double) * kResLen, cudaMemcpyDeviceToHost, h->s));
+  st = leave(h);
+  CU(cudaStreamSynchronize(h->s));
+  if (loss) *loss = h->h_result[kResSys];
+  if (grad)
+    for (int j = 0; j < 6; ++j) grad[j] = h->h_result[kResSys + 1 + j];
+  return st;
+}
+
+extern "C" xslam_status xslam_profile(xslam_t h, int enable) {
+  if (!h) return XSLAM_EINVAL;
+  if (enable && !h->profiling) {
+    for (int st = 0; st < XSLAM_NSTAGE; ++st)
+      for (int i = 0; i < kProfRing; ++i)
+        for (int k = 0; k < 2; ++k)
+          if (!h->pev[st][i][k]) CU(cudaEventCreate(&h->pev[st][i][k]));
+    for (int st = 0; st < XSLAM_NSTAGE; ++st) {
+      h->pcount[st] = 0;
+      h->pms[st] = 0;
+      h->plaunch[st] = 0;
+    }
+    h->pframes = 0;
+    CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * 2, h->s));
+  }
+  if (!enable && h->profiling) {
+    xslam_status st = prof_accumulate(h);
+    if (st != XSLAM_OK) return st;
+  }
+  h->profiling = enable != 0;
+  CU(cudaStreamSynchronize(h->s));
+  return XSLAM_OK;
+}
+
+extern "C" xslam_status xslam_profile_read(xslam_t h, double* ms, long long* launches, double* counters) {
+  if (!h) return XSLAM_EINVAL;
+  xslam_status st = prof_accumulate(h);
+  if (st != XSLAM_OK) return st;
+  unsigned long long c[2] = {0, 0};
+  CU(cudaMemcpy(c, h->b.stats, sizeof(c), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < XSLAM_NSTAGE; ++i) {
+    if (ms) ms[i] = h->pms[i];
+    if (launches) launches[i] = h->plaunch[i];
+  }
+  if (counters) {
+    counters[0] = (double)c[0];
+    counters[1] = (double)c[1];
+    counters[2] = (double)h->pframes;
+  }
+  return XSLAM_OK;
+}
+
+extern "C" const char* xslam_last_error(xslam_t h) { return h ? h->err.c_str() : g_create_err.c_str(); }

@@ -1,0 +1,388 @@
+// Projective point-to-plane ICP (X-SLAM Sec. 4.1, "Differentiable ICP") on 1 + K lanes: one launch
+// per Gauss-Newton iteration.
+//
+// Per pixel u of pyramid level l: V = D K_l^-1 u, N = normalize((V(u+x) - V) x (V(u+y) - V)) (Eq. vertex,
+// Eq. normal), p' = T_j V, u_hat = pi(K_l T_{k-1}^-1 p'), q and n = bilinear model vertex / normal at
+// u_hat (level-0 model maps read at pixel 2^l u_hat), r = (p' - q).n, J = [(p' x n)^T, n^T]; the
+// normal equations A = sum J J^T, g = sum J r (Eq. icp, Eq. "icp approx") are reduced, A x = -g is
+// solved and T_{j+1} = exp(x) T_j.
+//
+// GB300 mapping: a block holds L = 1 + K warps per replica; warp `lane` of a replica computes the
+// real part of its 32 pixels and, if lane > 0, the tangent of that lane, accumulating only 27 FP32
+// sums per thread; replicas of a block share pixel chunks through L1. Warp shuffles and shared
+// memory reduce each block to one FP32 partial per lane; the last block to finish (ticket counter,
+// no grid-wide wait) adds the partials in FP64, factors the real 6x6 matrix by Cholesky (FP64), solves
+// the K + 1 right-hand sides (x_0 from the real part, x_j = A^-1 (-g_j - A_j x_0) for each lane) and
+// composes exp(x) T_j on every lane in FP64.
+#include "internal.cuh"
+#include "se3.cuh"
+
+namespace xslam {
+
+constexpr int kGroup = 8;  // FP32 partials summed per group before the FP64 cross-block sum
+
+struct Lvl {
+  int W, H, s;
+  float fx, fy, cx, cy;
+};
+
+__device__ __forceinline__ void accum(float* acc, const float* Ja, const float ra, const float* Jb, const float rb) {
+  // acc += Ja Jb^T + Jb Ja^T (upper triangle) and Ja rb + Jb ra; called with (J, r, J, r) * 0.5 for
+  // the real lane and with (J, r, J_l, r_l) for a tangent lane.
+  int q = 0;
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = r; c < 6; ++c) acc[q++] += Ja[r] * Jb[c] + Jb[r] * Ja[c];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) acc[21 + r] += Ja[r] * rb + Jb[r] * ra;
+}
+
+__global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int flags, int reps) {
+  const int L = p.L;
+  const int warp = threadIdx.x >> 5, lid = threadIdx.x & 31;
+  const int ln = warp % L, rep = warp / L;
+  __shared__ float sT[kMaxLanes][12];
+  __shared__ float sP[kMaxLanes][12];
+  __shared__ int s_skip, s_last;
+  __shared__ float s_red[kNT * kMaxLanes];  // [rep][lane][27]; reps * L <= 16 by construction
+  __shared__ int s_cnt[32];
+  __shared__ double sA[kMaxLanes * kNT];
+  __shared__ double sx[kMaxLanes][6];
+  __shared__ double sLch[36];
+  __shared__ int s_ncorr, s_fail;
+
+  if (threadIdx.x == 0) s_skip = b.status[0];
+  for (int i = threadIdx.x; i < L * 12; i += blockDim.x) {
+    sT[i / 12][i % 12] = (float)b.pose[i];
+    sP[i / 12][i % 12] = (float)b.pose_prev[i];
+  }
+  __syncthreads();
+
+  float acc[kNT];
+#pragma unroll
+  for (int q = 0; q < kNT; ++q) acc[q] = 0.f;
+  int cnt = 0;
+
+  if (!s_skip) {
+    const float* D = b.pyr[0];
+    if (lv.s == 2) D = b.pyr[1];
+    if (lv.s == 4) D = b.pyr[2];
+    const size_t hw0 = (size_t)p.W * p.H;
+    const float* mdep = b.model;
+    const float* mV = b.model + hw0;
+    const float* mN = b.model + hw0 * (1 + 3 * L);
+    const float* T = sT[0];
+    const float* P = sP[0];
+    const int npx = lv.W * lv.H;
+    const int nchunk = (npx + 31) >> 5;
+    for (int ch = blockIdx.x * reps + rep; ch < nchunk; ch += gridDim.x * reps) {
+      const int px = (ch << 5) + lid;
+      if (px >= npx) continue;
+      const int u = px % lv.W, v = px / lv.W;
+      if (u >= lv.W - 1 || v >= lv.H - 1) continue;
+      const float d0 = D[px], dxp = D[px + 1], dyp = D[px + lv.W];
+      if (!(d0 > 0.f && dxp > 0.f && dyp > 0.f)) continue;
+      const float rx = (u - lv.cx) / lv.fx, ry = (v - lv.cy) / lv.fy;
+      const float rx1 = (u + 1 - lv.cx) / lv.fx, ry1 = (v + 1 - lv.cy) / lv.fy;
+      const float V[3] = {d0 * rx, d0 * ry, d0};
+      const float ex[3] = {dxp * rx1 - V[0], dxp * ry - V[1], dxp - V[2]};
+      const float ey[3] = {dyp * rx - V[0], dyp * ry1 - V[1], dyp - V[2]};
+      const float c[3] = {ex[1] * ey[2] - ex[2] * ey[1], ex[2] * ey[0] - ex[0] * ey[2], ex[0] * ey[1] - ex[1] * ey[0]};
+      const float n2m = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+      if (!(n2m > 0.f)) continue;
+      const float inm = 1.f / sqrtf(n2m);
+      const float Nm[3] = {c[0] * inm, c[1] * inm, c[2] * inm};
+      // p' = T_j V
+      float pp[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) pp[r] = T[4 * r] * V[0] + T[4 * r + 1] * V[1] + T[4 * r + 2] * V[2] + T[4 * r + 3];
+      // previous camera frame: P^T (p' - t_prev)
+      const float e0 = pp[0] - P[3], e1 = pp[1] - P[7], e2 = pp[2] - P[11];
+      const float pcx = P[0] * e0 + P[4] * e1 + P[8] * e2;
+      const float pcy = P[1] * e0 + P[5] * e1 + P[9] * e2;
+      const float pcz = P[2] * e0 + P[6] * e1 + P[10] * e2;
+      if (!(pcz > 0.f)) continue;
+      const float iz = 1.f / pcz;
+      const float qx = pcx * iz, qy = pcy * iz;
+      const float ux = lv.fx * qx + lv.cx, uy = lv.fy * qy + lv.cy;
+      const float ci = floorf(ux + kCellBias), cj = floorf(uy + kCellBias);
+      if (!(ci >= 0.f && ci <= (float)(lv.W - 2) && cj >= 0.f && cj <= (float)(lv.H - 2))) continue;
+      const int i0 = (int)ci, j0 = (int)cj;
+      const float a = ux - ci, bb = uy - cj;
+      const size_t t00 = (size_t)(j0 * lv.s) * p.W + (size_t)(i0 * lv.s);
+      const size_t t10 = t00 + lv.s, t01 = t00 + (size_t)lv.s * p.W, t11 = t01 + lv.s;
+      const float g00 = mdep[t00], g10 = mdep[t10], g01 = mdep[t01], g11 = mdep[t11];
+      if (!(g00 > 0.f && g10 > 0.f && g01 > 0.f && g11 > 0.f)) continue;
+      if (!(fabsf(g10 - g00) + fabsf(g01 - g00) + fabsf(g11 - g00) < p.disc_gate)) continue;
+      const float w00 = (1.f - a) * (1.f - bb), w10 = a * (1.f - bb), w01 = (1.f - a) * bb, w11 = a * bb;
+      float q[3], nn[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const float* Vp = mV + (size_t)r * hw0;
+        const float* Np = mN + (size_t)r * hw0;
+        q[r] = w00 * Vp[t00] + w10 * Vp[t10] + w01 * Vp[t01] + w11 * Vp[t11];
+        nn[r] = w00 * Np[t00] + w10 * Np[t10] + w01 * Np[t01] + w11 * Np[t11];
+      }
+      const float df[3] = {pp[0] - q[0], pp[1] - q[1], pp[2] - q[2]};
+      if (!(df[0] * df[0] + df[1] * df[1] + df[2] * df[2] <= p.dist_gate2)) continue;
+      float nw[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) nw[r] = T[4 * r] * Nm[0] + T[4 * r + 1] * Nm[1] + T[4 * r + 2] * Nm[2];
+      const float nl2 = nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2];
+      if (!(fabsf(nw[0] * nn[0] + nw[1] * nn[1] + nw[2] * nn[2]) >= p.cos_normal_gate * sqrtf(nl2))) continue;
+      const float res = df[0] * nn[0] + df[1] * nn[1] + df[2] * nn[2];
+      const float J[6] = {pp[1] * nn[2] - pp[2] * nn[1], pp[2] * nn[0] - pp[0] * nn[2], pp[0] * nn[1] - pp[1] * nn[0],
+                          nn[0], nn[1], nn[2]};
+      if (ln == 0) {
+        ++cnt;
+        const float hJ[6] = {0.5f * J[0], 0.5f * J[1], 0.5f * J[2], 0.5f * J[3], 0.5f * J[4], 0.5f * J[5]};
+        accum(acc, hJ, 0.5f * res, J, res);
+        continue;
+      }
+      // ---------------- tangent of lane `ln` ----------------
+      const float* Tl = sT[ln];
+      const float* Pl = sP[ln];
+      const float dDl = p.dD[ln];
+      // measured vertex tangent (DEPTH lanes move every depth by dD); the measured normal enters
+      // only the (real) normal gate, so its tangent is not needed
+      const float Vl[3] = {dDl * rx, dDl * ry, dDl};
+      float ppl[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        ppl[r] = Tl[4 * r] * V[0] + Tl[4 * r + 1] * V[1] + Tl[4 * r + 2] * V[2] + Tl[4 * r + 3] +
+                 T[4 * r] * Vl[0] + T[4 * r + 1] * Vl[1] + T[4 * r + 2] * Vl[2];
+      const float el0 = ppl[0] - Pl[3], el1 = ppl[1] - Pl[7], el2 = ppl[2] - Pl[11];
+      const float pcxl = Pl[0] * e0 + Pl[4] * e1 + Pl[8] * e2 + P[0] * el0 + P[4] * el1 + P[8] * el2;
+      const float pcyl = Pl[1] * e0 + Pl[5] * e1 + Pl[9] * e2 + P[1] * el0 + P[5] * el1 + P[9] * el2;
+      const float pczl = Pl[2] * e0 + Pl[6] * e1 + Pl[10] * e2 + P[2] * el0 + P[6] * el1 + P[10] * el2;
+      const float al = lv.fx * (pcxl - qx * pczl) * iz;
+      const float bl = lv.fy * (pcyl - qy * pczl) * iz;
+      const float w00l = -al * (1.f - bb) - (1.f - a) * bl, w10l = al * (1.f - bb) - a * bl;
+      const float w01l = -al * bb + (1.f - a) * bl, w11l = al * bb + a * bl;
+      const float* mVl = mV + (size_t)(3 * ln) * hw0;
+      const float* mNl = mN + (size_t)(3 * ln) * hw0;
+      float ql[3], nl[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const float* Vp = mV + (size_t)r * hw0;
+        const float* Np = mN + (size_t)r * hw0;
+        const float* Vpl = mVl + (size_t)r * hw0;
+        const float* Npl = mNl + (size_t)r * hw0;
+        ql[r] = w00l * Vp[t00] + w10l * Vp[t10] + w01l * Vp[t01] + w11l * Vp[t11] + w00 * Vpl[t00] + w10 * Vpl[t10] +
+                w01 * Vpl[t01] + w11 * Vpl[t11];
+        nl[r] = w00l * Np[t00] + w10l * Np[t10] + w01l * Np[t01] + w11l * Np[t11] + w00 * Npl[t00] + w10 * Npl[t10] +
+                w01 * Npl[t01] + w11 * Npl[t11];
+      }
+      const float dfl[3] = {ppl[0] - ql[0], ppl[1] - ql[1], ppl[2] - ql[2]};
+      const float resl = dfl[0] * nn[0] + dfl[1] * nn[1] + dfl[2] * nn[2] + df[0] * nl[0] + df[1] * nl[1] + df[2] * nl[2];
+      const float Jl[6] = {ppl[1] * nn[2] - ppl[2] * nn[1] + pp[1] * nl[2] - pp[2] * nl[1],
+                           ppl[2] * nn[0] - ppl[0] * nn[2] + pp[2] * nl[0] - pp[0] * nl[2],
+                           ppl[0] * nn[1] - ppl[1] * nn[0] + pp[0] * nl[1] - pp[1] * nl[0],
+                           nl[0], nl[1], nl[2]};
+      accum(acc, J, res, Jl, resl);
+    }
+  }
+
+  // ---------------- block reduction ----------------
+#pragma unroll
+  for (int q = 0; q < kNT; ++q) {
+    float x = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    acc[q] = x;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lid == 0) {
+#pragma unroll
+    for (int q = 0; q < kNT; ++q) s_red[(rep * L + ln) * kNT + q] = acc[q];
+    s_cnt[warp] = cnt;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) {
+    float s = 0.f;
+    for (int r = 0; r < reps; ++r) s += s_red[r * L * kNT + i];
+    b.partial[(size_t)blockIdx.x * L * kNT + i] = s;
+  }
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int r = 0; r < reps; ++r) c += s_cnt[r * L];
+    b.partial_n[blockIdx.x] = c;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(b.ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+
+  // ---------------- last block: FP64 cross-block sum ----------------
+  const int nblk = gridDim.x;
+  for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < nblk; g += kGroup) {
+      float f = 0.f;
+      const int ge = min(nblk, g + kGroup);
+      for (int k = g; k < ge; ++k) f += __ldcg(&b.partial[(size_t)k * L * kNT + i]);
+      s += (double)f;
+    }
+    sA[i] = s;
+  }
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int k = 0; k < nblk; ++k) c += __ldcg(&b.partial_n[k]);
+    s_ncorr = c;
+    *b.ticket = 0u;  // ready for the next launch
+  }
+  __syncthreads();
+
+  const bool update = !s_skip && !(flags & kIcpNoUpdate);
+  if (flags & kIcpNoUpdate) {
+    for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) b.result[kResSys + i] = sA[i];
+    if (threadIdx.x == 0) b.status[2] = s_ncorr;
+    return;
+  }
+  if (threadIdx.x == 0) {
+    int fail = s_skip;
+    if (!fail && (float)s_ncorr < p.min_corr_frac * (float)(lv.W * lv.H)) fail = 1;
+    if (!fail) {
+      // Cholesky of the real 6x6 A (upper-triangle storage, row-major)
+      double A[36];
+      int q = 0;
+      for (int r = 0; r < 6; ++r)
+        for (int c = r; c < 6; ++c) {
+          A[6 * r + c] = sA[q];
+          A[6 * c + r] = sA[q];
+          ++q;
+        }
+      for (int j = 0; j < 6 && !fail; ++j) {
+        double d = A[6 * j + j];
+        for (int k = 0; k < j; ++k) d -= sLch[6 * j + k] * sLch[6 * j + k];
+        if (!(d > 0.0)) {
+          fail = 1;
+          break;
+        }
+        const double ljj = sqrt(d);
+        sLch[6 * j + j] = ljj;
+        for (int i = j + 1; i < 6; ++i) {
+          double s = A[6 * i + j];
+          for (int k = 0; k < j; ++k) s -= sLch[6 * i + k] * sLch[6 * j + k];
+          sLch[6 * i + j] = s / ljj;
+        }
+      }
+      if (!fail) {
+        double y[6], x[6];
+        for (int i = 0; i < 6; ++i) {
+          double s = -sA[21 + i];
+          for (int k = 0; k < i; ++k) s -= sLch[6 * i + k] * y[k];
+          y[i] = s / sLch[6 * i + i];
+        }
+        for (int i = 5; i >= 0; --i) {
+          double s = y[i];
+          for (int k = i + 1; k < 6; ++k) s -= sLch[6 * k + i] * x[k];
+          x[i] = s / sLch[6 * i + i];
+        }
+        for (int i = 0; i < 6; ++i) sx[0][i] = x[i];
+      }
+    }
+    s_fail = fail;
+  }
+  __syncthreads();
+  if (update && !s_fail && threadIdx.x > 0 && threadIdx.x < L) {
+    // x_l = A^-1 (-g_l - A_l x_0)
+    const int l = threadIdx.x;
+    const double* Al = sA + l * kNT;
+    double Af[36];
+    int q = 0;
+    for (int r = 0; r < 6; ++r)
+      for (int c = r; c < 6; ++c) {
+        Af[6 * r + c] = Al[q];
+        Af[6 * c + r] = Al[q];
+        ++q;
+      }
+    double rhs[6], y[6], x[6];
+    for (int i = 0; i < 6; ++i) {
+      double s = -Al[21 + i];
+      for (int k = 0; k < 6; ++k) s -= Af[6 * i + k] * sx[0][k];
+      rhs[i] = s;
+    }
+    for (int i = 0; i < 6; ++i) {
+      double s = rhs[i];
+      for (int k = 0; k < i; ++k) s -= sLch[6 * i + k] * y[k];
+      y[i] = s / sLch[6 * i + i];
+    }
+    for (int i = 5; i >= 0; --i) {
+      double s = y[i];
+      for (int k = i + 1; k < 6; ++k) s -= sLch[6 * k + i] * x[k];
+      x[i] = s / sLch[6 * i + i];
+    }
+    for (int i = 0; i < 6; ++i) sx[l][i] = x[i];
+  }
+  __syncthreads();
+  // pose update T <- exp(x) T on every lane (thread l handles lane l)
+  double Tn[12];
+  const int l = threadIdx.x;
+  if (update && !s_fail && l < L) {
+    double E[12], E1[12], T0[12], Tl[12];
+    for (int i = 0; i < 12; ++i) T0[i] = b.pose[i];
+    if (l == 0) {
+      se3_exp_tangent(sx[0], nullptr, E, nullptr);
+      compose(E, T0, Tn);
+    } else {
+      for (int i = 0; i < 12; ++i) Tl[i] = b.pose[12 * l + i];
+      se3_exp_tangent(sx[0], sx[l], E, E1);
+      compose_tangent(E, E1, T0, Tl, Tn);
+    }
+  }
+  __syncthreads();
+  if (update && !s_fail && l < L)
+    for (int i = 0; i < 12; ++i) b.pose[12 * l + i] = Tn[i];
+  if (threadIdx.x == 0 && s_fail && !s_skip) b.status[0] = 1;
+  if (flags & kIcpLast) {
+    __syncthreads();
+    const int failed = b.status[0];
+    if (failed && l < L)
+      for (int i = 0; i < 12; ++i) b.pose[12 * l + i] = b.pose_prev[12 * l + i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (failed) b.status[1] += 1;
+      b.status[0] = 0;
+      b.status[2] = s_ncorr;
+    }
+  }
+}
+
+int icp_blocks(int level_pixels, int L) {
+  int reps = 16 / L;
+  if (reps < 1) reps = 1;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int nchunk = (level_pixels + 31) / 32;
+  int nblk = (nchunk + reps - 1) / reps;
+  if (nblk > sms) nblk = sms;
+  if (nblk < 1) nblk = 1;
+  return nblk;
+}
+
+cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int flags, int nblk, cudaStream_t s) {
+  Lvl lv;
+  lv.s = 1 << level;
+  lv.W = p.W >> level;
+  lv.H = p.H >> level;
+  lv.fx = p.fx / lv.s;
+  lv.fy = p.fy / lv.s;
+  lv.cx = p.cx / lv.s;
+  lv.cy = p.cy / lv.s;
+  int reps = 16 / p.L;
+  if (reps < 1) reps = 1;
+  const int threads = 32 * p.L * reps;
+  k_icp<<<nblk, threads, 0, s>>>(p, b, lv, flags, reps);
+  return cudaGetLastError();
+}
+
+}  // namespace xslam

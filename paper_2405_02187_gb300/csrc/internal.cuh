@@ -1,0 +1,84 @@
+// Internal definitions shared by the CUDA translation units of libxslam (not part of the C ABI).
+//
+// Lane model (X-SLAM Sec. 3, simplified CSFD arithmetic): a perturbed quantity x* = x + sum_j x_j i_j
+// is stored as one real value x and K imaginary values x_j. Products of two imaginary parts are
+// dropped (Eq. csfd_simplify_multiplication), so every imaginary part is the directional derivative
+// times h_j and is computed by the tangent (first-order) rule from the real values. Discrete
+// decisions (gates, floors, zero-crossing tests) use real parts only; the imaginary parts follow the
+// chosen branch.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace xslam {
+
+constexpr int kMaxLanes = 16;        // 1 real + up to 15 imaginary lanes
+constexpr int kNT = 27;              // 21 upper-triangle entries of J J^T + 6 of J r
+constexpr int kResSys = 12 + 18 * (kMaxLanes - 1);       // offset of the last ICP system in `result`
+constexpr int kResLen = kResSys + kNT * kMaxLanes + 8;   // doubles in `result` (+ loss / grad scratch)
+constexpr float kCellBias = 0.015625f;  // 2^-6 pixel: ICP bilinear-cell tie breaker (first iteration
+                                        // evaluates u_hat on integer pixels by construction)
+
+// Everything a kernel needs besides buffers; passed by value.
+struct Params {
+  // volume
+  int nx, ny, nz;
+  float voxel, mu, ox, oy, oz;
+  float w_max;              // <= 0: no cap
+  // camera (level 0)
+  float fx, fy, cx, cy;
+  int W, H;
+  // lanes: L = 1 + K
+  int L;
+  float dmu[kMaxLanes];     // Im mu of each lane (TRUNC seeds), lane 0 unused
+  float dD[kMaxLanes];      // Im D of each lane (DEPTH seeds on every pixel), lane 0 unused
+  double h[kMaxLanes];      // step of each lane for the read-out
+  // gates and ranges
+  float dist_gate2, cos_normal_gate, disc_gate, min_corr_frac;
+  float depth_min, depth_max, pyr_range;
+  int bilateral;            // 1: bilateral filter of the gated raw depth before the pyramid
+  float ray_step;           // dalpha in metres of camera depth
+  int m0, m1;               // ray samples alpha_m = m * ray_step, m0 <= m <= m1
+};
+
+// Device buffers owned by a handle.
+struct Buffers {
+  float* F;         // L planes of N: lane 0 = Re F, lane j = Im F (raw)
+  float* Wt;        // N
+  float* depth_in;  // H*W raw input
+  float* gated;     // H*W range-gated input (bilateral filter source)
+  float* pyr[3];    // range-gated level 0 and its two coarser levels
+  float* model;     // (1 + 6 L) planes of H*W: depth_g, V lanes (3 L), N lanes (3 L)
+  double* pose;     // L x 12 current pose lanes
+  double* pose_prev;// L x 12 pose lanes at which the model was ray cast
+  float* partial;   // ICP per-block partial sums: nblk x L x 27
+  int* partial_n;   // ICP per-block correspondence counts
+  unsigned* ticket; // last-block-done counter
+  int* status;      // [0] ICP failed in this frame, [1] frames failed since last sync, [2] last n_valid
+  double* result;   // read-out: 12 (pose) + 12 K (dpose) + 6 K (dtwist) + 27 L (last system)
+  unsigned long long* stats;  // [0] voxels updated by fusion, [1] pixels with a ray-cast surface
+};
+
+__host__ __device__ inline size_t vox_count(const Params& p) {
+  return (size_t)p.nx * p.ny * p.nz;
+}
+
+// ---------------------------------------------------------------------------------------------
+// launches (each defined in its own translation unit)
+// ---------------------------------------------------------------------------------------------
+cudaError_t launch_prepare(const Params& p, const Buffers& b, int levels, cudaStream_t s);
+cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s);
+cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose, float* depth,
+                           float* vmap, float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s);
+cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int iter_flags, int nblk, cudaStream_t s);
+cudaError_t launch_seed_pose(const Params& p, const Buffers& b, const int* kinds, const int* index, cudaStream_t s);
+cudaError_t launch_readout(const Params& p, const Buffers& b, cudaStream_t s);
+cudaError_t launch_loss(const Params& p, const Buffers& b, const float* depth, const float* model,
+                        const double* pose, double* out, int nblk, cudaStream_t s);
+int icp_blocks(int level_pixels, int L);
+
+// ICP iteration flags
+enum : int { kIcpFirst = 1, kIcpLast = 2, kIcpNoUpdate = 4 };
+
+}  // namespace xslam

@@ -1,0 +1,243 @@
+// Ray casting of the TSDF (X-SLAM Sec. 4.1, "Ray casting"; Eq. surface_prediction) on 1 + K lanes.
+//
+// Pixel u casts r(alpha) = alpha R K^-1 u_dot + t with alpha the camera depth. Samples sit at
+// alpha_m = m * dalpha (m0 <= m <= m1); a sample is valid if its trilinear cell is inside the volume
+// and its 8 corners are observed (W > 0). The march uses real parts only: the first pair of
+// consecutive valid samples with F_m > 0 >= F_{m+1} is the hit; a pair with F_m <= 0 < F_{m+1} ends
+// the ray. The hit pair is re-evaluated on every lane (complex pose, complex TSDF, same cells):
+// alpha0 = alpha_m - dalpha F_m / (F_{m+1} - F_m), V_g = r(alpha0), N_g = grad F / |grad F| from
+// central differences of the trilinear F at V_g +- one voxel per axis.
+// Samples outside the volume are invalid, so the march starts and stops at the volume's bounds
+// (widened by one sample), which visits every valid sample in the same order.
+#include "internal.cuh"
+
+namespace xslam {
+
+struct Tri {
+  size_t base;     // linear index of the min corner
+  float fx, fy, fz;
+  float val;       // trilinear F (real lane)
+  float g[3];      // d val / d g (continuous voxel coordinates)
+};
+
+// Cell and real trilinear value at continuous voxel coordinate (gx, gy, gz). Returns false if the
+// cell is outside the volume or a corner is unobserved.
+__device__ __forceinline__ bool tri_real(const Params& p, const float* __restrict__ F, const float* __restrict__ Wt,
+                                         float gx, float gy, float gz, Tri& t, bool want_grad) {
+  if (!(gx >= 0.f && gx < (float)(p.nx - 1) && gy >= 0.f && gy < (float)(p.ny - 1) && gz >= 0.f &&
+        gz < (float)(p.nz - 1)))
+    return false;
+  const int i = (int)floorf(gx), j = (int)floorf(gy), k = (int)floorf(gz);
+  const size_t sx = 1, sy = (size_t)p.nx, sz = (size_t)p.nx * p.ny;
+  const size_t b = i + sy * j + sz * k;
+  const float w000 = Wt[b], w100 = Wt[b + sx], w010 = Wt[b + sy], w110 = Wt[b + sx + sy];
+  const float w001 = Wt[b + sz], w101 = Wt[b + sx + sz], w011 = Wt[b + sy + sz], w111 = Wt[b + sx + sy + sz];
+  if (!(w000 > 0.f && w100 > 0.f && w010 > 0.f && w110 > 0.f && w001 > 0.f && w101 > 0.f && w011 > 0.f &&
+        w111 > 0.f))
+    return false;
+  const float c000 = F[b], c100 = F[b + sx], c010 = F[b + sy], c110 = F[b + sx + sy];
+  const float c001 = F[b + sz], c101 = F[b + sx + sz], c011 = F[b + sy + sz], c111 = F[b + sx + sy + sz];
+  const float fx = gx - i, fy = gy - j, fz = gz - k;
+  const float x00 = c000 + fx * (c100 - c000), x10 = c010 + fx * (c110 - c010);
+  const float x01 = c001 + fx * (c101 - c001), x11 = c011 + fx * (c111 - c011);
+  const float y0 = x00 + fy * (x10 - x00), y1 = x01 + fy * (x11 - x01);
+  t.val = y0 + fz * (y1 - y0);
+  t.base = b;
+  t.fx = fx;
+  t.fy = fy;
+  t.fz = fz;
+  if (want_grad) {
+    const float dx00 = c100 - c000, dx10 = c110 - c010, dx01 = c101 - c001, dx11 = c111 - c011;
+    t.g[0] = (1.f - fz) * ((1.f - fy) * dx00 + fy * dx10) + fz * ((1.f - fy) * dx01 + fy * dx11);
+    t.g[1] = (1.f - fz) * (x10 - x00) + fz * (x11 - x01);
+    t.g[2] = y1 - y0;
+  }
+  return true;
+}
+
+// Imaginary part of the trilinear F on lane plane Fl at the cell of t, with the sample position
+// moving by gl (voxel units): grad . gl + sum_c w_c Im F_c.
+__device__ __forceinline__ float tri_lane(const Params& p, const float* __restrict__ Fl, const Tri& t, float glx,
+                                          float gly, float glz) {
+  float v = t.g[0] * glx + t.g[1] * gly + t.g[2] * glz;
+  if (Fl) {
+    const size_t sx = 1, sy = (size_t)p.nx, sz = (size_t)p.nx * p.ny;
+    const size_t b = t.base;
+    const float x00 = Fl[b] + t.fx * (Fl[b + sx] - Fl[b]);
+    const float x10 = Fl[b + sy] + t.fx * (Fl[b + sx + sy] - Fl[b + sy]);
+    const float x01 = Fl[b + sz] + t.fx * (Fl[b + sx + sz] - Fl[b + sz]);
+    const float x11 = Fl[b + sy + sz] + t.fx * (Fl[b + sx + sy + sz] - Fl[b + sy + sz]);
+    const float y0 = x00 + t.fy * (x10 - x00), y1 = x01 + t.fy * (x11 - x01);
+    v += y0 + t.fz * (y1 - y0);
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_raycast(Params p, const float* __restrict__ F, const float* __restrict__ Wt,
+                                                 const double* __restrict__ pose, float* __restrict__ out_depth,
+                                                 float* __restrict__ vmap, float* __restrict__ nmap, int ignore_imag,
+                                                 double* __restrict__ pose_prev, unsigned long long* __restrict__ hits) {
+  __shared__ float sT[kMaxLanes][12];
+  for (int i = threadIdx.x + blockDim.x * threadIdx.y; i < p.L * 12; i += blockDim.x * blockDim.y) {
+    sT[i / 12][i % 12] = (float)pose[i];
+    if (pose_prev && blockIdx.x == 0 && blockIdx.y == 0) pose_prev[i] = pose[i];
+  }
+  __syncthreads();
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= p.W || v >= p.H) return;
+  const size_t hw = (size_t)p.W * p.H;
+  const size_t pix = (size_t)v * p.W + u;
+  const size_t n = vox_count(p);
+
+  const float* T = sT[0];
+  const float rx = (u - p.cx) / p.fx, ry = (v - p.cy) / p.fy;
+  const float dirx = T[0] * rx + T[1] * ry + T[2];
+  const float diry = T[4] * rx + T[5] * ry + T[6];
+  const float dirz = T[8] * rx + T[9] * ry + T[10];
+  const float inv_vox = 1.f / p.voxel;
+  // continuous voxel coordinate g(alpha) = g0 + alpha * gd
+  const float g0x = (T[3] - p.ox) * inv_vox - 0.5f, g0y = (T[7] - p.oy) * inv_vox - 0.5f,
+              g0z = (T[11] - p.oz) * inv_vox - 0.5f;
+  const float gdx = dirx * inv_vox, gdy = diry * inv_vox, gdz = dirz * inv_vox;
+
+  // alpha interval where 0 <= g < n - 1 on every axis (slab test), widened by one sample
+  float lo = p.m0 * p.ray_step, hi = p.m1 * p.ray_step;
+  {
+    const float g0[3] = {g0x, g0y, g0z}, gd[3] = {gdx, gdy, gdz};
+    const int nn[3] = {p.nx, p.ny, p.nz};
+    for (int a = 0; a < 3; ++a) {
+      if (gd[a] != 0.f) {
+        float t1 = (0.f - g0[a]) / gd[a], t2 = ((float)(nn[a] - 1) - g0[a]) / gd[a];
+        lo = fmaxf(lo, fminf(t1, t2));
+        hi = fminf(hi, fmaxf(t1, t2));
+      } else if (!(g0[a] >= 0.f && g0[a] < (float)(nn[a] - 1))) {
+        hi = -1.f;
+      }
+    }
+  }
+  int m_lo = max(p.m0, (int)floorf(lo / p.ray_step) - 1);
+  int m_hi = min(p.m1, (int)ceilf(hi / p.ray_step) + 1);
+
+  int m_hit = -1;
+  bool prev_valid = false, prev_pos = false;
+  for (int m = m_lo; m <= m_hi; ++m) {
+    const float al = m * p.ray_step;
+    Tri t;
+    const bool ok = tri_real(p, F, Wt, g0x + al * gdx, g0y + al * gdy, g0z + al * gdz, t, false);
+    if (prev_valid && ok) {
+      const bool pos = t.val > 0.f;
+      if (prev_pos && !pos) {
+        m_hit = m - 1;
+        break;
+      }
+      if (!prev_pos && pos) break;
+    }
+    prev_valid = ok;
+    prev_pos = ok && t.val > 0.f;
+  }
+
+  bool good = false;
+  float alpha0 = 0.f, vx = 0.f, vy = 0.f, vz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, nrm = 1.f;
+  Tri tm, tn, ts[6];
+  float am = 0.f, an = 0.f, den = 1.f;
+  if (m_hit >= 0) {
+    am = m_hit * p.ray_step;
+    an = (m_hit + 1) * p.ray_step;
+    bool ok = tri_real(p, F, Wt, g0x + am * gdx, g0y + am * gdy, g0z + am * gdz, tm, true);
+    ok &= tri_real(p, F, Wt, g0x + an * gdx, g0y + an * gdy, g0z + an * gdz, tn, true);
+    if (ok) {
+      den = tn.val - tm.val;
+      alpha0 = am - p.ray_step * tm.val / den;
+      vx = T[3] + alpha0 * dirx;
+      vy = T[7] + alpha0 * diry;
+      vz = T[11] + alpha0 * dirz;
+      const float gx = (vx - p.ox) * inv_vox - 0.5f, gy = (vy - p.oy) * inv_vox - 0.5f,
+                  gz = (vz - p.oz) * inv_vox - 0.5f;
+      ok &= tri_real(p, F, Wt, gx + 1.f, gy, gz, ts[0], true);
+      ok &= tri_real(p, F, Wt, gx - 1.f, gy, gz, ts[1], true);
+      ok &= tri_real(p, F, Wt, gx, gy + 1.f, gz, ts[2], true);
+      ok &= tri_real(p, F, Wt, gx, gy - 1.f, gz, ts[3], true);
+      ok &= tri_real(p, F, Wt, gx, gy, gz + 1.f, ts[4], true);
+      ok &= tri_real(p, F, Wt, gx, gy, gz - 1.f, ts[5], true);
+      if (ok) {
+        const float s = 0.5f * inv_vox;
+        nx = (ts[0].val - ts[1].val) * s;
+        ny = (ts[2].val - ts[3].val) * s;
+        nz = (ts[4].val - ts[5].val) * s;
+        const float n2 = nx * nx + ny * ny + nz * nz;
+        if (n2 > 0.f) {
+          nrm = sqrtf(n2);
+          good = true;
+        }
+      }
+    }
+  }
+  if (out_depth) out_depth[pix] = good ? alpha0 : 0.f;
+  if (hits) {
+    const unsigned m = __ballot_sync(__activemask(), good);
+    if (good && (threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(hits, (unsigned long long)__popc(m));
+  }
+  if (!vmap && !nmap) return;
+  if (!good) {
+    for (int l = 0; l < p.L; ++l)
+      for (int c = 0; c < 3; ++c) {
+        if (vmap) vmap[(size_t)(3 * l + c) * hw + pix] = 0.f;
+        if (nmap) nmap[(size_t)(3 * l + c) * hw + pix] = 0.f;
+      }
+    return;
+  }
+  const float Nx = nx / nrm, Ny = ny / nrm, Nz = nz / nrm;
+  if (vmap) {
+    vmap[pix] = vx;
+    vmap[hw + pix] = vy;
+    vmap[2 * hw + pix] = vz;
+  }
+  if (nmap) {
+    nmap[pix] = Nx;
+    nmap[hw + pix] = Ny;
+    nmap[2 * hw + pix] = Nz;
+  }
+  const float s = 0.5f * inv_vox;
+  for (int l = 1; l < p.L; ++l) {
+    const float* Tl = sT[l];
+    const float* Fl = ignore_imag ? nullptr : F + (size_t)l * n;
+    const float dlx = Tl[0] * rx + Tl[1] * ry + Tl[2];
+    const float dly = Tl[4] * rx + Tl[5] * ry + Tl[6];
+    const float dlz = Tl[8] * rx + Tl[9] * ry + Tl[10];
+    // sample positions move by alpha * dir_l + t_l
+    const float Fm_l = tri_lane(p, Fl, tm, (am * dlx + Tl[3]) * inv_vox, (am * dly + Tl[7]) * inv_vox,
+                                (am * dlz + Tl[11]) * inv_vox);
+    const float Fn_l = tri_lane(p, Fl, tn, (an * dlx + Tl[3]) * inv_vox, (an * dly + Tl[7]) * inv_vox,
+                                (an * dlz + Tl[11]) * inv_vox);
+    const float a0_l = -p.ray_step * (Fm_l * tn.val - tm.val * Fn_l) / (den * den);
+    const float vlx = a0_l * dirx + alpha0 * dlx + Tl[3];
+    const float vly = a0_l * diry + alpha0 * dly + Tl[7];
+    const float vlz = a0_l * dirz + alpha0 * dlz + Tl[11];
+    const float glx = vlx * inv_vox, gly = vly * inv_vox, glz = vlz * inv_vox;
+    const float gxl = (tri_lane(p, Fl, ts[0], glx, gly, glz) - tri_lane(p, Fl, ts[1], glx, gly, glz)) * s;
+    const float gyl = (tri_lane(p, Fl, ts[2], glx, gly, glz) - tri_lane(p, Fl, ts[3], glx, gly, glz)) * s;
+    const float gzl = (tri_lane(p, Fl, ts[4], glx, gly, glz) - tri_lane(p, Fl, ts[5], glx, gly, glz)) * s;
+    const float dot = Nx * gxl + Ny * gyl + Nz * gzl;
+    if (vmap) {
+      vmap[(size_t)(3 * l) * hw + pix] = vlx;
+      vmap[(size_t)(3 * l + 1) * hw + pix] = vly;
+      vmap[(size_t)(3 * l + 2) * hw + pix] = vlz;
+    }
+    if (nmap) {
+      nmap[(size_t)(3 * l) * hw + pix] = (gxl - Nx * dot) / nrm;
+      nmap[(size_t)(3 * l + 1) * hw + pix] = (gyl - Ny * dot) / nrm;
+      nmap[(size_t)(3 * l + 2) * hw + pix] = (gzl - Nz * dot) / nrm;
+    }
+  }
+}
+
+cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose, float* depth, float* vmap,
+                           float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s) {
+  dim3 blk(32, 8), grd((p.W + 31) / 32, (p.H + 7) / 8);
+  k_raycast<<<grd, blk, 0, s>>>(p, b.F, b.Wt, pose, depth, vmap, nmap, ignore_imag_volume ? 1 : 0,
+                                set_prev ? b.pose_prev : nullptr, set_prev ? b.stats + 1 : nullptr);
+  return cudaGetLastError();
+}
+
+}  // namespace xslam

@@ -54,6 +54,7 @@ class Workload:
     icp_iters: tuple = (10, 5, 4)  # finest level first
     depth_min: float = 0.2
     depth_max: float = 4.0
+    bilateral: bool = False  # the depth noise exceeds the pixel footprint: filter the raw depth
 
 
 # ----------------------------------------------------------------------------------------------
@@ -301,7 +302,7 @@ def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 
         poses.append(T)
     return Workload(f"room{dims}_{width}x{height}", intr, (dims, dims, dims), voxel, 4 * voxel,
                     (0.0, 0.0, 0.0), np.array(poses), np.array(depth), scene, seed,
-                    depth_min=0.3, depth_max=4.0)
+                    depth_min=0.3, depth_max=4.0, bilateral=True)
 
 
 def tiny(seed: int = 3, frames: int = 3, n: int = 24, width: int = 40, height: int = 30, noise=False,

@@ -1,0 +1,281 @@
+"""ctypes binding of libxslam (include/xslam.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels behind the C ABI; this module converts torch tensors and
+numpy arrays to pointers, checks shapes, and turns status codes into exceptions. It fails loudly
+if the shared library has not been built: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+POSE0, POSE, TRUNC, DEPTH = 0, 1, 2, 3
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTRACK, ESTATE = range(7)
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTRACK", 6: "ESTATE"}
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libxslam.so")
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_float_p = ctypes.POINTER(ctypes.c_float)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+
+
+class Seed(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("index", ctypes.c_int), ("h", ctypes.c_double)]
+
+
+class Intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int), ("height", ctypes.c_int)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("icp_levels", ctypes.c_int), ("icp_iters", ctypes.c_int * 4),
+                ("dist_gate_m", ctypes.c_float), ("normal_gate_deg", ctypes.c_float),
+                ("disc_gate_m", ctypes.c_float), ("min_corr_frac", ctypes.c_float),
+                ("ray_step_vox", ctypes.c_float), ("depth_min_m", ctypes.c_float),
+                ("depth_max_m", ctypes.c_float), ("pyr_range_m", ctypes.c_float),
+                ("bilateral", ctypes.c_int), ("w_max", ctypes.c_float)]
+
+
+class XSlamError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"xslam {_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+# (name, restype, argtypes): every symbol declared in include/xslam.h
+SYMBOLS = [
+    ("xslam_default_config", None, [ctypes.POINTER(Config)]),
+    ("xslam_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_float, ctypes.c_float, _c_float_p, ctypes.POINTER(Intrinsics),
+                                    ctypes.POINTER(Config), ctypes.c_int, ctypes.c_void_p]),
+    ("xslam_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("xslam_reset", ctypes.c_int, [ctypes.c_void_p]),
+    ("xslam_set_pose", ctypes.c_int, [ctypes.c_void_p, _c_double_p]),
+    ("xslam_frame", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Seed), ctypes.c_int,
+                                   _c_double_p, _c_double_p, _c_double_p]),
+    ("xslam_sync", ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
+    ("xslam_raycast", ctypes.c_int, [ctypes.c_void_p, _c_double_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("xslam_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_double_p, ctypes.c_int, _c_double_p,
+                                  _c_double_p, _c_double_p]),
+    ("xslam_read_tsdf", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("xslam_set_lanes", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Seed), ctypes.c_int]),
+    ("xslam_set_pose_lanes", ctypes.c_int, [ctypes.c_void_p, _c_double_p]),
+    ("xslam_get_pose_lanes", ctypes.c_int, [ctypes.c_void_p, _c_double_p]),
+    ("xslam_write_tsdf", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("xslam_measure", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("xslam_integrate", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("xslam_set_model", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       _c_double_p]),
+    ("xslam_icp_system", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_double_p, _c_double_p, _c_int_p]),
+    ("xslam_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("xslam_profile_read", ctypes.c_int, [ctypes.c_void_p, _c_double_p, ctypes.POINTER(ctypes.c_longlong),
+                                          _c_double_p]),
+    ("xslam_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+]
+STAGES = ("prepare", "icp", "integrate", "raycast", "other")
+
+
+def load(path: str = LIB_PATH):
+    """Load libxslam.so and declare its C signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run `python -m paper_2405_02187_gb300._build` "
+                           "(or __graft_entry__.build()) on a machine with nvcc")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SYMBOLS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_config() -> Config:
+    c = Config()
+    load().xslam_default_config(ctypes.byref(c))
+    return c
+
+
+def _dptr(a):
+    """Pointer to a float64 numpy array (contiguous)."""
+    return a.ctypes.data_as(_c_double_p)
+
+
+def _dev(t, dtype_name="float32"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous() or str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"expected a contiguous {dtype_name} CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _seeds(seeds):
+    arr = (Seed * max(1, len(seeds)))()
+    for i, s in enumerate(seeds):
+        kind, index, h = s
+        arr[i] = Seed(int(kind), int(index), float(h))
+    return arr
+
+
+class XSlam:
+    """One X-KinectFusion volume and its frame state (a handle of libxslam)."""
+
+    def __init__(self, dims, voxel, trunc, origin, intr, cfg: Config | None = None, max_lanes=6, stream=None):
+        self.lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.intr = intr
+        self.W, self.H = int(intr.width), int(intr.height)
+        K = Intrinsics(float(intr.fx), float(intr.fy), float(intr.cx), float(intr.cy), self.W, self.H)
+        org = (ctypes.c_float * 3)(*[float(o) for o in origin])
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = ctypes.c_void_p()
+        st = self.lib.xslam_create(ctypes.byref(h), *self.dims, float(voxel), float(trunc), org, ctypes.byref(K),
+                                   ctypes.byref(cfg) if cfg is not None else None, int(max_lanes),
+                                   ctypes.c_void_p(stream))
+        if st != OK:
+            raise XSlamError(st, self.lib.xslam_last_error(None).decode())
+        self.h = h
+        self.K = 0
+        self.max_lanes = max_lanes
+
+    # -- helpers ---------------------------------------------------------------------------
+    def _check(self, st, allow=(OK,)):
+        if st not in allow:
+            raise XSlamError(st, self.lib.xslam_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.xslam_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_vox(self):
+        return self.dims[0] * self.dims[1] * self.dims[2]
+
+    # -- sequence API ----------------------------------------------------------------------
+    def reset(self):
+        self._check(self.lib.xslam_reset(self.h))
+        self.K = 0
+
+    def set_pose(self, T):
+        T = np.ascontiguousarray(T, np.float64).reshape(12)
+        self._check(self.lib.xslam_set_pose(self.h, _dptr(T)))
+
+    def frame(self, depth, seeds=(), outputs=True):
+        """Run one frame. depth: CUDA float32 tensor (H, W) or host numpy float32 array.
+        Returns (pose (3,4), dpose (K,3,4), dtwist (K,6), status) or status if outputs is False."""
+        K = len(seeds)
+        sd = _seeds(seeds)
+        if isinstance(depth, np.ndarray):
+            depth = np.ascontiguousarray(depth, np.float32)
+            ptr, on_dev = ctypes.c_void_p(depth.ctypes.data), 0
+        elif not depth.is_cuda:  # a (pinned) host tensor
+            assert depth.is_contiguous() and str(depth.dtype) == "torch.float32"
+            ptr, on_dev = ctypes.c_void_p(depth.data_ptr()), 0
+        else:
+            ptr, on_dev = _dev(depth), 1
+        if not outputs:
+            st = self.lib.xslam_frame(self.h, ptr, on_dev, sd, K, None, None, None)
+            self._check(st, (OK, ENOTRACK))
+            self.K = K
+            return st
+        pose = np.zeros(12)
+        dpose = np.zeros(max(1, 12 * K))
+        dtw = np.zeros(max(1, 6 * K))
+        st = self.lib.xslam_frame(self.h, ptr, on_dev, sd, K, _dptr(pose), _dptr(dpose), _dptr(dtw))
+        self._check(st, (OK, ENOTRACK))
+        self.K = K
+        return pose.reshape(3, 4), dpose[:12 * K].reshape(K, 3, 4), dtw[:6 * K].reshape(K, 6), st
+
+    def sync(self):
+        n = ctypes.c_int(0)
+        st = self._check(self.lib.xslam_sync(self.h, ctypes.byref(n)), (OK, ENOTRACK))
+        return st, n.value
+
+    def raycast(self, T=None, depth=None, vmap=None, nmap=None):
+        Tp = None
+        if T is not None:
+            T = np.ascontiguousarray(T, np.float64).reshape(-1)
+            Tp = _dptr(T)
+        self._check(self.lib.xslam_raycast(self.h, Tp, _dev(depth), _dev(vmap), _dev(nmap)))
+
+    def grad(self, query_depth, T_q, order=1):
+        T_q = np.ascontiguousarray(T_q, np.float64).reshape(12)
+        loss = ctypes.c_double(0)
+        g = np.zeros(6)
+        H = np.zeros(21)
+        self._check(self.lib.xslam_grad(self.h, _dev(query_depth), _dptr(T_q), int(order), ctypes.byref(loss),
+                                        _dptr(g), _dptr(H)))
+        return loss.value, g
+
+    def read_tsdf(self, lane, out):
+        self._check(self.lib.xslam_read_tsdf(self.h, int(lane), _dev(out)))
+        return out
+
+    def profile(self, enable=True):
+        self._check(self.lib.xslam_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        """dict stage -> (ms, launches), plus counters (fused voxels, ray-cast surface pixels, frames)."""
+        ms = np.zeros(len(STAGES))
+        la = (ctypes.c_longlong * len(STAGES))()
+        c = np.zeros(3)
+        self._check(self.lib.xslam_profile_read(self.h, _dptr(ms), la, _dptr(c)))
+        return {s: (ms[i], la[i]) for i, s in enumerate(STAGES)}, dict(fused=c[0], hits=c[1], frames=c[2])
+
+    # -- stage API -------------------------------------------------------------------------
+    def set_lanes(self, seeds):
+        sd = _seeds(seeds)
+        self._check(self.lib.xslam_set_lanes(self.h, sd, len(seeds)))
+        self.K = len(seeds)
+
+    def set_pose_lanes(self, T):
+        T = np.ascontiguousarray(T, np.float64).reshape(-1)
+        assert T.size == 12 * (1 + self.K)
+        self._check(self.lib.xslam_set_pose_lanes(self.h, _dptr(T)))
+
+    def get_pose_lanes(self):
+        T = np.zeros(12 * (1 + self.K))
+        self._check(self.lib.xslam_get_pose_lanes(self.h, _dptr(T)))
+        return T.reshape(1 + self.K, 3, 4)
+
+    def write_tsdf(self, lane, t):
+        self._check(self.lib.xslam_write_tsdf(self.h, int(lane), _dev(t)))
+
+    def measure(self, depth, level=0, out=None):
+        self._check(self.lib.xslam_measure(self.h, _dev(depth), int(level), _dev(out)))
+        return out
+
+    def integrate(self, depth):
+        self._check(self.lib.xslam_integrate(self.h, _dev(depth)))
+
+    def set_model(self, depth, vmap, nmap, T_prev):
+        T_prev = np.ascontiguousarray(T_prev, np.float64).reshape(-1)
+        self._check(self.lib.xslam_set_model(self.h, _dev(depth), _dev(vmap), _dev(nmap), _dptr(T_prev)))
+
+    def icp_system(self, level, Tj):
+        Tj = np.ascontiguousarray(Tj, np.float64).reshape(-1)
+        out = np.zeros(27 * (1 + self.K))
+        n = ctypes.c_int(0)
+        self._check(self.lib.xslam_icp_system(self.h, int(level), _dptr(Tj), _dptr(out), ctypes.byref(n)))
+        return out.reshape(1 + self.K, 27), n.value

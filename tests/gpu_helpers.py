@@ -1,0 +1,61 @@
+"""Shared helpers of the GPU parity tests: conversions between the oracle's one-complex-run-per-seed
+results and the CUDA path's lane layout (lane 0 real, lane j the raw imaginary part of seed j)."""
+import numpy as np
+
+from oracle import pipeline as P
+from oracle import se3
+
+H_GPU = 1e-10  # imaginary step of the FP32 lanes
+H_ORA = 1e-20  # imaginary step of the complex128 oracle
+
+
+def oracle_cfg(wl):
+    return P.Config(icp_iters=tuple(wl.icp_iters), depth_min=wl.depth_min, depth_max=wl.depth_max,
+                    bilateral=wl.bilateral)
+
+
+def xslam_cfg(wl):
+    from paper_2405_02187_gb300 import xslam
+    c = xslam.default_config()
+    c.icp_levels = len(wl.icp_iters)
+    for i, n in enumerate(wl.icp_iters):
+        c.icp_iters[i] = n
+    c.depth_min_m = wl.depth_min
+    c.depth_max_m = wl.depth_max
+    c.bilateral = int(wl.bilateral)
+    return c
+
+
+def make_handle(wl, max_lanes=6):
+    from paper_2405_02187_gb300 import xslam
+    return xslam.XSlam(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, xslam_cfg(wl), max_lanes=max_lanes)
+
+
+def gpu_seeds(seeds, h=H_GPU):
+    return [(s.kind, s.index, h) for s in seeds]
+
+
+def pose_lanes(T_real, complex_poses, h_ora=H_ORA, h_gpu=H_GPU):
+    """(1 + K, 3, 4) GPU pose lanes from the real pose and one complex pose per seed."""
+    out = [np.asarray(T_real, np.float64)]
+    for Tc in complex_poses:
+        out.append(np.imag(Tc) / h_ora * h_gpu)
+    return np.stack(out)
+
+
+def promote_seeds(T, seeds, h=H_ORA):
+    """Complex initial pose of each seed's oracle run (POSE0 seeds perturb T, others keep it)."""
+    out = []
+    for s in seeds:
+        if s.kind == P.POSE0:
+            out.append(se3.promote_pose(T, s.index, h))
+        else:
+            out.append(np.asarray(T, np.complex128))
+    return out
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
