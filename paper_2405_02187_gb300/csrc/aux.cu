@@ -19,10 +19,10 @@ __global__ void k_seed_pose(double* pose, int L, const int* kinds, const int* in
     // [e] T0: rows of the generator applied to every column of [R | t]
     for (int q = 0; q < 4; ++q) {
       const double c0 = T0[q], c1 = T0[4 + q], c2 = T0[8 + q];
-      double r0 = 0, r1 = 0, r2 = 0;  // [w] c with w = unit e
-      if (e == 0) { r1 = c2; r2 = -c1; }
-      if (e == 1) { r0 = -c2; r2 = c0; }
-      if (e == 2) { r0 = c1; r1 = -c0; }
+      double r0 = 0, r1 = 0, r2 = 0;  // [w] c = w x c with w the unit vector e
+      if (e == 0) { r1 = -c2; r2 = c1; }
+      if (e == 1) { r0 = c2; r2 = -c0; }
+      if (e == 2) { r0 = -c1; r1 = c0; }
       Tl[q] = h * r0;
       Tl[4 + q] = h * r1;
       Tl[8 + q] = h * r2;

@@ -12,10 +12,9 @@
 namespace xslam {
 
 __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restrict__ D, const float (*sT)[12],
-                                           float* __restrict__ F, float* __restrict__ Wt, size_t v, size_t n) {
-  const int i = (int)(v % p.nx);
-  const int j = (int)((v / p.nx) % p.ny);
-  const int k = (int)(v / ((size_t)p.nx * p.ny));
+                                           float* __restrict__ F, float* __restrict__ Wt, int i, int j, int k,
+                                           size_t n) {
+  const size_t v = (size_t)i + (size_t)p.nx * ((size_t)j + (size_t)p.ny * k);
 
   const float* T = sT[0];
   const float dx = p.ox + (i + 0.5f) * p.voxel - T[3];
@@ -68,23 +67,56 @@ __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restr
   return true;
 }
 
-__global__ void __launch_bounds__(256) k_integrate(Params p, const float* __restrict__ D,
-                                                   const double* __restrict__ pose, float* __restrict__ F,
-                                                   float* __restrict__ Wt, unsigned long long* __restrict__ stats) {
+// Block of kBX x kBY x 1 voxels (x fastest: coalesced rows). A block whose box lies entirely behind the
+// camera or entirely to one side of the image is skipped as a whole: the projection of a convex set in
+// front of the camera is the convex hull of the projections of its corners, so no voxel of such a
+// block can pass the per-voxel image test.
+constexpr int kBX = 64, kBY = 4;
+
+__global__ void __launch_bounds__(kBX * kBY) k_integrate(Params p, const float* __restrict__ D,
+                                                        const double* __restrict__ pose, float* __restrict__ F,
+                                                        float* __restrict__ Wt, unsigned long long* __restrict__ stats) {
   __shared__ float sT[kMaxLanes][12];
-  for (int i = threadIdx.x; i < p.L * 12; i += blockDim.x) sT[i / 12][i % 12] = (float)pose[i];
+  __shared__ int s_out[8];
+  const int tid = threadIdx.x + kBX * threadIdx.y;
+  for (int i = tid; i < p.L * 12; i += kBX * kBY) sT[i / 12][i % 12] = (float)pose[i];
   __syncthreads();
+  const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kBY, k = blockIdx.z;
+  if (tid < 8) {
+    // corner c of the block's box of voxel centres: code bit 0 -> x, bit 1 -> y, bit 2 -> z half-voxel pad
+    const float* T = sT[0];
+    const float cx = p.ox + ((tid & 1) ? fminf(i0 + kBX, p.nx) : i0) * p.voxel;
+    const float cy = p.oy + ((tid & 2) ? fminf(j0 + kBY, p.ny) : j0) * p.voxel;
+    const float cz = p.oz + ((tid & 4) ? k + 1 : k) * p.voxel;
+    const float dx = cx - T[3], dy = cy - T[7], dz = cz - T[11];
+    const float px = T[0] * dx + T[4] * dy + T[8] * dz;
+    const float py = T[1] * dx + T[5] * dy + T[9] * dz;
+    const float pz = T[2] * dx + T[6] * dy + T[10] * dz;
+    int code = 0;  // bit 0: behind, 1: left, 2: right, 3: above, 4: below
+    if (!(pz > 0.f)) {
+      code = 1;  // a corner behind the camera only agrees with "behind"
+    } else {
+      const float x = p.fx * px / pz + p.cx, y = p.fy * py / pz + p.cy;
+      code = (x < 0.f ? 2 : 0) | (x >= (float)(p.W - 1) ? 4 : 0) | (y < 0.f ? 8 : 0) | (y >= (float)(p.H - 1) ? 16 : 0);
+    }
+    s_out[tid] = code;
+  }
+  __syncthreads();
+  {
+    int all = 31;
+    for (int c = 0; c < 8; ++c) all &= s_out[c];
+    if (all) return;  // every corner behind, or every corner beyond the same image edge
+  }
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
   const size_t n = vox_count(p);
-  const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool upd = v < n && fuse_voxel(p, D, sT, F, Wt, v, n);
+  const bool upd = i < p.nx && j < p.ny && fuse_voxel(p, D, sT, F, Wt, i, j, k, n);
   const int c = __syncthreads_count(upd);
-  if (threadIdx.x == 0 && c) atomicAdd(stats, (unsigned long long)c);
+  if (tid == 0 && c) atomicAdd(stats, (unsigned long long)c);
 }
 
 cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s) {
-  const size_t n = vox_count(p);
-  const unsigned grid = (unsigned)((n + 255) / 256);
-  k_integrate<<<grid, 256, 0, s>>>(p, b.pyr[0], b.pose, b.F, b.Wt, b.stats);
+  dim3 blk(kBX, kBY, 1), grd((p.nx + kBX - 1) / kBX, (p.ny + kBY - 1) / kBY, p.nz);
+  k_integrate<<<grd, blk, 0, s>>>(p, b.pyr[0], b.pose, b.F, b.Wt, b.stats);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,51 @@ struct Lvl {
   float fx, fy, cx, cy;
 };
 
+// index of (r, c), r <= c, in the row-major packed upper triangle of a 6x6 matrix
+__host__ __device__ constexpr int up6(int r, int c) { return r * 6 - r * (r - 1) / 2 + (c - r); }
+
+// Cholesky A = L L^T of the real 6x6 normal matrix (packed upper storage, FP64); L row-major 6x6
+// in shared memory. Returns false if A is not positive definite.
+__device__ bool cholesky6(const double* __restrict__ A, double* __restrict__ Lc) {
+  for (int j = 0; j < 6; ++j) {
+    double d = A[up6(j, j)];
+    for (int k = 0; k < j; ++k) d -= Lc[6 * j + k] * Lc[6 * j + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = sqrt(d), inv = 1.0 / ljj;
+    Lc[6 * j + j] = ljj;
+    for (int i = j + 1; i < 6; ++i) {
+      double s = A[up6(j, i)];
+      for (int k = 0; k < j; ++k) s -= Lc[6 * i + k] * Lc[6 * j + k];
+      Lc[6 * i + j] = s * inv;
+    }
+  }
+  return true;
+}
+
+// x = A^-1 (-g - Al x0) with A = L L^T; Al (packed upper) and x0 may be null (real lane).
+__device__ void solve6(const double* __restrict__ Lc, const double* __restrict__ g, const double* __restrict__ Al,
+                       const double* __restrict__ x0, double* __restrict__ x) {
+  double y[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double s = -g[i];
+    if (Al) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s -= Al[i <= k ? up6(i, k) : up6(k, i)] * x0[k];
+    }
+#pragma unroll
+    for (int k = 0; k < i; ++k) s -= Lc[6 * i + k] * y[k];
+    y[i] = s / Lc[6 * i + i];
+  }
+#pragma unroll
+  for (int i = 5; i >= 0; --i) {
+    double s = y[i];
+#pragma unroll
+    for (int k = i + 1; k < 6; ++k) s -= Lc[6 * k + i] * x[k];
+    x[i] = s / Lc[6 * i + i];
+  }
+}
+
 __device__ __forceinline__ void accum(float* acc, const float* Ja, const float ra, const float* Jb, const float rb) {
   // acc += Ja Jb^T + Jb Ja^T (upper triangle) and Ja rb + Jb ra; called with (J, r, J, r) * 0.5 for
   // the real lane and with (J, r, J_l, r_l) for a tangent lane.
@@ -200,10 +245,12 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
     s_cnt[warp] = cnt;
   }
   __syncthreads();
+  // partials are stored value-major ([value][block]) so that the last block reads each value's
+  // per-block sums with coalesced warp loads
   for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) {
     float s = 0.f;
     for (int r = 0; r < reps; ++r) s += s_red[r * L * kNT + i];
-    b.partial[(size_t)blockIdx.x * L * kNT + i] = s;
+    b.partial[(size_t)i * gridDim.x + blockIdx.x] = s;
   }
   if (threadIdx.x == 0) {
     int c = 0;
@@ -221,22 +268,28 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   __threadfence();
 
   // ---------------- last block: FP64 cross-block sum ----------------
+  // warp w takes values v = w, w + nwarps, ...; lane i adds blocks i, i + 32, ... in FP32 (at most a
+  // handful each), then the 32 lane sums are added in FP64 by a shuffle tree.
   const int nblk = gridDim.x;
-  for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) {
-    double s = 0.0;
-    for (int g = 0; g < nblk; g += kGroup) {
-      float f = 0.f;
-      const int ge = min(nblk, g + kGroup);
-      for (int k = g; k < ge; ++k) f += __ldcg(&b.partial[(size_t)k * L * kNT + i]);
-      s += (double)f;
-    }
-    sA[i] = s;
+  const int nwarps = blockDim.x >> 5;
+  for (int v = warp; v < L * kNT; v += nwarps) {
+    const float* src = b.partial + (size_t)v * nblk;
+    float f = 0.f;
+    for (int k = lid; k < nblk; k += 32) f += __ldcg(src + k);
+    double d = (double)f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lid == 0) sA[v] = d;
   }
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
     int c = 0;
-    for (int k = 0; k < nblk; ++k) c += __ldcg(&b.partial_n[k]);
-    s_ncorr = c;
-    *b.ticket = 0u;  // ready for the next launch
+    for (int k = lid; k < nblk; k += 32) c += __ldcg(&b.partial_n[k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lid == 0) {
+      s_ncorr = c;
+      *b.ticket = 0u;  // ready for the next launch
+    }
   }
   __syncthreads();
 
@@ -249,98 +302,38 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   if (threadIdx.x == 0) {
     int fail = s_skip;
     if (!fail && (float)s_ncorr < p.min_corr_frac * (float)(lv.W * lv.H)) fail = 1;
-    if (!fail) {
-      // Cholesky of the real 6x6 A (upper-triangle storage, row-major)
-      double A[36];
-      int q = 0;
-      for (int r = 0; r < 6; ++r)
-        for (int c = r; c < 6; ++c) {
-          A[6 * r + c] = sA[q];
-          A[6 * c + r] = sA[q];
-          ++q;
-        }
-      for (int j = 0; j < 6 && !fail; ++j) {
-        double d = A[6 * j + j];
-        for (int k = 0; k < j; ++k) d -= sLch[6 * j + k] * sLch[6 * j + k];
-        if (!(d > 0.0)) {
-          fail = 1;
-          break;
-        }
-        const double ljj = sqrt(d);
-        sLch[6 * j + j] = ljj;
-        for (int i = j + 1; i < 6; ++i) {
-          double s = A[6 * i + j];
-          for (int k = 0; k < j; ++k) s -= sLch[6 * i + k] * sLch[6 * j + k];
-          sLch[6 * i + j] = s / ljj;
-        }
-      }
-      if (!fail) {
-        double y[6], x[6];
-        for (int i = 0; i < 6; ++i) {
-          double s = -sA[21 + i];
-          for (int k = 0; k < i; ++k) s -= sLch[6 * i + k] * y[k];
-          y[i] = s / sLch[6 * i + i];
-        }
-        for (int i = 5; i >= 0; --i) {
-          double s = y[i];
-          for (int k = i + 1; k < 6; ++k) s -= sLch[6 * k + i] * x[k];
-          x[i] = s / sLch[6 * i + i];
-        }
-        for (int i = 0; i < 6; ++i) sx[0][i] = x[i];
-      }
-    }
+    if (!fail) fail = !cholesky6(sA, sLch);
+    if (!fail) solve6(sLch, sA + 21, nullptr, nullptr, sx[0]);
     s_fail = fail;
   }
   __syncthreads();
   if (update && !s_fail && threadIdx.x > 0 && threadIdx.x < L) {
-    // x_l = A^-1 (-g_l - A_l x_0)
-    const int l = threadIdx.x;
-    const double* Al = sA + l * kNT;
-    double Af[36];
-    int q = 0;
-    for (int r = 0; r < 6; ++r)
-      for (int c = r; c < 6; ++c) {
-        Af[6 * r + c] = Al[q];
-        Af[6 * c + r] = Al[q];
-        ++q;
-      }
-    double rhs[6], y[6], x[6];
-    for (int i = 0; i < 6; ++i) {
-      double s = -Al[21 + i];
-      for (int k = 0; k < 6; ++k) s -= Af[6 * i + k] * sx[0][k];
-      rhs[i] = s;
-    }
-    for (int i = 0; i < 6; ++i) {
-      double s = rhs[i];
-      for (int k = 0; k < i; ++k) s -= sLch[6 * i + k] * y[k];
-      y[i] = s / sLch[6 * i + i];
-    }
-    for (int i = 5; i >= 0; --i) {
-      double s = y[i];
-      for (int k = i + 1; k < 6; ++k) s -= sLch[6 * k + i] * x[k];
-      x[i] = s / sLch[6 * i + i];
-    }
-    for (int i = 0; i < 6; ++i) sx[l][i] = x[i];
+    const int l = threadIdx.x;  // x_l = A^-1 (-g_l - A_l x_0)
+    solve6(sLch, sA + l * kNT + 21, sA + l * kNT, sx[0], sx[l]);
   }
   __syncthreads();
   // pose update T <- exp(x) T on every lane (thread l handles lane l)
-  double Tn[12];
   const int l = threadIdx.x;
+  double Tn[12];
   if (update && !s_fail && l < L) {
     double E[12], E1[12], T0[12], Tl[12];
+#pragma unroll
     for (int i = 0; i < 12; ++i) T0[i] = b.pose[i];
     if (l == 0) {
       se3_exp_tangent(sx[0], nullptr, E, nullptr);
       compose(E, T0, Tn);
     } else {
+#pragma unroll
       for (int i = 0; i < 12; ++i) Tl[i] = b.pose[12 * l + i];
       se3_exp_tangent(sx[0], sx[l], E, E1);
       compose_tangent(E, E1, T0, Tl, Tn);
     }
   }
   __syncthreads();
-  if (update && !s_fail && l < L)
+  if (update && !s_fail && l < L) {
+#pragma unroll
     for (int i = 0; i < 12; ++i) b.pose[12 * l + i] = Tn[i];
+  }
   if (threadIdx.x == 0 && s_fail && !s_skip) b.status[0] = 1;
   if (flags & kIcpLast) {
     __syncthreads();

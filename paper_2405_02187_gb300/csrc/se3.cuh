@@ -14,28 +14,31 @@ struct Coef {
   double A, B, C, dA, dB, dC;  // values and derivatives with respect to x = th^2
 };
 
+// sum_{n=0}^{9} (-x)^n / (2n+1+s)! and its derivative in x by Horner's rule (s = 0: A, 1: B, 2: C)
+__device__ __forceinline__ void series(double x, int s, double& v, double& dv) {
+  constexpr double inv_fact[22] = {
+      1.0, 1.0, 1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0, 1.0 / 5040.0, 1.0 / 40320.0,
+      1.0 / 362880.0, 1.0 / 3628800.0, 1.0 / 39916800.0, 1.0 / 479001600.0, 1.0 / 6227020800.0,
+      1.0 / 87178291200.0, 1.0 / 1307674368000.0, 1.0 / 20922789888000.0, 1.0 / 355687428096000.0,
+      1.0 / 6402373705728000.0, 1.0 / 121645100408832000.0, 1.0 / 2432902008176640000.0,
+      1.0 / 51090942171709440000.0};
+  constexpr int N = 9;
+  v = ((N & 1) ? -1.0 : 1.0) * inv_fact[2 * N + 1 + s];
+  dv = 0.0;
+#pragma unroll
+  for (int n = N - 1; n >= 0; --n) {
+    dv = dv * x + v;
+    v = v * x + ((n & 1) ? -1.0 : 1.0) * inv_fact[2 * n + 1 + s];
+  }
+}
+
 __device__ __forceinline__ Coef se3_coef(double x) {
   Coef c;
   if (x < 0.25) {
-    // sum_n (-x)^n / (2n + 1 + s)!,  s = 0, 1, 2 for A, B, C (n <= 9: truncation < 1e-25)
-    double a = 0, b = 0, cc = 0, da = 0, db = 0, dc = 0;
-    double fa = 1.0, fb = 0.5, fc = 1.0 / 6.0;  // 1/(2n+1)!, 1/(2n+2)!, 1/(2n+3)! at n = 0
-    double xn = 1.0, xn1 = 0.0;                 // x^n and n x^(n-1) with the sign (-1)^n folded in
-    for (int n = 0; n <= 9; ++n) {
-      const double sgn = (n & 1) ? -1.0 : 1.0;
-      a += sgn * xn * fa;
-      b += sgn * xn * fb;
-      cc += sgn * xn * fc;
-      da += sgn * xn1 * fa;
-      db += sgn * xn1 * fb;
-      dc += sgn * xn1 * fc;
-      xn1 = (n + 1) * xn;
-      xn *= x;
-      fa /= (double)((2 * n + 2) * (2 * n + 3));
-      fb /= (double)((2 * n + 3) * (2 * n + 4));
-      fc /= (double)((2 * n + 4) * (2 * n + 5));
-    }
-    c.A = a; c.B = b; c.C = cc; c.dA = da; c.dB = db; c.dC = dc;
+    // power series (terms up to x^9: truncation below 1e-25 for x < 1/4)
+    series(x, 0, c.A, c.dA);
+    series(x, 1, c.B, c.dB);
+    series(x, 2, c.C, c.dC);
   } else {
     const double th = sqrt(x), s = sin(th), co = cos(th);
     c.A = s / th;
