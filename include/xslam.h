@@ -159,7 +159,8 @@ xslam_status xslam_set_pose_lanes(xslam_t h, const double* T);
 /* Read the current pose lanes into a host (1 + K) x 12 block. */
 xslam_status xslam_get_pose_lanes(xslam_t h, double* T);
 /* Overwrite one plane of the volume from device array in[nx ny nz] (lane as in xslam_read_tsdf; for
- * lane j >= 1 the values are the raw imaginary parts, not divided by h). */
+ * lane j >= 1 the values are the raw imaginary parts, not divided by h). Write lane 0 before lane -1:
+ * writing the weights marks every voxel with W = 0 as unobserved. */
 xslam_status xslam_write_tsdf(xslam_t h, int lane, const float* in);
 /* Surface measurement of device depth[H W] (range gate and Gaussian pyramid, Sec. 4.1); level l of
  * the result is copied to device out[(H >> l)(W >> l)] if out is not NULL. */

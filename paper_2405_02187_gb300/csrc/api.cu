@@ -110,8 +110,8 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   xslam_t h = nullptr;
   if (!out) return fail(h, XSLAM_EINVAL, "out is NULL");
   *out = nullptr;
-  if (nx < 2 || ny < 2 || nz < 2 || (size_t)nx * ny * nz > (size_t)1 << 34)
-    return fail(h, XSLAM_EINVAL, "volume dimensions must be >= 2 and at most 2^34 voxels");
+  if (nx < 2 || ny < 2 || nz < 2 || (size_t)nx * ny * nz >= ((size_t)1 << 31))
+    return fail(h, XSLAM_EINVAL, "volume dimensions must be >= 2 with fewer than 2^31 voxels");
   if (!(voxel_m > 0.f) || !(trunc_m > 0.f)) return fail(h, XSLAM_EINVAL, "voxel and truncation must be > 0");
   if (!origin_m || !K) return fail(h, XSLAM_EINVAL, "origin and intrinsics are required");
   if (max_lanes < 0 || max_lanes > kMaxLanes - 1) return fail(h, XSLAM_EINVAL, "max_lanes must be in 0..15");
@@ -165,6 +165,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return cleanup(XSLAM_ECUDA, "no CUDA device");
   cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (icp_configure() != cudaSuccess) return cleanup(XSLAM_ECUDA, "cannot configure the ICP kernel's shared memory");
   if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess)
@@ -246,6 +247,16 @@ extern "C" xslam_status xslam_destroy(xslam_t h) {
 __global__ void k_fill(float* a, size_t n, float v) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] = v;
 }
+// lane-0 read-out: unobserved voxels read F = 1 (the sentinel is internal)
+__global__ void k_read_re(const float* a, float* o, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    o[i] = a[i] > 1.f ? 1.f : a[i];
+}
+// after W is written: voxels with W = 0 are unobserved
+__global__ void k_mark_unobserved(float* F, const float* W, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    if (!(W[i] > 0.f)) F[i] = kUnobserved;
+}
 __global__ void k_scale(const float* a, float* o, size_t n, double s) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     o[i] = (float)((double)a[i] * s);
@@ -256,7 +267,7 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   const size_t n = vox_count(h->p);
   const int Lmax = 1 + h->max_lanes;
   const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
-  k_fill<<<g, 256, 0, h->s>>>(h->b.F, n, 1.f);
+  k_fill<<<g, 256, 0, h->s>>>(h->b.F, n, kUnobserved);
   CU(cudaGetLastError());
   if (Lmax > 1) CU(cudaMemsetAsync(h->b.F + n, 0, sizeof(float) * n * (Lmax - 1), h->s));
   CU(cudaMemsetAsync(h->b.Wt, 0, sizeof(float) * n, h->s));
@@ -539,7 +550,9 @@ extern "C" xslam_status xslam_read_tsdf(xslam_t h, int lane, float* out) {
   if (lane == -1) {
     CU(cudaMemcpyAsync(out, h->b.Wt, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->s));
   } else if (lane == 0) {
-    CU(cudaMemcpyAsync(out, h->b.F, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->s));
+    const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
+    k_read_re<<<g, 256, 0, h->s>>>(h->b.F, out, n);
+    CU(cudaGetLastError());
   } else {
     const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
     k_scale<<<g, 256, 0, h->s>>>(h->b.F + (size_t)lane * n, out, n, 1.0 / h->p.h[lane]);
@@ -558,6 +571,11 @@ extern "C" xslam_status xslam_write_tsdf(xslam_t h, int lane, const float* in) {
   if (st != XSLAM_OK) return st;
   float* dst = lane == -1 ? h->b.Wt : h->b.F + (size_t)lane * n;
   CU(cudaMemcpyAsync(dst, in, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->s));
+  if (lane == -1) {
+    const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
+    k_mark_unobserved<<<g, 256, 0, h->s>>>(h->b.F, h->b.Wt, n);
+    CU(cudaGetLastError());
+  }
   st = leave(h);
   CU(cudaStreamSynchronize(h->s));
   return st;

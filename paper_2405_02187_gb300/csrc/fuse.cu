@@ -42,9 +42,10 @@ __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restr
   const float FD = clamp ? 1.f : sdf / p.mu;
 
   const float w = Wt[v];
-  const float inv = 1.f / (w + 1.f);
-  F[v] = (w * F[v] + FD) * inv;
-  Wt[v] = (p.w_max > 0.f) ? fminf(w + 1.f, p.w_max) : w + 1.f;
+  const float w1 = w + 1.f;
+  const float inv = 1.f / w1;
+  F[v] = (w * F[v] + FD) / w1;  // an unobserved voxel (w = 0) takes F_D whatever its sentinel value
+  Wt[v] = (p.w_max > 0.f) ? fminf(w1, p.w_max) : w1;
 
   // tangents of L with respect to the pixel coordinates
   const float dLda = (1.f - bb) * (d10 - d00) + bb * (d11 - d01);

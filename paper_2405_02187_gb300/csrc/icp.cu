@@ -19,7 +19,7 @@
 
 namespace xslam {
 
-constexpr int kGroup = 8;  // FP32 partials summed per group before the FP64 cross-block sum
+constexpr int kMaxPartials = 256;  // upper bound of the grid size (partials per value)
 
 struct Lvl {
   int W, H, s;
@@ -29,27 +29,21 @@ struct Lvl {
 // index of (r, c), r <= c, in the row-major packed upper triangle of a 6x6 matrix
 __host__ __device__ constexpr int up6(int r, int c) { return r * 6 - r * (r - 1) / 2 + (c - r); }
 
-// Cholesky A = L L^T of the real 6x6 normal matrix (packed upper storage, FP64); L row-major 6x6
-// in shared memory. Returns false if A is not positive definite.
-__device__ bool cholesky6(const double* __restrict__ A, double* __restrict__ Lc) {
-  for (int j = 0; j < 6; ++j) {
-    double d = A[up6(j, j)];
-    for (int k = 0; k < j; ++k) d -= Lc[6 * j + k] * Lc[6 * j + k];
-    if (!(d > 0.0)) return false;
-    const double ljj = sqrt(d), inv = 1.0 / ljj;
-    Lc[6 * j + j] = ljj;
-    for (int i = j + 1; i < 6; ++i) {
-      double s = A[up6(j, i)];
-      for (int k = 0; k < j; ++k) s -= Lc[6 * i + k] * Lc[6 * j + k];
-      Lc[6 * i + j] = s * inv;
-    }
-  }
-  return true;
+// 1/d in FP64: FP32 seed refined by two Newton-Raphson steps (y <- y + y (1 - d y)); the error
+// squares each step (2^-24 -> 2^-48 -> below FP64 rounding). FP64 division is a long serial
+// sequence on GB300, and the solve is on the critical path of every ICP iteration.
+__device__ __forceinline__ double recip64(double d) {
+  double y = (double)(1.0f / (float)d);
+  double e = fma(-d, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-d, y, 1.0);
+  return fma(y, e, y);
 }
 
-// x = A^-1 (-g - Al x0) with A = L L^T; Al (packed upper) and x0 may be null (real lane).
-__device__ void solve6(const double* __restrict__ Lc, const double* __restrict__ g, const double* __restrict__ Al,
-                       const double* __restrict__ x0, double* __restrict__ x) {
+// x = A^-1 (-g - Al x0) with A = L D L^T (L unit lower, row-major 6x6; rD = 1/D); Al (packed upper)
+// and x0 may be null (real lane).
+__device__ void solve6(const double* __restrict__ Lc, const double* __restrict__ rD, const double* __restrict__ g,
+                       const double* __restrict__ Al, const double* __restrict__ x0, double* __restrict__ x) {
   double y[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -58,17 +52,23 @@ __device__ void solve6(const double* __restrict__ Lc, const double* __restrict__
 #pragma unroll
       for (int k = 0; k < 6; ++k) s -= Al[i <= k ? up6(i, k) : up6(k, i)] * x0[k];
     }
-#pragma unroll
-    for (int k = 0; k < i; ++k) s -= Lc[6 * i + k] * y[k];
-    y[i] = s / Lc[6 * i + i];
+    y[i] = s;
   }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+#pragma unroll
+    for (int k = 0; k < i; ++k) y[i] -= Lc[6 * i + k] * y[k];
+  }
+  double z[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) z[i] = y[i] * rD[i];
 #pragma unroll
   for (int i = 5; i >= 0; --i) {
-    double s = y[i];
 #pragma unroll
-    for (int k = i + 1; k < 6; ++k) s -= Lc[6 * k + i] * x[k];
-    x[i] = s / Lc[6 * i + i];
+    for (int k = i + 1; k < 6; ++k) z[i] -= Lc[6 * k + i] * z[k];
   }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) x[i] = z[i];
 }
 
 __device__ __forceinline__ void accum(float* acc, const float* Ja, const float ra, const float* Jb, const float rb) {
@@ -95,6 +95,8 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   __shared__ double sA[kMaxLanes * kNT];
   __shared__ double sx[kMaxLanes][6];
   __shared__ double sLch[36];
+  __shared__ double sD[6], sRD[6];
+  extern __shared__ float s_stage[];  // [27 L][nblk | 1] staged partials (last block only)
   __shared__ int s_ncorr, s_fail;
 
   if (threadIdx.x == 0) s_skip = b.status[0];
@@ -268,18 +270,15 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   __threadfence();
 
   // ---------------- last block: FP64 cross-block sum ----------------
-  // warp w takes values v = w, w + nwarps, ...; lane i adds blocks i, i + 32, ... in FP32 (at most a
-  // handful each), then the 32 lane sums are added in FP64 by a shuffle tree.
+  // stage every block's partials in shared memory with one burst of independent loads (stride padded
+  // to an odd count: conflict-free column reads), then each value is summed as FP32 groups of 8 blocks
+  // added by a pairwise FP64 tree.
   const int nblk = gridDim.x;
-  const int nwarps = blockDim.x >> 5;
-  for (int v = warp; v < L * kNT; v += nwarps) {
-    const float* src = b.partial + (size_t)v * nblk;
-    float f = 0.f;
-    for (int k = lid; k < nblk; k += 32) f += __ldcg(src + k);
-    double d = (double)f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    if (lid == 0) sA[v] = d;
+  const int NV = L * kNT;
+  const int stride = nblk | 1;
+  for (int i = threadIdx.x; i < NV * nblk; i += blockDim.x) {
+    const int v = i / nblk, k = i - v * nblk;
+    s_stage[v * stride + k] = __ldcg(b.partial + i);
   }
   if (warp == 0) {
     int c = 0;
@@ -292,6 +291,25 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
     }
   }
   __syncthreads();
+  for (int v = threadIdx.x; v < NV; v += blockDim.x) {
+    double gsum[kMaxPartials / 8];
+    int ng = 0;
+    const float* row = s_stage + v * stride;
+    for (int k = 0; k < nblk; k += 8) {
+      float f = 0.f;
+      const int ke = min(nblk, k + 8);
+      for (int q = k; q < ke; ++q) f += row[q];
+      gsum[ng++] = (double)f;
+    }
+    while (ng > 1) {
+      const int h = ng >> 1;
+      for (int q = 0; q < h; ++q) gsum[q] = gsum[2 * q] + gsum[2 * q + 1];
+      if (ng & 1) gsum[h] = gsum[ng - 1];
+      ng = h + (ng & 1);
+    }
+    sA[v] = gsum[0];
+  }
+  __syncthreads();
 
   const bool update = !s_skip && !(flags & kIcpNoUpdate);
   if (flags & kIcpNoUpdate) {
@@ -299,17 +317,35 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
     if (threadIdx.x == 0) b.status[2] = s_ncorr;
     return;
   }
+  // L D L^T of the real 6x6 A in FP64, one column at a time; the rows below the pivot in parallel
   if (threadIdx.x == 0) {
     int fail = s_skip;
     if (!fail && (float)s_ncorr < p.min_corr_frac * (float)(lv.W * lv.H)) fail = 1;
-    if (!fail) fail = !cholesky6(sA, sLch);
-    if (!fail) solve6(sLch, sA + 21, nullptr, nullptr, sx[0]);
     s_fail = fail;
   }
   __syncthreads();
+  for (int j = 0; j < 6 && !s_fail; ++j) {
+    if (threadIdx.x == 0) {
+      double d = sA[up6(j, j)];
+      for (int k = 0; k < j; ++k) d -= sLch[6 * j + k] * sLch[6 * j + k] * sD[k];
+      if (!(d > 0.0) || !(d < 1e300)) s_fail = 1;
+      sD[j] = d;
+      sRD[j] = recip64(d);
+    }
+    __syncthreads();
+    if (!s_fail && threadIdx.x > j && threadIdx.x < 6) {
+      const int i = threadIdx.x;
+      double s2 = sA[up6(j, i)];
+      for (int k = 0; k < j; ++k) s2 -= sLch[6 * i + k] * sLch[6 * j + k] * sD[k];
+      sLch[6 * i + j] = s2 * sRD[j];
+    }
+    __syncthreads();
+  }
+  if (!s_fail && threadIdx.x == 0) solve6(sLch, sRD, sA + 21, nullptr, nullptr, sx[0]);
+  __syncthreads();
   if (update && !s_fail && threadIdx.x > 0 && threadIdx.x < L) {
     const int l = threadIdx.x;  // x_l = A^-1 (-g_l - A_l x_0)
-    solve6(sLch, sA + l * kNT + 21, sA + l * kNT, sx[0], sx[l]);
+    solve6(sLch, sRD, sA + l * kNT + 21, sA + l * kNT, sx[0], sx[l]);
   }
   __syncthreads();
   // pose update T <- exp(x) T on every lane (thread l handles lane l)
@@ -349,6 +385,18 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   }
 }
 
+size_t icp_stage_bytes(int L, int nblk) { return sizeof(float) * (size_t)L * kNT * (size_t)(nblk | 1); }
+
+// blocks whose staged partials fit the dynamic shared-memory budget
+static int icp_max_blocks(int L) {
+  int m = (int)(kIcpStageBudget / (sizeof(float) * kNT * (size_t)L)) - 1;
+  return m < kMaxPartials ? m : kMaxPartials;
+}
+
+cudaError_t icp_configure() {
+  return cudaFuncSetAttribute(k_icp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIcpStageBudget);
+}
+
 int icp_blocks(int level_pixels, int L) {
   int reps = 16 / L;
   if (reps < 1) reps = 1;
@@ -358,6 +406,7 @@ int icp_blocks(int level_pixels, int L) {
   const int nchunk = (level_pixels + 31) / 32;
   int nblk = (nchunk + reps - 1) / reps;
   if (nblk > sms) nblk = sms;
+  if (nblk > icp_max_blocks(L)) nblk = icp_max_blocks(L);
   if (nblk < 1) nblk = 1;
   return nblk;
 }
@@ -374,7 +423,8 @@ cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int flags, 
   int reps = 16 / p.L;
   if (reps < 1) reps = 1;
   const int threads = 32 * p.L * reps;
-  k_icp<<<nblk, threads, 0, s>>>(p, b, lv, flags, reps);
+  const size_t smem = icp_stage_bytes(p.L, nblk);
+  k_icp<<<nblk, threads, smem, s>>>(p, b, lv, flags, reps);
   return cudaGetLastError();
 }
 

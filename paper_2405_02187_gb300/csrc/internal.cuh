@@ -17,6 +17,7 @@ constexpr int kMaxLanes = 16;        // 1 real + up to 15 imaginary lanes
 constexpr int kNT = 27;              // 21 upper-triangle entries of J J^T + 6 of J r
 constexpr int kResSys = 12 + 18 * (kMaxLanes - 1);       // offset of the last ICP system in `result`
 constexpr int kResLen = kResSys + kNT * kMaxLanes + 8;   // doubles in `result` (+ loss / grad scratch)
+constexpr float kUnobserved = 2.f;      // Re F of a voxel with W = 0 (observed values lie in [-1, 1])
 constexpr float kCellBias = 0.015625f;  // 2^-6 pixel: ICP bilinear-cell tie breaker (first iteration
                                         // evaluates u_hat on integer pixels by construction)
 
@@ -44,7 +45,7 @@ struct Params {
 
 // Device buffers owned by a handle.
 struct Buffers {
-  float* F;         // L planes of N: lane 0 = Re F, lane j = Im F (raw)
+  float* F;         // L planes of N: lane 0 = Re F (kUnobserved where W = 0), lane j = Im F (raw)
   float* Wt;        // N
   float* depth_in;  // H*W raw input
   float* gated;     // H*W range-gated input (bilateral filter source)
@@ -77,6 +78,9 @@ cudaError_t launch_readout(const Params& p, const Buffers& b, cudaStream_t s);
 cudaError_t launch_loss(const Params& p, const Buffers& b, const float* depth, const float* model,
                         const double* pose, double* out, int nblk, cudaStream_t s);
 int icp_blocks(int level_pixels, int L);
+size_t icp_stage_bytes(int L, int nblk);
+cudaError_t icp_configure();
+constexpr size_t kIcpStageBudget = 200 * 1024;  // dynamic shared memory for the staged ICP partials
 
 // ICP iteration flags
 enum : int { kIcpFirst = 1, kIcpLast = 2, kIcpNoUpdate = 4 };

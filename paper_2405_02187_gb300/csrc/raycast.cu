@@ -8,13 +8,15 @@
 // alpha0 = alpha_m - dalpha F_m / (F_{m+1} - F_m), V_g = r(alpha0), N_g = grad F / |grad F| from
 // central differences of the trilinear F at V_g +- one voxel per axis.
 // Samples outside the volume are invalid, so the march starts and stops at the volume's bounds
-// (widened by one sample), which visits every valid sample in the same order.
+// (widened by one sample), which visits every valid sample in the same order. An unobserved voxel
+// holds F = kUnobserved (> 1, outside the range of any observed average), so a sample's validity
+// and value come from the 8 F loads alone.
 #include "internal.cuh"
 
 namespace xslam {
 
 struct Tri {
-  size_t base;     // linear index of the min corner
+  unsigned base;   // linear index of the min corner
   float fx, fy, fz;
   float val;       // trilinear F (real lane)
   float g[3];      // d val / d g (continuous voxel coordinates)
@@ -22,21 +24,19 @@ struct Tri {
 
 // Cell and real trilinear value at continuous voxel coordinate (gx, gy, gz). Returns false if the
 // cell is outside the volume or a corner is unobserved.
-__device__ __forceinline__ bool tri_real(const Params& p, const float* __restrict__ F, const float* __restrict__ Wt,
-                                         float gx, float gy, float gz, Tri& t, bool want_grad) {
+__device__ __forceinline__ bool tri_real(const Params& p, const float* __restrict__ F, float gx, float gy, float gz,
+                                         Tri& t, bool want_grad) {
   if (!(gx >= 0.f && gx < (float)(p.nx - 1) && gy >= 0.f && gy < (float)(p.ny - 1) && gz >= 0.f &&
         gz < (float)(p.nz - 1)))
     return false;
-  const int i = (int)floorf(gx), j = (int)floorf(gy), k = (int)floorf(gz);
-  const size_t sx = 1, sy = (size_t)p.nx, sz = (size_t)p.nx * p.ny;
-  const size_t b = i + sy * j + sz * k;
-  const float w000 = Wt[b], w100 = Wt[b + sx], w010 = Wt[b + sy], w110 = Wt[b + sx + sy];
-  const float w001 = Wt[b + sz], w101 = Wt[b + sx + sz], w011 = Wt[b + sy + sz], w111 = Wt[b + sx + sy + sz];
-  if (!(w000 > 0.f && w100 > 0.f && w010 > 0.f && w110 > 0.f && w001 > 0.f && w101 > 0.f && w011 > 0.f &&
-        w111 > 0.f))
-    return false;
-  const float c000 = F[b], c100 = F[b + sx], c010 = F[b + sy], c110 = F[b + sx + sy];
-  const float c001 = F[b + sz], c101 = F[b + sx + sz], c011 = F[b + sy + sz], c111 = F[b + sx + sy + sz];
+  const int i = (int)gx, j = (int)gy, k = (int)gz;  // gx >= 0: truncation is floor
+  const unsigned sy = (unsigned)p.nx, sz = (unsigned)p.nx * (unsigned)p.ny;
+  const unsigned b = (unsigned)i + sy * (unsigned)j + sz * (unsigned)k;
+  const float c000 = __ldg(F + b), c100 = __ldg(F + b + 1), c010 = __ldg(F + b + sy), c110 = __ldg(F + b + 1 + sy);
+  const float c001 = __ldg(F + b + sz), c101 = __ldg(F + b + 1 + sz), c011 = __ldg(F + b + sy + sz),
+              c111 = __ldg(F + b + 1 + sy + sz);
+  const float mx = fmaxf(fmaxf(fmaxf(c000, c100), fmaxf(c010, c110)), fmaxf(fmaxf(c001, c101), fmaxf(c011, c111)));
+  if (!(mx <= 1.f)) return false;  // an unobserved corner
   const float fx = gx - i, fy = gy - j, fz = gz - k;
   const float x00 = c000 + fx * (c100 - c000), x10 = c010 + fx * (c110 - c010);
   const float x01 = c001 + fx * (c101 - c001), x11 = c011 + fx * (c111 - c011);
@@ -61,12 +61,12 @@ __device__ __forceinline__ float tri_lane(const Params& p, const float* __restri
                                           float gly, float glz) {
   float v = t.g[0] * glx + t.g[1] * gly + t.g[2] * glz;
   if (Fl) {
-    const size_t sx = 1, sy = (size_t)p.nx, sz = (size_t)p.nx * p.ny;
-    const size_t b = t.base;
-    const float x00 = Fl[b] + t.fx * (Fl[b + sx] - Fl[b]);
-    const float x10 = Fl[b + sy] + t.fx * (Fl[b + sx + sy] - Fl[b + sy]);
-    const float x01 = Fl[b + sz] + t.fx * (Fl[b + sx + sz] - Fl[b + sz]);
-    const float x11 = Fl[b + sy + sz] + t.fx * (Fl[b + sx + sy + sz] - Fl[b + sy + sz]);
+    const unsigned sy = (unsigned)p.nx, sz = (unsigned)p.nx * (unsigned)p.ny;
+    const unsigned b = t.base;
+    const float x00 = __ldg(Fl + b) + t.fx * (__ldg(Fl + b + 1) - __ldg(Fl + b));
+    const float x10 = __ldg(Fl + b + sy) + t.fx * (__ldg(Fl + b + 1 + sy) - __ldg(Fl + b + sy));
+    const float x01 = __ldg(Fl + b + sz) + t.fx * (__ldg(Fl + b + 1 + sz) - __ldg(Fl + b + sz));
+    const float x11 = __ldg(Fl + b + sy + sz) + t.fx * (__ldg(Fl + b + 1 + sy + sz) - __ldg(Fl + b + sy + sz));
     const float y0 = x00 + t.fy * (x10 - x00), y1 = x01 + t.fy * (x11 - x01);
     v += y0 + t.fz * (y1 - y0);
   }
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_raycast(Params p, const float* __restri
   for (int m = m_lo; m <= m_hi; ++m) {
     const float al = m * p.ray_step;
     Tri t;
-    const bool ok = tri_real(p, F, Wt, g0x + al * gdx, g0y + al * gdy, g0z + al * gdz, t, false);
+    const bool ok = tri_real(p, F, g0x + al * gdx, g0y + al * gdy, g0z + al * gdz, t, false);
     if (prev_valid && ok) {
       const bool pos = t.val > 0.f;
       if (prev_pos && !pos) {
@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(256) k_raycast(Params p, const float* __restri
   if (m_hit >= 0) {
     am = m_hit * p.ray_step;
     an = (m_hit + 1) * p.ray_step;
-    bool ok = tri_real(p, F, Wt, g0x + am * gdx, g0y + am * gdy, g0z + am * gdz, tm, true);
-    ok &= tri_real(p, F, Wt, g0x + an * gdx, g0y + an * gdy, g0z + an * gdz, tn, true);
+    bool ok = tri_real(p, F, g0x + am * gdx, g0y + am * gdy, g0z + am * gdz, tm, true);
+    ok &= tri_real(p, F, g0x + an * gdx, g0y + an * gdy, g0z + an * gdz, tn, true);
     if (ok) {
       den = tn.val - tm.val;
       alpha0 = am - p.ray_step * tm.val / den;
@@ -154,12 +154,12 @@ __global__ void __launch_bounds__(256) k_raycast(Params p, const float* __restri
       vz = T[11] + alpha0 * dirz;
       const float gx = (vx - p.ox) * inv_vox - 0.5f, gy = (vy - p.oy) * inv_vox - 0.5f,
                   gz = (vz - p.oz) * inv_vox - 0.5f;
-      ok &= tri_real(p, F, Wt, gx + 1.f, gy, gz, ts[0], true);
-      ok &= tri_real(p, F, Wt, gx - 1.f, gy, gz, ts[1], true);
-      ok &= tri_real(p, F, Wt, gx, gy + 1.f, gz, ts[2], true);
-      ok &= tri_real(p, F, Wt, gx, gy - 1.f, gz, ts[3], true);
-      ok &= tri_real(p, F, Wt, gx, gy, gz + 1.f, ts[4], true);
-      ok &= tri_real(p, F, Wt, gx, gy, gz - 1.f, ts[5], true);
+      ok &= tri_real(p, F, gx + 1.f, gy, gz, ts[0], true);
+      ok &= tri_real(p, F, gx - 1.f, gy, gz, ts[1], true);
+      ok &= tri_real(p, F, gx, gy + 1.f, gz, ts[2], true);
+      ok &= tri_real(p, F, gx, gy - 1.f, gz, ts[3], true);
+      ok &= tri_real(p, F, gx, gy, gz + 1.f, ts[4], true);
+      ok &= tri_real(p, F, gx, gy, gz - 1.f, ts[5], true);
       if (ok) {
         const float s = 0.5f * inv_vox;
         nx = (ts[0].val - ts[1].val) * s;
