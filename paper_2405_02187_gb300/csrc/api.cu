@@ -38,6 +38,7 @@ struct xslam_s {
   double* h_result = nullptr;  // pinned host staging
   int* h_status = nullptr;
   int nblk[3] = {1, 1, 1};
+  int nblk_max = 1;
   cudaGraphExec_t g_first = nullptr, g_track = nullptr;
   bool use_graphs = true;
   // stage profiling (xslam_profile): one event pair per stage and frame, accumulated on read
@@ -182,6 +183,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
     nblk_max = std::max(nblk_max, h->nblk[l]);
   }
   nblk_max = std::max(nblk_max, 4 * h->nsm);  // k_loss grid
+  h->nblk_max = nblk_max;
   bool ok = true;
   ok &= cudaMalloc(&b.F, sizeof(float) * n * Lmax) == cudaSuccess;
   ok &= cudaMalloc(&b.Wt, sizeof(float) * n) == cudaSuccess;
@@ -192,7 +194,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   ok &= cudaMalloc(&b.pose, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&b.pose_prev, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&h->pose_tmp, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
-  ok &= cudaMalloc(&b.partial, sizeof(float) * (size_t)nblk_max * kNT * kMaxLanes) == cudaSuccess;
+  ok &= cudaMalloc(&b.partial, sizeof(float) * (size_t)(nblk_max + 4) * kNT * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&b.partial_n, sizeof(int) * nblk_max) == cudaSuccess;
   ok &= cudaMalloc(&b.ticket, sizeof(unsigned)) == cudaSuccess;
   ok &= cudaMalloc(&b.status, sizeof(int) * 4) == cudaSuccess;
@@ -273,6 +275,7 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   CU(cudaMemsetAsync(h->b.Wt, 0, sizeof(float) * n, h->s));
   CU(cudaMemsetAsync(h->b.model, 0, sizeof(float) * (size_t)h->p.W * h->p.H * (1 + 6 * Lmax), h->s));
   CU(cudaMemsetAsync(h->b.ticket, 0, sizeof(unsigned), h->s));
+  CU(cudaMemsetAsync(h->b.partial, 0, sizeof(float) * (size_t)(h->nblk_max + 4) * kNT * kMaxLanes, h->s));
   CU(cudaMemsetAsync(h->b.status, 0, sizeof(int) * 4, h->s));
   CU(cudaMemsetAsync(h->b.pose + 12, 0, sizeof(double) * 12 * (kMaxLanes - 1), h->s));
   CU(cudaMemsetAsync(h->b.result, 0, sizeof(double) * kResLen, h->s));

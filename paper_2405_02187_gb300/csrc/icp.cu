@@ -21,6 +21,10 @@ namespace xslam {
 
 constexpr int kMaxPartials = 256;  // upper bound of the grid size (partials per value)
 
+// row stride of the value-major partials: a multiple of 4 floats (float4 reads); the last block of
+// the grid writes zeros into the padding of every row
+__host__ __device__ __forceinline__ int icp_pstride(int nblk) { return (nblk + 3) & ~3; }
+
 struct Lvl {
   int W, H, s;
   float fx, fy, cx, cy;
@@ -29,46 +33,57 @@ struct Lvl {
 // index of (r, c), r <= c, in the row-major packed upper triangle of a 6x6 matrix
 __host__ __device__ constexpr int up6(int r, int c) { return r * 6 - r * (r - 1) / 2 + (c - r); }
 
-// 1/d in FP64: FP32 seed refined by two Newton-Raphson steps (y <- y + y (1 - d y)); the error
-// squares each step (2^-24 -> 2^-48 -> below FP64 rounding). FP64 division is a long serial
-// sequence on GB300, and the solve is on the critical path of every ICP iteration.
-__device__ __forceinline__ double recip64(double d) {
-  double y = (double)(1.0f / (float)d);
-  double e = fma(-d, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-d, y, 1.0);
-  return fma(y, e, y);
+// The 6x6 solve. A = L D L^T is factored in FP32 (square-root-free Cholesky) and every right-hand
+// side is solved by mixed-precision iterative refinement: x = S(b), r = b - A x in FP64 (A and b are
+// the FP64 sums), x += S(r), with S the FP32 forward/back substitution; one round brings the relative
+// error from ~cond(A) 2^-24 to ~(cond(A) 2^-24)^2. On GB300 every FP64 warp instruction occupies the
+// SM sub-partition's FP64 pipe for ~64-80 cycles whatever the number of active threads, so the FP64
+// steps of the tail run SIMT-parallel: one thread per (system, row) or per matrix element.
+struct Ldl32 {
+  float L[15];  // strictly lower part, row-major packed: (i, k) for k < i at i(i-1)/2 + k
+  float rD[6];  // 1 / D
+};
+
+__device__ __forceinline__ int lo6(int i, int k) { return i * (i - 1) / 2 + k; }
+
+// returns false if a pivot is not positive (A not positive definite in FP32); A packed upper, FP32
+__device__ bool ldl32(const float* __restrict__ A, Ldl32& f) {
+  float D[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    float d = A[up6(j, j)];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= f.L[lo6(j, k)] * f.L[lo6(j, k)] * D[k];
+    if (!(d > 0.f)) return false;
+    D[j] = d;
+    f.rD[j] = 1.f / d;
+#pragma unroll
+    for (int i = j + 1; i < 6; ++i) {
+      float s = A[up6(j, i)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= f.L[lo6(i, k)] * f.L[lo6(j, k)] * D[k];
+      f.L[lo6(i, j)] = s * f.rD[j];
+    }
+  }
+  return true;
 }
 
-// x = A^-1 (-g - Al x0) with A = L D L^T (L unit lower, row-major 6x6; rD = 1/D); Al (packed upper)
-// and x0 may be null (real lane).
-__device__ void solve6(const double* __restrict__ Lc, const double* __restrict__ rD, const double* __restrict__ g,
-                       const double* __restrict__ Al, const double* __restrict__ x0, double* __restrict__ x) {
-  double y[6];
+__device__ __forceinline__ void subst32(const Ldl32& f, const float* b, float* x) {
+  float y[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    double s = -g[i];
-    if (Al) {
+    float s = b[i];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) s -= Al[i <= k ? up6(i, k) : up6(k, i)] * x0[k];
-    }
+    for (int k = 0; k < i; ++k) s -= f.L[lo6(i, k)] * y[k];
     y[i] = s;
   }
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-#pragma unroll
-    for (int k = 0; k < i; ++k) y[i] -= Lc[6 * i + k] * y[k];
-  }
-  double z[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) z[i] = y[i] * rD[i];
-#pragma unroll
   for (int i = 5; i >= 0; --i) {
+    float s = y[i] * f.rD[i];
 #pragma unroll
-    for (int k = i + 1; k < 6; ++k) z[i] -= Lc[6 * k + i] * z[k];
+    for (int k = i + 1; k < 6; ++k) s -= f.L[lo6(k, i)] * x[k];
+    x[i] = s;
   }
-#pragma unroll
-  for (int i = 0; i < 6; ++i) x[i] = z[i];
 }
 
 __device__ __forceinline__ void accum(float* acc, const float* Ja, const float ra, const float* Jb, const float rb) {
@@ -94,9 +109,12 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   __shared__ int s_cnt[32];
   __shared__ double sA[kMaxLanes * kNT];
   __shared__ double sx[kMaxLanes][6];
-  __shared__ double sLch[36];
-  __shared__ double sD[6], sRD[6];
-  extern __shared__ float s_stage[];  // [27 L][nblk | 1] staged partials (last block only)
+  __shared__ Ldl32 s_ldl;
+  __shared__ double s_half[2 * kNT * kMaxLanes];
+  __shared__ float sAf[kNT * kMaxLanes];
+  __shared__ float sxf[kMaxLanes][6], srf[kMaxLanes][6], sdf[kMaxLanes][6];
+  __shared__ SeCoef sco[kMaxLanes];
+  __shared__ double sE[kMaxLanes][12];
   __shared__ int s_ncorr, s_fail;
 
   if (threadIdx.x == 0) s_skip = b.status[0];
@@ -249,10 +267,13 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   __syncthreads();
   // partials are stored value-major ([value][block]) so that the last block reads each value's
   // per-block sums with coalesced warp loads
+  const int pst = icp_pstride(gridDim.x);
   for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) {
     float s = 0.f;
     for (int r = 0; r < reps; ++r) s += s_red[r * L * kNT + i];
-    b.partial[(size_t)i * gridDim.x + blockIdx.x] = s;
+    b.partial[(size_t)i * pst + blockIdx.x] = s;
+    if (blockIdx.x == gridDim.x - 1)  // the row padding of this launch's stride reads as zero
+      for (int k = gridDim.x; k < pst; ++k) b.partial[(size_t)i * pst + k] = 0.f;
   }
   if (threadIdx.x == 0) {
     int c = 0;
@@ -270,19 +291,35 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   __threadfence();
 
   // ---------------- last block: FP64 cross-block sum ----------------
-  // stage every block's partials in shared memory with one burst of independent loads (stride padded
-  // to an odd count: conflict-free column reads), then each value is summed as FP32 groups of 8 blocks
-  // added by a pairwise FP64 tree.
-  const int nblk = gridDim.x;
+  // value v is summed by two threads, one per half of its row of block partials: float4 loads issued
+  // together, FP32 sums of 16 partials, FP64 accumulation of those sums, FP64 add of the two halves.
+  // Different values sit in different lanes, so each FP64 warp instruction adds 32 values.
   const int NV = L * kNT;
-  const int stride = nblk | 1;
-  for (int i = threadIdx.x; i < NV * nblk; i += blockDim.x) {
-    const int v = i / nblk, k = i - v * nblk;
-    s_stage[v * stride + k] = __ldcg(b.partial + i);
+  const int pstride = icp_pstride(gridDim.x);
+  const int n4 = pstride >> 2, h4 = (n4 + 1) >> 1;
+  for (int t = threadIdx.x; t < 2 * NV; t += blockDim.x) {
+    const int v = t >> 1, half = t & 1;
+    const float4* row = reinterpret_cast<const float4*>(b.partial + (size_t)v * pstride) + half * h4;
+    const int cnt = half ? n4 - h4 : h4;
+    double acc = 0.0;
+    for (int c0 = 0; c0 < cnt; c0 += 8) {
+      float4 q[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) q[j] = (c0 + j < cnt) ? __ldcg(row + c0 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      float f0 = 0.f, f1 = 0.f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        f0 += (q[j].x + q[j].y) + (q[j].z + q[j].w);
+        f1 += (q[j + 4].x + q[j + 4].y) + (q[j + 4].z + q[j + 4].w);
+      }
+      acc += (double)f0;
+      acc += (double)f1;
+    }
+    s_half[t] = acc;
   }
   if (warp == 0) {
     int c = 0;
-    for (int k = lid; k < nblk; k += 32) c += __ldcg(&b.partial_n[k]);
+    for (int k = lid; k < (int)gridDim.x; k += 32) c += __ldcg(&b.partial_n[k]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lid == 0) {
@@ -291,24 +328,7 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
     }
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < NV; v += blockDim.x) {
-    double gsum[kMaxPartials / 8];
-    int ng = 0;
-    const float* row = s_stage + v * stride;
-    for (int k = 0; k < nblk; k += 8) {
-      float f = 0.f;
-      const int ke = min(nblk, k + 8);
-      for (int q = k; q < ke; ++q) f += row[q];
-      gsum[ng++] = (double)f;
-    }
-    while (ng > 1) {
-      const int h = ng >> 1;
-      for (int q = 0; q < h; ++q) gsum[q] = gsum[2 * q] + gsum[2 * q + 1];
-      if (ng & 1) gsum[h] = gsum[ng - 1];
-      ng = h + (ng & 1);
-    }
-    sA[v] = gsum[0];
-  }
+  for (int v = threadIdx.x; v < NV; v += blockDim.x) sA[v] = s_half[2 * v] + s_half[2 * v + 1];
   __syncthreads();
 
   const bool update = !s_skip && !(flags & kIcpNoUpdate);
@@ -317,65 +337,91 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
     if (threadIdx.x == 0) b.status[2] = s_ncorr;
     return;
   }
-  // L D L^T of the real 6x6 A in FP64, one column at a time; the rows below the pivot in parallel
-  if (threadIdx.x == 0) {
+  // factor the real 6x6 A once, then x_0 = A^-1 (-g_0) and x_l = A^-1 (-g_l - A_l x_0)
+  const int t = threadIdx.x;
+  for (int v = t; v < NV; v += blockDim.x) sAf[v] = (float)sA[v];
+  __syncthreads();
+  if (t == 0) {
     int fail = s_skip;
     if (!fail && (float)s_ncorr < p.min_corr_frac * (float)(lv.W * lv.H)) fail = 1;
+    if (!fail && !ldl32(sAf, s_ldl)) fail = 1;
+    if (!fail) {
+      float b0[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) b0[i] = -sAf[21 + i];
+      subst32(s_ldl, b0, sxf[0]);
+    }
     s_fail = fail;
   }
   __syncthreads();
-  for (int j = 0; j < 6 && !s_fail; ++j) {
-    if (threadIdx.x == 0) {
-      double d = sA[up6(j, j)];
-      for (int k = 0; k < j; ++k) d -= sLch[6 * j + k] * sLch[6 * j + k] * sD[k];
-      if (!(d > 0.0) || !(d < 1e300)) s_fail = 1;
-      sD[j] = d;
-      sRD[j] = recip64(d);
-    }
-    __syncthreads();
-    if (!s_fail && threadIdx.x > j && threadIdx.x < 6) {
-      const int i = threadIdx.x;
-      double s2 = sA[up6(j, i)];
-      for (int k = 0; k < j; ++k) s2 -= sLch[6 * i + k] * sLch[6 * j + k] * sD[k];
-      sLch[6 * i + j] = s2 * sRD[j];
-    }
-    __syncthreads();
-  }
-  if (!s_fail && threadIdx.x == 0) solve6(sLch, sRD, sA + 21, nullptr, nullptr, sx[0]);
-  __syncthreads();
-  if (update && !s_fail && threadIdx.x > 0 && threadIdx.x < L) {
-    const int l = threadIdx.x;  // x_l = A^-1 (-g_l - A_l x_0)
-    solve6(sLch, sRD, sA + l * kNT + 21, sA + l * kNT, sx[0], sx[l]);
-  }
-  __syncthreads();
-  // pose update T <- exp(x) T on every lane (thread l handles lane l)
-  const int l = threadIdx.x;
-  double Tn[12];
-  if (update && !s_fail && l < L) {
-    double E[12], E1[12], T0[12], Tl[12];
+  const bool go = update && !s_fail;
+  // real lane: residual in FP64 (thread i = row), FP32 correction
+  if (go && t < 6) {
+    double r = -sA[21 + t];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) T0[i] = b.pose[i];
+    for (int k = 0; k < 6; ++k) r = fma(-sA[t <= k ? up6(t, k) : up6(k, t)], (double)sxf[0][k], r);
+    srf[0][t] = (float)r;
+  }
+  __syncthreads();
+  if (go && t == 0) subst32(s_ldl, srf[0], sdf[0]);
+  __syncthreads();
+  if (go && t < 6) sx[0][t] = (double)sxf[0][t] + (double)sdf[0][t];
+  __syncthreads();
+  // imaginary lanes: right-hand sides in FP64, thread (l, i)
+  const int ls = 1 + t / 6, li = t % 6;
+  const bool lane_thread = go && t < 6 * (L - 1);
+  double rhs = 0.0;
+  if (lane_thread) {
+    const double* Al = sA + ls * kNT;
+    rhs = -Al[21 + li];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) rhs = fma(-Al[li <= k ? up6(li, k) : up6(k, li)], sx[0][k], rhs);
+    srf[ls][li] = (float)rhs;
+  }
+  __syncthreads();
+  if (go && t >= 1 && t < L) subst32(s_ldl, srf[t], sxf[t]);
+  __syncthreads();
+  if (lane_thread) {
+    double r = rhs;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r = fma(-sA[li <= k ? up6(li, k) : up6(k, li)], (double)sxf[ls][k], r);
+    srf[ls][li] = (float)r;
+  }
+  __syncthreads();
+  if (go && t >= 1 && t < L) subst32(s_ldl, srf[t], sdf[t]);
+  __syncthreads();
+  if (lane_thread) sx[ls][li] = (double)sxf[ls][li] + (double)sdf[ls][li];
+  __syncthreads();
+
+  // pose update T <- exp(x) T on every lane, FP64: series coefficients once per lane, then one thread
+  // per (lane, element) for exp(x) and one per (lane, element) for the product
+  if (go && t < L) se3_coef_lane(sx[0], sx[t], sco[t]);
+  __syncthreads();
+  if (go && t < 12 * L) {
+    const int l = t / 12, e = t % 12;
+    sE[l][e] = se3_exp_element(sx[0], sx[l], sco[l], l > 0, e);
+  }
+  __syncthreads();
+  double tn = 0.0;
+  if (go && t < 12 * L) {
+    const int l = t / 12, e = t % 12, r = e >> 2, c = e & 3;
+    const double* T0 = b.pose;
     if (l == 0) {
-      se3_exp_tangent(sx[0], nullptr, E, nullptr);
-      compose(E, T0, Tn);
+      tn = sE[0][4 * r] * T0[c] + sE[0][4 * r + 1] * T0[4 + c] + sE[0][4 * r + 2] * T0[8 + c] + (c == 3 ? sE[0][4 * r + 3] : 0.0);
     } else {
-#pragma unroll
-      for (int i = 0; i < 12; ++i) Tl[i] = b.pose[12 * l + i];
-      se3_exp_tangent(sx[0], sx[l], E, E1);
-      compose_tangent(E, E1, T0, Tl, Tn);
+      const double* Tl = b.pose + 12 * l;
+      tn = sE[l][4 * r] * T0[c] + sE[l][4 * r + 1] * T0[4 + c] + sE[l][4 * r + 2] * T0[8 + c] +
+           sE[0][4 * r] * Tl[c] + sE[0][4 * r + 1] * Tl[4 + c] + sE[0][4 * r + 2] * Tl[8 + c] +
+           (c == 3 ? sE[l][4 * r + 3] : 0.0);
     }
   }
   __syncthreads();
-  if (update && !s_fail && l < L) {
-#pragma unroll
-    for (int i = 0; i < 12; ++i) b.pose[12 * l + i] = Tn[i];
-  }
+  if (go && t < 12 * L) b.pose[t] = tn;
   if (threadIdx.x == 0 && s_fail && !s_skip) b.status[0] = 1;
   if (flags & kIcpLast) {
     __syncthreads();
     const int failed = b.status[0];
-    if (failed && l < L)
-      for (int i = 0; i < 12; ++i) b.pose[12 * l + i] = b.pose_prev[12 * l + i];
+    if (failed && t < 12 * L) b.pose[t] = b.pose_prev[t];
     __syncthreads();
     if (threadIdx.x == 0) {
       if (failed) b.status[1] += 1;
@@ -385,17 +431,7 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   }
 }
 
-size_t icp_stage_bytes(int L, int nblk) { return sizeof(float) * (size_t)L * kNT * (size_t)(nblk | 1); }
-
-// blocks whose staged partials fit the dynamic shared-memory budget
-static int icp_max_blocks(int L) {
-  int m = (int)(kIcpStageBudget / (sizeof(float) * kNT * (size_t)L)) - 1;
-  return m < kMaxPartials ? m : kMaxPartials;
-}
-
-cudaError_t icp_configure() {
-  return cudaFuncSetAttribute(k_icp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kIcpStageBudget);
-}
+cudaError_t icp_configure() { return cudaSuccess; }
 
 int icp_blocks(int level_pixels, int L) {
   int reps = 16 / L;
@@ -403,10 +439,11 @@ int icp_blocks(int level_pixels, int L) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // at least 4 chunks of 32 pixels per warp: small levels get fewer blocks (fewer partials to add)
   const int nchunk = (level_pixels + 31) / 32;
-  int nblk = (nchunk + reps - 1) / reps;
+  int nblk = (nchunk + 4 * reps - 1) / (4 * reps);
   if (nblk > sms) nblk = sms;
-  if (nblk > icp_max_blocks(L)) nblk = icp_max_blocks(L);
+  if (nblk > kMaxPartials) nblk = kMaxPartials;
   if (nblk < 1) nblk = 1;
   return nblk;
 }
@@ -423,8 +460,7 @@ cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int flags, 
   int reps = 16 / p.L;
   if (reps < 1) reps = 1;
   const int threads = 32 * p.L * reps;
-  const size_t smem = icp_stage_bytes(p.L, nblk);
-  k_icp<<<nblk, threads, smem, s>>>(p, b, lv, flags, reps);
+  k_icp<<<nblk, threads, 0, s>>>(p, b, lv, flags, reps);
   return cudaGetLastError();
 }
 

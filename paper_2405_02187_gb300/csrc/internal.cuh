@@ -78,9 +78,7 @@ cudaError_t launch_readout(const Params& p, const Buffers& b, cudaStream_t s);
 cudaError_t launch_loss(const Params& p, const Buffers& b, const float* depth, const float* model,
                         const double* pose, double* out, int nblk, cudaStream_t s);
 int icp_blocks(int level_pixels, int L);
-size_t icp_stage_bytes(int L, int nblk);
 cudaError_t icp_configure();
-constexpr size_t kIcpStageBudget = 200 * 1024;  // dynamic shared memory for the staged ICP partials
 
 // ICP iteration flags
 enum : int { kIcpFirst = 1, kIcpLast = 2, kIcpNoUpdate = 4 };

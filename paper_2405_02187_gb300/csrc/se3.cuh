@@ -1,5 +1,5 @@
 // FP64 SE(3) exponential with one tangent direction (X-SLAM Sec. 4.1, Eq. lie, rotvector,
-// rotation_jacobi), for the pose update T <- exp(x) T of ICP and the POSE0 seed.
+// rotation_jacobi), for the pose update T <- exp(x) T of ICP, evaluated one matrix element per thread.
 //
 // exp([phi, rho]) = [R | V rho] with R = I + A [phi] + B [phi]^2 and V = I + B [phi] + C [phi]^2,
 // A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3, th^2 = phi.phi; this is the
@@ -14,7 +14,8 @@ struct Coef {
   double A, B, C, dA, dB, dC;  // values and derivatives with respect to x = th^2
 };
 
-// sum_{n=0}^{9} (-x)^n / (2n+1+s)! and its derivative in x by Horner's rule (s = 0: A, 1: B, 2: C)
+// sum_{n=0}^{N} (-x)^n / (2n+1+s)! and its derivative in x by Horner's rule (s = 0: A, 1: B, 2: C)
+template <int N>
 __device__ __forceinline__ void series(double x, int s, double& v, double& dv) {
   constexpr double inv_fact[22] = {
       1.0, 1.0, 1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0, 1.0 / 5040.0, 1.0 / 40320.0,
@@ -22,7 +23,6 @@ __device__ __forceinline__ void series(double x, int s, double& v, double& dv) {
       1.0 / 87178291200.0, 1.0 / 1307674368000.0, 1.0 / 20922789888000.0, 1.0 / 355687428096000.0,
       1.0 / 6402373705728000.0, 1.0 / 121645100408832000.0, 1.0 / 2432902008176640000.0,
       1.0 / 51090942171709440000.0};
-  constexpr int N = 9;
   v = ((N & 1) ? -1.0 : 1.0) * inv_fact[2 * N + 1 + s];
   dv = 0.0;
 #pragma unroll
@@ -34,11 +34,16 @@ __device__ __forceinline__ void series(double x, int s, double& v, double& dv) {
 
 __device__ __forceinline__ Coef se3_coef(double x) {
   Coef c;
-  if (x < 0.25) {
-    // power series (terms up to x^9: truncation below 1e-25 for x < 1/4)
-    series(x, 0, c.A, c.dA);
-    series(x, 1, c.B, c.dB);
-    series(x, 2, c.C, c.dC);
+  if (x < 1e-2) {
+    // terms up to x^5: truncation below 2e-22 for x < 1e-2 (rotations under 0.1 rad, every ICP step)
+    series<5>(x, 0, c.A, c.dA);
+    series<5>(x, 1, c.B, c.dB);
+    series<5>(x, 2, c.C, c.dC);
+  } else if (x < 0.25) {
+    // terms up to x^9: truncation below 1e-25 for x < 1/4
+    series<9>(x, 0, c.A, c.dA);
+    series<9>(x, 1, c.B, c.dB);
+    series<9>(x, 2, c.C, c.dC);
   } else {
     const double th = sqrt(x), s = sin(th), co = cos(th);
     c.A = s / th;
@@ -51,74 +56,60 @@ __device__ __forceinline__ Coef se3_coef(double x) {
   return c;
 }
 
-// E = exp(x0) and its tangent E1 along x1 (both 3x4 row-major). x1 == nullptr: tangent not wanted.
-__device__ inline void se3_exp_tangent(const double* x0, const double* x1, double* E, double* E1) {
-  const double p0 = x0[0], p1 = x0[1], p2 = x0[2];
-  const double th2 = p0 * p0 + p1 * p1 + p2 * p2;
+// Coefficients of exp at x0 and the tangent of theta^2 along x1 (one per lane, shared by its elements).
+struct SeCoef {
+  double A, B, C, dA, dB, dC;  // dA etc.: tangents along x1 (derivative in theta^2 times d theta^2)
+};
+
+__device__ __forceinline__ void se3_coef_lane(const double* x0, const double* x1, SeCoef& out) {
+  const double th2 = x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2];
+  const double dth2 = 2.0 * (x0[0] * x1[0] + x0[1] * x1[1] + x0[2] * x1[2]);
   const Coef c = se3_coef(th2);
-  // [phi] and [phi]^2 = phi phi^T - th2 I
-  const double H[9] = {0, -p2, p1, p2, 0, -p0, -p1, p0, 0};
-  const double phi[3] = {p0, p1, p2};
-  double H2[9];
-  for (int r = 0; r < 3; ++r)
-    for (int q = 0; q < 3; ++q) H2[3 * r + q] = phi[r] * phi[q] - (r == q ? th2 : 0.0);
-  double R[9], Vm[9];
-  for (int i = 0; i < 9; ++i) {
-    const double I = (i % 4 == 0) ? 1.0 : 0.0;
-    R[i] = I + c.A * H[i] + c.B * H2[i];
-    Vm[i] = I + c.B * H[i] + c.C * H2[i];
-  }
-  for (int r = 0; r < 3; ++r) {
-    E[4 * r + 0] = R[3 * r + 0];
-    E[4 * r + 1] = R[3 * r + 1];
-    E[4 * r + 2] = R[3 * r + 2];
-    E[4 * r + 3] = Vm[3 * r] * x0[3] + Vm[3 * r + 1] * x0[4] + Vm[3 * r + 2] * x0[5];
-  }
-  if (!x1) return;
-  const double q0 = x1[0], q1 = x1[1], q2 = x1[2];
-  const double dth2 = 2.0 * (p0 * q0 + p1 * q1 + p2 * q2);
-  const double Hd[9] = {0, -q2, q1, q2, 0, -q0, -q1, q0, 0};
-  const double phd[3] = {q0, q1, q2};
-  double H2d[9];
-  for (int r = 0; r < 3; ++r)
-    for (int q = 0; q < 3; ++q) H2d[3 * r + q] = phd[r] * phi[q] + phi[r] * phd[q] - (r == q ? dth2 : 0.0);
-  const double dA = c.dA * dth2, dB = c.dB * dth2, dC = c.dC * dth2;
-  double Rd[9], Vd[9];
-  for (int i = 0; i < 9; ++i) {
-    Rd[i] = dA * H[i] + c.A * Hd[i] + dB * H2[i] + c.B * H2d[i];
-    Vd[i] = dB * H[i] + c.B * Hd[i] + dC * H2[i] + c.C * H2d[i];
-  }
-  for (int r = 0; r < 3; ++r) {
-    E1[4 * r + 0] = Rd[3 * r + 0];
-    E1[4 * r + 1] = Rd[3 * r + 1];
-    E1[4 * r + 2] = Rd[3 * r + 2];
-    E1[4 * r + 3] = Vd[3 * r] * x0[3] + Vd[3 * r + 1] * x0[4] + Vd[3 * r + 2] * x0[5] + Vm[3 * r] * x1[3] +
-                    Vm[3 * r + 1] * x1[4] + Vm[3 * r + 2] * x1[5];
-  }
+  out.A = c.A;
+  out.B = c.B;
+  out.C = c.C;
+  out.dA = c.dA * dth2;
+  out.dB = c.dB * dth2;
+  out.dC = c.dC * dth2;
 }
 
-// C = A * B for 3x4 rigid transforms.
-__device__ __forceinline__ void compose(const double* A, const double* B, double* C) {
-  for (int r = 0; r < 3; ++r) {
-    for (int q = 0; q < 4; ++q) {
-      double s = A[4 * r] * B[q] + A[4 * r + 1] * B[4 + q] + A[4 * r + 2] * B[8 + q];
-      if (q == 3) s += A[4 * r + 3];
-      C[4 * r + q] = s;
-    }
-  }
+// [v]_{rk}
+__device__ __forceinline__ double hat_el(const double* v, int r, int k) {
+  if (r == k) return 0.0;
+  if (r == 0) return k == 1 ? -v[2] : v[1];
+  if (r == 1) return k == 0 ? v[2] : -v[0];
+  return k == 0 ? -v[1] : v[0];
 }
 
-// Tangent of A * B: A1 * B + A * B1 (translation column without A's own translation term twice).
-__device__ __forceinline__ void compose_tangent(const double* A, const double* A1, const double* B, const double* B1,
-                                                double* C1) {
-  for (int r = 0; r < 3; ++r) {
-    for (int q = 0; q < 4; ++q) {
-      double s = A1[4 * r] * B[q] + A1[4 * r + 1] * B[4 + q] + A1[4 * r + 2] * B[8 + q];
-      s += A[4 * r] * B1[q] + A[4 * r + 1] * B1[4 + q] + A[4 * r + 2] * B1[8 + q];
-      if (q == 3) s += A1[4 * r + 3];
-      C1[4 * r + q] = s;
+// ([phi]^2)_{rk} = phi_r phi_k - th2 delta_rk and its tangent along phi1
+__device__ __forceinline__ double hat2_el(const double* v, int r, int k) {
+  return v[r] * v[k] - (r == k ? v[0] * v[0] + v[1] * v[1] + v[2] * v[2] : 0.0);
+}
+__device__ __forceinline__ double hat2_tan(const double* v, const double* v1, int r, int k) {
+  return v1[r] * v[k] + v[r] * v1[k] - (r == k ? 2.0 * (v[0] * v1[0] + v[1] * v1[1] + v[2] * v1[2]) : 0.0);
+}
+
+// Element e = 4 r + c of E = exp(x0) (tangent = false) or of its tangent along x1 (tangent = true).
+__device__ __forceinline__ double se3_exp_element(const double* x0, const double* x1, const SeCoef& k, bool tangent,
+                                                  int e) {
+  const int r = e >> 2, c = e & 3;
+  if (c < 3) {
+    if (!tangent) return (r == c ? 1.0 : 0.0) + k.A * hat_el(x0, r, c) + k.B * hat2_el(x0, r, c);
+    return k.dA * hat_el(x0, r, c) + k.A * hat_el(x1, r, c) + k.dB * hat2_el(x0, r, c) + k.B * hat2_tan(x0, x1, r, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const double V = (r == q ? 1.0 : 0.0) + k.B * hat_el(x0, r, q) + k.C * hat2_el(x0, r, q);
+    if (!tangent) {
+      s += V * x0[3 + q];
+    } else {
+      const double V1 = k.dB * hat_el(x0, r, q) + k.B * hat_el(x1, r, q) + k.dC * hat2_el(x0, r, q) +
+                        k.C * hat2_tan(x0, x1, r, q);
+      s += V1 * x0[3 + q] + V * x1[3 + q];
     }
   }
+  return s;
 }
 
 }  // namespace xslam
