@@ -98,6 +98,17 @@ __device__ __forceinline__ void accum(float* acc, const float* Ja, const float r
   for (int r = 0; r < 6; ++r) acc[21 + r] += Ja[r] * rb + Jb[r] * ra;
 }
 
+// fields of the per-pixel record handed from the real warp to the lane warps (SoA, [field][32])
+enum : int {
+  RV = 0, RD, RRX, RRY, RE, RQX = RE + 3, RQY, RIZ, RA, RB, RT, RPP, RN = RPP + 3, RDF = RN + 3, RDQA = RDF + 3,
+  RDQB = RDQA + 3, RDNA = RDQB + 3, RDNB = RDNA + 3, RJ = RDNB + 3, RRES = RJ + 6, kRec
+};
+constexpr int kMaxReps = 4;
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int flags, int reps) {
   const int L = p.L;
   const int warp = threadIdx.x >> 5, lid = threadIdx.x & 31;
@@ -116,6 +127,7 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   __shared__ SeCoef sco[kMaxLanes];
   __shared__ double sE[kMaxLanes][12];
   __shared__ int s_ncorr, s_fail;
+  extern __shared__ float s_rec[];  // [rep][buffer][field][pixel]: dynamic, reps * 2 * kRec * 32 floats
 
   if (threadIdx.x == 0) s_skip = b.status[0];
   for (int i = threadIdx.x; i < L * 12; i += blockDim.x) {
@@ -129,25 +141,40 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   for (int q = 0; q < kNT; ++q) acc[q] = 0.f;
   int cnt = 0;
 
-  if (!s_skip) {
-    const float* D = b.pyr[0];
-    if (lv.s == 2) D = b.pyr[1];
-    if (lv.s == 4) D = b.pyr[2];
-    const size_t hw0 = (size_t)p.W * p.H;
-    const float* mdep = b.model;
-    const float* mV = b.model + hw0;
-    const float* mN = b.model + hw0 * (1 + 3 * L);
-    const float* T = sT[0];
-    const float* P = sP[0];
-    const int npx = lv.W * lv.H;
-    const int nchunk = (npx + 31) >> 5;
-    for (int ch = blockIdx.x * reps + rep; ch < nchunk; ch += gridDim.x * reps) {
+  // Pixel chunks of 32 flow through each replica: the real warp computes a chunk's correspondences
+  // into a shared-memory record (double-buffered), a named barrier hands it to the lane warps, which
+  // add their tangents while the real warp computes the next chunk.
+  int nloop = 0;
+  const int npx = lv.W * lv.H;
+  const int nchunk = (npx + 31) >> 5;
+  {
+    const int base = blockIdx.x * reps + rep, stride = gridDim.x * reps;
+    nloop = (!s_skip && base < nchunk) ? (nchunk - base + stride - 1) / stride : 0;
+  }
+  const float* D = lv.s == 1 ? b.pyr[0] : (lv.s == 2 ? b.pyr[1] : b.pyr[2]);
+  const size_t hw0 = (size_t)p.W * p.H;
+  const float* mdep = b.model;
+  const float* mV = b.model + hw0;
+  const float* mN = b.model + hw0 * (1 + 3 * L);
+  float* recbase = s_rec + (size_t)rep * 2 * kRec * 32;
+  for (int it = 0; it < nloop; ++it) {
+    float* rec = recbase + (it & 1) * kRec * 32;
+    const int ch = blockIdx.x * reps + rep + it * gridDim.x * reps;
+    if (ln == 0) {
+      // ---------------- real part (producer) ----------------
       const int px = (ch << 5) + lid;
-      if (px >= npx) continue;
-      const int u = px % lv.W, v = px / lv.W;
-      if (u >= lv.W - 1 || v >= lv.H - 1) continue;
-      const float d0 = D[px], dxp = D[px + 1], dyp = D[px + lv.W];
-      if (!(d0 > 0.f && dxp > 0.f && dyp > 0.f)) continue;
+      bool ok = px < npx;
+      const int u = ok ? px % lv.W : 0, v = ok ? px / lv.W : 0;
+      ok = ok && u < lv.W - 1 && v < lv.H - 1;
+      float d0 = 0.f, dxp = 0.f, dyp = 0.f;
+      if (ok) {
+        d0 = D[px];
+        dxp = D[px + 1];
+        dyp = D[px + lv.W];
+      }
+      ok = ok && d0 > 0.f && dxp > 0.f && dyp > 0.f;
+      const float* T = sT[0];
+      const float* P = sP[0];
       const float rx = (u - lv.cx) / lv.fx, ry = (v - lv.cy) / lv.fy;
       const float rx1 = (u + 1 - lv.cx) / lv.fx, ry1 = (v + 1 - lv.cy) / lv.fy;
       const float V[3] = {d0 * rx, d0 * ry, d0};
@@ -155,97 +182,160 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
       const float ey[3] = {dyp * rx - V[0], dyp * ry1 - V[1], dyp - V[2]};
       const float c[3] = {ex[1] * ey[2] - ex[2] * ey[1], ex[2] * ey[0] - ex[0] * ey[2], ex[0] * ey[1] - ex[1] * ey[0]};
       const float n2m = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-      if (!(n2m > 0.f)) continue;
-      const float inm = 1.f / sqrtf(n2m);
+      ok = ok && n2m > 0.f;
+      const float inm = ok ? 1.f / sqrtf(n2m) : 0.f;
       const float Nm[3] = {c[0] * inm, c[1] * inm, c[2] * inm};
-      // p' = T_j V
       float pp[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) pp[r] = T[4 * r] * V[0] + T[4 * r + 1] * V[1] + T[4 * r + 2] * V[2] + T[4 * r + 3];
-      // previous camera frame: P^T (p' - t_prev)
       const float e0 = pp[0] - P[3], e1 = pp[1] - P[7], e2 = pp[2] - P[11];
       const float pcx = P[0] * e0 + P[4] * e1 + P[8] * e2;
       const float pcy = P[1] * e0 + P[5] * e1 + P[9] * e2;
       const float pcz = P[2] * e0 + P[6] * e1 + P[10] * e2;
-      if (!(pcz > 0.f)) continue;
-      const float iz = 1.f / pcz;
+      ok = ok && pcz > 0.f;
+      const float iz = ok ? 1.f / pcz : 0.f;
       const float qx = pcx * iz, qy = pcy * iz;
       const float ux = lv.fx * qx + lv.cx, uy = lv.fy * qy + lv.cy;
       const float ci = floorf(ux + kCellBias), cj = floorf(uy + kCellBias);
-      if (!(ci >= 0.f && ci <= (float)(lv.W - 2) && cj >= 0.f && cj <= (float)(lv.H - 2))) continue;
-      const int i0 = (int)ci, j0 = (int)cj;
+      ok = ok && ci >= 0.f && ci <= (float)(lv.W - 2) && cj >= 0.f && cj <= (float)(lv.H - 2);
+      const int i0 = ok ? (int)ci : 0, j0 = ok ? (int)cj : 0;
       const float a = ux - ci, bb = uy - cj;
       const size_t t00 = (size_t)(j0 * lv.s) * p.W + (size_t)(i0 * lv.s);
       const size_t t10 = t00 + lv.s, t01 = t00 + (size_t)lv.s * p.W, t11 = t01 + lv.s;
-      const float g00 = mdep[t00], g10 = mdep[t10], g01 = mdep[t01], g11 = mdep[t11];
-      if (!(g00 > 0.f && g10 > 0.f && g01 > 0.f && g11 > 0.f)) continue;
-      if (!(fabsf(g10 - g00) + fabsf(g01 - g00) + fabsf(g11 - g00) < p.disc_gate)) continue;
+      float g00 = 0.f, g10 = 0.f, g01 = 0.f, g11 = 0.f;
+      if (ok) {
+        g00 = mdep[t00];
+        g10 = mdep[t10];
+        g01 = mdep[t01];
+        g11 = mdep[t11];
+      }
+      ok = ok && g00 > 0.f && g10 > 0.f && g01 > 0.f && g11 > 0.f;
+      ok = ok && fabsf(g10 - g00) + fabsf(g01 - g00) + fabsf(g11 - g00) < p.disc_gate;
       const float w00 = (1.f - a) * (1.f - bb), w10 = a * (1.f - bb), w01 = (1.f - a) * bb, w11 = a * bb;
-      float q[3], nn[3];
+      float q[3] = {0.f, 0.f, 0.f}, nn[3] = {0.f, 0.f, 0.f};
+      float dqa[3] = {0.f, 0.f, 0.f}, dqb[3] = {0.f, 0.f, 0.f}, dna[3] = {0.f, 0.f, 0.f}, dnb[3] = {0.f, 0.f, 0.f};
+      if (ok) {
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const float* Vp = mV + (size_t)r * hw0;
-        const float* Np = mN + (size_t)r * hw0;
-        q[r] = w00 * Vp[t00] + w10 * Vp[t10] + w01 * Vp[t01] + w11 * Vp[t11];
-        nn[r] = w00 * Np[t00] + w10 * Np[t10] + w01 * Np[t01] + w11 * Np[t11];
+        for (int r = 0; r < 3; ++r) {
+          const float* Vp = mV + (size_t)r * hw0;
+          const float* Np = mN + (size_t)r * hw0;
+          const float v00 = Vp[t00], v10 = Vp[t10], v01 = Vp[t01], v11 = Vp[t11];
+          const float m00 = Np[t00], m10 = Np[t10], m01 = Np[t01], m11 = Np[t11];
+          q[r] = w00 * v00 + w10 * v10 + w01 * v01 + w11 * v11;
+          nn[r] = w00 * m00 + w10 * m10 + w01 * m01 + w11 * m11;
+          dqa[r] = (1.f - bb) * (v10 - v00) + bb * (v11 - v01);
+          dqb[r] = (1.f - a) * (v01 - v00) + a * (v11 - v10);
+          dna[r] = (1.f - bb) * (m10 - m00) + bb * (m11 - m01);
+          dnb[r] = (1.f - a) * (m01 - m00) + a * (m11 - m10);
+        }
       }
       const float df[3] = {pp[0] - q[0], pp[1] - q[1], pp[2] - q[2]};
-      if (!(df[0] * df[0] + df[1] * df[1] + df[2] * df[2] <= p.dist_gate2)) continue;
+      ok = ok && df[0] * df[0] + df[1] * df[1] + df[2] * df[2] <= p.dist_gate2;
       float nw[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) nw[r] = T[4 * r] * Nm[0] + T[4 * r + 1] * Nm[1] + T[4 * r + 2] * Nm[2];
       const float nl2 = nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2];
-      if (!(fabsf(nw[0] * nn[0] + nw[1] * nn[1] + nw[2] * nn[2]) >= p.cos_normal_gate * sqrtf(nl2))) continue;
+      ok = ok && fabsf(nw[0] * nn[0] + nw[1] * nn[1] + nw[2] * nn[2]) >= p.cos_normal_gate * sqrtf(nl2);
       const float res = df[0] * nn[0] + df[1] * nn[1] + df[2] * nn[2];
       const float J[6] = {pp[1] * nn[2] - pp[2] * nn[1], pp[2] * nn[0] - pp[0] * nn[2], pp[0] * nn[1] - pp[1] * nn[0],
                           nn[0], nn[1], nn[2]};
-      if (ln == 0) {
+      if (ok) {
         ++cnt;
         const float hJ[6] = {0.5f * J[0], 0.5f * J[1], 0.5f * J[2], 0.5f * J[3], 0.5f * J[4], 0.5f * J[5]};
         accum(acc, hJ, 0.5f * res, J, res);
-        continue;
       }
-      // ---------------- tangent of lane `ln` ----------------
-      const float* Tl = sT[ln];
-      const float* Pl = sP[ln];
-      const float dDl = p.dD[ln];
-      // measured vertex tangent (DEPTH lanes move every depth by dD); the measured normal enters
-      // only the (real) normal gate, so its tangent is not needed
-      const float Vl[3] = {dDl * rx, dDl * ry, dDl};
-      float ppl[3];
+      if (L > 1) {
+        float* R_ = rec + lid;
+        R_[RV * 32] = __int_as_float(ok ? 1 : 0);
+        if (ok) {
+          R_[RD * 32] = d0;
+          R_[RRX * 32] = rx;
+          R_[RRY * 32] = ry;
+          R_[RE * 32] = e0;
+          R_[(RE + 1) * 32] = e1;
+          R_[(RE + 2) * 32] = e2;
+          R_[RQX * 32] = qx;
+          R_[RQY * 32] = qy;
+          R_[RIZ * 32] = iz;
+          R_[RA * 32] = a;
+          R_[RB * 32] = bb;
+          R_[RT * 32] = __int_as_float((int)t00);
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
-        ppl[r] = Tl[4 * r] * V[0] + Tl[4 * r + 1] * V[1] + Tl[4 * r + 2] * V[2] + Tl[4 * r + 3] +
-                 T[4 * r] * Vl[0] + T[4 * r + 1] * Vl[1] + T[4 * r + 2] * Vl[2];
-      const float el0 = ppl[0] - Pl[3], el1 = ppl[1] - Pl[7], el2 = ppl[2] - Pl[11];
-      const float pcxl = Pl[0] * e0 + Pl[4] * e1 + Pl[8] * e2 + P[0] * el0 + P[4] * el1 + P[8] * el2;
-      const float pcyl = Pl[1] * e0 + Pl[5] * e1 + Pl[9] * e2 + P[1] * el0 + P[5] * el1 + P[9] * el2;
-      const float pczl = Pl[2] * e0 + Pl[6] * e1 + Pl[10] * e2 + P[2] * el0 + P[6] * el1 + P[10] * el2;
-      const float al = lv.fx * (pcxl - qx * pczl) * iz;
-      const float bl = lv.fy * (pcyl - qy * pczl) * iz;
-      const float w00l = -al * (1.f - bb) - (1.f - a) * bl, w10l = al * (1.f - bb) - a * bl;
-      const float w01l = -al * bb + (1.f - a) * bl, w11l = al * bb + a * bl;
-      const float* mVl = mV + (size_t)(3 * ln) * hw0;
-      const float* mNl = mN + (size_t)(3 * ln) * hw0;
-      float ql[3], nl[3];
+          for (int r = 0; r < 3; ++r) {
+            R_[(RPP + r) * 32] = pp[r];
+            R_[(RN + r) * 32] = nn[r];
+            R_[(RDF + r) * 32] = df[r];
+            R_[(RDQA + r) * 32] = dqa[r];
+            R_[(RDQB + r) * 32] = dqb[r];
+            R_[(RDNA + r) * 32] = dna[r];
+            R_[(RDNB + r) * 32] = dnb[r];
+          }
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const float* Vp = mV + (size_t)r * hw0;
-        const float* Np = mN + (size_t)r * hw0;
-        const float* Vpl = mVl + (size_t)r * hw0;
-        const float* Npl = mNl + (size_t)r * hw0;
-        ql[r] = w00l * Vp[t00] + w10l * Vp[t10] + w01l * Vp[t01] + w11l * Vp[t11] + w00 * Vpl[t00] + w10 * Vpl[t10] +
-                w01 * Vpl[t01] + w11 * Vpl[t11];
-        nl[r] = w00l * Np[t00] + w10l * Np[t10] + w01l * Np[t01] + w11l * Np[t11] + w00 * Npl[t00] + w10 * Npl[t10] +
-                w01 * Npl[t01] + w11 * Npl[t11];
+          for (int r = 0; r < 6; ++r) R_[(RJ + r) * 32] = J[r];
+          R_[RRES * 32] = res;
+        }
       }
-      const float dfl[3] = {ppl[0] - ql[0], ppl[1] - ql[1], ppl[2] - ql[2]};
-      const float resl = dfl[0] * nn[0] + dfl[1] * nn[1] + dfl[2] * nn[2] + df[0] * nl[0] + df[1] * nl[1] + df[2] * nl[2];
-      const float Jl[6] = {ppl[1] * nn[2] - ppl[2] * nn[1] + pp[1] * nl[2] - pp[2] * nl[1],
-                           ppl[2] * nn[0] - ppl[0] * nn[2] + pp[2] * nl[0] - pp[0] * nl[2],
-                           ppl[0] * nn[1] - ppl[1] * nn[0] + pp[0] * nl[1] - pp[1] * nl[0],
-                           nl[0], nl[1], nl[2]};
-      accum(acc, J, res, Jl, resl);
+    }
+    if (L > 1) named_barrier(1 + rep, 32 * L);
+    if (ln > 0) {
+      // ---------------- tangent of lane `ln` (consumer) ----------------
+      const float* R_ = rec + lid;
+      if (__float_as_int(R_[RV * 32])) {
+        const float* T = sT[0];
+        const float* P = sP[0];
+        const float* Tl = sT[ln];
+        const float* Pl = sP[ln];
+        const float d0 = R_[RD * 32], rx = R_[RRX * 32], ry = R_[RRY * 32];
+        const float V[3] = {d0 * rx, d0 * ry, d0};
+        const float dDl = p.dD[ln];
+        const float Vl[3] = {dDl * rx, dDl * ry, dDl};
+        const float e0 = R_[RE * 32], e1 = R_[(RE + 1) * 32], e2 = R_[(RE + 2) * 32];
+        const float qx = R_[RQX * 32], qy = R_[RQY * 32], iz = R_[RIZ * 32];
+        const float a = R_[RA * 32], bb = R_[RB * 32];
+        const size_t t00 = (size_t)__float_as_int(R_[RT * 32]);
+        const size_t t10 = t00 + lv.s, t01 = t00 + (size_t)lv.s * p.W, t11 = t01 + lv.s;
+        float pp[3], nn[3], df[3], J[6];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          pp[r] = R_[(RPP + r) * 32];
+          nn[r] = R_[(RN + r) * 32];
+          df[r] = R_[(RDF + r) * 32];
+        }
+#pragma unroll
+        for (int r = 0; r < 6; ++r) J[r] = R_[(RJ + r) * 32];
+        const float res = R_[RRES * 32];
+        float ppl[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          ppl[r] = Tl[4 * r] * V[0] + Tl[4 * r + 1] * V[1] + Tl[4 * r + 2] * V[2] + Tl[4 * r + 3] +
+                   T[4 * r] * Vl[0] + T[4 * r + 1] * Vl[1] + T[4 * r + 2] * Vl[2];
+        const float el0 = ppl[0] - Pl[3], el1 = ppl[1] - Pl[7], el2 = ppl[2] - Pl[11];
+        const float pcxl = Pl[0] * e0 + Pl[4] * e1 + Pl[8] * e2 + P[0] * el0 + P[4] * el1 + P[8] * el2;
+        const float pcyl = Pl[1] * e0 + Pl[5] * e1 + Pl[9] * e2 + P[1] * el0 + P[5] * el1 + P[9] * el2;
+        const float pczl = Pl[2] * e0 + Pl[6] * e1 + Pl[10] * e2 + P[2] * el0 + P[6] * el1 + P[10] * el2;
+        const float al = lv.fx * (pcxl - qx * pczl) * iz;
+        const float bl = lv.fy * (pcyl - qy * pczl) * iz;
+        const float w00 = (1.f - a) * (1.f - bb), w10 = a * (1.f - bb), w01 = (1.f - a) * bb, w11 = a * bb;
+        const float* mVl = mV + (size_t)(3 * ln) * hw0;
+        const float* mNl = mN + (size_t)(3 * ln) * hw0;
+        float ql[3], nl[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const float* Vpl = mVl + (size_t)r * hw0;
+          const float* Npl = mNl + (size_t)r * hw0;
+          ql[r] = R_[(RDQA + r) * 32] * al + R_[(RDQB + r) * 32] * bl + w00 * Vpl[t00] + w10 * Vpl[t10] +
+                  w01 * Vpl[t01] + w11 * Vpl[t11];
+          nl[r] = R_[(RDNA + r) * 32] * al + R_[(RDNB + r) * 32] * bl + w00 * Npl[t00] + w10 * Npl[t10] +
+                  w01 * Npl[t01] + w11 * Npl[t11];
+        }
+        const float dfl[3] = {ppl[0] - ql[0], ppl[1] - ql[1], ppl[2] - ql[2]};
+        const float resl = dfl[0] * nn[0] + dfl[1] * nn[1] + dfl[2] * nn[2] + df[0] * nl[0] + df[1] * nl[1] + df[2] * nl[2];
+        const float Jl[6] = {ppl[1] * nn[2] - ppl[2] * nn[1] + pp[1] * nl[2] - pp[2] * nl[1],
+                             ppl[2] * nn[0] - ppl[0] * nn[2] + pp[2] * nl[0] - pp[0] * nl[2],
+                             ppl[0] * nn[1] - ppl[1] * nn[0] + pp[0] * nl[1] - pp[1] * nl[0],
+                             nl[0], nl[1], nl[2]};
+        accum(acc, J, res, Jl, resl);
+      }
     }
   }
 
@@ -431,11 +521,20 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   }
 }
 
-cudaError_t icp_configure() { return cudaSuccess; }
+static size_t icp_rec_bytes(int reps) { return sizeof(float) * (size_t)reps * 2 * kRec * 32; }
+
+cudaError_t icp_configure() {
+  return cudaFuncSetAttribute(k_icp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)icp_rec_bytes(kMaxReps));
+}
+
+int icp_reps(int L) {
+  int reps = 16 / L;
+  if (reps > kMaxReps) reps = kMaxReps;
+  return reps < 1 ? 1 : reps;
+}
 
 int icp_blocks(int level_pixels, int L) {
-  int reps = 16 / L;
-  if (reps < 1) reps = 1;
+  const int reps = icp_reps(L);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -457,10 +556,9 @@ cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int flags, 
   lv.fy = p.fy / lv.s;
   lv.cx = p.cx / lv.s;
   lv.cy = p.cy / lv.s;
-  int reps = 16 / p.L;
-  if (reps < 1) reps = 1;
+  int reps = icp_reps(p.L);
   const int threads = 32 * p.L * reps;
-  k_icp<<<nblk, threads, 0, s>>>(p, b, lv, flags, reps);
+  k_icp<<<nblk, threads, icp_rec_bytes(reps), s>>>(p, b, lv, flags, reps);
   return cudaGetLastError();
 }
 

@@ -78,6 +78,7 @@ cudaError_t launch_readout(const Params& p, const Buffers& b, cudaStream_t s);
 cudaError_t launch_loss(const Params& p, const Buffers& b, const float* depth, const float* model,
                         const double* pose, double* out, int nblk, cudaStream_t s);
 int icp_blocks(int level_pixels, int L);
+int icp_reps(int L);
 cudaError_t icp_configure();
 
 // ICP iteration flags
