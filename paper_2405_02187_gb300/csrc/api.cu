@@ -140,6 +140,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   Params& p = h->p;
   memset(&p, 0, sizeof(p));
   p.nx = nx; p.ny = ny; p.nz = nz;
+  p.bnx = (nx + 7) / 8; p.bny = (ny + 7) / 8; p.bnz = (nz + 7) / 8;
   p.voxel = voxel_m; p.mu = trunc_m;
   p.ox = origin_m[0]; p.oy = origin_m[1]; p.oz = origin_m[2];
   p.w_max = c.w_max;
@@ -200,6 +201,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   ok &= cudaMalloc(&b.status, sizeof(int) * 4) == cudaSuccess;
   ok &= cudaMalloc(&b.result, sizeof(double) * kResLen) == cudaSuccess;
   ok &= cudaMalloc(&b.stats, sizeof(unsigned long long) * 2) == cudaSuccess;
+  ok &= cudaMalloc(&b.bricks, (size_t)p.bnx * p.bny * p.bnz) == cudaSuccess;
   ok &= cudaMalloc(&h->d_kinds, sizeof(int) * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&h->d_index, sizeof(int) * kMaxLanes) == cudaSuccess;
   if (max_lanes >= 6) ok &= cudaMalloc(&h->model_q, sizeof(float) * hw * (1 + 6 * 7)) == cudaSuccess;
@@ -230,7 +232,7 @@ extern "C" xslam_status xslam_destroy(xslam_t h) {
   cudaFree(b.F); cudaFree(b.Wt); cudaFree(b.depth_in); cudaFree(b.gated);
   for (int l = 0; l < 3; ++l) cudaFree(b.pyr[l]);
   cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp);
-  cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats);
+  cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.bricks);
   for (int st = 0; st < XSLAM_NSTAGE; ++st)
     for (int i = 0; i < kProfRing; ++i)
       for (int k = 0; k < 2; ++k)
@@ -280,6 +282,7 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   CU(cudaMemsetAsync(h->b.pose + 12, 0, sizeof(double) * 12 * (kMaxLanes - 1), h->s));
   CU(cudaMemsetAsync(h->b.result, 0, sizeof(double) * kResLen, h->s));
   CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * 2, h->s));
+  CU(cudaMemsetAsync(h->b.bricks, 2, (size_t)h->p.bnx * h->p.bny * h->p.bnz, h->s));  // all unobserved
   h->frame = 0;
   h->K = 0;
   h->p.L = 1;
@@ -579,6 +582,7 @@ extern "C" xslam_status xslam_write_tsdf(xslam_t h, int lane, const float* in) {
     k_mark_unobserved<<<g, 256, 0, h->s>>>(h->b.F, h->b.Wt, n);
     CU(cudaGetLastError());
   }
+  if (lane <= 0) CU(launch_brick_flags(h->p, h->b, h->s));
   st = leave(h);
   CU(cudaStreamSynchronize(h->s));
   return st;

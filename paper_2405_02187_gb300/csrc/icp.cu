@@ -124,10 +124,11 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   __shared__ double s_half[2 * kNT * kMaxLanes];
   __shared__ float sAf[kNT * kMaxLanes];
   __shared__ float sxf[kMaxLanes][6], srf[kMaxLanes][6], sdf[kMaxLanes][6];
-  __shared__ SeCoef sco[kMaxLanes];
-  __shared__ double sE[kMaxLanes][12];
+  __shared__ SeCoefF scf[kMaxLanes];
+  __shared__ float sxs[kMaxLanes][6];
+  __shared__ float sdl[kMaxLanes][12];
   __shared__ int s_ncorr, s_fail;
-  extern __shared__ float s_rec[];  // [rep][buffer][field][pixel]: dynamic, reps * 2 * kRec * 32 floats
+  extern __shared__ float s_rec[];  // [rep][chunk of the group][field][pixel]: reps * L * kRec * 32 floats
 
   if (threadIdx.x == 0) s_skip = b.status[0];
   for (int i = threadIdx.x; i < L * 12; i += blockDim.x) {
@@ -141,27 +142,31 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   for (int q = 0; q < kNT; ++q) acc[q] = 0.f;
   int cnt = 0;
 
-  // Pixel chunks of 32 flow through each replica: the real warp computes a chunk's correspondences
-  // into a shared-memory record (double-buffered), a named barrier hands it to the lane warps, which
-  // add their tangents while the real warp computes the next chunk.
-  int nloop = 0;
+  // Work unit: a group of L chunks of 32 pixels per replica. Every warp of the replica computes the
+  // real part of one chunk of the group (correspondence, residual, Jacobian, bilinear derivatives) into
+  // a shared-memory record; after a named barrier every warp reads all L records and adds the sums of
+  // its own lane: lane 0 the real normal equations, lane l > 0 their tangent, for which it loads only
+  // lane l's model taps. A second barrier frees the records for the next group.
+  int nloop = 0, gbase = 0, gstride = 1;
   const int npx = lv.W * lv.H;
   const int nchunk = (npx + 31) >> 5;
   {
-    const int base = blockIdx.x * reps + rep, stride = gridDim.x * reps;
-    nloop = (!s_skip && base < nchunk) ? (nchunk - base + stride - 1) / stride : 0;
+    const int ngroup = (nchunk + L - 1) / L;
+    gbase = blockIdx.x * reps + rep;
+    gstride = gridDim.x * reps;
+    nloop = (!s_skip && gbase < ngroup) ? (ngroup - gbase + gstride - 1) / gstride : 0;
   }
   const float* D = lv.s == 1 ? b.pyr[0] : (lv.s == 2 ? b.pyr[1] : b.pyr[2]);
   const size_t hw0 = (size_t)p.W * p.H;
   const float* mdep = b.model;
   const float* mV = b.model + hw0;
   const float* mN = b.model + hw0 * (1 + 3 * L);
-  float* recbase = s_rec + (size_t)rep * 2 * kRec * 32;
+  float* recs = s_rec + (size_t)rep * L * kRec * 32;
   for (int it = 0; it < nloop; ++it) {
-    float* rec = recbase + (it & 1) * kRec * 32;
-    const int ch = blockIdx.x * reps + rep + it * gridDim.x * reps;
-    if (ln == 0) {
-      // ---------------- real part (producer) ----------------
+    const int ch = (gbase + it * gstride) * L + ln;
+    {
+      // ---------------- real part (every warp produces one chunk's records) ----------------
+      float* rec = recs + ln * kRec * 32;
       const int px = (ch << 5) + lid;
       bool ok = px < npx;
       const int u = ok ? px % lv.W : 0, v = ok ? px / lv.W : 0;
@@ -239,12 +244,7 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
       const float res = df[0] * nn[0] + df[1] * nn[1] + df[2] * nn[2];
       const float J[6] = {pp[1] * nn[2] - pp[2] * nn[1], pp[2] * nn[0] - pp[0] * nn[2], pp[0] * nn[1] - pp[1] * nn[0],
                           nn[0], nn[1], nn[2]};
-      if (ok) {
-        ++cnt;
-        const float hJ[6] = {0.5f * J[0], 0.5f * J[1], 0.5f * J[2], 0.5f * J[3], 0.5f * J[4], 0.5f * J[5]};
-        accum(acc, hJ, 0.5f * res, J, res);
-      }
-      if (L > 1) {
+      {
         float* R_ = rec + lid;
         R_[RV * 32] = __int_as_float(ok ? 1 : 0);
         if (ok) {
@@ -276,11 +276,20 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
         }
       }
     }
-    if (L > 1) named_barrier(1 + rep, 32 * L);
-    if (ln > 0) {
-      // ---------------- tangent of lane `ln` (consumer) ----------------
-      const float* R_ = rec + lid;
-      if (__float_as_int(R_[RV * 32])) {
+    named_barrier(1 + rep, 32 * L);
+    for (int j = 0; j < L; ++j) {
+      // ---------------- lane `ln` of the records of chunk j (consumer) ----------------
+      const float* R_ = recs + j * kRec * 32 + lid;
+      if (!__float_as_int(R_[RV * 32])) continue;
+      if (ln == 0) {
+        ++cnt;
+        float J[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) J[r] = R_[(RJ + r) * 32];
+        const float res = R_[RRES * 32];
+        const float hJ[6] = {0.5f * J[0], 0.5f * J[1], 0.5f * J[2], 0.5f * J[3], 0.5f * J[4], 0.5f * J[5]};
+        accum(acc, hJ, 0.5f * res, J, res);
+      } else {
         const float* T = sT[0];
         const float* P = sP[0];
         const float* Tl = sT[ln];
@@ -337,6 +346,7 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
         accum(acc, J, res, Jl, resl);
       }
     }
+    named_barrier(1 + rep, 32 * L);
   }
 
   // ---------------- block reduction ----------------
@@ -483,27 +493,27 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   if (lane_thread) sx[ls][li] = (double)sxf[ls][li] + (double)sdf[ls][li];
   __syncthreads();
 
-  // pose update T <- exp(x) T on every lane, FP64: series coefficients once per lane, then one thread
-  // per (lane, element) for exp(x) and one per (lane, element) for the product
-  if (go && t < L) se3_coef_lane(sx[0], sx[t], sco[t]);
+  // pose update T <- exp(x) T on every lane: delta = exp(x) - I in FP32 (coefficients once per lane,
+  // then one thread per (lane, element)), T + delta T composed in FP64 one element per thread
+  if (go && t < 6 * L) sxs[t / 6][t % 6] = (float)sx[t / 6][t % 6];
+  __syncthreads();
+  if (go && t < L) se3_coef_lane_f(sxs[0], sxs[t], scf[t]);
   __syncthreads();
   if (go && t < 12 * L) {
     const int l = t / 12, e = t % 12;
-    sE[l][e] = se3_exp_element(sx[0], sx[l], sco[l], l > 0, e);
+    sdl[l][e] = se3_delta_element(sxs[0], sxs[l], scf[l], l > 0, e);
   }
   __syncthreads();
   double tn = 0.0;
   if (go && t < 12 * L) {
     const int l = t / 12, e = t % 12, r = e >> 2, c = e & 3;
     const double* T0 = b.pose;
-    if (l == 0) {
-      tn = sE[0][4 * r] * T0[c] + sE[0][4 * r + 1] * T0[4 + c] + sE[0][4 * r + 2] * T0[8 + c] + (c == 3 ? sE[0][4 * r + 3] : 0.0);
-    } else {
-      const double* Tl = b.pose + 12 * l;
-      tn = sE[l][4 * r] * T0[c] + sE[l][4 * r + 1] * T0[4 + c] + sE[l][4 * r + 2] * T0[8 + c] +
-           sE[0][4 * r] * Tl[c] + sE[0][4 * r + 1] * Tl[4 + c] + sE[0][4 * r + 2] * Tl[8 + c] +
-           (c == 3 ? sE[l][4 * r + 3] : 0.0);
-    }
+    const double* Tl = b.pose + 12 * l;
+    // lane 0: T0 + d0 T0; lane l: Tl + dl T0 + d0 Tl (translation column adds the delta's own column)
+    tn = Tl[e] + (double)sdl[l][4 * r] * T0[c] + (double)sdl[l][4 * r + 1] * T0[4 + c] +
+         (double)sdl[l][4 * r + 2] * T0[8 + c] + (c == 3 ? (double)sdl[l][4 * r + 3] : 0.0);
+    if (l > 0)
+      tn += (double)sdl[0][4 * r] * Tl[c] + (double)sdl[0][4 * r + 1] * Tl[4 + c] + (double)sdl[0][4 * r + 2] * Tl[8 + c];
   }
   __syncthreads();
   if (go && t < 12 * L) b.pose[t] = tn;
@@ -521,10 +531,10 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   }
 }
 
-static size_t icp_rec_bytes(int reps) { return sizeof(float) * (size_t)reps * 2 * kRec * 32; }
+static size_t icp_rec_bytes(int reps, int L) { return sizeof(float) * (size_t)reps * L * kRec * 32; }
 
 cudaError_t icp_configure() {
-  return cudaFuncSetAttribute(k_icp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)icp_rec_bytes(kMaxReps));
+  return cudaFuncSetAttribute(k_icp, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
 }
 
 int icp_reps(int L) {
@@ -558,7 +568,7 @@ cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int flags, 
   lv.cy = p.cy / lv.s;
   int reps = icp_reps(p.L);
   const int threads = 32 * p.L * reps;
-  k_icp<<<nblk, threads, icp_rec_bytes(reps), s>>>(p, b, lv, flags, reps);
+  k_icp<<<nblk, threads, icp_rec_bytes(reps, p.L), s>>>(p, b, lv, flags, reps);
   return cudaGetLastError();
 }
 

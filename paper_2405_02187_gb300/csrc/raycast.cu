@@ -11,6 +11,11 @@
 // (widened by one sample), which visits every valid sample in the same order. An unobserved voxel
 // holds F = kUnobserved (> 1, outside the range of any observed average), so a sample's validity
 // and value come from the 8 F loads alone.
+// Free space is crossed brick by brick: if a sample's trilinear cell lies inside one 8^3 brick whose
+// voxels all hold exactly F = 1 (or are all unobserved), every later sample whose cell stays inside
+// that brick has F = 1 exactly (or is invalid), so no pair among them can be a hit or end the ray;
+// the march jumps to the last such sample. The brick's cell box is convex and each coordinate of the
+// sample position is monotone in the sample index, so checking the last sample is enough.
 #include "internal.cuh"
 
 namespace xslam {
@@ -76,7 +81,8 @@ __device__ __forceinline__ float tri_lane(const Params& p, const float* __restri
 __global__ void __launch_bounds__(256) k_raycast(Params p, const float* __restrict__ F, const float* __restrict__ Wt,
                                                  const double* __restrict__ pose, float* __restrict__ out_depth,
                                                  float* __restrict__ vmap, float* __restrict__ nmap, int ignore_imag,
-                                                 double* __restrict__ pose_prev, unsigned long long* __restrict__ hits) {
+                                                 double* __restrict__ pose_prev, unsigned long long* __restrict__ hits,
+                                                 const unsigned char* __restrict__ bricks) {
   __shared__ float sT[kMaxLanes][12];
   for (int i = threadIdx.x + blockDim.x * threadIdx.y; i < p.L * 12; i += blockDim.x * blockDim.y) {
     sT[i / 12][i % 12] = (float)pose[i];
@@ -123,8 +129,48 @@ __global__ void __launch_bounds__(256) k_raycast(Params p, const float* __restri
   bool prev_valid = false, prev_pos = false;
   for (int m = m_lo; m <= m_hi; ++m) {
     const float al = m * p.ray_step;
+    const float gx = g0x + al * gdx, gy = g0y + al * gdy, gz = g0z + al * gdz;
+    if (bricks && gx >= 0.f && gx < (float)(p.nx - 1) && gy >= 0.f && gy < (float)(p.ny - 1) && gz >= 0.f &&
+        gz < (float)(p.nz - 1)) {
+      const int ci = (int)gx, cj = (int)gy, ck = (int)gz;
+      if ((ci & 7) != 7 && (cj & 7) != 7 && (ck & 7) != 7) {
+        const int bi = ci >> 3, bj = cj >> 3, bk = ck >> 3;
+        const unsigned fl = __ldg(bricks + bi + p.bnx * (bj + p.bny * bk));
+        if (fl == 1u || fl == 2u) {
+          // last sample whose cell stays in the brick's interior: min corner in [8b, 8b + 6] per axis
+          const float g0[3] = {g0x, g0y, g0z}, gd[3] = {gdx, gdy, gdz};
+          const int lo[3] = {8 * bi, 8 * bj, 8 * bk};
+          const int nn[3] = {p.nx, p.ny, p.nz};
+          float a_end = (m_hi + 1) * p.ray_step;
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) {
+            const int hi = min(lo[ax] + 7, nn[ax] - 1);  // g < hi keeps the cell in the brick and the volume
+            if (gd[ax] > 0.f) a_end = fminf(a_end, ((float)hi - g0[ax]) / gd[ax]);
+            else if (gd[ax] < 0.f) a_end = fminf(a_end, ((float)lo[ax] - g0[ax]) / gd[ax]);
+          }
+          int m2 = min(m_hi, (int)ceilf(a_end / p.ray_step));
+          for (; m2 > m; --m2) {  // confirm with the sample positions the march itself computes
+            const float a2 = m2 * p.ray_step;
+            const float hx = g0x + a2 * gdx, hy = g0y + a2 * gdy, hz = g0z + a2 * gdz;
+            if (hx >= (float)lo[0] && hx < (float)min(lo[0] + 7, p.nx - 1) && hy >= (float)lo[1] &&
+                hy < (float)min(lo[1] + 7, p.ny - 1) && hz >= (float)lo[2] && hz < (float)min(lo[2] + 7, p.nz - 1))
+              break;
+          }
+          if (fl == 1u) {
+            if (prev_valid && !prev_pos) break;  // entering observed free space from behind a surface
+            prev_valid = true;
+            prev_pos = true;
+          } else {
+            prev_valid = false;
+            prev_pos = false;
+          }
+          m = m2;
+          continue;
+        }
+      }
+    }
     Tri t;
-    const bool ok = tri_real(p, F, g0x + al * gdx, g0y + al * gdy, g0z + al * gdz, t, false);
+    const bool ok = tri_real(p, F, gx, gy, gz, t, false);
     if (prev_valid && ok) {
       const bool pos = t.val > 0.f;
       if (prev_pos && !pos) {
@@ -236,7 +282,7 @@ cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose
                            float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s) {
   dim3 blk(32, 8), grd((p.W + 31) / 32, (p.H + 7) / 8);
   k_raycast<<<grd, blk, 0, s>>>(p, b.F, b.Wt, pose, depth, vmap, nmap, ignore_imag_volume ? 1 : 0,
-                                set_prev ? b.pose_prev : nullptr, set_prev ? b.stats + 1 : nullptr);
+                                set_prev ? b.pose_prev : nullptr, set_prev ? b.stats + 1 : nullptr, b.bricks);
   return cudaGetLastError();
 }
 

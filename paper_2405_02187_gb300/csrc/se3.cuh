@@ -1,5 +1,8 @@
-// FP64 SE(3) exponential with one tangent direction (X-SLAM Sec. 4.1, Eq. lie, rotvector,
-// rotation_jacobi), for the pose update T <- exp(x) T of ICP, evaluated one matrix element per thread.
+// SE(3) exponential with one tangent direction (X-SLAM Sec. 4.1, Eq. lie, rotvector, rotation_jacobi)
+// for the pose update T <- exp(x) T of ICP, evaluated one matrix element per thread. The ICP step x is
+// small, so the update is formed as exp(x) = I + delta with delta computed in FP32 (its relative
+// precision is what matters) and T <- T + delta T composed in FP64; FP64 variants are kept for
+// reference use.
 //
 // exp([phi, rho]) = [R | V rho] with R = I + A [phi] + B [phi]^2 and V = I + B [phi] + C [phi]^2,
 // A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3, th^2 = phi.phi; this is the
@@ -106,6 +109,88 @@ __device__ __forceinline__ double se3_exp_element(const double* x0, const double
     } else {
       const double V1 = k.dB * hat_el(x0, r, q) + k.B * hat_el(x1, r, q) + k.dC * hat2_el(x0, r, q) +
                         k.C * hat2_tan(x0, x1, r, q);
+      s += V1 * x0[3 + q] + V * x1[3 + q];
+    }
+  }
+  return s;
+}
+
+// ---- FP32 increment: delta = exp(x) - I for the small ICP step x, composed in FP64 by the caller ----
+// A, B, C of exp and their tangents in FP32 (series for theta^2 < 1/4, closed form above)
+struct SeCoefF {
+  float A, B, C, dA, dB, dC;
+};
+
+template <int N>
+__device__ __forceinline__ void series_f(float x, int s, float& v, float& dv) {
+  constexpr float inv_fact[16] = {1.f, 1.f, 1.f / 2, 1.f / 6, 1.f / 24, 1.f / 120, 1.f / 720, 1.f / 5040,
+                                  1.f / 40320, 1.f / 362880, 1.f / 3628800, 1.f / 39916800, 1.f / 479001600,
+                                  1.f / 6227020800.f, 1.f / 87178291200.f, 1.f / 1307674368000.f};
+  v = ((N & 1) ? -1.f : 1.f) * inv_fact[2 * N + 1 + s];
+  dv = 0.f;
+#pragma unroll
+  for (int n = N - 1; n >= 0; --n) {
+    dv = dv * x + v;
+    v = v * x + ((n & 1) ? -1.f : 1.f) * inv_fact[2 * n + 1 + s];
+  }
+}
+
+__device__ __forceinline__ void se3_coef_lane_f(const float* x0, const float* x1, SeCoefF& out) {
+  const float th2 = x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2];
+  const float dth2 = 2.f * (x0[0] * x1[0] + x0[1] * x1[1] + x0[2] * x1[2]);
+  float A, B, C, dA, dB, dC;
+  if (th2 < 0.25f) {  // terms up to x^6: truncation below 2e-12 relative for x < 1/4
+    series_f<6>(th2, 0, A, dA);
+    series_f<6>(th2, 1, B, dB);
+    series_f<6>(th2, 2, C, dC);
+  } else {
+    const float th = sqrtf(th2), s = sinf(th), co = cosf(th);
+    A = s / th;
+    B = (1.f - co) / th2;
+    C = (th - s) / (th2 * th);
+    dA = (th * co - s) / (2.f * th2 * th);
+    dB = (th * s - 2.f * (1.f - co)) / (2.f * th2 * th2);
+    dC = ((1.f - co) * th - 3.f * (th - s)) / (2.f * th2 * th2 * th);
+  }
+  out.A = A;
+  out.B = B;
+  out.C = C;
+  out.dA = dA * dth2;
+  out.dB = dB * dth2;
+  out.dC = dC * dth2;
+}
+
+__device__ __forceinline__ float hat_el_f(const float* v, int r, int k) {
+  if (r == k) return 0.f;
+  if (r == 0) return k == 1 ? -v[2] : v[1];
+  if (r == 1) return k == 0 ? v[2] : -v[0];
+  return k == 0 ? -v[1] : v[0];
+}
+__device__ __forceinline__ float hat2_el_f(const float* v, int r, int k) {
+  return v[r] * v[k] - (r == k ? v[0] * v[0] + v[1] * v[1] + v[2] * v[2] : 0.f);
+}
+__device__ __forceinline__ float hat2_tan_f(const float* v, const float* v1, int r, int k) {
+  return v1[r] * v[k] + v[r] * v1[k] - (r == k ? 2.f * (v[0] * v1[0] + v[1] * v1[1] + v[2] * v1[2]) : 0.f);
+}
+
+// Element e = 4 r + c of exp(x0) - I (tangent = false) or of the tangent of exp along x1 (true).
+__device__ __forceinline__ float se3_delta_element(const float* x0, const float* x1, const SeCoefF& k, bool tangent,
+                                                   int e) {
+  const int r = e >> 2, c = e & 3;
+  if (c < 3) {
+    if (!tangent) return k.A * hat_el_f(x0, r, c) + k.B * hat2_el_f(x0, r, c);
+    return k.dA * hat_el_f(x0, r, c) + k.A * hat_el_f(x1, r, c) + k.dB * hat2_el_f(x0, r, c) +
+           k.B * hat2_tan_f(x0, x1, r, c);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float V = (r == q ? 1.f : 0.f) + k.B * hat_el_f(x0, r, q) + k.C * hat2_el_f(x0, r, q);
+    if (!tangent) {
+      s += V * x0[3 + q];
+    } else {
+      const float V1 = k.dB * hat_el_f(x0, r, q) + k.B * hat_el_f(x1, r, q) + k.dC * hat2_el_f(x0, r, q) +
+                       k.C * hat2_tan_f(x0, x1, r, q);
       s += V1 * x0[3 + q] + V * x1[3 + q];
     }
   }
