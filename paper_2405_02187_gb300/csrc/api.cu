@@ -140,7 +140,6 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   Params& p = h->p;
   memset(&p, 0, sizeof(p));
   p.nx = nx; p.ny = ny; p.nz = nz;
-  p.bnx = (nx + 7) / 8; p.bny = (ny + 7) / 8; p.bnz = (nz + 7) / 8;
   p.voxel = voxel_m; p.mu = trunc_m;
   p.ox = origin_m[0]; p.oy = origin_m[1]; p.oz = origin_m[2];
   p.w_max = c.w_max;
@@ -201,7 +200,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   ok &= cudaMalloc(&b.status, sizeof(int) * 4) == cudaSuccess;
   ok &= cudaMalloc(&b.result, sizeof(double) * kResLen) == cudaSuccess;
   ok &= cudaMalloc(&b.stats, sizeof(unsigned long long) * 2) == cudaSuccess;
-  ok &= cudaMalloc(&b.bricks, (size_t)p.bnx * p.bny * p.bnz) == cudaSuccess;
+  ok &= cudaMalloc(&b.hit, sizeof(int) * hw) == cudaSuccess;
   ok &= cudaMalloc(&h->d_kinds, sizeof(int) * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&h->d_index, sizeof(int) * kMaxLanes) == cudaSuccess;
   if (max_lanes >= 6) ok &= cudaMalloc(&h->model_q, sizeof(float) * hw * (1 + 6 * 7)) == cudaSuccess;
@@ -232,7 +231,7 @@ extern "C" xslam_status xslam_destroy(xslam_t h) {
   cudaFree(b.F); cudaFree(b.Wt); cudaFree(b.depth_in); cudaFree(b.gated);
   for (int l = 0; l < 3; ++l) cudaFree(b.pyr[l]);
   cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp);
-  cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.bricks);
+  cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.hit);
   for (int st = 0; st < XSLAM_NSTAGE; ++st)
     for (int i = 0; i < kProfRing; ++i)
       for (int k = 0; k < 2; ++k)
@@ -282,7 +281,6 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   CU(cudaMemsetAsync(h->b.pose + 12, 0, sizeof(double) * 12 * (kMaxLanes - 1), h->s));
   CU(cudaMemsetAsync(h->b.result, 0, sizeof(double) * kResLen, h->s));
   CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * 2, h->s));
-  CU(cudaMemsetAsync(h->b.bricks, 2, (size_t)h->p.bnx * h->p.bny * h->p.bnz, h->s));  // all unobserved
   h->frame = 0;
   h->K = 0;
   h->p.L = 1;
@@ -384,7 +382,7 @@ static cudaError_t enqueue_first(xslam_t h) {
   if ((e = launch_raycast(h->p, h->b, h->b.pose, h->b.model, h->b.model + hw, h->b.model + hw * (1 + 3 * h->p.L),
                           false, true, h->s)) != cudaSuccess)
     return e;
-  stage_end(h, XSLAM_STAGE_RAYCAST, 1);
+  stage_end(h, XSLAM_STAGE_RAYCAST, 2);
   stage_begin(h, XSLAM_STAGE_OTHER);
   e = launch_readout(h->p, h->b, h->s);
   stage_end(h, XSLAM_STAGE_OTHER, 1);
@@ -418,7 +416,7 @@ static cudaError_t enqueue_track(xslam_t h) {
   if ((e = launch_raycast(h->p, h->b, h->b.pose, h->b.model, h->b.model + hw, h->b.model + hw * (1 + 3 * h->p.L),
                           false, true, h->s)) != cudaSuccess)
     return e;
-  stage_end(h, XSLAM_STAGE_RAYCAST, 1);
+  stage_end(h, XSLAM_STAGE_RAYCAST, 2);
   stage_begin(h, XSLAM_STAGE_OTHER);
   e = launch_readout(h->p, h->b, h->s);
   stage_end(h, XSLAM_STAGE_OTHER, 1);
@@ -582,7 +580,7 @@ extern "C" xslam_status xslam_write_tsdf(xslam_t h, int lane, const float* in) {
     k_mark_unobserved<<<g, 256, 0, h->s>>>(h->b.F, h->b.Wt, n);
     CU(cudaGetLastError());
   }
-  if (lane <= 0) CU(launch_brick_flags(h->p, h->b, h->s));
+
   st = leave(h);
   CU(cudaStreamSynchronize(h->s));
   return st;

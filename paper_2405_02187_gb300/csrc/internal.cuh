@@ -25,7 +25,6 @@ constexpr float kCellBias = 0.015625f;  // 2^-6 pixel: ICP bilinear-cell tie bre
 struct Params {
   // volume
   int nx, ny, nz;
-  int bnx, bny, bnz;        // 8^3 bricks per axis (rounded up)
   float voxel, mu, ox, oy, oz;
   float w_max;              // <= 0: no cap
   // camera (level 0)
@@ -60,7 +59,7 @@ struct Buffers {
   int* status;      // [0] ICP failed in this frame, [1] frames failed since last sync, [2] last n_valid
   double* result;   // read-out: 12 (pose) + 12 K (dpose) + 6 K (dtwist) + 27 L (last system)
   unsigned long long* stats;  // [0] voxels updated by fusion, [1] pixels with a ray-cast surface
-  unsigned char* bricks;      // per 8^3 brick: 1 = every voxel F = 1 exactly, 2 = every voxel unobserved, 0 = mixed
+  int* hit;                   // per pixel: index m of the first sample of the ray-cast hit pair, -1 = none
 };
 
 __host__ __device__ inline size_t vox_count(const Params& p) {
@@ -72,7 +71,6 @@ __host__ __device__ inline size_t vox_count(const Params& p) {
 // ---------------------------------------------------------------------------------------------
 cudaError_t launch_prepare(const Params& p, const Buffers& b, int levels, cudaStream_t s);
 cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s);
-cudaError_t launch_brick_flags(const Params& p, const Buffers& b, cudaStream_t s);
 cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose, float* depth,
                            float* vmap, float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s);
 cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int iter_flags, int nblk, cudaStream_t s);

@@ -11,11 +11,9 @@
 // (widened by one sample), which visits every valid sample in the same order. An unobserved voxel
 // holds F = kUnobserved (> 1, outside the range of any observed average), so a sample's validity
 // and value come from the 8 F loads alone.
-// Free space is crossed brick by brick: if a sample's trilinear cell lies inside one 8^3 brick whose
-// voxels all hold exactly F = 1 (or are all unobserved), every later sample whose cell stays inside
-// that brick has F = 1 exactly (or is invalid), so no pair among them can be a hit or end the ray;
-// the march jumps to the last such sample. The brick's cell box is convex and each coordinate of the
-// sample position is monotone in the sample index, so checking the last sample is enough.
+// Two kernels: k_march (real lane only, small register footprint, many warps per SM to hide the
+// gather latency) records per pixel the index of the hit pair's first sample; k_refine re-evaluates
+// the pair and the six normal samples on every lane and writes the model maps.
 #include "internal.cuh"
 
 namespace xslam {
@@ -78,11 +76,82 @@ __device__ __forceinline__ float tri_lane(const Params& p, const float* __restri
   return v;
 }
 
-__global__ void __launch_bounds__(256) k_raycast(Params p, const float* __restrict__ F, const float* __restrict__ Wt,
-                                                 const double* __restrict__ pose, float* __restrict__ out_depth,
-                                                 float* __restrict__ vmap, float* __restrict__ nmap, int ignore_imag,
-                                                 double* __restrict__ pose_prev, unsigned long long* __restrict__ hits,
-                                                 const unsigned char* __restrict__ bricks) {
+// The ray of pixel (u, v) in continuous voxel coordinates: g(alpha) = g0 + alpha * gd (real pose).
+struct Ray {
+  float rx, ry;               // K^-1 (u, v, 1)
+  float dirx, diry, dirz;     // R K^-1 (u, v, 1)
+  float g0x, g0y, g0z, gdx, gdy, gdz;
+};
+
+__device__ __forceinline__ Ray make_ray(const Params& p, const float* T, int u, int v) {
+  Ray r;
+  r.rx = (u - p.cx) / p.fx;
+  r.ry = (v - p.cy) / p.fy;
+  r.dirx = T[0] * r.rx + T[1] * r.ry + T[2];
+  r.diry = T[4] * r.rx + T[5] * r.ry + T[6];
+  r.dirz = T[8] * r.rx + T[9] * r.ry + T[10];
+  const float inv_vox = 1.f / p.voxel;
+  r.g0x = (T[3] - p.ox) * inv_vox - 0.5f;
+  r.g0y = (T[7] - p.oy) * inv_vox - 0.5f;
+  r.g0z = (T[11] - p.oz) * inv_vox - 0.5f;
+  r.gdx = r.dirx * inv_vox;
+  r.gdy = r.diry * inv_vox;
+  r.gdz = r.dirz * inv_vox;
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_march(Params p, const float* __restrict__ F, const double* __restrict__ pose,
+                                               int* __restrict__ hit) {
+  __shared__ float sT[12];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  if (tid < 12) sT[tid] = (float)pose[tid];
+  __syncthreads();
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  if (u >= p.W || v >= p.H) return;
+  const Ray ry = make_ray(p, sT, u, v);
+  // alpha interval where 0 <= g < n - 1 on every axis (slab test), widened by one sample
+  float lo = p.m0 * p.ray_step, hi = p.m1 * p.ray_step;
+  {
+    const float g0[3] = {ry.g0x, ry.g0y, ry.g0z}, gd[3] = {ry.gdx, ry.gdy, ry.gdz};
+    const int nn[3] = {p.nx, p.ny, p.nz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (gd[a] != 0.f) {
+        const float t1 = (0.f - g0[a]) / gd[a], t2 = ((float)(nn[a] - 1) - g0[a]) / gd[a];
+        lo = fmaxf(lo, fminf(t1, t2));
+        hi = fminf(hi, fmaxf(t1, t2));
+      } else if (!(g0[a] >= 0.f && g0[a] < (float)(nn[a] - 1))) {
+        hi = -1.f;
+      }
+    }
+  }
+  const int m_lo = max(p.m0, (int)floorf(lo / p.ray_step) - 1);
+  const int m_hi = min(p.m1, (int)ceilf(hi / p.ray_step) + 1);
+  int m_hit = -1;
+  bool prev_valid = false, prev_pos = false;
+  for (int m = m_lo; m <= m_hi; ++m) {
+    const float al = m * p.ray_step;
+    Tri t;
+    const bool ok = tri_real(p, F, ry.g0x + al * ry.gdx, ry.g0y + al * ry.gdy, ry.g0z + al * ry.gdz, t, false);
+    if (prev_valid && ok) {
+      const bool pos = t.val > 0.f;
+      if (prev_pos && !pos) {
+        m_hit = m - 1;
+        break;
+      }
+      if (!prev_pos && pos) break;
+    }
+    prev_valid = ok;
+    prev_pos = ok && t.val > 0.f;
+  }
+  hit[(size_t)v * p.W + u] = m_hit;
+}
+
+__global__ void __launch_bounds__(256) k_refine(Params p, const float* __restrict__ F, const double* __restrict__ pose,
+                                                const int* __restrict__ hit, float* __restrict__ out_depth,
+                                                float* __restrict__ vmap, float* __restrict__ nmap, int ignore_imag,
+                                                double* __restrict__ pose_prev, unsigned long long* __restrict__ hits) {
   __shared__ float sT[kMaxLanes][12];
   for (int i = threadIdx.x + blockDim.x * threadIdx.y; i < p.L * 12; i += blockDim.x * blockDim.y) {
     sT[i / 12][i % 12] = (float)pose[i];
@@ -95,93 +164,10 @@ __global__ void __launch_bounds__(256) k_raycast(Params p, const float* __restri
   const size_t hw = (size_t)p.W * p.H;
   const size_t pix = (size_t)v * p.W + u;
   const size_t n = vox_count(p);
-
   const float* T = sT[0];
-  const float rx = (u - p.cx) / p.fx, ry = (v - p.cy) / p.fy;
-  const float dirx = T[0] * rx + T[1] * ry + T[2];
-  const float diry = T[4] * rx + T[5] * ry + T[6];
-  const float dirz = T[8] * rx + T[9] * ry + T[10];
+  const Ray ry = make_ray(p, T, u, v);
   const float inv_vox = 1.f / p.voxel;
-  // continuous voxel coordinate g(alpha) = g0 + alpha * gd
-  const float g0x = (T[3] - p.ox) * inv_vox - 0.5f, g0y = (T[7] - p.oy) * inv_vox - 0.5f,
-              g0z = (T[11] - p.oz) * inv_vox - 0.5f;
-  const float gdx = dirx * inv_vox, gdy = diry * inv_vox, gdz = dirz * inv_vox;
-
-  // alpha interval where 0 <= g < n - 1 on every axis (slab test), widened by one sample
-  float lo = p.m0 * p.ray_step, hi = p.m1 * p.ray_step;
-  {
-    const float g0[3] = {g0x, g0y, g0z}, gd[3] = {gdx, gdy, gdz};
-    const int nn[3] = {p.nx, p.ny, p.nz};
-    for (int a = 0; a < 3; ++a) {
-      if (gd[a] != 0.f) {
-        float t1 = (0.f - g0[a]) / gd[a], t2 = ((float)(nn[a] - 1) - g0[a]) / gd[a];
-        lo = fmaxf(lo, fminf(t1, t2));
-        hi = fminf(hi, fmaxf(t1, t2));
-      } else if (!(g0[a] >= 0.f && g0[a] < (float)(nn[a] - 1))) {
-        hi = -1.f;
-      }
-    }
-  }
-  int m_lo = max(p.m0, (int)floorf(lo / p.ray_step) - 1);
-  int m_hi = min(p.m1, (int)ceilf(hi / p.ray_step) + 1);
-
-  int m_hit = -1;
-  bool prev_valid = false, prev_pos = false;
-  for (int m = m_lo; m <= m_hi; ++m) {
-    const float al = m * p.ray_step;
-    const float gx = g0x + al * gdx, gy = g0y + al * gdy, gz = g0z + al * gdz;
-    if (bricks && gx >= 0.f && gx < (float)(p.nx - 1) && gy >= 0.f && gy < (float)(p.ny - 1) && gz >= 0.f &&
-        gz < (float)(p.nz - 1)) {
-      const int ci = (int)gx, cj = (int)gy, ck = (int)gz;
-      if ((ci & 7) != 7 && (cj & 7) != 7 && (ck & 7) != 7) {
-        const int bi = ci >> 3, bj = cj >> 3, bk = ck >> 3;
-        const unsigned fl = __ldg(bricks + bi + p.bnx * (bj + p.bny * bk));
-        if (fl == 1u || fl == 2u) {
-          // last sample whose cell stays in the brick's interior: min corner in [8b, 8b + 6] per axis
-          const float g0[3] = {g0x, g0y, g0z}, gd[3] = {gdx, gdy, gdz};
-          const int lo[3] = {8 * bi, 8 * bj, 8 * bk};
-          const int nn[3] = {p.nx, p.ny, p.nz};
-          float a_end = (m_hi + 1) * p.ray_step;
-#pragma unroll
-          for (int ax = 0; ax < 3; ++ax) {
-            const int hi = min(lo[ax] + 7, nn[ax] - 1);  // g < hi keeps the cell in the brick and the volume
-            if (gd[ax] > 0.f) a_end = fminf(a_end, ((float)hi - g0[ax]) / gd[ax]);
-            else if (gd[ax] < 0.f) a_end = fminf(a_end, ((float)lo[ax] - g0[ax]) / gd[ax]);
-          }
-          int m2 = min(m_hi, (int)ceilf(a_end / p.ray_step));
-          for (; m2 > m; --m2) {  // confirm with the sample positions the march itself computes
-            const float a2 = m2 * p.ray_step;
-            const float hx = g0x + a2 * gdx, hy = g0y + a2 * gdy, hz = g0z + a2 * gdz;
-            if (hx >= (float)lo[0] && hx < (float)min(lo[0] + 7, p.nx - 1) && hy >= (float)lo[1] &&
-                hy < (float)min(lo[1] + 7, p.ny - 1) && hz >= (float)lo[2] && hz < (float)min(lo[2] + 7, p.nz - 1))
-              break;
-          }
-          if (fl == 1u) {
-            if (prev_valid && !prev_pos) break;  // entering observed free space from behind a surface
-            prev_valid = true;
-            prev_pos = true;
-          } else {
-            prev_valid = false;
-            prev_pos = false;
-          }
-          m = m2;
-          continue;
-        }
-      }
-    }
-    Tri t;
-    const bool ok = tri_real(p, F, gx, gy, gz, t, false);
-    if (prev_valid && ok) {
-      const bool pos = t.val > 0.f;
-      if (prev_pos && !pos) {
-        m_hit = m - 1;
-        break;
-      }
-      if (!prev_pos && pos) break;
-    }
-    prev_valid = ok;
-    prev_pos = ok && t.val > 0.f;
-  }
+  const int m_hit = hit[pix];
 
   bool good = false;
   float alpha0 = 0.f, vx = 0.f, vy = 0.f, vz = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, nrm = 1.f;
@@ -190,14 +176,14 @@ __global__ void __launch_bounds__(256) k_raycast(Params p, const float* __restri
   if (m_hit >= 0) {
     am = m_hit * p.ray_step;
     an = (m_hit + 1) * p.ray_step;
-    bool ok = tri_real(p, F, g0x + am * gdx, g0y + am * gdy, g0z + am * gdz, tm, true);
-    ok &= tri_real(p, F, g0x + an * gdx, g0y + an * gdy, g0z + an * gdz, tn, true);
+    bool ok = tri_real(p, F, ry.g0x + am * ry.gdx, ry.g0y + am * ry.gdy, ry.g0z + am * ry.gdz, tm, true);
+    ok &= tri_real(p, F, ry.g0x + an * ry.gdx, ry.g0y + an * ry.gdy, ry.g0z + an * ry.gdz, tn, true);
     if (ok) {
       den = tn.val - tm.val;
       alpha0 = am - p.ray_step * tm.val / den;
-      vx = T[3] + alpha0 * dirx;
-      vy = T[7] + alpha0 * diry;
-      vz = T[11] + alpha0 * dirz;
+      vx = T[3] + alpha0 * ry.dirx;
+      vy = T[7] + alpha0 * ry.diry;
+      vz = T[11] + alpha0 * ry.dirz;
       const float gx = (vx - p.ox) * inv_vox - 0.5f, gy = (vy - p.oy) * inv_vox - 0.5f,
                   gz = (vz - p.oz) * inv_vox - 0.5f;
       ok &= tri_real(p, F, gx + 1.f, gy, gz, ts[0], true);
@@ -248,18 +234,18 @@ __global__ void __launch_bounds__(256) k_raycast(Params p, const float* __restri
   for (int l = 1; l < p.L; ++l) {
     const float* Tl = sT[l];
     const float* Fl = ignore_imag ? nullptr : F + (size_t)l * n;
-    const float dlx = Tl[0] * rx + Tl[1] * ry + Tl[2];
-    const float dly = Tl[4] * rx + Tl[5] * ry + Tl[6];
-    const float dlz = Tl[8] * rx + Tl[9] * ry + Tl[10];
+    const float dlx = Tl[0] * ry.rx + Tl[1] * ry.ry + Tl[2];
+    const float dly = Tl[4] * ry.rx + Tl[5] * ry.ry + Tl[6];
+    const float dlz = Tl[8] * ry.rx + Tl[9] * ry.ry + Tl[10];
     // sample positions move by alpha * dir_l + t_l
     const float Fm_l = tri_lane(p, Fl, tm, (am * dlx + Tl[3]) * inv_vox, (am * dly + Tl[7]) * inv_vox,
                                 (am * dlz + Tl[11]) * inv_vox);
     const float Fn_l = tri_lane(p, Fl, tn, (an * dlx + Tl[3]) * inv_vox, (an * dly + Tl[7]) * inv_vox,
                                 (an * dlz + Tl[11]) * inv_vox);
     const float a0_l = -p.ray_step * (Fm_l * tn.val - tm.val * Fn_l) / (den * den);
-    const float vlx = a0_l * dirx + alpha0 * dlx + Tl[3];
-    const float vly = a0_l * diry + alpha0 * dly + Tl[7];
-    const float vlz = a0_l * dirz + alpha0 * dlz + Tl[11];
+    const float vlx = a0_l * ry.dirx + alpha0 * dlx + Tl[3];
+    const float vly = a0_l * ry.diry + alpha0 * dly + Tl[7];
+    const float vlz = a0_l * ry.dirz + alpha0 * dlz + Tl[11];
     const float glx = vlx * inv_vox, gly = vly * inv_vox, glz = vlz * inv_vox;
     const float gxl = (tri_lane(p, Fl, ts[0], glx, gly, glz) - tri_lane(p, Fl, ts[1], glx, gly, glz)) * s;
     const float gyl = (tri_lane(p, Fl, ts[2], glx, gly, glz) - tri_lane(p, Fl, ts[3], glx, gly, glz)) * s;
@@ -281,8 +267,9 @@ __global__ void __launch_bounds__(256) k_raycast(Params p, const float* __restri
 cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose, float* depth, float* vmap,
                            float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s) {
   dim3 blk(32, 8), grd((p.W + 31) / 32, (p.H + 7) / 8);
-  k_raycast<<<grd, blk, 0, s>>>(p, b.F, b.Wt, pose, depth, vmap, nmap, ignore_imag_volume ? 1 : 0,
-                                set_prev ? b.pose_prev : nullptr, set_prev ? b.stats + 1 : nullptr, b.bricks);
+  k_march<<<grd, blk, 0, s>>>(p, b.F, pose, b.hit);
+  k_refine<<<grd, blk, 0, s>>>(p, b.F, pose, b.hit, depth, vmap, nmap, ignore_imag_volume ? 1 : 0,
+                               set_prev ? b.pose_prev : nullptr, set_prev ? b.stats + 1 : nullptr);
   return cudaGetLastError();
 }
 
