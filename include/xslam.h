@@ -192,7 +192,36 @@ xslam_status xslam_profile(xslam_t h, int enable);
  * TSDF update, pixels with a ray-cast surface, frames. Any pointer may be NULL. */
 xslam_status xslam_profile_read(xslam_t h, double* ms, long long* launches, double* counters);
 
-/* Description of the last error on this handle (or of the last failed create if h is NULL). */
+/*
+ * ICP normal equations without any allocation. The paper has no counterpart: this is a deployment
+ * variant of xslam_icp_system for callers that cannot allocate device memory where they need it (code
+ * inside a framework-owned memory pool, real-time loops in which cudaMalloc would synchronise the
+ * device, plug-ins that may only use buffers their host hands them). Stateless: every input and output
+ * is the caller's; all scratch (block partial sums, block ticket, pose lanes, result) lives in one
+ * file-scope device array of about 290 KB that every GPU which loads the library keeps until exit.
+ *   depth   device, pyramid level `level` (0..2) of the measured depth: (H >> level) x (W >> level)
+ *   K       level-0 intrinsics and size (H, W divisible by 2^level, at least 4 pixels per level)
+ *   model   device, level-0 model maps as (1 + 6 (1 + K_lanes)) planes of H x W: depth, vertex lanes,
+ *           normal lanes (the layout of xslam_set_model / xslam_raycast)
+ *   Tj, T_prev  host (1 + K_lanes) x 12 pose lanes (current estimate; pose the model was cast at)
+ *   seeds   the K_lanes seeds (DEPTH seeds on every pixel enter the measured vertices; the others
+ *           enter only through the pose lanes and the model); cfg may be NULL (defaults)
+ *   out     host (1 + K_lanes) x 27, as in xslam_icp_system; n_valid may be NULL
+ *   cuda_stream  the stream the call is ordered on (NULL = legacy default); the call synchronises it
+ * Limits: K_lanes <= 15 and at most 160 thread blocks (the grid this library picks on a GB300 is at
+ * most one block per SM); larger requests return XSLAM_EINVAL with a message in
+ * xslam_last_error(NULL). The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture. Calls share the
+ * array: calls that overlap on the GPU (other streams, other host threads) race; the call clears the
+ * scratch it needs cleared (ticket, status) itself. No cudaMalloc, cudaFree or allocating library
+ * routine is called.
+ */
+xslam_status xslam_icp_system_noalloc(const float* depth, int level, const xslam_intrinsics* K, const float* model,
+                                      const double* Tj, const double* T_prev, const xslam_seed* seeds, int K_lanes,
+                                      const xslam_config* cfg, double* out, int* n_valid, void* cuda_stream);
+
+/* Description of the last error on this handle; with h = NULL, of the last failed call made without a
+ * handle (xslam_create, xslam_icp_system_noalloc). */
 const char* xslam_last_error(xslam_t h);
 
 #ifdef __cplusplus

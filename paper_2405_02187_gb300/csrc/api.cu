@@ -53,6 +53,8 @@ struct xslam_s {
 
 static std::string g_create_err;
 
+void xslam::set_handleless_error(const char* msg) { g_create_err = msg; }
+
 static xslam_status fail(xslam_t h, xslam_status st, const std::string& msg) {
   if (h) h->err = msg;
   else g_create_err = msg;

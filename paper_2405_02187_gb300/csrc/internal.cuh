@@ -82,6 +82,9 @@ int icp_blocks(int level_pixels, int L);
 int icp_reps(int L);
 cudaError_t icp_configure();
 
+// message of the last failed call made without a handle (returned by xslam_last_error(NULL))
+void set_handleless_error(const char* msg);
+
 // ICP iteration flags
 enum : int { kIcpFirst = 1, kIcpLast = 2, kIcpNoUpdate = 4 };
 

@@ -75,6 +75,10 @@ SYMBOLS = [
     ("xslam_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("xslam_profile_read", ctypes.c_int, [ctypes.c_void_p, _c_double_p, ctypes.POINTER(ctypes.c_longlong),
                                           _c_double_p]),
+    ("xslam_icp_system_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Intrinsics),
+                                                ctypes.c_void_p, _c_double_p, _c_double_p, ctypes.POINTER(Seed),
+                                                ctypes.c_int, ctypes.POINTER(Config), _c_double_p, _c_int_p,
+                                                ctypes.c_void_p]),
     ("xslam_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
 STAGES = ("prepare", "icp", "integrate", "raycast", "other")
@@ -95,6 +99,28 @@ def load(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def icp_system_noalloc(depth, level, intr, model, Tj, T_prev, seeds=(), cfg: Config | None = None, stream=None):
+    """ICP normal equations with no allocation inside the library (see xslam_icp_system_noalloc):
+    depth is the level's CUDA float32 depth, model the (1 + 6 (1 + K)) x H x W CUDA float32 maps.
+    Returns ((1 + K, 27) array, n_valid)."""
+    lib = load()
+    K = len(seeds)
+    Kin = Intrinsics(float(intr.fx), float(intr.fy), float(intr.cx), float(intr.cy), int(intr.width), int(intr.height))
+    Tj = np.ascontiguousarray(Tj, np.float64).reshape(-1)
+    T_prev = np.ascontiguousarray(T_prev, np.float64).reshape(-1)
+    out = np.zeros(27 * (1 + K))
+    n = ctypes.c_int(0)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.xslam_icp_system_noalloc(_dev(depth), int(level), ctypes.byref(Kin), _dev(model), _dptr(Tj), _dptr(T_prev),
+                                      _seeds(seeds), K, ctypes.byref(cfg) if cfg is not None else None, _dptr(out),
+                                      ctypes.byref(n), ctypes.c_void_p(stream))
+    if st != OK:
+        raise XSlamError(st, lib.xslam_last_error(None).decode())
+    return out.reshape(1 + K, 27), n.value
 
 
 def default_config() -> Config:
