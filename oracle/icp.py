@@ -40,13 +40,17 @@ CELL_BIAS = 2.0 ** -6
 
 
 def correspondences(D, lintr, level, Tj, Tprev, model, dist_gate=0.1, normal_gate_deg=20.0,
-                    disc_gate=0.1, log=None, pix=None):
+                    disc_gate=0.1, log=None, pix=None, vn=None):
     """Per-pixel residual r, Jacobian J (N, 6) and validity mask at one pyramid level.
     ``log``, if a list, receives the discrete decisions (validity, bilinear cells); ``pix`` restricts
-    the result to those linear pixel indices (each pixel is independent)."""
+    the result to those linear pixel indices (each pixel is independent); ``vn`` = (V, N, valid) of
+    D's vertex and normal maps if already computed."""
     fx, fy, cx, cy, W, H = lintr
-    V = measure.vertex_map(D, lintr)
-    Nm, vvalid = measure.normal_map(D, V)
+    if vn is None:
+        V = measure.vertex_map(D, lintr)
+        Nm, vvalid = measure.normal_map(D, V)
+    else:
+        V, Nm, vvalid = vn
     V = V.reshape(-1, 3)
     Nm = Nm.reshape(-1, 3)
     valid = vvalid.reshape(-1)

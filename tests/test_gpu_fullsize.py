@@ -1,0 +1,135 @@
+"""Parity at the headline size: 256^3 x 1 cm room, 640x480 depth, K = 6 POSE0 lanes, the launch
+configuration bench.py times. The oracle cannot run whole frames at this size in a test, so each stage
+is compared on sampled outputs it computes one by one from the GPU's own state: the fusion of sampled
+voxels from the volume before the update, the ray cast of sampled pixels from the volume after it,
+and the level-0 ICP normal equations against the GPU's ray-cast model."""
+import numpy as np
+import pytest
+
+from gpu_helpers import H_GPU, H_ORA, gpu_seeds, make_handle, oracle_cfg, rel_err
+from oracle import fusion, icp, measure, raycast, se3
+from oracle import pipeline as P
+from paper_2405_02187_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SEEDS = [P.Seed(P.POSE0, j) for j in range(6)]
+
+
+@pytest.fixture(scope="module")
+def state():
+    wl = synth.room_walk(frames=5, device="cuda")
+    x = make_handle(wl, max_lanes=6)
+    x.set_pose(wl.poses[0])
+    dev = torch.tensor(wl.depth, device="cuda")
+    for k in range(3):
+        pose, _, _, st = x.frame(dev[k], gpu_seeds(SEEDS))
+        assert st == 0
+    n = x.n_vox
+    buf = torch.empty(n, device="cuda")
+
+    def volume():
+        F = x.read_tsdf(0, buf).cpu().numpy().astype(np.float64)
+        W = x.read_tsdf(-1, buf).cpu().numpy().astype(np.float64)
+        lanes = [x.read_tsdf(j + 1, buf).cpu().numpy().astype(np.float64) for j in range(len(SEEDS))]
+        return F, W, lanes
+
+    before = volume()
+    T = x.get_pose_lanes()
+    x.integrate(dev[3])
+    after = volume()
+    return dict(wl=wl, x=x, dev=dev, T=T, before=before, after=after)
+
+
+def _complex_pose(T, j):
+    """Oracle complex pose of lane j from the GPU lanes (Im scaled from h_gpu to h_oracle)."""
+    return T[0] + 1j * T[j + 1] / H_GPU * H_ORA
+
+
+def test_fullsize_fusion_sampled(state):
+    wl, T = state["wl"], state["T"]
+    F0, W0, L0 = state["before"]
+    F1, W1, L1 = state["after"]
+    rng = np.random.default_rng(0)
+    n = F0.size
+    changed = np.nonzero(W1 != W0)[0]
+    assert changed.size > 100000
+    idx = np.unique(np.concatenate([rng.choice(changed, 20000, replace=False), rng.integers(0, n, 20000)]))
+    D = measure.bilateral(measure.range_gate(wl.depth[3].astype(np.float64), wl.depth_min, wl.depth_max))
+    Fr, Wr = F0.copy(), W0.copy()
+    upd = fusion.integrate(Fr, Wr, D, T[0], wl.intr, wl.dims, wl.origin, wl.voxel, wl.trunc, idx=idx)
+    agree = Wr[idx] == W1[idx]
+    assert (~agree).mean() < 2e-3
+    obs = idx[agree & (W1[idx] > 0)]
+    assert np.abs(F1[obs] - Fr[obs]).max() < 1e-4
+    for j in range(len(SEEDS)):
+        Fc = F0 + 1j * L0[j] * H_ORA
+        Wc = W0.copy()
+        fusion.integrate(Fc, Wc, D, _complex_pose(T, j), wl.intr, wl.dims, wl.origin, wl.voxel, wl.trunc, idx=idx)
+        upd_obs = obs[W1[obs] != W0[obs]]
+        assert rel_err(L1[j][upd_obs], Fc.imag[upd_obs] / H_ORA) < 1e-3, j
+
+
+def test_fullsize_raycast_sampled(state):
+    wl, x, T = state["wl"], state["x"], state["T"]
+    F1, W1, L1 = state["after"]
+    H, Wd = wl.intr.height, wl.intr.width
+    Ln = 1 + len(SEEDS)
+    dep = torch.empty((H, Wd), device="cuda")
+    vm = torch.empty((3 * Ln, H, Wd), device="cuda")
+    nm = torch.empty((3 * Ln, H, Wd), device="cuda")
+    x.raycast(T, dep, vm, nm)
+    gd = dep.cpu().numpy().reshape(-1)
+    gv = vm.cpu().numpy().astype(np.float64).reshape(3 * Ln, -1)
+    gn = nm.cpu().numpy().astype(np.float64).reshape(3 * Ln, -1)
+    rng = np.random.default_rng(1)
+    pix = np.sort(rng.choice(H * Wd, 2500, replace=False))
+    args = (wl.intr, wl.dims, wl.origin, wl.voxel, wl.depth_min, wl.depth_max)
+    od, oV, oN = raycast.raycast(F1, W1, T[0], *args, pix=pix)
+    mg, mo = gd[pix] > 0, od > 0
+    assert mo.mean() > 0.5 and (mg != mo).mean() < 5e-3
+    both = mg & mo
+    assert np.abs(gd[pix][both] - od[both]).max() < 1e-4
+    assert np.abs(gv[:3, pix].T[both] - oV[both]).max() < 1e-4
+    assert np.abs(gn[:3, pix].T[both] - oN[both]).max() < 2e-3
+    for j in (0, 2, 4):
+        Fc = F1 + 1j * L1[j] * H_ORA
+        _, cV, cN = raycast.raycast(Fc, W1, _complex_pose(T, j), *args, pix=pix)
+        gvl = gv[3 * (j + 1):3 * (j + 2), pix].T[both] / H_GPU
+        gnl = gn[3 * (j + 1):3 * (j + 2), pix].T[both] / H_GPU
+        assert rel_err(gvl, cV.imag[both] / H_ORA) < 1e-3, j
+        assert rel_err(gnl, cN.imag[both] / H_ORA) < 1e-3, j
+
+
+def test_fullsize_icp_system(state):
+    wl, x, T, dev = state["wl"], state["x"], state["T"], state["dev"]
+    H, Wd = wl.intr.height, wl.intr.width
+    Ln = 1 + len(SEEDS)
+    dep = torch.empty((H, Wd), device="cuda")
+    vm = torch.empty((3 * Ln, H, Wd), device="cuda")
+    nm = torch.empty((3 * Ln, H, Wd), device="cuda")
+    x.raycast(T, dep, vm, nm)
+    x.set_model(dep, vm, nm, T)
+    x.measure(dev[4], 0, None)
+    Tj = T.copy()
+    Tj[0] = se3.compose(se3.se3_exp(np.array([0.003, -0.002, 0.004, 0.006, -0.003, 0.002])), T[0])
+    g, nv = x.icp_system(0, Tj)
+    md = dep.cpu().numpy().astype(np.float64)
+    mv = vm.cpu().numpy().astype(np.float64)
+    mn = nm.cpu().numpy().astype(np.float64)
+    pyr = measure.pyramid(measure.bilateral(measure.range_gate(wl.depth[4].astype(np.float64), wl.depth_min,
+                                                               wl.depth_max)), 3, oracle_cfg(wl).pyr_range)
+    li = measure.level_intrinsics(wl.intr, 0)
+    model = dict(depth=md, V=np.moveaxis(mv[:3], 0, -1), N=np.moveaxis(mn[:3], 0, -1))
+    r, J, valid = icp.correspondences(pyr[0], li, 0, Tj[0], T[0], model)
+    A, b, n = icp.normal_equations(r, J, valid)
+    iu = np.triu_indices(6)
+    assert abs(nv - n) <= 2e-3 * n
+    assert rel_err(g[0], np.concatenate([A[iu], -b])) < 2e-4
+    for j in (1, 3, 5):
+        mc = dict(depth=md, V=np.moveaxis(mv[:3] + 1j * mv[3 * (j + 1):3 * (j + 2)] / H_GPU * H_ORA, 0, -1),
+                  N=np.moveaxis(mn[:3] + 1j * mn[3 * (j + 1):3 * (j + 2)] / H_GPU * H_ORA, 0, -1))
+        rc, Jc, vc = icp.correspondences(pyr[0], li, 0, _complex_pose(Tj, j), _complex_pose(T, j), mc)
+        Ac, bc, _ = icp.normal_equations(rc, Jc, vc)
+        assert rel_err(g[j + 1] / H_GPU, np.concatenate([Ac[iu], -bc]).imag / H_ORA) < 1e-3, j

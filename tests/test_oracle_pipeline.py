@@ -97,3 +97,24 @@ def test_gauge_invariance(wl):
     out = P.run(wl, [P.Seed(P.POSE0, j) for j in range(6)])
     M = out["dtwist"][:, -1, :]  # rows: seed direction j; columns: twist components
     assert np.abs(M - np.eye(6)).max() < 0.1
+
+
+def test_relocalisation_gradient_matches_fd(wl):
+    """The relocalisation loss gradient (Sec. 5.2 point-to-plane reading): CSFD vs central finite
+    differences of the real loss, and a smaller loss at the true pose than at a displaced one."""
+    from oracle import reloc, se3
+    r, _ = _run_one(wl, None)
+    D = r.measure(wl.depth[2])[0]
+    args = (wl.intr, wl.dims, wl.origin, wl.voxel)
+    T = se3.compose(se3.se3_exp(np.array([0.004, -0.003, 0.002, 0.003, 0.002, -0.002])), wl.poses[2])
+    E, g, n = reloc.gradient(r.F, r.W, T, D, *args)
+    assert n > 200
+    hfd = 1e-7
+    for j in range(6):
+        e = np.zeros(6)
+        e[j] = hfd
+        Ep, _ = reloc.loss(r.F, r.W, se3.compose(se3.se3_exp(e), T), D, *args)
+        Em, _ = reloc.loss(r.F, r.W, se3.compose(se3.se3_exp(-e), T), D, *args)
+        assert abs((Ep - Em) / (2 * hfd) - g[j]) <= 1e-4 * np.abs(g).max() + 1e-12
+    E_true, _ = reloc.loss(r.F, r.W, wl.poses[2], D, *args)
+    assert E_true < E
