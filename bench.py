@@ -14,7 +14,10 @@ twist of the first pose). Prints one JSON line (rank 0):
                frames): algorithmic bytes per launch / its mean launch time, against the measured HBM
                copy bandwidth;
   cpu_baseline the CPU oracle (complex128, one process per lane) timed on the machine's host cores on
-               frame 1 of the same sequence, which also gives the derivative error of the GPU lanes.
+               frame 1 of the same sequence, which also gives the derivative error of the GPU lanes;
+  plain_fp64   the plain FP64 complex path (include/xslam_plain.h: complex<double>, one run per seed,
+               no lane batching) on the same frames, and the FP32 lanes' derivative error against it;
+  uncomplexified_fp32  the same frames with no imaginary lanes (K = 0).
 
 --impl reference times the oracle alone on sampled steps of the same workload (see _reference).
 Multi-GPU (torchrun): every rank runs its own independent sequence (replicas, no collective in the
@@ -357,8 +360,10 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     e0.record()
+    dtw_all = {}
     for k in range(W, W + K):
         pose, dpose, dtw, st = x.frame(host[k], seeds)
+        dtw_all[k] = dtw
     e1.record()
     torch.cuda.synchronize()
     barrier()
@@ -370,6 +375,47 @@ def run_ours(args, rank, world, local_rank):
         ms_e2e = float(t.item())
     e2e = dict(value=round(K * world / (ms_e2e / 1000.0), 2), unit="frames/s",
                h2d_bytes_per_step=int(4 * wl.intr.width * wl.intr.height), d2h_bytes_per_step=int(8 * (12 + 18 * L)))
+
+    # ---- beside the headline: the uncomplexified FP32 run (K = 0) and the plain FP64 complex path ----
+    x = xslam.XSlam(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, cfg, max_lanes=0)
+    x.set_pose(wl.poses[0])
+    for k in range(W):
+        x.frame(depth_dev[k], [], outputs=False)
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(W, W + K):
+        x.frame(depth_dev[k], [], outputs=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_real = e0.elapsed_time(e1)
+    x.close()
+    real32 = dict(value=round(K * world / (ms_real / 1000.0), 2), unit="frames/s", ms_per_step=round(ms_real / K, 4),
+                  lanes=0)
+    plain = None
+    if not args.no_plain:
+        # the plain path runs the same frames from frame 0 (its pose chain is its own), fewer of them
+        Kp = min(K, args.plain_steps)
+        xp = xslam.XSlamPlain(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, cfg, max_runs=L)
+        xp.set_pose(wl.poses[0])
+        seeds_p = [(xslam.POSE0, j % 6, 1e-20) for j in range(L)]
+        for k in range(W):
+            xp.frame(depth_dev[k], seeds_p)
+        torch.cuda.synchronize()
+        e0.record()
+        for k in range(W, W + Kp):
+            _, _, dtw_p, _ = xp.frame(depth_dev[k], seeds_p)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_plain = e0.elapsed_time(e1)
+        xp.close()
+        last = W + Kp - 1
+        err = float(np.linalg.norm(dtw_all[last] - dtw_p) / np.linalg.norm(dtw_p))
+        plain = dict(value=round(Kp * world / (ms_plain / 1000.0), 3), unit="frames/s", ms_per_step=round(ms_plain / Kp, 3),
+                     steps=Kp, dtype="c128", runs=L,
+                     method="complex<double> AoS voxels, one complex run per seed, one thread per pixel/voxel, "
+                            "no lane batching, no graphs",
+                     speedup_of_value=round(value / (Kp * world / (ms_plain / 1000.0)), 2),
+                     grad_rel_err_fp32_lanes_vs_plain=err, grad_err_frame=last)
 
     # ---- CPU oracle on the host cores (rank 0, N = 1): frame 1 of the same sequence ----
     cpu = None
@@ -400,6 +446,7 @@ def run_ours(args, rank, world, local_rank):
                             tracking_failures=int(n_fail)),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(round(launches_per_frame * K)),
                 clocks=clk, stage_ms_per_frame=stage_ms, grad_rel_err_vs_oracle=grad_err,
+                plain_fp64=plain, uncomplexified_fp32=real32,
                 per_frame=dict(fused_voxels=round(per_frame["fused"]), surface_pixels=round(per_frame["hits"])))
     if rank == 0:
         print(json.dumps(line))
@@ -444,6 +491,8 @@ def main():
     ap.add_argument("--workload", choices=("room256", "orbit64"), default="room256")
     ap.add_argument("--lanes", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 complex path beside the headline")
+    ap.add_argument("--plain-steps", type=int, default=20, help="timed frames of the plain FP64 path")
     ap.add_argument("--ref-shards", type=int, default=128)
     args = ap.parse_args()
     if args.warmup < 3:

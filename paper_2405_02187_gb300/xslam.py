@@ -80,6 +80,16 @@ SYMBOLS = [
                                                 ctypes.c_int, ctypes.POINTER(Config), _c_double_p, _c_int_p,
                                                 ctypes.c_void_p]),
     ("xslam_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    # include/xslam_plain.h: the plain FP64 complex path
+    ("xslam_plain_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_float, ctypes.c_float, _c_float_p, ctypes.POINTER(Intrinsics),
+                                          ctypes.POINTER(Config), ctypes.c_int, ctypes.c_void_p]),
+    ("xslam_plain_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("xslam_plain_set_pose", ctypes.c_int, [ctypes.c_void_p, _c_double_p]),
+    ("xslam_plain_frame", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Seed),
+                                         ctypes.c_int, _c_double_p, _c_double_p, _c_double_p]),
+    ("xslam_plain_read_tsdf", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("xslam_plain_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
 STAGES = ("prepare", "icp", "integrate", "raycast", "other")
 
@@ -305,3 +315,72 @@ class XSlam:
         n = ctypes.c_int(0)
         self._check(self.lib.xslam_icp_system(self.h, int(level), _dptr(Tj), _dptr(out), ctypes.byref(n)))
         return out.reshape(1 + self.K, 27), n.value
+
+
+class XSlamPlain:
+    """The plain FP64 complex path (include/xslam_plain.h): one complex<double> run per seed."""
+
+    def __init__(self, dims, voxel, trunc, origin, intr, cfg: Config | None = None, max_runs=6, stream=None):
+        self.lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.W, self.H = int(intr.width), int(intr.height)
+        K = Intrinsics(float(intr.fx), float(intr.fy), float(intr.cx), float(intr.cy), self.W, self.H)
+        org = (ctypes.c_float * 3)(*[float(o) for o in origin])
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        h = ctypes.c_void_p()
+        st = self.lib.xslam_plain_create(ctypes.byref(h), *self.dims, float(voxel), float(trunc), org, ctypes.byref(K),
+                                         ctypes.byref(cfg) if cfg is not None else None, int(max_runs),
+                                         ctypes.c_void_p(stream))
+        if st != OK:
+            raise XSlamError(st, self.lib.xslam_plain_last_error(None).decode())
+        self.h = h
+        self.max_runs = max_runs
+
+    def _check(self, st, allow=(OK,)):
+        if st not in allow:
+            raise XSlamError(st, self.lib.xslam_plain_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.xslam_plain_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_vox(self):
+        return self.dims[0] * self.dims[1] * self.dims[2]
+
+    def set_pose(self, T):
+        T = np.ascontiguousarray(T, np.float64).reshape(12)
+        self._check(self.lib.xslam_plain_set_pose(self.h, _dptr(T)))
+
+    def frame(self, depth, seeds=()):
+        """Run one frame of every run; returns (pose (3,4), dpose (K,3,4), dtwist (K,6), status)."""
+        K = len(seeds)
+        if isinstance(depth, np.ndarray):
+            depth = np.ascontiguousarray(depth, np.float32)
+            ptr, on_dev = ctypes.c_void_p(depth.ctypes.data), 0
+        elif not depth.is_cuda:
+            assert depth.is_contiguous() and str(depth.dtype) == "torch.float32"
+            ptr, on_dev = ctypes.c_void_p(depth.data_ptr()), 0
+        else:
+            ptr, on_dev = _dev(depth), 1
+        pose = np.zeros(12)
+        dpose = np.zeros(max(1, 12 * K))
+        dtw = np.zeros(max(1, 6 * K))
+        st = self.lib.xslam_plain_frame(self.h, ptr, on_dev, _seeds(seeds), K, _dptr(pose), _dptr(dpose), _dptr(dtw))
+        self._check(st, (OK, ENOTRACK))
+        return pose.reshape(3, 4), dpose[:12 * K].reshape(K, 3, 4), dtw[:6 * K].reshape(K, 6), st
+
+    def read_tsdf(self, run, part, out):
+        """part 0: Re F, 1: Im F / h, 2: W, into a CUDA float64 tensor of nx*ny*nz."""
+        self._check(self.lib.xslam_plain_read_tsdf(self.h, int(run), int(part), _dev(out, "float64")))
+        return out

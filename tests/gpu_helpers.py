@@ -59,3 +59,23 @@ def rel_err(a, b):
     b = np.asarray(b, np.float64)
     den = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def f32_params(wl):
+    """The workload and oracle Config with every parameter rounded to float32 as the C ABI passes it
+    (voxel size, truncation, origin, intrinsics, gates, depth range), for comparisons at FP64 rounding."""
+    import dataclasses
+    import math
+
+    from paper_2405_02187_gb300 import synth
+
+    f = lambda v: float(np.float32(v))  # noqa: E731
+    it = wl.intr
+    intr = synth.Intrinsics(f(it.fx), f(it.fy), f(it.cx), f(it.cy), it.width, it.height)
+    w = dataclasses.replace(wl, voxel=f(wl.voxel), trunc=f(wl.trunc), origin=tuple(f(o) for o in wl.origin),
+                            intr=intr, depth_min=f(wl.depth_min), depth_max=f(wl.depth_max))
+    cfg = P.Config(icp_iters=tuple(wl.icp_iters), dist_gate=f(0.1), normal_gate_deg=20.0, disc_gate=f(0.1),
+                   min_corr_frac=f(0.1), depth_min=w.depth_min, depth_max=w.depth_max, pyr_range=f(0.09),
+                   bilateral=wl.bilateral)
+    assert math.isinf(cfg.w_max)
+    return w, cfg

@@ -91,3 +91,28 @@ def test_null_handle_calls(lib):
     assert lib.xslam_destroy(None) == xslam.OK
     assert lib.xslam_frame(None, None, 0, None, 0, None, None, None) == xslam.EINVAL
     assert lib.xslam_sync(None, None) == xslam.EINVAL
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(dims=(1, 8, 8)), "dims"),
+    (dict(voxel=0.0), "voxel"),
+    (dict(max_runs=0), "max_runs"),
+    (dict(max_runs=17), "max_runs"),
+    (dict(intr=(0.0, 100.0, 31.5, 23.5, 64, 48)), "intrinsics"),
+])
+def test_plain_create_rejects_bad_arguments(lib, kw, msg):
+    dims = kw.get("dims", (8, 8, 8))
+    K = xslam.Intrinsics(*kw.get("intr", (100.0, 100.0, 31.5, 23.5, 64, 48)))
+    org = (ctypes.c_float * 3)(0, 0, 0)
+    h = ctypes.c_void_p()
+    st = lib.xslam_plain_create(ctypes.byref(h), *dims, kw.get("voxel", 0.01), 0.04, org, ctypes.byref(K), None,
+                                kw.get("max_runs", 2), None)
+    assert st == xslam.EINVAL and not h.value
+    assert msg in lib.xslam_plain_last_error(None).decode()
+
+
+def test_plain_null_handle_calls(lib):
+    assert lib.xslam_plain_destroy(None) == xslam.OK
+    assert lib.xslam_plain_frame(None, None, 0, None, 0, None, None, None) == xslam.EINVAL
+    assert lib.xslam_plain_set_pose(None, None) == xslam.EINVAL
+    assert lib.xslam_plain_read_tsdf(None, 0, 0, None) == xslam.EINVAL
