@@ -53,6 +53,14 @@ struct xslam_s {
 
 static std::string g_create_err;
 
+bool xslam::pdl_enabled() {
+  static const bool on = [] {
+    const char* env = getenv("XSLAM_PDL");
+    return !(env && env[0] == '0');
+  }();
+  return on;
+}
+
 void xslam::set_handleless_error(const char* msg) { g_create_err = msg; }
 
 static xslam_status fail(xslam_t h, xslam_status st, const std::string& msg) {

@@ -7,6 +7,7 @@ namespace xslam {
 
 // lanes j >= 1: Im exp(h_j i e_idx) T0 = h_j G_idx T0 (exact to O(h^3)); lane 0 untouched.
 __global__ void k_seed_pose(double* pose, int L, const int* kinds, const int* index, Params p) {
+  pdl_enter();
   const int l = threadIdx.x;
   if (l < 1 || l >= L) return;
   const double* T0 = pose;
@@ -33,6 +34,7 @@ __global__ void k_seed_pose(double* pose, int L, const int* kinds, const int* in
 }
 
 __global__ void k_readout(const double* __restrict__ pose, int L, Params p, double* __restrict__ out) {
+  pdl_enter();
   const int l = threadIdx.x;
   if (l == 0)
     for (int i = 0; i < 12; ++i) out[i] = pose[i];
@@ -67,6 +69,7 @@ __global__ void k_readout(const double* __restrict__ pose, int L, Params p, doub
 __global__ void __launch_bounds__(256) k_loss(Params p, const float* __restrict__ D, const float* __restrict__ model,
                                               const double* __restrict__ pose, float* __restrict__ partial,
                                               unsigned* __restrict__ ticket, double* __restrict__ out) {
+  pdl_enter();
   __shared__ float sT[kMaxLanes][12];
   __shared__ float s_red[8][kMaxLanes + 1];
   __shared__ int s_last;
@@ -138,18 +141,21 @@ __global__ void __launch_bounds__(256) k_loss(Params p, const float* __restrict_
 }
 
 cudaError_t launch_seed_pose(const Params& p, const Buffers& b, const int* kinds, const int* index, cudaStream_t s) {
-  k_seed_pose<<<1, 32, 0, s>>>(b.pose, p.L, kinds, index, p);
+  const cudaError_t e = launch_pdl(k_seed_pose, dim3(1), dim3(32), 0, s, b.pose, p.L, kinds, index, p);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_readout(const Params& p, const Buffers& b, cudaStream_t s) {
-  k_readout<<<1, 32, 0, s>>>(b.pose, p.L, p, b.result);
+  const cudaError_t e = launch_pdl(k_readout, dim3(1), dim3(32), 0, s, b.pose, p.L, p, b.result);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_loss(const Params& p, const Buffers& b, const float* depth, const float* model, const double* pose,
                         double* out, int nblk, cudaStream_t s) {
-  k_loss<<<nblk, 256, 0, s>>>(p, depth, model, pose, b.partial, b.ticket, out);
+  const cudaError_t e = launch_pdl(k_loss, dim3(nblk), dim3(256), 0, s, p, depth, model, pose, b.partial, b.ticket, out);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -78,6 +78,7 @@ __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restr
 __global__ void __launch_bounds__(kBX * kBY) k_integrate(Params p, const float* __restrict__ D,
                                                         const double* __restrict__ pose, float* __restrict__ F,
                                                         float* __restrict__ Wt, unsigned long long* __restrict__ stats) {
+  pdl_enter();
   __shared__ float sT[kMaxLanes][12];
   __shared__ int s_out[8];
   const int tid = threadIdx.x + kBX * threadIdx.y;
@@ -128,7 +129,8 @@ __global__ void __launch_bounds__(kBX * kBY) k_integrate(Params p, const float* 
 
 cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s) {
   dim3 blk(kBX, kBY, 1), grd((p.nx + kBX - 1) / kBX, (p.ny + kBY - 1) / kBY, (p.nz + kBZ - 1) / kBZ);
-  k_integrate<<<grd, blk, 0, s>>>(p, b.pyr[0], b.pose, b.F, b.Wt, b.stats);
+  const cudaError_t e = launch_pdl(k_integrate, grd, blk, 0, s, p, b.pyr[0], b.pose, b.F, b.Wt, b.stats);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

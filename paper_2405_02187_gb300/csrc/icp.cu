@@ -110,6 +110,7 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
 }
 
 __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int flags, int reps) {
+  pdl_enter();
   const int L = p.L;
   const int warp = threadIdx.x >> 5, lid = threadIdx.x & 31;
   const int ln = warp % L, rep = warp / L;
@@ -391,41 +392,51 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   __threadfence();
 
   // ---------------- last block: FP64 cross-block sum ----------------
-  // value v is summed by two threads, one per half of its row of block partials: float4 loads issued
-  // together, FP32 sums of 16 partials, FP64 accumulation of those sums, FP64 add of the two halves.
+  // value v is summed by two threads, one per half of its row of block partials: all float4 loads of a
+  // half (up to 20, i.e. grids of up to 160 blocks) issued together, so the read costs one L2 round
+  // trip; FP32 sums of 16 partials, FP64 accumulation of those sums, FP64 add of the two halves.
   // Different values sit in different lanes, so each FP64 warp instruction adds 32 values.
   const int NV = L * kNT;
   const int pstride = icp_pstride(gridDim.x);
-  const int n4 = pstride >> 2, h4 = (n4 + 1) >> 1;
-  for (int t = threadIdx.x; t < 2 * NV; t += blockDim.x) {
-    const int v = t >> 1, half = t & 1;
-    const float4* row = reinterpret_cast<const float4*>(b.partial + (size_t)v * pstride) + half * h4;
-    const int cnt = half ? n4 - h4 : h4;
-    double acc = 0.0;
-    for (int c0 = 0; c0 < cnt; c0 += 8) {
-      float4 q[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) q[j] = (c0 + j < cnt) ? __ldcg(row + c0 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-      float f0 = 0.f, f1 = 0.f;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        f0 += (q[j].x + q[j].y) + (q[j].z + q[j].w);
-        f1 += (q[j + 4].x + q[j + 4].y) + (q[j + 4].z + q[j + 4].w);
-      }
-      acc += (double)f0;
-      acc += (double)f1;
-    }
-    s_half[t] = acc;
-  }
-  if (warp == 0) {
+  if (warp == (int)(blockDim.x >> 5) - 1) {
+    // the last warp adds the per-block correspondence counts: 8 loads per lane in flight at once
     int c = 0;
-    for (int k = lid; k < (int)gridDim.x; k += 32) c += __ldcg(&b.partial_n[k]);
+    for (int k0 = 0; k0 < (int)gridDim.x; k0 += 256) {
+      int q[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int k = k0 + lid + 32 * j;
+        q[j] = k < (int)gridDim.x ? __ldcg(&b.partial_n[k]) : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) c += q[j];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lid == 0) {
       s_ncorr = c;
       *b.ticket = 0u;  // ready for the next launch
     }
+  }
+  const int n4 = pstride >> 2, h4 = (n4 + 1) >> 1;
+  for (int t = threadIdx.x; t < 2 * NV; t += blockDim.x) {
+    const int v = t >> 1, half = t & 1;
+    const float4* row = reinterpret_cast<const float4*>(b.partial + (size_t)v * pstride) + half * h4;
+    const int cnt = half ? n4 - h4 : h4;
+    double acc = 0.0;
+    for (int c0 = 0; c0 < cnt; c0 += 20) {
+      float4 q[20];
+#pragma unroll
+      for (int j = 0; j < 20; ++j) q[j] = (c0 + j < cnt) ? __ldcg(row + c0 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int g = 0; g < 5; ++g) {
+        float f = 0.f;
+#pragma unroll
+        for (int j = 4 * g; j < 4 * g + 4; ++j) f += (q[j].x + q[j].y) + (q[j].z + q[j].w);
+        acc += (double)f;
+      }
+    }
+    s_half[t] = acc;
   }
   __syncthreads();
   for (int v = threadIdx.x; v < NV; v += blockDim.x) sA[v] = s_half[2 * v] + s_half[2 * v + 1];
@@ -568,7 +579,8 @@ cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int flags, 
   lv.cy = p.cy / lv.s;
   int reps = icp_reps(p.L);
   const int threads = 32 * p.L * reps;
-  k_icp<<<nblk, threads, icp_rec_bytes(reps, p.L), s>>>(p, b, lv, flags, reps);
+  const cudaError_t e = launch_pdl(k_icp, dim3(nblk), dim3(threads), icp_rec_bytes(reps, p.L), s, p, b, lv, flags, reps);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -67,6 +67,35 @@ __host__ __device__ inline size_t vox_count(const Params& p) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Programmatic dependent launch. Every kernel of the frame chain is launched with programmatic stream
+// serialization and begins with pdl_enter(): griddepcontrol.wait returns once the preceding kernel in
+// the stream has completed and its writes are visible, and launch_dependents then lets the next kernel
+// be scheduled, so that its blocks are resident (and past their own launch latency) when this one ends.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// false when the environment sets XSLAM_PDL=0 (plain stream-ordered launches, for comparison)
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// ---------------------------------------------------------------------------------------------
 // launches (each defined in its own translation unit)
 // ---------------------------------------------------------------------------------------------
 cudaError_t launch_prepare(const Params& p, const Buffers& b, int levels, cudaStream_t s);

@@ -13,6 +13,7 @@
 namespace xslam {
 
 __global__ void k_gate(const float* __restrict__ in, float* __restrict__ out, int n, float dmin, float dmax) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float d = in[i];
@@ -20,6 +21,7 @@ __global__ void k_gate(const float* __restrict__ in, float* __restrict__ out, in
 }
 
 __global__ void k_bilateral(const float* __restrict__ src, float* __restrict__ dst, int W, int H) {
+  pdl_enter();
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y * blockDim.y + threadIdx.y;
   if (u >= W || v >= H) return;
@@ -50,6 +52,7 @@ __global__ void k_bilateral(const float* __restrict__ src, float* __restrict__ d
 
 __global__ void k_pyr_down(const float* __restrict__ src, int Ws, int Hs, float* __restrict__ dst, int Wd, int Hd,
                            float range) {
+  pdl_enter();
   int u = blockIdx.x * blockDim.x + threadIdx.x;
   int v = blockIdx.y * blockDim.y + threadIdx.y;
   if (u >= Wd || v >= Hd) return;
@@ -80,20 +83,21 @@ __global__ void k_pyr_down(const float* __restrict__ src, int Ws, int Hs, float*
 
 cudaError_t launch_prepare(const Params& p, const Buffers& b, int levels, cudaStream_t s) {
   const int n = p.W * p.H;
+  cudaError_t e;
   if (p.bilateral) {
     // gate into the full-size scratch image, filter into level 0
-    k_gate<<<(n + 255) / 256, 256, 0, s>>>(b.depth_in, b.gated, n, p.depth_min, p.depth_max);
+    e = launch_pdl(k_gate, dim3((n + 255) / 256), dim3(256), 0, s, b.depth_in, b.gated, n, p.depth_min, p.depth_max);
     dim3 blk(32, 8), grd((p.W + 31) / 32, (p.H + 7) / 8);
-    k_bilateral<<<grd, blk, 0, s>>>(b.gated, b.pyr[0], p.W, p.H);
+    if (e == cudaSuccess) e = launch_pdl(k_bilateral, grd, blk, 0, s, b.gated, b.pyr[0], p.W, p.H);
   } else {
-    k_gate<<<(n + 255) / 256, 256, 0, s>>>(b.depth_in, b.pyr[0], n, p.depth_min, p.depth_max);
+    e = launch_pdl(k_gate, dim3((n + 255) / 256), dim3(256), 0, s, b.depth_in, b.pyr[0], n, p.depth_min, p.depth_max);
   }
   for (int l = 1; l < levels; ++l) {
     const int Ws = p.W >> (l - 1), Hs = p.H >> (l - 1), Wd = p.W >> l, Hd = p.H >> l;
     dim3 blk(32, 8), grd((Wd + 31) / 32, (Hd + 7) / 8);
-    k_pyr_down<<<grd, blk, 0, s>>>(b.pyr[l - 1], Ws, Hs, b.pyr[l], Wd, Hd, p.pyr_range);
+    if (e == cudaSuccess) e = launch_pdl(k_pyr_down, grd, blk, 0, s, b.pyr[l - 1], Ws, Hs, b.pyr[l], Wd, Hd, p.pyr_range);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace xslam

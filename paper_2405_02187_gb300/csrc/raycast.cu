@@ -102,6 +102,7 @@ __device__ __forceinline__ Ray make_ray(const Params& p, const float* T, int u, 
 
 __global__ void __launch_bounds__(256) k_march(Params p, const float* __restrict__ F, const double* __restrict__ pose,
                                                int* __restrict__ hit) {
+  pdl_enter();
   __shared__ float sT[12];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   if (tid < 12) sT[tid] = (float)pose[tid];
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(256) k_refine(Params p, const float* __restric
                                                 const int* __restrict__ hit, float* __restrict__ out_depth,
                                                 float* __restrict__ vmap, float* __restrict__ nmap, int ignore_imag,
                                                 double* __restrict__ pose_prev, unsigned long long* __restrict__ hits) {
+  pdl_enter();
   __shared__ float sT[kMaxLanes][12];
   for (int i = threadIdx.x + blockDim.x * threadIdx.y; i < p.L * 12; i += blockDim.x * blockDim.y) {
     sT[i / 12][i % 12] = (float)pose[i];
@@ -267,10 +269,10 @@ __global__ void __launch_bounds__(256) k_refine(Params p, const float* __restric
 cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose, float* depth, float* vmap,
                            float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s) {
   dim3 blk(32, 8), grd((p.W + 31) / 32, (p.H + 7) / 8);
-  k_march<<<grd, blk, 0, s>>>(p, b.F, pose, b.hit);
-  k_refine<<<grd, blk, 0, s>>>(p, b.F, pose, b.hit, depth, vmap, nmap, ignore_imag_volume ? 1 : 0,
-                               set_prev ? b.pose_prev : nullptr, set_prev ? b.stats + 1 : nullptr);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(k_march, grd, blk, 0, s, p, b.F, pose, b.hit);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_refine, grd, blk, 0, s, p, b.F, pose, b.hit, depth, vmap, nmap, ignore_imag_volume ? 1 : 0,
+                    set_prev ? b.pose_prev : nullptr, set_prev ? b.stats + 1 : nullptr);
 }
 
 }  // namespace xslam

@@ -40,8 +40,10 @@ def test_plain_matches_oracle_tiny(bilateral):
         assert st == xslam.OK
         assert np.abs(pose - ref["pose"][k]).max() < 1e-10
         for j in range(len(seeds)):
-            assert rel_err(dpose[j], ref["dpose"][j, k]) < 1e-8, (k, j)
-            assert rel_err(dtw[j], ref["dtwist"][j, k]) < 1e-8, (k, j)
+            # relative to the derivative's scale, with a floor of 1: d pose / d mu vanishes (to 1e-17)
+            # once ICP has converged on the noise-free scene
+            for a, b in ((dpose[j], ref["dpose"][j, k]), (dtw[j], ref["dtwist"][j, k])):
+                assert np.abs(a - b).max() <= 1e-8 * max(1.0, np.abs(b).max()), (k, j)
     # the TSDF of every run: real part and derivative
     buf = torch.empty(x.n_vox, device="cuda", dtype=torch.float64)
     for j in range(len(seeds)):
