@@ -261,6 +261,30 @@ def algorithmic_bytes(stage, wl, K, per_frame):
 
 
 # ------------------------------------------------------------------------------------------------
+# replicas: one independent sequence per rank, the slowest rank's time
+# ------------------------------------------------------------------------------------------------
+def replica_seed(rank):
+    """Seed of rank's sequence: every replica tracks its own trajectory (no data exchange)."""
+    return 2 + rank
+
+
+def max_over_ranks(x, device="cpu"):
+    """The largest x over the ranks of the default process group (x itself when there is none)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, ms_max):
+    """Whole-job units/s: every rank processed units_per_rank in at most ms_max milliseconds."""
+    return units_per_rank * world / (ms_max / 1000.0)
+
+
+# ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
@@ -277,7 +301,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     W, K, L = args.warmup, args.steps, args.lanes
     nf = W + K + 1
-    wl = make_workload(args.workload, 2 + rank, nf, dev)
+    wl = make_workload(args.workload, replica_seed(rank), nf, dev)
     if args.workload == "room256" and nf > 300:
         print("note: more frames than the 300-frame sequence were generated", file=sys.stderr)
     cfg = xslam_cfg(wl)
@@ -315,11 +339,8 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     _, n_fail = x.sync()
     x.close()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = K * world / (ms / 1000.0)
+    ms = max_over_ranks(ms, dev)
+    value = replica_throughput(K, world, ms)
 
     # ---- profiled pass over the same frames: per-stage device time (no graphs) ----
     x = handle()
@@ -369,11 +390,8 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ms_e2e = e0.elapsed_time(e1)
     x.close()
-    if dist:
-        t = torch.tensor([ms_e2e], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = dict(value=round(K * world / (ms_e2e / 1000.0), 2), unit="frames/s",
+    ms_e2e = max_over_ranks(ms_e2e, dev)
+    e2e = dict(value=round(replica_throughput(K, world, ms_e2e), 2), unit="frames/s",
                h2d_bytes_per_step=int(4 * wl.intr.width * wl.intr.height), d2h_bytes_per_step=int(8 * (12 + 18 * L)))
 
     # ---- beside the headline: the uncomplexified FP32 run (K = 0) and the plain FP64 complex path ----
