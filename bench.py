@@ -17,7 +17,10 @@ twist of the first pose). Prints one JSON line (rank 0):
                frame 1 of the same sequence, which also gives the derivative error of the GPU lanes;
   plain_fp64   the plain FP64 complex path (include/xslam_plain.h: complex<double>, one run per seed,
                no lane batching) on the same frames, and the FP32 lanes' derivative error against it;
-  uncomplexified_fp32  the same frames with no imaginary lanes (K = 0).
+  uncomplexified_fp32  the same frames with no imaginary lanes (K = 0);
+  batched      32 independent trajectories of 50-400 frames (mixed image sizes, grids and lane
+               counts) advanced together through include/xslam_batch.h: aggregate frames/s and the
+               per-trajectory frame latency.
 
 --impl reference times the oracle alone on sampled steps of the same workload (see _reference).
 Multi-GPU (torchrun): every rank runs its own independent sequence (replicas, no collective in the
@@ -435,6 +438,8 @@ def run_ours(args, rank, world, local_rank):
                      speedup_of_value=round(value / (Kp * world / (ms_plain / 1000.0)), 2),
                      grad_rel_err_fp32_lanes_vs_plain=err, grad_err_frame=last)
 
+    batched = None if args.no_batch else run_batch(args, dev, rank)
+
     # ---- CPU oracle on the host cores (rank 0, N = 1): frame 1 of the same sequence ----
     cpu = None
     grad_err = None
@@ -464,10 +469,106 @@ def run_ours(args, rank, world, local_rank):
                             tracking_failures=int(n_fail)),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(round(launches_per_frame * K)),
                 clocks=clk, stage_ms_per_frame=stage_ms, grad_rel_err_vs_oracle=grad_err,
-                plain_fp64=plain, uncomplexified_fp32=real32,
+                plain_fp64=plain, uncomplexified_fp32=real32, batched=batched,
                 per_frame=dict(fused_voxels=round(per_frame["fused"]), surface_pixels=round(per_frame["hits"])))
     if rank == 0:
         print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------------------------------
+# batched trajectories (include/xslam_batch.h)
+# ------------------------------------------------------------------------------------------------
+def run_batch(args, dev, rank):
+    """Many trajectories of uneven length, image size, grid and lane count, advanced together: one
+    CUDA graph per step. The ICP grid is picked by the library's autotuner on the first steps; the
+    timed pass then runs every trajectory from frame 0 to its end. Returns the JSON object."""
+    import torch
+    from paper_2405_02187_gb300 import synth, xslam
+
+    t0 = time.perf_counter()
+    trajs = synth.batch_trajectories(seed=7 + rank, n=args.batch_n, min_frames=args.batch_min, max_frames=args.batch_max,
+                                     device=dev, resident=True)
+    gen_s = time.perf_counter() - t0
+    lens = [wl.depth.shape[0] for wl, _ in trajs]
+    handles = []
+    for wl, lanes in trajs:
+        x = xslam.XSlam(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, xslam_cfg(wl), max_lanes=len(lanes))
+        x.set_lanes([(k, j, H_GPU) for k, j in lanes])
+        x.set_pose(wl.poses[0])
+        handles.append(x)
+    depth = [wl.depth for wl, _ in trajs]
+    batch = xslam.XSlamBatch(handles)
+    tune_steps = 6
+    frames = [[d[k] if k < n else None for d, n in zip(depth, lens)] for k in range(tune_steps)]
+    divisor, tune_ms = batch.autotune(frames, tune_steps)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(lens)
+    e0.record()
+    for k in range(steps):
+        batch.step([d[k] if k < n else None for d, n in zip(depth, lens)])
+    e1.record()
+    fails = batch.sync()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    total = sum(lens)
+    # algorithmic bytes of the whole run (the per-kernel unit counts of the single-trajectory roofline)
+    moved = 0.0
+    for (wl, lanes), x, n in zip(trajs, handles, lens):
+        _, cnt = x.profile_read()
+        L = 1 + len(lanes)
+        hw = wl.intr.width * wl.intr.height
+        per = dict(fused=cnt["fused"] / n, hits=cnt["hits"] / n)
+        moved += n * (algorithmic_bytes("integrate", wl, len(lanes), per) + algorithmic_bytes("raycast", wl, len(lanes), per))
+        moved += (n - 1) * sum(it * (hw >> (2 * lv)) * (4 + 4 + 24 * L) for lv, it in enumerate(wl.icp_iters))
+    # per-trajectory frame latency inside a step, from a second batch over the first steps
+    batch.close()
+    for (wl, lanes), x in zip(trajs, handles):
+        x.reset()
+        x.set_lanes([(k, j, H_GPU) for k, j in lanes])
+        x.set_pose(wl.poses[0])
+    batch = xslam.XSlamBatch(handles)
+    lat = []
+    for k in range(min(12, min(lens))):
+        batch.step([d[k] for d in depth])
+        if k >= 2:
+            lat.append(batch.latency())
+    batch.close()
+    lat = np.mean(np.array(lat), 0) if lat else np.zeros(len(lens))
+    # the same trajectories one at a time (their own graphs, default grids): frames 2..7 of each
+    seq = []
+    for (wl, lanes), x, d in zip(trajs, handles, depth):
+        x.reset()
+        x.set_pose(wl.poses[0])
+        sd = [(k, j, H_GPU) for k, j in lanes]
+        for k in range(2):
+            x.frame(d[k], sd, outputs=False)
+        e0.record()
+        for k in range(2, 8):
+            x.frame(d[k], sd, outputs=False)
+        e1.record()
+        torch.cuda.synchronize()
+        seq.append(e0.elapsed_time(e1) / 6)
+    seq_ms = float(sum(t * n for t, n in zip(seq, lens)))
+    peak, peak_src = measured_peaks()
+    vox = [int(np.prod(wl.dims)) for wl, _ in trajs]
+    return dict(
+        workload=f"{len(trajs)} room walks of {min(lens)}-{max(lens)} frames, 320x240 or 640x480, grids "
+                 f"{min(wl.dims[0] for wl, _ in trajs)}^3-{max(wl.dims[0] for wl, _ in trajs)}^3 over a 2.56 m room, "
+                 f"K {min(len(l) for _, l in trajs)}-{max(len(l) for _, l in trajs)}",
+        frames=total, steps=steps, value=round(total / (ms / 1000.0), 1), unit="frames/s (all trajectories)",
+        ms=round(ms, 1), ms_per_step=round(ms / steps, 3), tracking_failures=int(sum(fails)),
+        sequential=dict(ms=round(seq_ms, 1), value=round(total / (seq_ms / 1000.0), 1),
+                        note="each trajectory alone through xslam_frame (graphs), frames 2-7 timed, times its length"),
+        speedup_vs_sequential=round(seq_ms / ms, 2),
+        roofline=dict(bound="hbm", achieved=round(moved / (ms * 1e-3) / 1e9, 1), peak=peak, unit="GB/s",
+                      frac=round(moved / (ms * 1e-3) / 1e9 / peak, 4), algorithmic_gb=round(moved / 1e9, 2),
+                      note="algorithmic bytes of every ICP, fusion and ray-cast launch of the run / its time"),
+        icp_grid_divisor=divisor, autotune_ms_per_step={str(d): round(float(m), 3) for d, m in zip((1, 2, 4, 8, 16), tune_ms)},
+        latency_ms_per_frame=dict(min=round(float(lat.min()), 3), median=round(float(np.median(lat)), 3),
+                                  max=round(float(lat.max()), 3)),
+        state_gb=round(sum(v * 4 * (2 + len(l)) for v, (_, l) in zip(vox, trajs)) / 1e9, 2),
+        input_gb=round(sum(wl.depth.numel() * 4 for wl, _ in trajs) / 1e9, 2), generate_s=round(gen_s, 1))
 
 
 # ------------------------------------------------------------------------------------------------
@@ -511,6 +612,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 complex path beside the headline")
     ap.add_argument("--plain-steps", type=int, default=20, help="timed frames of the plain FP64 path")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-trajectories run")
+    ap.add_argument("--batch-n", type=int, default=32)
+    ap.add_argument("--batch-min", type=int, default=50)
+    ap.add_argument("--batch-max", type=int, default=400)
     ap.add_argument("--ref-shards", type=int, default=128)
     args = ap.parse_args()
     if args.warmup < 3:

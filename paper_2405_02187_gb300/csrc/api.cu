@@ -13,43 +13,10 @@
 #include <string>
 
 #include "../../include/xslam.h"
+#include "handle.cuh"
 #include "internal.cuh"
 
 using namespace xslam;
-
-static constexpr int kProfRing = 256;
-
-struct xslam_s {
-  Params p;
-  Buffers b;
-  xslam_config cfg;
-  int max_lanes = 0;
-  int nsm = 148;
-  cudaStream_t s = nullptr;     // internal stream
-  cudaStream_t user = nullptr;  // caller's stream
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  int frame = 0;
-  int K = 0;
-  xslam_seed seeds[kMaxLanes];
-  int* d_kinds = nullptr;   // device copies of lane kinds / indices
-  int* d_index = nullptr;
-  double* pose_tmp = nullptr;  // scratch pose lanes (raycast / grad)
-  float* model_q = nullptr;    // scratch model maps of xslam_grad (7 lanes)
-  double* h_result = nullptr;  // pinned host staging
-  int* h_status = nullptr;
-  int nblk[3] = {1, 1, 1};
-  int nblk_max = 1;
-  cudaGraphExec_t g_first = nullptr, g_track = nullptr;
-  bool use_graphs = true;
-  // stage profiling (xslam_profile): one event pair per stage and frame, accumulated on read
-  bool profiling = false;
-  cudaEvent_t pev[XSLAM_NSTAGE][kProfRing][2] = {};
-  int pcount[XSLAM_NSTAGE] = {};      // pairs recorded and not yet accumulated
-  double pms[XSLAM_NSTAGE] = {};      // accumulated milliseconds
-  long long plaunch[XSLAM_NSTAGE] = {};
-  long long pframes = 0;
-  std::string err;
-};
 
 static std::string g_create_err;
 
@@ -432,6 +399,10 @@ static cudaError_t enqueue_track(xslam_t h) {
   stage_end(h, XSLAM_STAGE_OTHER, 1);
   return e;
 }
+
+cudaError_t xslam::enqueue_chain(xslam_t h, bool first) { return first ? enqueue_first(h) : enqueue_track(h); }
+
+void xslam::handle_drop_graphs(xslam_t h) { drop_graphs(h); }
 
 // Fold the recorded event pairs into the per-stage totals (synchronises the stream).
 static xslam_status prof_accumulate(xslam_t h) {

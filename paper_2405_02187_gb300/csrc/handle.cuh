@@ -1,0 +1,49 @@
+// The handle behind xslam_t (include/xslam.h), shared by the C ABI (api.cu) and the batch driver
+// (batch.cu).
+#pragma once
+
+#include <string>
+
+#include "../../include/xslam.h"
+#include "internal.cuh"
+
+constexpr int kProfRing = 256;
+
+struct xslam_s {
+  xslam::Params p;
+  xslam::Buffers b;
+  xslam_config cfg;
+  int max_lanes = 0;
+  int nsm = 148;
+  cudaStream_t s = nullptr;     // internal stream
+  cudaStream_t user = nullptr;  // caller's stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int frame = 0;
+  int K = 0;
+  xslam_seed seeds[xslam::kMaxLanes];
+  int* d_kinds = nullptr;   // device copies of lane kinds / indices
+  int* d_index = nullptr;
+  double* pose_tmp = nullptr;  // scratch pose lanes (raycast / grad)
+  float* model_q = nullptr;    // scratch model maps of xslam_grad (7 lanes)
+  double* h_result = nullptr;  // pinned host staging
+  int* h_status = nullptr;
+  int nblk[3] = {1, 1, 1};
+  int nblk_max = 1;
+  cudaGraphExec_t g_first = nullptr, g_track = nullptr;
+  bool use_graphs = true;
+  // stage profiling (xslam_profile): one event pair per stage and frame, accumulated on read
+  bool profiling = false;
+  cudaEvent_t pev[XSLAM_NSTAGE][kProfRing][2] = {};
+  int pcount[XSLAM_NSTAGE] = {};      // pairs recorded and not yet accumulated
+  double pms[XSLAM_NSTAGE] = {};      // accumulated milliseconds
+  long long plaunch[XSLAM_NSTAGE] = {};
+  long long pframes = 0;
+  std::string err;
+};
+
+namespace xslam {
+// enqueues one frame chain (frame 0 when first, else a tracking frame) on the handle's stream
+cudaError_t enqueue_chain(xslam_t h, bool first);
+// drops the handle's captured frame graphs (after a change of lanes or grid sizes)
+void handle_drop_graphs(xslam_t h);
+}  // namespace xslam

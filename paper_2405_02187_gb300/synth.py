@@ -152,6 +152,11 @@ def render_depth(scene, intr: Intrinsics, pose: np.ndarray, device="cpu") -> np.
     """Exact camera-z depth of the nearest primitive for every pixel (float64, 0 = no hit).
 
     Evaluated in float64 with torch on ``device``; the result is returned as a numpy array."""
+    return render_depth_t(scene, intr, pose, device).cpu().numpy()
+
+
+def render_depth_t(scene, intr: Intrinsics, pose: np.ndarray, device="cpu"):
+    """render_depth as a float64 torch tensor on ``device`` (no copy to the host)."""
     pose = np.asarray(pose, np.float64)
     R = torch.tensor(pose[:, :3], dtype=torch.float64, device=device)
     o = torch.tensor(pose[:, 3], dtype=torch.float64, device=device)
@@ -159,8 +164,7 @@ def render_depth(scene, intr: Intrinsics, pose: np.ndarray, device="cpu") -> np.
     best = torch.full(d.shape[:2], math.inf, dtype=torch.float64, device=device)
     for prim in scene:
         best = torch.minimum(best, _HIT[type(prim)](prim, o, d))
-    best = torch.where(torch.isfinite(best), best, torch.zeros_like(best))
-    return best.cpu().numpy()
+    return torch.where(torch.isfinite(best), best, torch.zeros_like(best))
 
 
 # ----------------------------------------------------------------------------------------------
@@ -258,11 +262,15 @@ def _room_scene(rng, lo, hi, n_prims, keep_out_lo, keep_out_hi, clearance):
 
 
 def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 480, dims=256,
-              voxel: float = 0.01, noise: bool = True, device="cpu") -> Workload:
+              voxel: float = 0.01, noise: bool = True, device="cpu", resident: bool = False) -> Workload:
     """Room of 12 random spheres/boxes inside walls that fill a (dims*voxel)^3 volume, 640x480 frames
     (f=525, c=(319.5, 239.5)); random-walk camera (translation <= 2 cm per frame, rotation <= 1.5 deg
     about a random axis) kept in the middle of the room with its view axis within 35 degrees of
-    horizontal; depth noise sigma = 1.5 mm * z^2."""
+    horizontal; depth noise sigma = 1.5 mm * z^2.
+
+    resident=True keeps the frames on ``device`` as one float32 torch tensor (frames, H, W) and draws
+    the noise there from a torch generator seeded with ``seed`` (a different stream of normals than
+    the numpy one, for large batched workloads)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     s = width / 640.0
     intr = Intrinsics(525.0 * s, 525.0 * s, (width - 1) / 2.0, (height - 1) / 2.0, width, height)
@@ -277,6 +285,9 @@ def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 
     q = axis_angle_quat((0.0, 1.0, 0.0), rng.uniform(0, 2 * math.pi))
     base = look_at(np.zeros(3), (0.0, 0.0, 1.0))[:, :3]  # y down, z forward along +z
     poses, depth = [], []
+    if resident:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(seed)
     for k in range(frames):
         if k > 0:
             for _ in range(100):
@@ -297,12 +308,20 @@ def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 
                     break
         R = quat_to_matrix(q) @ base
         T = np.concatenate([R, eye[:, None]], 1)
-        d = render_depth(scene, intr, T, device)
-        depth.append(add_noise(d, rng, sigma_quad=0.0015) if noise else d.astype(np.float32))
+        if resident:
+            d = render_depth_t(scene, intr, T, device)
+            if noise:
+                z = torch.randn(d.shape, generator=gen, dtype=torch.float64, device=d.device)
+                nd = d + z * (0.0015 * d * d)
+                d = torch.where((d > 0) & (nd > 0), nd, torch.zeros_like(nd))
+            depth.append(d.to(torch.float32))
+        else:
+            d = render_depth(scene, intr, T, device)
+            depth.append(add_noise(d, rng, sigma_quad=0.0015) if noise else d.astype(np.float32))
         poses.append(T)
     return Workload(f"room{dims}_{width}x{height}", intr, (dims, dims, dims), voxel, 4 * voxel,
-                    (0.0, 0.0, 0.0), np.array(poses), np.array(depth), scene, seed,
-                    depth_min=0.3, depth_max=4.0, bilateral=True)
+                    (0.0, 0.0, 0.0), np.array(poses), torch.stack(depth) if resident else np.array(depth), scene,
+                    seed, depth_min=0.3, depth_max=4.0, bilateral=True)
 
 
 def tiny(seed: int = 3, frames: int = 3, n: int = 24, width: int = 40, height: int = 30, noise=False,
@@ -329,3 +348,25 @@ def tiny(seed: int = 3, frames: int = 3, n: int = 24, width: int = 40, height: i
         poses.append(T)
     return Workload("corner24_40x30", intr, (n, n, n), voxel, 4 * voxel, (-half, -half, -half),
                     np.array(poses), np.array(depth), scene, seed, icp_iters=(10, 5))
+
+
+def batch_trajectories(seed: int = 7, n: int = 32, min_frames: int = 50, max_frames: int = 400,
+                       grids=(128, 192, 256, 320, 384), sizes=((320, 240), (640, 480)), max_k: int = 12,
+                       side: float = 2.56, noise: bool = True, device="cpu", resident: bool = False):
+    """n independent room walks of uneven length for batched runs: trajectory i has a seeded length
+    in [min_frames, max_frames], image size from ``sizes``, a cubic grid from ``grids`` over the same
+    side-metre room (voxel = side / grid, truncation 4 voxels) and K in [1, max_k] perturbation lanes.
+    Returns a list of (Workload, lanes) with lanes = [(kind, index), ...] drawn from the POSE0 twist
+    components, then TRUNC, DEPTH and further POSE0 components. resident: as for room_walk."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    order = [(0, j) for j in range(6)] + [(2, 0), (3, -1)] + [(0, j) for j in range(6)]
+    out = []
+    for i in range(n):
+        frames = int(rng.integers(min_frames, max_frames + 1))
+        w, h = sizes[int(rng.integers(0, len(sizes)))]
+        g = int(grids[int(rng.integers(0, len(grids)))])
+        k = int(rng.integers(1, max_k + 1))
+        wl = room_walk(seed=int(rng.integers(0, 2 ** 31)), frames=frames, width=w, height=h, dims=g, voxel=side / g,
+                       noise=noise, device=device, resident=resident)
+        out.append((wl, order[:k]))
+    return out

@@ -90,6 +90,17 @@ SYMBOLS = [
                                          ctypes.c_int, _c_double_p, _c_double_p, _c_double_p]),
     ("xslam_plain_read_tsdf", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("xslam_plain_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    # include/xslam_batch.h: many trajectories per step
+    ("xslam_batch_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    ("xslam_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("xslam_batch_step", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("xslam_batch_sync", ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
+    ("xslam_batch_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_double_p, _c_double_p, _c_double_p]),
+    ("xslam_batch_latency", ctypes.c_int, [ctypes.c_void_p, _c_float_p]),
+    ("xslam_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _c_int_p,
+                                            _c_float_p]),
+    ("xslam_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
 STAGES = ("prepare", "icp", "integrate", "raycast", "other")
 
@@ -384,3 +395,77 @@ class XSlamPlain:
         """part 0: Re F, 1: Im F / h, 2: W, into a CUDA float64 tensor of nx*ny*nz."""
         self._check(self.lib.xslam_plain_read_tsdf(self.h, int(run), int(part), _dev(out, "float64")))
         return out
+
+
+class XSlamBatch:
+    """Several XSlam handles advanced together, one CUDA graph per step (include/xslam_batch.h).
+    Every handle must be before its first frame with its lanes (set_lanes) and pose (set_pose) set."""
+
+    def __init__(self, handles, stream=None):
+        self.lib = load()
+        self.handles = list(handles)  # keeps them alive
+        n = len(self.handles)
+        arr = (ctypes.c_void_p * n)(*[h.h for h in self.handles])
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        b = ctypes.c_void_p()
+        st = self.lib.xslam_batch_create(ctypes.byref(b), n, arr, ctypes.c_void_p(stream))
+        if st != OK:
+            raise XSlamError(st, self.lib.xslam_batch_last_error(None).decode())
+        self.b = b
+        self.n = n
+        self._keep = None
+
+    def _check(self, st):
+        if st != OK:
+            raise XSlamError(st, self.lib.xslam_batch_last_error(self.b).decode())
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.xslam_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptrs(self, depths):
+        assert len(depths) == self.n
+        return (ctypes.c_void_p * self.n)(*[None if d is None else _dev(d).value for d in depths])
+
+    def step(self, depths):
+        """depths: n CUDA float32 tensors (or None for a trajectory that does not advance)."""
+        self._keep = list(depths)  # the tensors must outlive the asynchronous step
+        self._check(self.lib.xslam_batch_step(self.b, self._ptrs(depths)))
+
+    def sync(self):
+        nf = (ctypes.c_int * self.n)()
+        self._check(self.lib.xslam_batch_sync(self.b, nf))
+        return list(nf)
+
+    def read(self, i):
+        K = self.handles[i].K
+        pose = np.zeros(12)
+        dpose = np.zeros(max(1, 12 * K))
+        dtw = np.zeros(max(1, 6 * K))
+        self._check(self.lib.xslam_batch_read(self.b, int(i), _dptr(pose), _dptr(dpose), _dptr(dtw)))
+        return pose.reshape(3, 4), dpose[:12 * K].reshape(K, 3, 4), dtw[:6 * K].reshape(K, 6)
+
+    def latency(self):
+        ms = np.zeros(self.n, np.float32)
+        self._check(self.lib.xslam_batch_latency(self.b, ms.ctypes.data_as(_c_float_p)))
+        return ms
+
+    def autotune(self, frames, steps):
+        """frames[s][i]: CUDA depth tensor of trajectory i at step s (None = inactive)."""
+        flat = []
+        for s_ in range(steps):
+            flat += [None if d is None else _dev(d).value for d in frames[s_]]
+        arr = (ctypes.c_void_p * len(flat))(*flat)
+        d = ctypes.c_int(0)
+        ms = np.zeros(5, np.float32)
+        self._check(self.lib.xslam_batch_autotune(self.b, arr, int(steps), ctypes.byref(d), ms.ctypes.data_as(_c_float_p)))
+        return d.value, ms
