@@ -178,6 +178,8 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   ok &= cudaMalloc(&b.result, sizeof(double) * kResLen) == cudaSuccess;
   ok &= cudaMalloc(&b.stats, sizeof(unsigned long long) * 2) == cudaSuccess;
   ok &= cudaMalloc(&b.hit, sizeof(int) * hw) == cudaSuccess;
+  ok &= cudaMalloc(&b.tiles, sizeof(int) * (size_t)fuse_tile_count(p)) == cudaSuccess;
+  ok &= cudaMalloc(&b.tile_ctr, sizeof(unsigned) * 2) == cudaSuccess;
   ok &= cudaMalloc(&h->d_kinds, sizeof(int) * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&h->d_index, sizeof(int) * kMaxLanes) == cudaSuccess;
   if (max_lanes >= 6) ok &= cudaMalloc(&h->model_q, sizeof(float) * hw * (1 + 6 * 7)) == cudaSuccess;
@@ -209,6 +211,7 @@ extern "C" xslam_status xslam_destroy(xslam_t h) {
   for (int l = 0; l < 3; ++l) cudaFree(b.pyr[l]);
   cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp);
   cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.hit);
+  cudaFree(b.tiles); cudaFree(b.tile_ctr);
   for (int st = 0; st < XSLAM_NSTAGE; ++st)
     for (int i = 0; i < kProfRing; ++i)
       for (int k = 0; k < 2; ++k)
@@ -258,6 +261,7 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   CU(cudaMemsetAsync(h->b.pose + 12, 0, sizeof(double) * 12 * (kMaxLanes - 1), h->s));
   CU(cudaMemsetAsync(h->b.result, 0, sizeof(double) * kResLen, h->s));
   CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * 2, h->s));
+  CU(cudaMemsetAsync(h->b.tile_ctr, 0, sizeof(unsigned) * 2, h->s));
   h->frame = 0;
   h->K = 0;
   h->p.L = 1;
@@ -694,6 +698,7 @@ extern "C" xslam_status xslam_profile(xslam_t h, int enable) {
     }
     h->pframes = 0;
     CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * 2, h->s));
+  CU(cudaMemsetAsync(h->b.tile_ctr, 0, sizeof(unsigned) * 2, h->s));
   }
   if (!enable && h->profiling) {
     xslam_status st = prof_accumulate(h);

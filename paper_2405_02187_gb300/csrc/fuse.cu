@@ -8,16 +8,24 @@
 // so culled voxels cost no volume traffic. Imaginary lanes follow by the tangent rule through the
 // same arithmetic (pose lanes through p_c and x, TRUNC lanes through mu, DEPTH lanes through L).
 //
-// Thread block = 32 x 8 voxel columns, each thread walking 8 voxels along z. A block whose box lies
-// entirely behind the camera or beyond one image edge is skipped (exact: the projection of a convex
-// set in front of the camera is the hull of its corners' projections).
+// The volume is cut into 8 x 8 x 8 tiles. A first kernel lists the tiles the frame can touch (a tile
+// whose box lies entirely behind the camera or beyond one image edge cannot: exact, as the projection
+// of a convex set in front of the camera is the hull of its corners' projections); a fixed grid then
+// walks the list, a thread per voxel column of 8 along z (small tiles: at 640x480 in a 256^3 room an
+// 8^3 tile list holds about twice the updated voxels, a 32 x 8 x 8 one nearly four times). The update kernel is instantiated for each
+// lane count, so every lane of a voxel is loaded before any is stored (one memory round trip per
+// voxel rather than one per lane).
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace xslam {
 
-constexpr int kBX = 32, kBY = 8, kBZ = 8;
+constexpr int kBX = 8, kBY = 8, kBZ = 8;  // tile of voxels
+constexpr int kTPB = 4;                   // tiles per block iteration: 4 x 64 threads
 
-// Update voxel (i, j, k) if the frame observes it; returns whether it did.
+// Update voxel (i, j, k) if the frame observes it; returns whether it did. NL = 1 + K lanes.
+template <int NL>
 __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restrict__ D, const float (*sT)[12],
                                            float* __restrict__ F, float* __restrict__ Wt, int i, int j, int k,
                                            size_t n) {
@@ -47,17 +55,24 @@ __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restr
   const bool clamp = sdf >= p.mu;
   const float FD = clamp ? 1.f : sdf / p.mu;
 
+  // every lane of the voxel is loaded before any is stored: the loads then leave together (one
+  // memory round trip per voxel) instead of one round trip per lane behind each store to F
   const float w = Wt[v];
+  const float f0 = F[v];
+  float fl[NL];
+#pragma unroll
+  for (int l = 1; l < NL; ++l) fl[l] = F[(size_t)l * n + v];
   const float w1 = w + 1.f;
   const float inv = 1.f / w1;
-  const float Fn = (w * F[v] + FD) / w1;  // an unobserved voxel (w = 0) takes F_D whatever its sentinel value
+  const float Fn = (w * f0 + FD) / w1;  // an unobserved voxel (w = 0) takes F_D whatever its sentinel value
   F[v] = Fn;
   Wt[v] = (p.w_max > 0.f) ? fminf(w1, p.w_max) : w1;
 
   // tangents of L with respect to the pixel coordinates
   const float dLda = (1.f - bb) * (d10 - d00) + bb * (d11 - d01);
   const float dLdb = (1.f - a) * (d01 - d00) + a * (d11 - d10);
-  for (int l = 1; l < p.L; ++l) {
+#pragma unroll
+  for (int l = 1; l < NL; ++l) {
     const float* Tl = sT[l];
     // p_c' = dR^T (p - t) - R^T dt
     const float ex = Tl[3], ey = Tl[7], ez = Tl[11];
@@ -69,69 +84,148 @@ __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restr
     const float L_l = dLda * x_l + dLdb * y_l + p.dD[l];
     const float sdf_l = L_l - pcz_l;
     const float FD_l = clamp ? 0.f : (sdf_l - FD * p.dmu[l]) / p.mu;
-    float* Fl = F + (size_t)l * n + v;
-    *Fl = (w * (*Fl) + FD_l) * inv;
+    F[(size_t)l * n + v] = (w * fl[l] + FD_l) * inv;
   }
   return true;
 }
 
-__global__ void __launch_bounds__(kBX * kBY) k_integrate(Params p, const float* __restrict__ D,
-                                                        const double* __restrict__ pose, float* __restrict__ F,
-                                                        float* __restrict__ Wt, unsigned long long* __restrict__ stats) {
+// One thread per 8 x 8 x 8 tile: a tile any of whose voxels the frame can update is appended to the
+// list (warp-aggregated atomics). The test is the exact corner test: the tile's box (padded by half a
+// voxel around the voxel centres) is skipped if all 8 corners lie behind the camera or beyond the
+// same image edge.
+__global__ void __launch_bounds__(256) k_fuse_tiles(Params p, const double* __restrict__ pose, int* __restrict__ tiles,
+                                                   unsigned* __restrict__ ctr) {
   pdl_enter();
-  __shared__ float sT[kMaxLanes][12];
-  __shared__ int s_out[8];
-  const int tid = threadIdx.x + kBX * threadIdx.y;
-  for (int i = tid; i < p.L * 12; i += kBX * kBY) sT[i / 12][i % 12] = (float)pose[i];
-  __syncthreads();
-  const int i0 = blockIdx.x * kBX, j0 = blockIdx.y * kBY, k0 = blockIdx.z * kBZ;
-  if (tid < 8) {
-    // corner of the block's box (padded by half a voxel around the voxel centres)
-    const float* T = sT[0];
-    const float cx = p.ox + ((tid & 1) ? min(i0 + kBX, p.nx) : i0) * p.voxel;
-    const float cy = p.oy + ((tid & 2) ? min(j0 + kBY, p.ny) : j0) * p.voxel;
-    const float cz = p.oz + ((tid & 4) ? min(k0 + kBZ, p.nz) : k0) * p.voxel;
-    const float dx = cx - T[3], dy = cy - T[7], dz = cz - T[11];
-    const float px = T[0] * dx + T[4] * dy + T[8] * dz;
-    const float py = T[1] * dx + T[5] * dy + T[9] * dz;
-    const float pz = T[2] * dx + T[6] * dy + T[10] * dz;
-    int code;  // bit 0: behind, 1: left, 2: right, 3: above, 4: below
-    if (!(pz > 0.f)) {
-      code = 1;  // a corner behind the camera only agrees with "behind"
-    } else {
-      const float x = p.fx * px / pz + p.cx, y = p.fy * py / pz + p.cy;
-      code = (x < 0.f ? 2 : 0) | (x >= (float)(p.W - 1) ? 4 : 0) | (y < 0.f ? 8 : 0) | (y >= (float)(p.H - 1) ? 16 : 0);
-    }
-    s_out[tid] = code;
-  }
-  __syncthreads();
-  {
-    int all = 31;
+  const int ntx = (p.nx + kBX - 1) / kBX, nty = (p.ny + kBY - 1) / kBY, ntz = (p.nz + kBZ - 1) / kBZ;
+  const int nt = ntx * nty * ntz;
+  float T[12];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) all &= s_out[c];
-    if (all) return;  // nothing in this box can be updated
+  for (int e = 0; e < 12; ++e) T[e] = (float)pose[e];
+  for (int t0 = blockIdx.x * blockDim.x; t0 < nt; t0 += gridDim.x * blockDim.x) {
+    const int t = t0 + threadIdx.x;
+    bool keep = false;
+    if (t < nt) {
+      const int i0 = (t % ntx) * kBX, j0 = ((t / ntx) % nty) * kBY, k0 = (t / (ntx * nty)) * kBZ;
+      int all = 31;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float cx = p.ox + ((c & 1) ? min(i0 + kBX, p.nx) : i0) * p.voxel;
+        const float cy = p.oy + ((c & 2) ? min(j0 + kBY, p.ny) : j0) * p.voxel;
+        const float cz = p.oz + ((c & 4) ? min(k0 + kBZ, p.nz) : k0) * p.voxel;
+        const float dx = cx - T[3], dy = cy - T[7], dz = cz - T[11];
+        const float px = T[0] * dx + T[4] * dy + T[8] * dz;
+        const float py = T[1] * dx + T[5] * dy + T[9] * dz;
+        const float pz = T[2] * dx + T[6] * dy + T[10] * dz;
+        int code;  // bit 0: behind, 1: left, 2: right, 3: above, 4: below
+        if (!(pz > 0.f)) {
+          code = 1;  // a corner behind the camera only agrees with "behind"
+        } else {
+          const float x = p.fx * px / pz + p.cx, y = p.fy * py / pz + p.cy;
+          code = (x < 0.f ? 2 : 0) | (x >= (float)(p.W - 1) ? 4 : 0) | (y < 0.f ? 8 : 0) | (y >= (float)(p.H - 1) ? 16 : 0);
+        }
+        all &= code;
+      }
+      keep = all == 0;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (m) {
+      const int lane = threadIdx.x & 31;
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(ctr, (unsigned)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (keep) tiles[base + __popc(m & ((1u << lane) - 1u))] = t;
+    }
   }
-  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+}
+
+// Fixed grid over the tile list; a block takes 4 tiles at a time, a thread per voxel column of a tile
+// (a warp covers 8 x 4 columns), each thread walking the tile's 8 voxels along z. The last block to
+// finish clears the list counters for the next launch.
+template <int NL>
+__global__ void __launch_bounds__(kBX * kBY * kTPB) k_integrate(Params p, const float* __restrict__ D,
+                                                        const double* __restrict__ pose, float* __restrict__ F,
+                                                        float* __restrict__ Wt, unsigned long long* __restrict__ stats,
+                                                        const int* __restrict__ tiles, unsigned* __restrict__ ctr) {
+  pdl_enter();
+  __shared__ float sT[NL][12];
+  __shared__ bool s_last;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < NL * 12; i += blockDim.x) sT[i / 12][i % 12] = (float)pose[i];
+  __syncthreads();
+  const unsigned count = ctr[0];
+  const int ntx = (p.nx + kBX - 1) / kBX, nty = (p.ny + kBY - 1) / kBY;
   const size_t n = vox_count(p);
+  const int sub = tid / (kBX * kBY), cx = tid % kBX, cy = (tid / kBX) % kBY;
   int cnt = 0;
-  if (i < p.nx && j < p.ny) {
-    for (int dk = 0; dk < kBZ; ++dk) {
-      const int k = k0 + dk;
-      if (k >= p.nz) break;
-      cnt += fuse_voxel(p, D, sT, F, Wt, i, j, k, n);
+  for (unsigned q = blockIdx.x * kTPB + sub; q < count; q += gridDim.x * kTPB) {
+    const int t = tiles[q];
+    const int i = (t % ntx) * kBX + cx, j = ((t / ntx) % nty) * kBY + cy;
+    const int k0 = (t / (ntx * nty)) * kBZ;
+    if (i < p.nx && j < p.ny) {
+      for (int dk = 0; dk < kBZ; ++dk) {
+        const int k = k0 + dk;
+        if (k >= p.nz) break;
+        cnt += fuse_voxel<NL>(p, D, sT, F, Wt, i, j, k, n);
+      }
     }
   }
   // updated-voxel count: warp sums, one atomic per warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if (threadIdx.x == 0 && cnt) atomicAdd(stats, (unsigned long long)cnt);
+  if ((tid & 31) == 0 && cnt) atomicAdd(stats, (unsigned long long)cnt);
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(ctr + 1, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && tid == 0) {
+    ctr[0] = 0u;
+    ctr[1] = 0u;
+  }
+}
+
+template <int NL>
+static cudaError_t launch_integrate_nl(const Params& p, const Buffers& b, int grid, cudaStream_t s) {
+  return launch_pdl(k_integrate<NL>, dim3(grid), dim3(kBX * kBY * kTPB), 0, s, p, b.pyr[0], b.pose, b.F, b.Wt, b.stats,
+                    b.tiles, b.tile_ctr);
+}
+
+int fuse_tile_count(const Params& p) {
+  return ((p.nx + kBX - 1) / kBX) * ((p.ny + kBY - 1) / kBY) * ((p.nz + kBZ - 1) / kBZ);
 }
 
 cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s) {
-  dim3 blk(kBX, kBY, 1), grd((p.nx + kBX - 1) / kBX, (p.ny + kBY - 1) / kBY, (p.nz + kBZ - 1) / kBZ);
-  const cudaError_t e = launch_pdl(k_integrate, grd, blk, 0, s, p, b.pyr[0], b.pose, b.F, b.Wt, b.stats);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int nt = fuse_tile_count(p);
+  cudaError_t e = launch_pdl(k_fuse_tiles, dim3(std::min((nt + 255) / 256, 4 * sms)), dim3(256), 0, s, p, b.pose,
+                             b.tiles, b.tile_ctr);
   if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  const int grid = std::max(1, std::min((nt + kTPB - 1) / kTPB, 4 * sms));
+  switch (p.L) {
+    case 1: return launch_integrate_nl<1>(p, b, grid, s);
+    case 2: return launch_integrate_nl<2>(p, b, grid, s);
+    case 3: return launch_integrate_nl<3>(p, b, grid, s);
+    case 4: return launch_integrate_nl<4>(p, b, grid, s);
+    case 5: return launch_integrate_nl<5>(p, b, grid, s);
+    case 6: return launch_integrate_nl<6>(p, b, grid, s);
+    case 7: return launch_integrate_nl<7>(p, b, grid, s);
+    case 8: return launch_integrate_nl<8>(p, b, grid, s);
+    case 9: return launch_integrate_nl<9>(p, b, grid, s);
+    case 10: return launch_integrate_nl<10>(p, b, grid, s);
+    case 11: return launch_integrate_nl<11>(p, b, grid, s);
+    case 12: return launch_integrate_nl<12>(p, b, grid, s);
+    case 13: return launch_integrate_nl<13>(p, b, grid, s);
+    case 14: return launch_integrate_nl<14>(p, b, grid, s);
+    case 15: return launch_integrate_nl<15>(p, b, grid, s);
+    case 16: return launch_integrate_nl<16>(p, b, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace xslam

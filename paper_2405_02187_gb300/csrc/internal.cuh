@@ -60,6 +60,8 @@ struct Buffers {
   double* result;   // read-out: 12 (pose) + 12 K (dpose) + 6 K (dtwist) + 27 L (last system)
   unsigned long long* stats;  // [0] voxels updated by fusion, [1] pixels with a ray-cast surface
   int* hit;                   // per pixel: index m of the first sample of the ray-cast hit pair, -1 = none
+  int* tiles;                 // fusion: tiles the frame can touch (fuse_tile_count entries at most)
+  unsigned* tile_ctr;         // fusion: [0] listed tiles, [1] finished blocks (both 0 between launches)
 };
 
 __host__ __device__ inline size_t vox_count(const Params& p) {
@@ -100,6 +102,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // ---------------------------------------------------------------------------------------------
 cudaError_t launch_prepare(const Params& p, const Buffers& b, int levels, cudaStream_t s);
 cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s);
+int fuse_tile_count(const Params& p);
 cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose, float* depth,
                            float* vmap, float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s);
 cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int iter_flags, int nblk, cudaStream_t s);
