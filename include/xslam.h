@@ -138,10 +138,17 @@ xslam_status xslam_raycast(xslam_t h, const double* T, float* depth, float* vmap
  * Relocalisation loss of a query depth frame and its derivatives with respect to the query pose
  * (Sec. 5.2 with the point-to-plane reading): E(T_q) = mean over pixels of r_u^2 with
  * r_u = ((T_q V_q(u)) - V_g(u)) . N_g(u), where V_g, N_g are ray cast from the volume at T_q itself and
- * V_q = D_q K^-1 u (pixels whose vertex or model is invalid, or that fail the ICP gates, are skipped).
- * order 1: *loss and grad[6] (left twist, Eq. csfd on six lanes, one per twist component);
- * order 2 is not built (XSLAM_EINVAL). query_depth is a device pointer. Needs max_lanes >= 6 and a
- * handle with no frame-sequence lanes in use (call between sequences or on a separate handle).
+ * V_q = D_q K^-1 u (pixels whose vertex or model is invalid, or that fail the distance gate, are
+ * skipped). query_depth is a device pointer (range gated, and bilaterally filtered if the handle's
+ * configuration says so). Derivatives are with respect to a left twist xi of T_q (phi then rho).
+ * order 1: *loss and grad[6] (Eq. csfd on six lanes, one per twist component). Needs max_lanes >= 6
+ *   and a handle with no frame-sequence lanes in use (call between sequences or on a separate handle).
+ * order 2: *loss, grad[6] and hess[21], the upper triangle of the Hessian row by row ((0,0), (0,1),
+ *   ..., (0,5), (1,1), ...), from the second-order (bicomplex) step of Sec. 3 in truncated arithmetic:
+ *   each of the 21 pairs j <= k evaluates the ray-cast refinement and the residual on numbers
+ *   a + b e1 + c e2 + d e1 e2 (e1^2 = e2^2 = 0) from T = exp(e1 G_j + e2 G_k) T_q, with the real pose's
+ *   ray-cast and gating decisions. Any handle (no lanes needed); the handle's frame state is kept.
+ * Any output pointer may be NULL. Errors: XSLAM_EINVAL (NULL input, order not 1 or 2, non-finite T_q).
  */
 xslam_status xslam_grad(xslam_t h, const float* query_depth, const double T_q[12], int order, double* loss,
                         double grad[6], double* hess);

@@ -171,6 +171,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   ok &= cudaMalloc(&b.pose, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&b.pose_prev, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&h->pose_tmp, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
+  ok &= cudaMalloc(&h->hess_poses, sizeof(float) * 21 * 12 * 4) == cudaSuccess;
   ok &= cudaMalloc(&b.partial, sizeof(float) * (size_t)(nblk_max + 4) * kNT * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&b.partial_n, sizeof(int) * nblk_max) == cudaSuccess;
   ok &= cudaMalloc(&b.ticket, sizeof(unsigned)) == cudaSuccess;
@@ -209,7 +210,7 @@ extern "C" xslam_status xslam_destroy(xslam_t h) {
   Buffers& b = h->b;
   cudaFree(b.F); cudaFree(b.Wt); cudaFree(b.depth_in); cudaFree(b.gated);
   for (int l = 0; l < 3; ++l) cudaFree(b.pyr[l]);
-  cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp);
+  cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp); cudaFree(h->hess_poses);
   cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.hit);
   cudaFree(b.tiles); cudaFree(b.tile_ctr);
   for (int st = 0; st < XSLAM_NSTAGE; ++st)
@@ -646,11 +647,80 @@ extern "C" xslam_status xslam_icp_system(xslam_t h, int level, const double* Tj,
   return st;
 }
 
+// The 21 truncated-bicomplex start poses exp(e1 G_j + e2 G_k) T_q (j <= k) of the order-2 loss:
+// (I + e1 G_j + e2 G_k + e1 e2 (G_j G_k + G_k G_j) / 2) T_q, exact with e1^2 = e2^2 = 0; G_j the
+// generators of the left twist (phi then rho). Out: [pair][element][a, e1, e2, e1 e2] as float.
+static void hess_poses(const double* Tq, float* out) {
+  double G[6][4][4] = {};
+  for (int j = 0; j < 3; ++j) {  // [e_j]x
+    const int a = (j + 1) % 3, b = (j + 2) % 3;
+    G[j][b][a] = 1.0;
+    G[j][a][b] = -1.0;
+  }
+  for (int j = 3; j < 6; ++j) G[j][j - 3][3] = 1.0;
+  double T[4][4] = {};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 4; ++c) T[r][c] = Tq[4 * r + c];
+  T[3][3] = 1.0;
+  auto mul = [](const double A[4][4], const double B[4][4], double C[4][4]) {
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) {
+        double s = 0.0;
+        for (int k = 0; k < 4; ++k) s += A[r][k] * B[k][c];
+        C[r][c] = s;
+      }
+  };
+  int q = 0;
+  for (int j = 0; j < 6; ++j)
+    for (int k = j; k < 6; ++k, ++q) {
+      double GjT[4][4], GkT[4][4], GjGk[4][4], GkGj[4][4], S[4][4], ST[4][4];
+      mul(G[j], T, GjT);
+      mul(G[k], T, GkT);
+      mul(G[j], G[k], GjGk);
+      mul(G[k], G[j], GkGj);
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) S[r][c] = 0.5 * (GjGk[r][c] + GkGj[r][c]);
+      mul(S, T, ST);
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 4; ++c) {
+          float* o = out + 4 * (12 * q + 4 * r + c);
+          o[0] = (float)T[r][c];
+          o[1] = (float)GjT[r][c];
+          o[2] = (float)GkT[r][c];
+          o[3] = (float)ST[r][c];
+        }
+    }
+}
+
 extern "C" xslam_status xslam_grad(xslam_t h, const float* query_depth, const double* T_q, int order, double* loss,
                                    double* grad, double* hess) {
-  (void)hess;
   if (!h || !query_depth || !T_q) return fail(h, XSLAM_EINVAL, "NULL argument");
-  if (order != 1) return fail(h, XSLAM_EINVAL, "only order 1 is built");
+  if (order != 1 && order != 2) return fail(h, XSLAM_EINVAL, "order must be 1 or 2");
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(T_q[i])) return fail(h, XSLAM_EINVAL, "T_q has a non-finite entry");
+  if (order == 2) {
+    float hp[21 * 12 * 4];
+    hess_poses(T_q, hp);
+    xslam_status st = enter(h);
+    if (st != XSLAM_OK) return st;
+    CU(cudaMemcpyAsync(h->hess_poses, hp, sizeof(hp), cudaMemcpyHostToDevice, h->s));
+    CU(cudaMemcpyAsync(h->pose_tmp, T_q, sizeof(double) * 12, cudaMemcpyHostToDevice, h->s));
+    if ((st = copy_depth(h, query_depth, 1)) != XSLAM_OK) return st;
+    CU(launch_prepare(h->p, h->b, 1, h->s));
+    CU(launch_march(h->p, h->b, h->pose_tmp, h->s));
+    const int nblk = std::min((int)((size_t)h->p.W * h->p.H + 127) / 128, 4 * h->nsm);
+    CU(launch_hess(h->p, h->b, h->b.pyr[0], h->hess_poses, h->b.result + kResSys, nblk, h->s));
+    CU(cudaMemcpyAsync(h->h_result, h->b.result, sizeof(double) * kResLen, cudaMemcpyDeviceToHost, h->s));
+    st = leave(h);
+    CU(cudaStreamSynchronize(h->s));
+    const double* r = h->h_result + kResSys;
+    if (loss) *loss = r[0];
+    if (grad)
+      for (int j = 0; j < 6; ++j) grad[j] = r[1 + j];
+    if (hess)
+      for (int q = 0; q < 21; ++q) hess[q] = r[7 + q];
+    return st;
+  }
   if (h->max_lanes < 6 || !h->model_q) return fail(h, XSLAM_EINVAL, "xslam_grad needs max_lanes >= 6");
   if (h->K != 0) return fail(h, XSLAM_ESTATE, "xslam_grad needs a handle without sequence lanes (reset first)");
   Params p = h->p;

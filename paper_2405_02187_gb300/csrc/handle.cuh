@@ -24,6 +24,7 @@ struct xslam_s {
   int* d_kinds = nullptr;   // device copies of lane kinds / indices
   int* d_index = nullptr;
   double* pose_tmp = nullptr;  // scratch pose lanes (raycast / grad)
+  float* hess_poses = nullptr;  // the 21 truncated-bicomplex start poses of xslam_grad order 2
   float* model_q = nullptr;    // scratch model maps of xslam_grad (7 lanes)
   double* h_result = nullptr;  // pinned host staging
   int* h_status = nullptr;

@@ -105,9 +105,15 @@ cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s);
 int fuse_tile_count(const Params& p);
 cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose, float* depth,
                            float* vmap, float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s);
+// the real march alone: hit[pixel] = first sample of the hit pair, -1 = none
+cudaError_t launch_march(const Params& p, const Buffers& b, const double* pose, cudaStream_t s);
 cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int iter_flags, int nblk, cudaStream_t s);
 cudaError_t launch_seed_pose(const Params& p, const Buffers& b, const int* kinds, const int* index, cudaStream_t s);
 cudaError_t launch_readout(const Params& p, const Buffers& b, cudaStream_t s);
+// relocalisation loss, gradient and Hessian (hess.cu); poses: 21 x 12 truncated-bicomplex pose
+// elements (4 floats each), out: [E, g(6), H upper (21), count]
+cudaError_t launch_hess(const Params& p, const Buffers& b, const float* depth, const float* poses, double* out,
+                        int nblk, cudaStream_t s);
 cudaError_t launch_loss(const Params& p, const Buffers& b, const float* depth, const float* model,
                         const double* pose, double* out, int nblk, cudaStream_t s);
 int icp_blocks(int level_pixels, int L);

@@ -15,90 +15,9 @@
 // gather latency) records per pixel the index of the hit pair's first sample; k_refine re-evaluates
 // the pair and the six normal samples on every lane and writes the model maps.
 #include "internal.cuh"
+#include "raycast.cuh"
 
 namespace xslam {
-
-struct Tri {
-  unsigned base;   // linear index of the min corner
-  float fx, fy, fz;
-  float val;       // trilinear F (real lane)
-  float g[3];      // d val / d g (continuous voxel coordinates)
-};
-
-// Cell and real trilinear value at continuous voxel coordinate (gx, gy, gz). Returns false if the
-// cell is outside the volume or a corner is unobserved.
-__device__ __forceinline__ bool tri_real(const Params& p, const float* __restrict__ F, float gx, float gy, float gz,
-                                         Tri& t, bool want_grad) {
-  if (!(gx >= 0.f && gx < (float)(p.nx - 1) && gy >= 0.f && gy < (float)(p.ny - 1) && gz >= 0.f &&
-        gz < (float)(p.nz - 1)))
-    return false;
-  const int i = (int)gx, j = (int)gy, k = (int)gz;  // gx >= 0: truncation is floor
-  const unsigned sy = (unsigned)p.nx, sz = (unsigned)p.nx * (unsigned)p.ny;
-  const unsigned b = (unsigned)i + sy * (unsigned)j + sz * (unsigned)k;
-  const float c000 = __ldg(F + b), c100 = __ldg(F + b + 1), c010 = __ldg(F + b + sy), c110 = __ldg(F + b + 1 + sy);
-  const float c001 = __ldg(F + b + sz), c101 = __ldg(F + b + 1 + sz), c011 = __ldg(F + b + sy + sz),
-              c111 = __ldg(F + b + 1 + sy + sz);
-  const float mx = fmaxf(fmaxf(fmaxf(c000, c100), fmaxf(c010, c110)), fmaxf(fmaxf(c001, c101), fmaxf(c011, c111)));
-  if (!(mx <= 1.f)) return false;  // an unobserved corner
-  const float fx = gx - i, fy = gy - j, fz = gz - k;
-  const float x00 = c000 + fx * (c100 - c000), x10 = c010 + fx * (c110 - c010);
-  const float x01 = c001 + fx * (c101 - c001), x11 = c011 + fx * (c111 - c011);
-  const float y0 = x00 + fy * (x10 - x00), y1 = x01 + fy * (x11 - x01);
-  t.val = y0 + fz * (y1 - y0);
-  t.base = b;
-  t.fx = fx;
-  t.fy = fy;
-  t.fz = fz;
-  if (want_grad) {
-    const float dx00 = c100 - c000, dx10 = c110 - c010, dx01 = c101 - c001, dx11 = c111 - c011;
-    t.g[0] = (1.f - fz) * ((1.f - fy) * dx00 + fy * dx10) + fz * ((1.f - fy) * dx01 + fy * dx11);
-    t.g[1] = (1.f - fz) * (x10 - x00) + fz * (x11 - x01);
-    t.g[2] = y1 - y0;
-  }
-  return true;
-}
-
-// Imaginary part of the trilinear F on lane plane Fl at the cell of t, with the sample position
-// moving by gl (voxel units): grad . gl + sum_c w_c Im F_c.
-__device__ __forceinline__ float tri_lane(const Params& p, const float* __restrict__ Fl, const Tri& t, float glx,
-                                          float gly, float glz) {
-  float v = t.g[0] * glx + t.g[1] * gly + t.g[2] * glz;
-  if (Fl) {
-    const unsigned sy = (unsigned)p.nx, sz = (unsigned)p.nx * (unsigned)p.ny;
-    const unsigned b = t.base;
-    const float x00 = __ldg(Fl + b) + t.fx * (__ldg(Fl + b + 1) - __ldg(Fl + b));
-    const float x10 = __ldg(Fl + b + sy) + t.fx * (__ldg(Fl + b + 1 + sy) - __ldg(Fl + b + sy));
-    const float x01 = __ldg(Fl + b + sz) + t.fx * (__ldg(Fl + b + 1 + sz) - __ldg(Fl + b + sz));
-    const float x11 = __ldg(Fl + b + sy + sz) + t.fx * (__ldg(Fl + b + 1 + sy + sz) - __ldg(Fl + b + sy + sz));
-    const float y0 = x00 + t.fy * (x10 - x00), y1 = x01 + t.fy * (x11 - x01);
-    v += y0 + t.fz * (y1 - y0);
-  }
-  return v;
-}
-
-// The ray of pixel (u, v) in continuous voxel coordinates: g(alpha) = g0 + alpha * gd (real pose).
-struct Ray {
-  float rx, ry;               // K^-1 (u, v, 1)
-  float dirx, diry, dirz;     // R K^-1 (u, v, 1)
-  float g0x, g0y, g0z, gdx, gdy, gdz;
-};
-
-__device__ __forceinline__ Ray make_ray(const Params& p, const float* T, int u, int v) {
-  Ray r;
-  r.rx = (u - p.cx) / p.fx;
-  r.ry = (v - p.cy) / p.fy;
-  r.dirx = T[0] * r.rx + T[1] * r.ry + T[2];
-  r.diry = T[4] * r.rx + T[5] * r.ry + T[6];
-  r.dirz = T[8] * r.rx + T[9] * r.ry + T[10];
-  const float inv_vox = 1.f / p.voxel;
-  r.g0x = (T[3] - p.ox) * inv_vox - 0.5f;
-  r.g0y = (T[7] - p.oy) * inv_vox - 0.5f;
-  r.g0z = (T[11] - p.oz) * inv_vox - 0.5f;
-  r.gdx = r.dirx * inv_vox;
-  r.gdy = r.diry * inv_vox;
-  r.gdz = r.dirz * inv_vox;
-  return r;
-}
 
 __global__ void __launch_bounds__(256) k_march(Params p, const float* __restrict__ F, const double* __restrict__ pose,
                                                int* __restrict__ hit) {
@@ -264,6 +183,11 @@ __global__ void __launch_bounds__(256) k_refine(Params p, const float* __restric
       nmap[(size_t)(3 * l + 2) * hw + pix] = (gzl - Nz * dot) / nrm;
     }
   }
+}
+
+cudaError_t launch_march(const Params& p, const Buffers& b, const double* pose, cudaStream_t s) {
+  dim3 blk(32, 8), grd((p.W + 31) / 32, (p.H + 7) / 8);
+  return launch_pdl(k_march, grd, blk, 0, s, p, b.F, pose, b.hit);
 }
 
 cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose, float* depth, float* vmap,

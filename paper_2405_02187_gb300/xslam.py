@@ -273,6 +273,12 @@ class XSlam:
         H = np.zeros(21)
         self._check(self.lib.xslam_grad(self.h, _dev(query_depth), _dptr(T_q), int(order), ctypes.byref(loss),
                                         _dptr(g), _dptr(H)))
+        if order == 2:
+            Hm = np.zeros((6, 6))
+            iu = np.triu_indices(6)
+            Hm[iu] = H
+            Hm[(iu[1], iu[0])] = H
+            return loss.value, g, Hm
         return loss.value, g
 
     def read_tsdf(self, lane, out):
