@@ -20,7 +20,9 @@ twist of the first pose). Prints one JSON line (rank 0):
   uncomplexified_fp32  the same frames with no imaginary lanes (K = 0);
   batched      32 independent trajectories of 50-400 frames (mixed image sizes, grids and lane
                counts) advanced together through include/xslam_batch.h: aggregate frames/s and the
-               per-trajectory frame latency.
+               per-trajectory frame latency;
+  second_order relocalisation on a 512^3 map: gradient descent vs Newton's method with the Hessian
+               from xslam_grad order 2, and the time of one Hessian evaluation.
 
 --impl reference times the oracle alone on sampled steps of the same workload (see _reference).
 Multi-GPU (torchrun): every rank runs its own independent sequence (replicas, no collective in the
@@ -439,6 +441,7 @@ def run_ours(args, rank, world, local_rank):
                      grad_rel_err_fp32_lanes_vs_plain=err, grad_err_frame=last)
 
     batched = None if args.no_batch else run_batch(args, dev, rank)
+    second = None if args.no_second_order else run_second_order(args, dev, rank)
 
     # ---- CPU oracle on the host cores (rank 0, N = 1): frame 1 of the same sequence ----
     cpu = None
@@ -469,7 +472,7 @@ def run_ours(args, rank, world, local_rank):
                             tracking_failures=int(n_fail)),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(round(launches_per_frame * K)),
                 clocks=clk, stage_ms_per_frame=stage_ms, grad_rel_err_vs_oracle=grad_err,
-                plain_fp64=plain, uncomplexified_fp32=real32, batched=batched,
+                plain_fp64=plain, uncomplexified_fp32=real32, batched=batched, second_order=second,
                 per_frame=dict(fused_voxels=round(per_frame["fused"]), surface_pixels=round(per_frame["hits"])))
     if rank == 0:
         print(json.dumps(line))
@@ -572,6 +575,79 @@ def run_batch(args, dev, rank):
 
 
 # ------------------------------------------------------------------------------------------------
+# second order: relocalisation with the Hessian (xslam_grad order 2)
+# ------------------------------------------------------------------------------------------------
+def run_second_order(args, dev, rank):
+    """A 512^3 x 0.8 cm map of a 40-primitive scene built from a 500-frame walk; 100 query frames of
+    that walk start from their true pose perturbed by up to 5 cm / 3 degrees and are relocalised by
+    gradient descent and by Newton's method with the eta switch (loss, gradient and Hessian from the
+    GPU). Also the time of one order-2 evaluation (21 second-order directions) and of one order-1."""
+    import torch
+    from paper_2405_02187_gb300 import reloc, synth, xslam
+
+    t0 = time.perf_counter()
+    frames = args.reloc_frames
+    wl = synth.room_walk(seed=11 + rank, frames=frames, dims=512, voxel=0.008, n_prims=40, device=dev, resident=True)
+    gen_s = time.perf_counter() - t0
+    x = xslam.XSlam(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, xslam_cfg(wl), max_lanes=6)
+    x.set_pose(wl.poses[0])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(frames):
+        x.frame(wl.depth[k], [], outputs=False)
+    e1.record()
+    _, n_fail = x.sync()
+    map_ms = e0.elapsed_time(e1)
+    rng = np.random.Generator(np.random.PCG64(5 + rank))
+    queries = []
+    for _ in range(args.reloc_queries):
+        k = int(rng.integers(frames // 5, frames))
+        dxi = np.concatenate([rng.uniform(-1, 1, 3) * math.radians(3.0) / math.sqrt(3.0),
+                              rng.uniform(-1, 1, 3) * 0.05 / math.sqrt(3.0)])
+        queries.append((k, reloc.compose(reloc.se3_exp(dxi), wl.poses[k])))
+    out = {}
+    for method in ("gd", "newton"):
+        errs, its, evals = [], [], 0
+        t1 = time.perf_counter()
+        for k, T0 in queries:
+            r = reloc.relocalise(x, wl.depth[k], T0, method=method, eta=args.reloc_eta, iters=args.reloc_iters)
+            errs.append(reloc.pose_error(r.T, wl.poses[k]))
+            its.append(r.iterations)
+            evals += r.evaluations
+        wall = time.perf_counter() - t1
+        e = np.array(errs)
+        out[method] = dict(median_cm=round(float(np.median(e[:, 0])) * 100, 3), median_deg=round(float(np.median(e[:, 1])), 4),
+                           recall_1cm_1deg=round(float(np.mean((e[:, 0] < 0.01) & (e[:, 1] < 1.0))), 3),
+                           mean_iterations=round(float(np.mean(its)), 2), evaluations=evals, wall_s=round(wall, 2))
+    init = np.array([reloc.pose_error(T0, wl.poses[k]) for k, T0 in queries])
+    # throughput of the derivative evaluations at one query
+    k, T0 = queries[0]
+    for order in (1, 2):
+        for _ in range(3):
+            x.grad(wl.depth[k], T0, order=order)
+    times = {}
+    for order in (1, 2):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        n = 20
+        for _ in range(n):
+            x.grad(wl.depth[k], T0, order=order)
+        times[order] = (time.perf_counter() - t1) / n * 1e3
+    x.close()
+    return dict(
+        workload=f"{wl.dims[0]}^3 x {wl.voxel * 100:.1f} cm map of a 40-primitive room from a {frames}-frame 640x480 walk; "
+                 f"{len(queries)} queries at their true pose perturbed by up to 5 cm / 3 deg",
+        map_ms_per_frame=round(map_ms / frames, 3), map_tracking_failures=int(n_fail),
+        initial=dict(median_cm=round(float(np.median(init[:, 0])) * 100, 3), median_deg=round(float(np.median(init[:, 1])), 4)),
+        gradient_descent=out["gd"], newton_eta=dict(out["newton"], eta=args.reloc_eta),
+        hessian=dict(ms_per_evaluation=round(times[2], 3), per_s=round(1000.0 / times[2], 1),
+                     directions=21, note="loss + gradient + 21 second-order directions over 640x480, host round trip included"),
+        gradient=dict(ms_per_evaluation=round(times[1], 3), per_s=round(1000.0 / times[1], 1)),
+        generate_s=round(gen_s, 1))
+
+
+# ------------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle as it stands
 # ------------------------------------------------------------------------------------------------
 def _reference(args, rank):
@@ -613,6 +689,11 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 complex path beside the headline")
     ap.add_argument("--plain-steps", type=int, default=20, help="timed frames of the plain FP64 path")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-trajectories run")
+    ap.add_argument("--no-second-order", action="store_true", help="skip the relocalisation / Hessian run")
+    ap.add_argument("--reloc-frames", type=int, default=500)
+    ap.add_argument("--reloc-queries", type=int, default=100)
+    ap.add_argument("--reloc-iters", type=int, default=30)
+    ap.add_argument("--reloc-eta", type=float, default=1e-3)
     ap.add_argument("--batch-n", type=int, default=32)
     ap.add_argument("--batch-min", type=int, default=50)
     ap.add_argument("--batch-max", type=int, default=400)

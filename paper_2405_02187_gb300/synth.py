@@ -262,8 +262,9 @@ def _room_scene(rng, lo, hi, n_prims, keep_out_lo, keep_out_hi, clearance):
 
 
 def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 480, dims=256,
-              voxel: float = 0.01, noise: bool = True, device="cpu", resident: bool = False) -> Workload:
-    """Room of 12 random spheres/boxes inside walls that fill a (dims*voxel)^3 volume, 640x480 frames
+              voxel: float = 0.01, noise: bool = True, device="cpu", resident: bool = False,
+              n_prims: int = 12) -> Workload:
+    """Room of n_prims (12) random spheres/boxes inside walls that fill a (dims*voxel)^3 volume, 640x480 frames
     (f=525, c=(319.5, 239.5)); random-walk camera (translation <= 2 cm per frame, rotation <= 1.5 deg
     about a random axis) kept in the middle of the room with its view axis within 35 degrees of
     horizontal; depth noise sigma = 1.5 mm * z^2.
@@ -280,7 +281,7 @@ def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 
     hi = np.full(3, side - margin)
     cam_lo = np.full(3, 0.33 * side)
     cam_hi = np.full(3, 0.67 * side)
-    scene = _room_scene(rng, lo, hi, 12, cam_lo, cam_hi, 0.35)
+    scene = _room_scene(rng, lo, hi, n_prims, cam_lo, cam_hi, 0.35)
     eye = rng.uniform(cam_lo + 0.1, cam_hi - 0.1)
     q = axis_angle_quat((0.0, 1.0, 0.0), rng.uniform(0, 2 * math.pi))
     base = look_at(np.zeros(3), (0.0, 0.0, 1.0))[:, :3]  # y down, z forward along +z

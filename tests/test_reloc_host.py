@@ -1,0 +1,59 @@
+"""Host side of relocalisation (paper_2405_02187_gb300/reloc.py) without a GPU: the SE(3) exponential
+against the matrix exponential, and the optimiser's control flow on a fake handle whose loss is a known
+quadratic in the left twist."""
+import numpy as np
+import scipy.linalg
+
+from paper_2405_02187_gb300 import reloc
+
+
+def _twist_matrix(xi):
+    M = np.zeros((4, 4))
+    M[:3, :3] = reloc._hat(xi[:3])
+    M[:3, 3] = xi[3:]
+    return M
+
+
+def test_se3_exp_is_the_matrix_exponential():
+    rng = np.random.default_rng(0)
+    for scale in (1e-9, 1e-3, 0.3, 2.0):
+        xi = rng.standard_normal(6) * scale
+        assert np.allclose(reloc.se3_exp(xi), scipy.linalg.expm(_twist_matrix(xi))[:3], atol=1e-12, rtol=1e-10)
+
+
+class _Quadratic:
+    """E(T) = 1/2 d^T A d with d the left twist taking T* to T (a log of T T*^-1, to first order)."""
+
+    def __init__(self, A, T_star):
+        self.A, self.T_star, self.calls = A, T_star, 0
+
+    def _d(self, T):
+        dR = T[:, :3] @ self.T_star[:, :3].T
+        w = 0.5 * np.array([dR[2, 1] - dR[1, 2], dR[0, 2] - dR[2, 0], dR[1, 0] - dR[0, 1]])
+        t = T[:, 3] - dR @ self.T_star[:, 3]
+        return np.concatenate([w, t])
+
+    def grad(self, depth, T, order=1):
+        self.calls += 1
+        d = self._d(np.asarray(T))
+        E = 0.5 * d @ self.A @ d
+        g = self.A @ d
+        return (E, g, self.A.copy()) if order == 2 else (E, g)
+
+
+def test_newton_converges_faster_than_gradient_descent():
+    rng = np.random.default_rng(1)
+    Q = np.linalg.qr(rng.standard_normal((6, 6)))[0]
+    A = Q @ np.diag([1e-2, 3e-2, 0.1, 0.5, 1.0, 2.0]) @ Q.T  # condition number 200
+    T_star = reloc.se3_exp(rng.standard_normal(6) * 0.3)
+    T0 = reloc.compose(reloc.se3_exp(np.array([0.03, -0.02, 0.01, 0.05, -0.04, 0.02])), T_star)
+    f = _Quadratic(A, T_star)
+    rn = reloc.relocalise(f, None, T0, method="newton", eta=1.0, iters=30)
+    rg = reloc.relocalise(_Quadratic(A, T_star), None, T0, method="gd", iters=30)
+    en = reloc.pose_error(rn.T, T_star)
+    eg = reloc.pose_error(rg.T, T_star)
+    assert rn.newton_steps >= 1 and en[0] < 1e-6 and en[1] < 1e-4
+    assert eg[0] > 10 * en[0] and rg.loss > rn.loss
+    # above eta the Newton method takes gradient steps only
+    r = reloc.relocalise(_Quadratic(A, T_star), None, T0, method="newton", eta=0.0, iters=5)
+    assert r.newton_steps == 0
