@@ -76,6 +76,9 @@ typedef struct {
   int bilateral;         /* 1: bilateral filter of the gated raw depth (Sec. 4.1; 7x7, spatial
                             sigma 4.5 px, range sigma 0.03 m), 0: off [0]                         */
   float w_max;           /* cap of the TSDF weight after each update; <= 0 means none [0]           */
+  int icp_newton;        /* 1: Newton ICP (Sec. 4.1, second-order ICP; the Hessian of each iteration's
+                            energy by the second-order complex step), for the real pose only: lanes
+                            must be 0 (XSLAM_EINVAL otherwise); 0: Gauss-Newton [0]                  */
 } xslam_config;
 
 /* Fill *cfg with the defaults above. */

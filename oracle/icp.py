@@ -128,3 +128,86 @@ def track(pyr, intr, T_init, T_prev, model, iters=(10, 5, 4), min_corr_frac=0.1,
                 return np.asarray(T_init), False
             T = se3.compose(se3.se3_exp(x), T)
     return T, True
+
+
+# ---------------------------------------------------------------------------------------------------
+# Newton ICP (Sec. 4.1: "a second-order ICP procedure using Newton's method at each ICP step", the
+# Hessian from Eq. csfd_hessian). Readings: the energy of an iteration is E(xi) = sum_u r_u(exp(xi) T_j)^2
+# with the correspondences' bilinear cells, validity and gates fixed at the real T_j (as in the
+# Gauss-Newton iteration); r, q and n follow xi through p', u_hat and the bilinear weights exactly (no
+# linearisation); the step is xi = -H^-1 g. Where H is not positive definite it is damped: H + mu I with
+# mu = 0, then 10^(k-4) trace(H) / 6 for k = 1..6, the first that is; none: the frame fails like a singular
+# Gauss-Newton system.
+# ---------------------------------------------------------------------------------------------------
+def newton_energy(D, lintr, level, Tj, Tprev, model, h=1e-20, **gates):
+    """(E, g, H, n_valid) of the iteration energy at Tj by the bicomplex step (oracle/bicomplex.py)."""
+    from . import reloc
+    from .bicomplex import Bicomplex
+    fx, fy, cx, cy, W, H_ = lintr
+    log = []
+    correspondences(D, lintr, level, Tj, Tprev, model, log=log, **gates)
+    valid, ci, cj = log[0], log[1], log[2]
+    idx = np.nonzero(valid)[0]
+    n = idx.size
+    H = np.zeros((6, 6))
+    g = np.zeros(6)
+    if n == 0:
+        return 0.0, g, H, 0
+    V = measure.vertex_map(D, lintr).reshape(-1, 3)[idx]
+    i0, j0 = ci[idx], cj[idx]
+    s = 2 ** level
+    taps = [(j0 * s, i0 * s), (j0 * s, (i0 + 1) * s), ((j0 + 1) * s, i0 * s), ((j0 + 1) * s, (i0 + 1) * s)]
+    mV = [model["V"][t] for t in taps]
+    mN = [model["N"][t] for t in taps]
+    Pinv = se3.inverse(np.asarray(Tprev, np.float64))
+    E = 0.0
+    for j in range(6):
+        for k in range(j, 6):
+            T = reloc.bicomplex_pose(Tj, j, k, h)
+            pp = [T[r, 0] * V[:, 0] + T[r, 1] * V[:, 1] + T[r, 2] * V[:, 2] + T[r, 3] for r in range(3)]
+            pc = [pp[0] * Pinv[r, 0] + pp[1] * Pinv[r, 1] + pp[2] * Pinv[r, 2] + Pinv[r, 3] for r in range(3)]
+            ux = fx * pc[0] / pc[2] + cx
+            uy = fy * pc[1] / pc[2] + cy
+            a = ux - i0
+            b = uy - j0
+            w = [(1 - a) * (1 - b), a * (1 - b), (1 - a) * b, a * b]
+            q = [w[0] * mV[0][:, r] + w[1] * mV[1][:, r] + w[2] * mV[2][:, r] + w[3] * mV[3][:, r] for r in range(3)]
+            nn = [w[0] * mN[0][:, r] + w[1] * mN[1][:, r] + w[2] * mN[2][:, r] + w[3] * mN[3][:, r] for r in range(3)]
+            res = (pp[0] - q[0]) * nn[0] + (pp[1] - q[1]) * nn[1] + (pp[2] - q[2]) * nn[2]
+            r2 = res * res
+            Es = Bicomplex(np.sum(r2.z1), np.sum(r2.z2))
+            H[j, k] = H[k, j] = float(Es.i1i2()) / (h * h)
+            if j == k:
+                g[j] = float(Es.i1()) / h
+                E = float(Es.real)
+    return E, g, H, n
+
+
+def newton_solve(H, g):
+    """x = -(H + mu I)^-1 g with the damping reading above; None if no damping makes H positive definite."""
+    tr = np.trace(H) / 6.0
+    for k in range(7):
+        mu = 0.0 if k == 0 else 10.0 ** (k - 4) * tr
+        try:
+            L = np.linalg.cholesky(H + mu * np.eye(6))
+        except np.linalg.LinAlgError:
+            continue
+        return -np.linalg.solve(L.T, np.linalg.solve(L, g))
+    return None
+
+
+def track_newton(pyr, intr, T_init, T_prev, model, iters=(10, 5, 4), min_corr_frac=0.1, **gates):
+    """Multi-level ICP from coarse to fine with Newton steps (real poses); returns (T_k, ok)."""
+    T = np.asarray(T_init, np.float64)
+    for level in range(len(iters) - 1, -1, -1):
+        lintr = measure.level_intrinsics(intr, level)
+        npx = lintr[4] * lintr[5]
+        for _ in range(iters[level]):
+            E, g, H, nv = newton_energy(pyr[level], lintr, level, T, T_prev, model, **gates)
+            if nv < min_corr_frac * npx:
+                return np.asarray(T_init), False
+            x = newton_solve(H, g)
+            if x is None:
+                return np.asarray(T_init), False
+            T = se3.compose(se3.se3_exp(x), T)
+    return T, True

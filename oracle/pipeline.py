@@ -43,6 +43,7 @@ class Config:
     pyr_range: float = 0.09
     w_max: float = np.inf
     bilateral: bool = False
+    icp_newton: bool = False  # Newton ICP (real runs only)
 
 
 @dataclasses.dataclass
@@ -102,8 +103,13 @@ class XKinectFusion:
         ok = True
         if self.k > 0:
             gates = dict(dist_gate=c.dist_gate, normal_gate_deg=c.normal_gate_deg, disc_gate=c.disc_gate)
-            self.T, ok = icp.track(pyr, self.intr, self.T, self.T, self.model, c.icp_iters,
-                                   c.min_corr_frac, log=self.decisions, **gates)
+            if c.icp_newton:
+                assert not self.pert, "Newton ICP runs the real pose only"
+                self.T, ok = icp.track_newton(pyr, self.intr, self.T, self.T, self.model, c.icp_iters,
+                                              c.min_corr_frac, **gates)
+            else:
+                self.T, ok = icp.track(pyr, self.intr, self.T, self.T, self.model, c.icp_iters,
+                                       c.min_corr_frac, log=self.decisions, **gates)
         fusion.integrate(self.F, self.W, pyr[0], self.T, self.intr, self.dims, self.origin,
                          self.voxel, self.mu, c.disc_gate, c.w_max, log=self.decisions)
         d, V, N = raycast.raycast(self.F, self.W, self.T, self.intr, self.dims, self.origin, self.voxel,

@@ -59,6 +59,7 @@ extern "C" void xslam_default_config(xslam_config* c) {
   c->pyr_range_m = 0.09f;
   c->bilateral = 0;
   c->w_max = 0.f;
+  c->icp_newton = 0;
 }
 
 static void drop_graphs(xslam_t h) {
@@ -100,6 +101,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   for (int l = 0; l < c.icp_levels; ++l)
     if (c.icp_iters[l] < 0 || c.icp_iters[l] > 100) return fail(h, XSLAM_EINVAL, "icp_iters must be 0..100");
   if (c.bilateral != 0 && c.bilateral != 1) return fail(h, XSLAM_EINVAL, "bilateral must be 0 or 1");
+  if (c.icp_newton != 0 && c.icp_newton != 1) return fail(h, XSLAM_EINVAL, "icp_newton must be 0 or 1");
   const int div = 1 << (c.icp_levels - 1);
   if (K->width < 4 * div || K->height < 4 * div || K->width % div || K->height % div)
     return fail(h, XSLAM_EINVAL, "image size must be divisible by 2^(icp_levels-1) and at least 4 pixels per level");
@@ -292,6 +294,7 @@ extern "C" xslam_status xslam_set_lanes(xslam_t h, const xslam_seed* seeds, int 
   if (!h) return XSLAM_EINVAL;
   if (K < 0 || K > h->max_lanes) return fail(h, XSLAM_EINVAL, "K must be in 0..max_lanes");
   if (K > 0 && !seeds) return fail(h, XSLAM_EINVAL, "seeds is NULL");
+  if (K > 0 && h->cfg.icp_newton) return fail(h, XSLAM_EINVAL, "Newton ICP runs the real pose only (K must be 0)");
   int kinds[kMaxLanes] = {0}, index[kMaxLanes] = {0};
   Params p = h->p;
   p.L = 1 + K;
@@ -385,7 +388,11 @@ static cudaError_t enqueue_track(xslam_t h) {
     for (int it = 0; it < h->cfg.icp_iters[l]; ++it) {
       int flags = 0;
       if (l == last_level && it == h->cfg.icp_iters[l] - 1) flags |= kIcpLast;
-      if ((e = launch_icp(h->p, h->b, l, flags, h->nblk[l], h->s)) != cudaSuccess) return e;
+      if (h->cfg.icp_newton)
+        e = launch_icp_newton(h->p, h->b, l, flags, icp_newton_blocks((h->p.W >> l) * (h->p.H >> l), h->nsm), h->s);
+      else
+        e = launch_icp(h->p, h->b, l, flags, h->nblk[l], h->s);
+      if (e != cudaSuccess) return e;
       ++n_icp;
     }
   }

@@ -107,6 +107,9 @@ cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose
                            float* vmap, float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s);
 // the real march alone: hit[pixel] = first sample of the hit pair, -1 = none
 cudaError_t launch_march(const Params& p, const Buffers& b, const double* pose, cudaStream_t s);
+// Newton ICP iteration (icp_newton.cu): real pose, lanes unused
+cudaError_t launch_icp_newton(const Params& p, const Buffers& b, int level, int flags, int nblk, cudaStream_t s);
+int icp_newton_blocks(int level_pixels, int sms);
 cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int iter_flags, int nblk, cudaStream_t s);
 cudaError_t launch_seed_pose(const Params& p, const Buffers& b, const int* kinds, const int* index, cudaStream_t s);
 cudaError_t launch_readout(const Params& p, const Buffers& b, cudaStream_t s);
