@@ -22,7 +22,8 @@ twist of the first pose). Prints one JSON line (rank 0):
                counts) advanced together through include/xslam_batch.h: aggregate frames/s and the
                per-trajectory frame latency;
   second_order relocalisation on a 512^3 map: gradient descent vs Newton's method with the Hessian
-               from xslam_grad order 2, and the time of one Hessian evaluation.
+               from xslam_grad order 2, and the time of one Hessian evaluation;
+  newton_icp   tracking failures and error of Gauss-Newton vs Newton ICP as the frame step grows.
 
 --impl reference times the oracle alone on sampled steps of the same workload (see _reference).
 Multi-GPU (torchrun): every rank runs its own independent sequence (replicas, no collective in the
@@ -442,6 +443,7 @@ def run_ours(args, rank, world, local_rank):
 
     batched = None if args.no_batch else run_batch(args, dev, rank)
     second = None if args.no_second_order else run_second_order(args, dev, rank)
+    newton = None if args.no_newton else run_newton_icp(args, dev, rank)
 
     # ---- CPU oracle on the host cores (rank 0, N = 1): frame 1 of the same sequence ----
     cpu = None
@@ -472,7 +474,7 @@ def run_ours(args, rank, world, local_rank):
                             tracking_failures=int(n_fail)),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(round(launches_per_frame * K)),
                 clocks=clk, stage_ms_per_frame=stage_ms, grad_rel_err_vs_oracle=grad_err,
-                plain_fp64=plain, uncomplexified_fp32=real32, batched=batched, second_order=second,
+                plain_fp64=plain, uncomplexified_fp32=real32, batched=batched, second_order=second, newton_icp=newton,
                 per_frame=dict(fused_voxels=round(per_frame["fused"]), surface_pixels=round(per_frame["hits"])))
     if rank == 0:
         print(json.dumps(line))
@@ -648,6 +650,49 @@ def run_second_order(args, dev, rank):
 
 
 # ------------------------------------------------------------------------------------------------
+# Newton ICP against Gauss-Newton as the frame step grows
+# ------------------------------------------------------------------------------------------------
+def run_newton_icp(args, dev, rank):
+    """The room sequence tracked with every s-th frame (s = 1, 2, 4, 6, 8) by Gauss-Newton, by Newton
+    ICP with the eta switch (eta = 1e-4 m^2) and by Newton steps only (real pose, K = 0): tracking
+    failures, the translation RMSE against the ground truth, and the device time per frame."""
+    import torch
+    from paper_2405_02187_gb300 import synth, xslam
+
+    n = args.newton_frames
+    steps = (1, 2, 4, 6, 8)
+    wl = synth.room_walk(seed=21 + rank, frames=n * max(steps), device=dev, resident=True)
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for method in ("gauss_newton", "newton", "newton_only"):
+        rows = {}
+        for s in steps:
+            cfg = xslam_cfg(wl)
+            cfg.icp_newton = 0 if method == "gauss_newton" else 1
+            cfg.icp_newton_eta = float("inf") if method == "newton_only" else 1e-4
+            x = xslam.XSlam(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, cfg, max_lanes=0)
+            x.set_pose(wl.poses[0])
+            idx = list(range(0, n * s, s))
+            poses = []
+            torch.cuda.synchronize()
+            e0.record()
+            for k in idx:
+                pose, _, _, st = x.frame(wl.depth[k], [])
+                poses.append(pose)
+            e1.record()
+            torch.cuda.synchronize()
+            _, fails = x.sync()
+            err = np.array([np.linalg.norm(pz[:, 3] - wl.poses[k][:, 3]) for pz, k in zip(poses, idx)])
+            rows[str(s)] = dict(failures=int(fails), rmse_cm=round(float(np.sqrt(np.mean(err ** 2))) * 100, 3),
+                                final_cm=round(float(err[-1]) * 100, 3), ms_per_frame=round(e0.elapsed_time(e1) / len(idx), 3))
+            x.close()
+        out[method] = rows
+    return dict(workload=f"{n} frames of the 640x480 room walk taken every s-th frame, 256^3 x 1 cm, K = 0; "
+                         "ms_per_frame includes the pose read-back per frame",
+                frame_step=list(steps), **out)
+
+
+# ------------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle as it stands
 # ------------------------------------------------------------------------------------------------
 def _reference(args, rank):
@@ -694,6 +739,8 @@ def main():
     ap.add_argument("--reloc-queries", type=int, default=100)
     ap.add_argument("--reloc-iters", type=int, default=30)
     ap.add_argument("--reloc-eta", type=float, default=1e-3)
+    ap.add_argument("--no-newton", action="store_true", help="skip the Newton-ICP frame-step comparison")
+    ap.add_argument("--newton-frames", type=int, default=40)
     ap.add_argument("--batch-n", type=int, default=32)
     ap.add_argument("--batch-min", type=int, default=50)
     ap.add_argument("--batch-max", type=int, default=400)

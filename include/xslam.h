@@ -79,6 +79,9 @@ typedef struct {
   int icp_newton;        /* 1: Newton ICP (Sec. 4.1, second-order ICP; the Hessian of each iteration's
                             energy by the second-order complex step), for the real pose only: lanes
                             must be 0 (XSLAM_EINVAL otherwise); 0: Gauss-Newton [0]                  */
+  float icp_newton_eta;  /* Newton ICP: an iteration uses the Hessian when the mean squared residual is
+                            at most this (m^2) and the Hessian is positive definite, else the
+                            Gauss-Newton matrix of the same exact first derivatives [1e-4]          */
 } xslam_config;
 
 /* Fill *cfg with the defaults above. */

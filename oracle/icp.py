@@ -135,12 +135,17 @@ def track(pyr, intr, T_init, T_prev, model, iters=(10, 5, 4), min_corr_frac=0.1,
 # Hessian from Eq. csfd_hessian). Readings: the energy of an iteration is E(xi) = sum_u r_u(exp(xi) T_j)^2
 # with the correspondences' bilinear cells, validity and gates fixed at the real T_j (as in the
 # Gauss-Newton iteration); r, q and n follow xi through p', u_hat and the bilinear weights exactly (no
-# linearisation); the step is xi = -H^-1 g. Where H is not positive definite it is damped: H + mu I with
-# mu = 0, then 10^(k-4) trace(H) / 6 for k = 1..6, the first that is; none: the frame fails like a singular
-# Gauss-Newton system.
+# linearisation). When the mean squared residual is at most eta and H is positive definite, the step is
+# the Newton step xi = -H^-1 g; otherwise it is the point-to-plane Gauss-Newton step of the same iteration
+# (A x = b with the correspondences held fixed, ``normal_equations``). This is the switch the paper
+# applies to relocalisation (Sec. 5.2: a first-order direction while the loss exceeds eta, Newton's
+# below it). eta = inf gives Newton steps only, a singular H damped as H + mu I with
+# mu = 10^(k-4) trace(H) / 6 for the first k = 1..6 that makes it positive definite (none: the frame
+# fails).
 # ---------------------------------------------------------------------------------------------------
 def newton_energy(D, lintr, level, Tj, Tprev, model, h=1e-20, **gates):
-    """(E, g, H, n_valid) of the iteration energy at Tj by the bicomplex step (oracle/bicomplex.py)."""
+    """(E, g, H, n_valid, A) of the iteration energy at Tj by the bicomplex step (oracle/bicomplex.py);
+    A = 2 sum dr dr^T, the Gauss-Newton part of H, from the same pairs' first-order parts."""
     from . import reloc
     from .bicomplex import Bicomplex
     fx, fy, cx, cy, W, H_ = lintr
@@ -150,9 +155,10 @@ def newton_energy(D, lintr, level, Tj, Tprev, model, h=1e-20, **gates):
     idx = np.nonzero(valid)[0]
     n = idx.size
     H = np.zeros((6, 6))
+    A = np.zeros((6, 6))
     g = np.zeros(6)
     if n == 0:
-        return 0.0, g, H, 0
+        return 0.0, g, H, 0, A
     V = measure.vertex_map(D, lintr).reshape(-1, 3)[idx]
     i0, j0 = ci[idx], cj[idx]
     s = 2 ** level
@@ -177,10 +183,11 @@ def newton_energy(D, lintr, level, Tj, Tprev, model, h=1e-20, **gates):
             r2 = res * res
             Es = Bicomplex(np.sum(r2.z1), np.sum(r2.z2))
             H[j, k] = H[k, j] = float(Es.i1i2()) / (h * h)
+            A[j, k] = A[k, j] = 2.0 * float(np.sum(res.i1() * res.i2())) / (h * h)
             if j == k:
                 g[j] = float(Es.i1()) / h
                 E = float(Es.real)
-    return E, g, H, n
+    return E, g, H, n, A
 
 
 def newton_solve(H, g):
@@ -196,17 +203,25 @@ def newton_solve(H, g):
     return None
 
 
-def track_newton(pyr, intr, T_init, T_prev, model, iters=(10, 5, 4), min_corr_frac=0.1, **gates):
-    """Multi-level ICP from coarse to fine with Newton steps (real poses); returns (T_k, ok)."""
+def track_newton(pyr, intr, T_init, T_prev, model, iters=(10, 5, 4), min_corr_frac=0.1, eta=1e-4, **gates):
+    """Multi-level ICP from coarse to fine with Newton steps (real poses) and the eta switch above;
+    returns (T_k, ok)."""
     T = np.asarray(T_init, np.float64)
     for level in range(len(iters) - 1, -1, -1):
         lintr = measure.level_intrinsics(intr, level)
         npx = lintr[4] * lintr[5]
         for _ in range(iters[level]):
-            E, g, H, nv = newton_energy(pyr[level], lintr, level, T, T_prev, model, **gates)
+            E, g, H, nv, _ = newton_energy(pyr[level], lintr, level, T, T_prev, model, **gates)
             if nv < min_corr_frac * npx:
                 return np.asarray(T_init), False
-            x = newton_solve(H, g)
+            if not np.isfinite(eta):
+                x = newton_solve(H, g)
+            elif E <= eta * nv and np.all(np.linalg.eigvalsh(H) > 0):
+                x = -np.linalg.solve(H, g)
+            else:
+                r, J, valid = correspondences(pyr[level], lintr, level, T, T_prev, model, **gates)
+                A, b, _ = normal_equations(r, J, valid)
+                x = solve(A, b)
             if x is None:
                 return np.asarray(T_init), False
             T = se3.compose(se3.se3_exp(x), T)

@@ -44,6 +44,7 @@ class Config:
     w_max: float = np.inf
     bilateral: bool = False
     icp_newton: bool = False  # Newton ICP (real runs only)
+    icp_newton_eta: float = 1e-4  # m^2: mean squared residual below which the Newton matrix is used
 
 
 @dataclasses.dataclass
@@ -106,7 +107,7 @@ class XKinectFusion:
             if c.icp_newton:
                 assert not self.pert, "Newton ICP runs the real pose only"
                 self.T, ok = icp.track_newton(pyr, self.intr, self.T, self.T, self.model, c.icp_iters,
-                                              c.min_corr_frac, **gates)
+                                              c.min_corr_frac, eta=c.icp_newton_eta, **gates)
             else:
                 self.T, ok = icp.track(pyr, self.intr, self.T, self.T, self.model, c.icp_iters,
                                        c.min_corr_frac, log=self.decisions, **gates)

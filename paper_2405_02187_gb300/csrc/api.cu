@@ -60,6 +60,7 @@ extern "C" void xslam_default_config(xslam_config* c) {
   c->bilateral = 0;
   c->w_max = 0.f;
   c->icp_newton = 0;
+  c->icp_newton_eta = 1e-4f;
 }
 
 static void drop_graphs(xslam_t h) {
@@ -133,6 +134,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   p.depth_max = c.depth_max_m;
   p.pyr_range = c.pyr_range_m;
   p.bilateral = c.bilateral;
+  p.icp_newton_eta = c.icp_newton_eta;
   const double step = (double)c.ray_step_vox * (double)voxel_m;
   p.ray_step = (float)step;
   p.m0 = ray_m0(c.depth_min_m, step);

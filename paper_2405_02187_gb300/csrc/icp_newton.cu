@@ -4,11 +4,14 @@
 // One launch per iteration. The energy of the iteration is E(xi) = sum_u r_u(exp(xi) T_j)^2 with the
 // correspondences' bilinear cells, validity and gates fixed at the real T_j (exactly as the
 // Gauss-Newton kernel decides them); r, the projection u_hat and the bilinear model point and normal
-// follow xi exactly. Its gradient and Hessian come from 21 truncated-bicomplex evaluations per pixel
-// (pair j <= k from exp(e1 G_j + e2 G_k) T_j); the last block sums them in FP64 and takes the step
-// xi = -H^-1 g (FP64 Cholesky; where H is not positive definite, H + mu I with mu = 10^(k-4) trace(H)/6
-// for the first k = 1..6 that is; none: the frame fails), T_{j+1} = exp(xi) T_j in FP64. The frame
-// failure protocol is the Gauss-Newton kernel's (status flags, fall back to T_{k-1}).
+// follow xi exactly. Its gradient g and Hessian H come from 21 truncated-bicomplex evaluations per pixel
+// (pair j <= k from exp(e1 G_j + e2 G_k) T_j); beside them each pixel adds the point-to-plane
+// Gauss-Newton system A = sum J J^T, b = -sum J r (correspondences held fixed). The last block sums all
+// in FP64 (Cholesky factors in FP64 too) and steps with the switch of Sec. 5.2: Newton, xi = -H^-1 g,
+// when the mean squared residual is at most eta and H is positive definite, else the Gauss-Newton
+// step A xi = b (A not positive definite: the frame fails); eta = inf: Newton only, a singular H damped
+// as H + mu I, mu = 10^(k-4) trace(H)/6 for the first k = 1..6 that is positive definite (none: the
+// frame fails). T_{j+1} = exp(xi) T_j in FP64; the frame failure protocol is the Gauss-Newton kernel's.
 #include "hd.cuh"
 #include "internal.cuh"
 #include "se3.cuh"
@@ -18,7 +21,7 @@ namespace xslam {
 namespace {
 
 constexpr int kPairs = 21;
-constexpr int kOut = 29;  // count, E, g[6], H[21]
+constexpr int kOut = 56;  // count, E, g[6], H[21], A[21], b[6]
 constexpr int kNThreads = 128;
 constexpr float kCellBiasN = 0.015625f;  // 2^-6, the Gauss-Newton kernel's cell tie-break
 
@@ -31,6 +34,37 @@ __device__ __forceinline__ void gen4(int j, double G[4][4]) {
     G[a][b] = -1.0;
   } else {
     G[j - 3][3] = 1.0;
+  }
+}
+
+// Cholesky of the symmetric 6x6 M + mu I into L; false if a pivot is not positive
+__device__ bool chol6(const double M[6][6], double mu, double L[6][6]) {
+  for (int j = 0; j < 6; ++j) {
+    double dsum = M[j][j] + mu;
+    for (int k = 0; k < j; ++k) dsum -= L[j][k] * L[j][k];
+    if (!(dsum > 0.0)) return false;
+    L[j][j] = sqrt(dsum);
+    for (int i = j + 1; i < 6; ++i) {
+      double t = M[i][j];
+      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+      L[i][j] = t / L[j][j];
+    }
+  }
+  return true;
+}
+
+// x = (L L^T)^-1 rhs
+__device__ void chol6_solve(const double L[6][6], const double* rhs, double* x) {
+  double y[6];
+  for (int i = 0; i < 6; ++i) {
+    double t = rhs[i];
+    for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+    y[i] = t / L[i][i];
+  }
+  for (int i = 5; i >= 0; --i) {
+    double t = y[i];
+    for (int k = i + 1; k < 6; ++k) t -= L[k][i] * x[k];
+    x[i] = t / L[i][i];
   }
 }
 
@@ -155,6 +189,16 @@ __global__ void __launch_bounds__(kNThreads) k_icp_newton(Params p, Buffers b, i
     {
       const float r0 = (pp[0] - q[0]) * n[0] + (pp[1] - q[1]) * n[1] + (pp[2] - q[2]) * n[2];
       E += r0 * r0;
+      // the point-to-plane Gauss-Newton system of this correspondence
+      const float J[6] = {pp[1] * n[2] - pp[2] * n[1], pp[2] * n[0] - pp[0] * n[2], pp[0] * n[1] - pp[1] * n[0],
+                          n[0], n[1], n[2]};
+      int e = 0;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+#pragma unroll
+        for (int k = i; k < 6; ++k) s_acc[27 + e++][tid] += J[i] * J[k];
+        s_acc[48 + i][tid] -= J[i] * r0;
+      }
     }
     for (int qq = 0; qq < kPairs; ++qq) {
       const HD* T = sT[qq];
@@ -218,49 +262,34 @@ __global__ void __launch_bounds__(kNThreads) k_icp_newton(Params p, Buffers b, i
   if (!fail && ncorr < (double)p.min_corr_frac * npx) fail = 1;
   double x[6] = {0, 0, 0, 0, 0, 0};
   if (!fail) {
-    double Hm[6][6], g[6];
+    double Hm[6][6], Am[6][6], g[6], bv[6], L[6][6];
     int e = 0;
     for (int i = 0; i < 6; ++i)
       for (int k = i; k < 6; ++k) {
         Hm[i][k] = Hm[k][i] = s_sum[8 + e];
+        Am[i][k] = Am[k][i] = s_sum[29 + e];
         ++e;
       }
-    for (int i = 0; i < 6; ++i) g[i] = s_sum[2 + i];
-    const double tr = (Hm[0][0] + Hm[1][1] + Hm[2][2] + Hm[3][3] + Hm[4][4] + Hm[5][5]) / 6.0;
-    bool solved = false;
-    for (int kk = 0; kk < 7 && !solved; ++kk) {
-      const double mu = kk == 0 ? 0.0 : pow(10.0, kk - 4) * tr;
-      double L[6][6];
-      bool pd = true;
-      for (int j = 0; j < 6 && pd; ++j) {
-        double dsum = Hm[j][j] + mu;
-        for (int k = 0; k < j; ++k) dsum -= L[j][k] * L[j][k];
-        if (!(dsum > 0.0)) {
-          pd = false;
-          break;
-        }
-        L[j][j] = sqrt(dsum);
-        for (int i = j + 1; i < 6; ++i) {
-          double t = Hm[i][j];
-          for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-          L[i][j] = t / L[j][j];
-        }
-      }
-      if (!pd) continue;
-      double y[6];
-      for (int i = 0; i < 6; ++i) {
-        double t = -g[i];
-        for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
-        y[i] = t / L[i][i];
-      }
-      for (int i = 5; i >= 0; --i) {
-        double t = y[i];
-        for (int k = i + 1; k < 6; ++k) t -= L[k][i] * x[k];
-        x[i] = t / L[i][i];
-      }
-      solved = true;
+    for (int i = 0; i < 6; ++i) {
+      g[i] = -s_sum[2 + i];  // the Newton right-hand side -g
+      bv[i] = s_sum[50 + i];
     }
-    if (!solved) fail = 1;
+    if (isinf(p.icp_newton_eta)) {
+      const double tr = (Hm[0][0] + Hm[1][1] + Hm[2][2] + Hm[3][3] + Hm[4][4] + Hm[5][5]) / 6.0;
+      bool solved = false;
+      for (int kk = 0; kk < 7 && !solved; ++kk)
+        if (chol6(Hm, kk == 0 ? 0.0 : pow(10.0, kk - 4) * tr, L)) {
+          chol6_solve(L, g, x);
+          solved = true;
+        }
+      if (!solved) fail = 1;
+    } else if (s_sum[1] <= (double)p.icp_newton_eta * ncorr && chol6(Hm, 0.0, L)) {
+      chol6_solve(L, g, x);
+    } else if (chol6(Am, 0.0, L)) {
+      chol6_solve(L, bv, x);
+    } else {
+      fail = 1;
+    }
   }
   if (!fail) {
     const double zero[6] = {0, 0, 0, 0, 0, 0};

@@ -40,6 +40,7 @@ struct Params {
   float depth_min, depth_max, pyr_range;
   int bilateral;            // 1: bilateral filter of the gated raw depth before the pyramid
   float ray_step;           // dalpha in metres of camera depth
+  float icp_newton_eta;     // Newton ICP: mean squared residual (m^2) below which the Hessian is used
   int m0, m1;               // ray samples alpha_m = m * ray_step, m0 <= m <= m1
 };
 

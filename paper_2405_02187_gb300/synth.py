@@ -235,39 +235,52 @@ def small_orbit(seed: int = 1, frames: int = 20, noise: bool = True, device="cpu
                     np.array(poses), np.array(depth), scene, seed)
 
 
-def _room_scene(rng, lo, hi, n_prims, keep_out_lo, keep_out_hi, clearance):
+def _room_scene(rng, side, margin, n_prims, obj_r):
+    """Walls of a side-metre room (margin inside the volume) and n_prims random spheres and boxes
+    inside the central column of horizontal radius obj_r around the room's vertical axis."""
+    lo, hi = np.full(3, margin), np.full(3, side - margin)
     scene = [Room(tuple(lo), tuple(hi))]
-    lo = np.asarray(lo)
-    hi = np.asarray(hi)
-    kl = np.asarray(keep_out_lo) - clearance
-    kh = np.asarray(keep_out_hi) + clearance
+    c = side / 2.0
     while len(scene) < n_prims + 1:
         kind = rng.integers(0, 2)
+        ang = rng.uniform(0, 2 * math.pi)
+        rad = obj_r * math.sqrt(rng.uniform())
         if kind == 0:
-            r = rng.uniform(0.08, 0.3)
-            c = rng.uniform(lo + r, hi - r)
-            blo, bhi = c - r, c + r
-            prim = Sphere(tuple(c), float(r))
+            r = rng.uniform(0.08, 0.3) * side / 2.56
+            cen = np.array([c + rad * math.cos(ang), rng.uniform(lo[1] + r, 0.75 * side), c + rad * math.sin(ang)])
+            prim = Sphere(tuple(cen), float(r))
         else:
-            size = rng.uniform(0.1, 0.5, 3)
-            c = rng.uniform(lo + size / 2, hi - size / 2)
+            size = rng.uniform(0.1, 0.5, 3) * side / 2.56
+            cen = np.array([c + rad * math.cos(ang), rng.uniform(lo[1] + size[1] / 2, 0.75 * side), c + rad * math.sin(ang)])
             if rng.uniform() < 0.5:  # rest on the floor
-                c[1] = lo[1] + size[1] / 2
-            blo, bhi = c - size / 2, c + size / 2
-            prim = Box(tuple(blo), tuple(bhi))
-        if np.all(bhi > kl) and np.all(blo < kh):
-            continue  # would intrude into the camera region
+                cen[1] = lo[1] + size[1] / 2
+            prim = Box(tuple(cen - size / 2), tuple(cen + size / 2))
         scene.append(prim)
     return scene
+
+
+def _inward_ok(eye, R, c, r_lo, r_hi, y_lo, y_hi):
+    """The camera constraints of the room walk: on the ring around the room's vertical axis, at a
+    height in range, looking inward (the horizontal view direction within 35 degrees of the axis
+    direction), within 35 degrees of horizontal, upright."""
+    dx, dz = c - eye[0], c - eye[2]
+    rr = math.hypot(dx, dz)
+    fwd = R[:, 2]
+    up_cam = -R[:, 1]
+    h = math.hypot(fwd[0], fwd[2])
+    inward = h > 0 and (fwd[0] * dx + fwd[2] * dz) / (h * rr) > math.cos(math.radians(35))
+    return (r_lo < rr < r_hi and y_lo < eye[1] < y_hi and inward and abs(fwd[1]) < math.sin(math.radians(35))
+            and up_cam[1] > 0.5)
 
 
 def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 480, dims=256,
               voxel: float = 0.01, noise: bool = True, device="cpu", resident: bool = False,
               n_prims: int = 12) -> Workload:
-    """Room of n_prims (12) random spheres/boxes inside walls that fill a (dims*voxel)^3 volume, 640x480 frames
-    (f=525, c=(319.5, 239.5)); random-walk camera (translation <= 2 cm per frame, rotation <= 1.5 deg
-    about a random axis) kept in the middle of the room with its view axis within 35 degrees of
-    horizontal; depth noise sigma = 1.5 mm * z^2.
+    """Room of n_prims (12) random spheres/boxes in the central part of a (dims*voxel)^3 volume walled
+    on all sides, seen at 640x480 (f=525, c=(319.5, 239.5)) by a camera that walks a ring around
+    them facing inward (translation <= 2 cm, rotation <= 1.5 deg about a random axis per frame; the
+    view within 35 degrees of the direction to the room's axis and of horizontal); depth noise
+    sigma = 1.5 mm * z^2. Lengths scale with the room side (2.56 m at 256^3 x 1 cm).
 
     resident=True keeps the frames on ``device`` as one float32 torch tensor (frames, H, W) and draws
     the noise there from a torch generator seeded with ``seed`` (a different stream of normals than
@@ -276,21 +289,29 @@ def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 
     s = width / 640.0
     intr = Intrinsics(525.0 * s, 525.0 * s, (width - 1) / 2.0, (height - 1) / 2.0, width, height)
     side = dims * voxel
-    margin = 0.06 * side / 2.56
-    lo = np.full(3, margin)
-    hi = np.full(3, side - margin)
-    cam_lo = np.full(3, 0.33 * side)
-    cam_hi = np.full(3, 0.67 * side)
-    scene = _room_scene(rng, lo, hi, n_prims, cam_lo, cam_hi, 0.35)
-    eye = rng.uniform(cam_lo + 0.1, cam_hi - 0.1)
-    q = axis_angle_quat((0.0, 1.0, 0.0), rng.uniform(0, 2 * math.pi))
+    k = side / 2.56
+    margin = 0.06 * k
+    c = side / 2.0
+    r_lo, r_hi = 0.95 * k, 1.12 * k          # camera ring (walls at 1.22 k from the axis)
+    y_lo, y_hi = 0.85 * k, 1.7 * k
+    scene = _room_scene(rng, side, margin, n_prims, 0.5 * k)  # objects within 0.5 k + 0.3 k of the axis
     base = look_at(np.zeros(3), (0.0, 0.0, 1.0))[:, :3]  # y down, z forward along +z
+    while True:  # a start pose on the ring looking at the axis, within the constraints
+        ang = rng.uniform(0, 2 * math.pi)
+        rad = rng.uniform(r_lo + 0.03 * k, r_hi - 0.03 * k)
+        eye = np.array([c + rad * math.cos(ang), rng.uniform(y_lo + 0.05 * k, y_hi - 0.05 * k), c + rad * math.sin(ang)])
+        yaw = math.atan2(c - eye[0], c - eye[2]) + rng.uniform(-0.3, 0.3)
+        q = axis_angle_quat((0.0, 1.0, 0.0), yaw)
+        pitch = axis_angle_quat((1.0, 0.0, 0.0), rng.uniform(-0.2, 0.2))
+        q = np.array([q[0] * pitch[0] - q[1:] @ pitch[1:], *(q[0] * pitch[1:] + pitch[0] * q[1:] + np.cross(q[1:], pitch[1:]))])
+        if _inward_ok(eye, quat_to_matrix(q) @ base, c, r_lo, r_hi, y_lo, y_hi):
+            break
     poses, depth = [], []
     if resident:
         gen = torch.Generator(device=device)
         gen.manual_seed(seed)
-    for k in range(frames):
-        if k > 0:
+    for f in range(frames):
+        if f > 0:
             for _ in range(100):
                 step = rng.standard_normal(3)
                 step *= rng.uniform() ** (1 / 3) * 0.02 / np.linalg.norm(step)
@@ -299,12 +320,8 @@ def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 
                 nq = np.array([
                     dq[0] * q[0] - dq[1:] @ q[1:],
                     *(dq[0] * q[1:] + q[0] * dq[1:] + np.cross(dq[1:], q[1:]))])
-                R = quat_to_matrix(nq) @ base
-                fwd = R[:, 2]
-                up_cam = -R[:, 1]
                 ne = eye + step
-                if (np.all(ne > cam_lo) and np.all(ne < cam_hi) and abs(fwd[1]) < math.sin(math.radians(35))
-                        and up_cam[1] > 0.5):
+                if _inward_ok(ne, quat_to_matrix(nq) @ base, c, r_lo, r_hi, y_lo, y_hi):
                     eye, q = ne, nq
                     break
         R = quat_to_matrix(q) @ base

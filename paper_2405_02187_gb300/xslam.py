@@ -36,7 +36,8 @@ class Config(ctypes.Structure):
                 ("disc_gate_m", ctypes.c_float), ("min_corr_frac", ctypes.c_float),
                 ("ray_step_vox", ctypes.c_float), ("depth_min_m", ctypes.c_float),
                 ("depth_max_m", ctypes.c_float), ("pyr_range_m", ctypes.c_float),
-                ("bilateral", ctypes.c_int), ("w_max", ctypes.c_float), ("icp_newton", ctypes.c_int)]
+                ("bilateral", ctypes.c_int), ("w_max", ctypes.c_float), ("icp_newton", ctypes.c_int),
+                ("icp_newton_eta", ctypes.c_float)]
 
 
 class XSlamError(RuntimeError):

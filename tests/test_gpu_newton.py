@@ -13,20 +13,22 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _newton_handle(wl):
+def _newton_handle(wl, eta=1e-4):
     cfg = xslam_cfg(wl)
     cfg.icp_newton = 1
+    cfg.icp_newton_eta = eta
     return xslam.XSlam(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, cfg, max_lanes=2)
 
 
-@pytest.mark.parametrize("which", ["tiny", "orbit"])
-def test_newton_sequence_matches_oracle(which):
+@pytest.mark.parametrize("which,eta", [("tiny", float("inf")), ("orbit", float("inf")), ("orbit", 1e-4)])
+def test_newton_sequence_matches_oracle(which, eta):
+    """eta = inf: Newton steps only; 1e-4: the switch to Gauss-Newton steps above it."""
     wl = synth.tiny(frames=3) if which == "tiny" else synth.small_orbit(frames=8)
     n = wl.depth.shape[0]
-    x = _newton_handle(wl)
+    x = _newton_handle(wl, eta)
     x.set_pose(wl.poses[0])
     out = [x.frame(torch.tensor(wl.depth[k], device="cuda"), []) for k in range(n)]
-    ref = P.run(wl, [], frames=n, cfg=dataclasses.replace(oracle_cfg(wl), icp_newton=True))
+    ref = P.run(wl, [], frames=n, cfg=dataclasses.replace(oracle_cfg(wl), icp_newton=True, icp_newton_eta=eta))
     assert ref["ok"].all()
     for k in range(n):
         assert out[k][3] == xslam.OK

@@ -33,7 +33,7 @@ def test_newton_energy_derivatives(setup):
     lintr = measure.level_intrinsics(wl.intr, level)
     Tprev = r.T
     Tj = se3.compose(se3.se3_exp(np.array([0.003, -0.002, 0.002, 0.004, -0.003, 0.002])), Tprev)
-    E, g, H, n = icp.newton_energy(pyr[level], lintr, level, Tj, Tprev, r.model)
+    E, g, H, n, A = icp.newton_energy(pyr[level], lintr, level, Tj, Tprev, r.model)
     assert n > 300
     E0, valid0 = _E(pyr, lintr, level, Tj, Tprev, r.model)
     assert abs(E - E0) <= 1e-12 * E0
@@ -55,6 +55,11 @@ def test_newton_energy_derivatives(setup):
 
     Hfd = np.stack([(grad_at(d * np.eye(6)[k]) - grad_at(-d * np.eye(6)[k])) / (2 * d) for k in range(6)], 1)
     assert np.abs(H - Hfd).max() <= 1e-6 * np.abs(H).max()
+    # A is 2 J~ J~^T of the exact first derivatives (the complex step of each residual)
+    rr0, _, v0 = icp.correspondences(pyr[level], lintr, level, Tj, Tprev, r.model)
+    Jt = np.stack([icp.correspondences(pyr[level], lintr, level, se3.promote_pose(Tj, j, h), Tprev, r.model)[0].imag[v0] / h
+                   for j in range(6)], 1)
+    assert np.abs(A - 2.0 * Jt.T @ Jt).max() <= 1e-9 * np.abs(A).max()
 
 
 def test_newton_hessian_is_gauss_newton_at_zero_residual(setup):
@@ -63,7 +68,7 @@ def test_newton_hessian_is_gauss_newton_at_zero_residual(setup):
     lintr = measure.level_intrinsics(wl.intr, level)
     T_true = r.T  # frame 1's tracked pose; the noise-free frame 1 seen again has near-zero residuals
     pyr1 = r.measure(wl.depth[1])
-    E, g, H, n = icp.newton_energy(pyr1[level], lintr, level, T_true, T_true, r.model)
+    E, g, H, n, _ = icp.newton_energy(pyr1[level], lintr, level, T_true, T_true, r.model)
     rr, J, valid = icp.correspondences(pyr1[level], lintr, level, T_true, T_true, r.model)
     A = 2.0 * J[valid].T @ J[valid]
     assert np.median(np.abs(rr[valid])) < 2e-3
