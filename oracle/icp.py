@@ -24,9 +24,9 @@ Readings of the paper used here:
     (the weights a = u_hat - cell then lie in [-2^-6, 1 - 2^-6)): at the first iteration
     T_j = T_{k-1}, so u_hat equals the integer pixel u up to rounding, and an unbiased floor would
     pick the cell on either side of u depending on the last bit; the bias removes that tie;
-  * iterations run coarse to fine, a fixed number per level (no early exit); an iteration with fewer
-    than min_corr_frac of the level's pixels as correspondences, or whose real A is not positive
-    definite, fails the frame: the pose falls back to the initial guess T_{k-1}.
+  * iterations run coarse to fine, a fixed number per level (no early exit unless a stop tolerance is
+    given); an iteration with fewer than min_corr_frac of the level's pixels as correspondences, or
+    whose real A is not positive definite, fails the frame: the pose falls back to T_{k-1}.
 """
 from __future__ import annotations
 
@@ -112,21 +112,33 @@ def solve(A, b):
     return np.linalg.solve(A, b)
 
 
-def track(pyr, intr, T_init, T_prev, model, iters=(10, 5, 4), min_corr_frac=0.1, log=None, **gates):
-    """Multi-level ICP from coarse to fine; returns (T_k, ok)."""
+def track(pyr, intr, T_init, T_prev, model, iters=(10, 5, 4), min_corr_frac=0.1, log=None, stop_tol=0.0,
+          levels=None, stats=None, **gates):
+    """Multi-level ICP from coarse to fine; returns (T_k, ok). On a failure the pose falls back to
+    T_prev, the pose the model was ray cast at.
+
+    stop_tol > 0: a level ends early after an iteration whose real step |x| is below stop_tol (the
+    step itself is applied); 0 runs the fixed counts. levels: (first, last) pyramid levels to run,
+    first >= last (default: all, coarsest first). stats: a dict whose "iterations" entry counts the
+    iterations run."""
     T = np.asarray(T_init)
-    for level in range(len(iters) - 1, -1, -1):
+    first, last = (len(iters) - 1, 0) if levels is None else levels
+    for level in range(first, last - 1, -1):
         lintr = measure.level_intrinsics(intr, level)
         npx = lintr[4] * lintr[5]
         for _ in range(iters[level]):
+            if stats is not None:
+                stats["iterations"] = stats.get("iterations", 0) + 1
             r, J, valid = correspondences(pyr[level], lintr, level, T, T_prev, model, log=log, **gates)
             A, b, nv = normal_equations(r, J, valid)
             if nv < min_corr_frac * npx:
-                return np.asarray(T_init), False
+                return np.asarray(T_prev), False
             x = solve(A, b)
             if x is None:
-                return np.asarray(T_init), False
+                return np.asarray(T_prev), False
             T = se3.compose(se3.se3_exp(x), T)
+            if stop_tol > 0 and np.linalg.norm(np.real(x)) < stop_tol:
+                break
     return T, True
 
 

@@ -24,7 +24,7 @@ import dataclasses
 
 import numpy as np
 
-from . import fusion, icp, measure, raycast, se3
+from . import fusion, icp, measure, mlp, proposal, raycast, se3
 from .csfd import H_ORACLE
 
 POSE0, POSE, TRUNC, DEPTH = 0, 1, 2, 3
@@ -45,6 +45,19 @@ class Config:
     bilateral: bool = False
     icp_newton: bool = False  # Newton ICP (real runs only)
     icp_newton_eta: float = 1e-4  # m^2: mean squared residual below which the Newton matrix is used
+    icp_seed: str = "prev"     # ICP start: "prev" T_{k-1} (Sec. 4.1) or "cv" constant velocity
+    icp_stop: float = 0.0      # > 0: a level ends after a step |x| below this (oracle/icp.py track)
+    proposal: object = None    # a Proposal: learned start pose judged against the "icp_seed" start
+
+
+@dataclasses.dataclass
+class Proposal:
+    """The learned proposal (oracle/mlp.py, oracle/proposal.py): the network seeds a second ICP run;
+    both runs go from the coarsest level down to judge_level, the lower judge J wins (the network's
+    run only if it did not fail and J_B <= J_A) and continues to level 0."""
+    params: list
+    scale: np.ndarray
+    judge_level: int = 2
 
 
 @dataclasses.dataclass
@@ -83,6 +96,9 @@ class XKinectFusion:
         self.k = 0
         self.model = None
         self.decisions = []  # every discrete branch taken, for mask-identity checks
+        self.T_pp = self.T   # T_{k-2} of the constant-velocity start
+        self.feat_prev = None
+        self.stats = dict(iterations=0, judged=0, accepted=0)
 
     def measure(self, depth):
         D = np.asarray(depth, np.float64)
@@ -109,8 +125,9 @@ class XKinectFusion:
                 self.T, ok = icp.track_newton(pyr, self.intr, self.T, self.T, self.model, c.icp_iters,
                                               c.min_corr_frac, eta=c.icp_newton_eta, **gates)
             else:
-                self.T, ok = icp.track(pyr, self.intr, self.T, self.T, self.model, c.icp_iters,
-                                       c.min_corr_frac, log=self.decisions, **gates)
+                self.T, ok = self.track(pyr, depth, gates)
+        if c.proposal is not None:
+            self.feat_prev = mlp.features(np.real(np.asarray(depth, np.float64)), c.depth_min, c.depth_max)
         fusion.integrate(self.F, self.W, pyr[0], self.T, self.intr, self.dims, self.origin,
                          self.voxel, self.mu, c.disc_gate, c.w_max, log=self.decisions)
         d, V, N = raycast.raycast(self.F, self.W, self.T, self.intr, self.dims, self.origin, self.voxel,
@@ -118,6 +135,42 @@ class XKinectFusion:
         self.model = dict(depth=d, V=V, N=N)
         self.k += 1
         return self.T, ok
+
+
+    def track(self, pyr, depth, gates):
+        """ICP of frame k > 0 from the configured start; returns (T_k, ok)."""
+        c = self.cfg
+        T1 = self.T
+        seed_a = proposal.cv_seed(T1, self.T_pp) if c.icp_seed == "cv" else T1
+        self.T_pp = T1
+        kw = dict(stop_tol=c.icp_stop, stats=self.stats, **gates)
+        levels = len(c.icp_iters)
+        if c.proposal is None:
+            T, ok = icp.track(pyr, self.intr, seed_a, T1, self.model, c.icp_iters, c.min_corr_frac,
+                              log=self.decisions, **kw)
+            return T, ok
+        P = c.proposal
+        x = np.concatenate([self.feat_prev, mlp.features(np.real(np.asarray(depth, np.float64)), c.depth_min,
+                                                          c.depth_max)])[None]
+        y, _ = mlp.forward(P.params, x, bf16_ops=True)
+        xi = np.asarray(P.scale, np.float64) * y[0]
+        seed_b = proposal.proposal_seed(T1, xi)
+        jl = P.judge_level
+        lintr = measure.level_intrinsics(self.intr, jl)
+        res = []
+        for seed in (seed_a, seed_b):
+            T, ok = icp.track(pyr, self.intr, seed, T1, self.model, c.icp_iters, c.min_corr_frac,
+                              levels=(levels - 1, jl), **kw)
+            res.append((T, ok, proposal.judge(pyr[jl], lintr, jl, T, T1, self.model, c.dist_gate)))
+        (Ta, oka, Ja), (Tb, okb, Jb) = res
+        accept = okb and (not oka or Jb <= Ja)
+        self.stats["judged"] += 1
+        self.stats["accepted"] += int(accept)
+        T, ok = (Tb, okb) if accept else (Ta, oka)
+        if ok and jl > 0:
+            T, ok = icp.track(pyr, self.intr, T, T1, self.model, c.icp_iters, c.min_corr_frac,
+                              levels=(jl - 1, 0), **kw)
+        return (T, True) if ok else (T1, False)
 
 
 def run(wl, seeds=(), frames=None, cfg: Config = None):
