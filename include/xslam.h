@@ -82,6 +82,11 @@ typedef struct {
   float icp_newton_eta;  /* Newton ICP: an iteration uses the Hessian when the mean squared residual is
                             at most this (m^2) and the Hessian is positive definite, else the
                             Gauss-Newton matrix of the same exact first derivatives [1e-4]          */
+  int icp_seed;          /* ICP start of frame k: 0 the previous pose T_{k-1} (Sec. 4.1), 1 constant
+                            velocity T_{k-1} T_{k-2}^-1 T_{k-1} (T_0 at k = 1), on every lane [0]    */
+  float icp_stop;        /* > 0: a pyramid level ends after an iteration whose real step (twist
+                            norm) is below this; the remaining iterations of the level are skipped
+                            (Gauss-Newton ICP only); 0: fixed iteration counts [0]                  */
 } xslam_config;
 
 /* Fill *cfg with the defaults above. */

@@ -14,6 +14,7 @@
 
 #include "../../include/xslam.h"
 #include "handle.cuh"
+#include "mlp.cuh"
 #include "internal.cuh"
 
 using namespace xslam;
@@ -61,6 +62,8 @@ extern "C" void xslam_default_config(xslam_config* c) {
   c->w_max = 0.f;
   c->icp_newton = 0;
   c->icp_newton_eta = 1e-4f;
+  c->icp_seed = 0;
+  c->icp_stop = 0.f;
 }
 
 static void drop_graphs(xslam_t h) {
@@ -103,6 +106,9 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
     if (c.icp_iters[l] < 0 || c.icp_iters[l] > 100) return fail(h, XSLAM_EINVAL, "icp_iters must be 0..100");
   if (c.bilateral != 0 && c.bilateral != 1) return fail(h, XSLAM_EINVAL, "bilateral must be 0 or 1");
   if (c.icp_newton != 0 && c.icp_newton != 1) return fail(h, XSLAM_EINVAL, "icp_newton must be 0 or 1");
+  if (c.icp_seed != 0 && c.icp_seed != 1) return fail(h, XSLAM_EINVAL, "icp_seed must be 0 or 1");
+  if (!(c.icp_stop >= 0.f) || !std::isfinite(c.icp_stop)) return fail(h, XSLAM_EINVAL, "icp_stop must be >= 0");
+  if (c.icp_stop > 0.f && c.icp_newton) return fail(h, XSLAM_EINVAL, "icp_stop applies to Gauss-Newton ICP only");
   const int div = 1 << (c.icp_levels - 1);
   if (K->width < 4 * div || K->height < 4 * div || K->width % div || K->height % div)
     return fail(h, XSLAM_EINVAL, "image size must be divisible by 2^(icp_levels-1) and at least 4 pixels per level");
@@ -135,6 +141,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   p.pyr_range = c.pyr_range_m;
   p.bilateral = c.bilateral;
   p.icp_newton_eta = c.icp_newton_eta;
+  p.icp_stop = c.icp_stop;
   const double step = (double)c.ray_step_vox * (double)voxel_m;
   p.ray_step = (float)step;
   p.m0 = ray_m0(c.depth_min_m, step);
@@ -179,9 +186,17 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   ok &= cudaMalloc(&b.partial, sizeof(float) * (size_t)(nblk_max + 4) * kNT * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&b.partial_n, sizeof(int) * nblk_max) == cudaSuccess;
   ok &= cudaMalloc(&b.ticket, sizeof(unsigned)) == cudaSuccess;
-  ok &= cudaMalloc(&b.status, sizeof(int) * 4) == cudaSuccess;
+  ok &= cudaMalloc(&b.status, sizeof(int) * 8) == cudaSuccess;
   ok &= cudaMalloc(&b.result, sizeof(double) * kResLen) == cudaSuccess;
-  ok &= cudaMalloc(&b.stats, sizeof(unsigned long long) * 2) == cudaSuccess;
+  ok &= cudaMalloc(&b.stats, sizeof(unsigned long long) * kNStat) == cudaSuccess;
+  h->judge_nblk = std::min(2 * h->nsm, std::max(1, (int)((hw + 255) / 256)));
+  ok &= cudaMalloc(&h->q.pose_pp, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
+  ok &= cudaMalloc(&h->q.candA, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
+  ok &= cudaMalloc(&h->q.candB, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
+  ok &= cudaMalloc(&h->q.judge, sizeof(double) * 2) == cudaSuccess;
+  ok &= cudaMalloc(&h->q.failA, sizeof(int)) == cudaSuccess;
+  ok &= cudaMalloc(&h->q.partial, sizeof(double) * 2 * h->judge_nblk) == cudaSuccess;
+  ok &= cudaMalloc(&h->q.ticket, sizeof(unsigned)) == cudaSuccess;
   ok &= cudaMalloc(&b.hit, sizeof(int) * hw) == cudaSuccess;
   ok &= cudaMalloc(&b.tiles, sizeof(int) * (size_t)fuse_tile_count(p)) == cudaSuccess;
   ok &= cudaMalloc(&b.tile_ctr, sizeof(unsigned) * 2) == cudaSuccess;
@@ -189,7 +204,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   ok &= cudaMalloc(&h->d_index, sizeof(int) * kMaxLanes) == cudaSuccess;
   if (max_lanes >= 6) ok &= cudaMalloc(&h->model_q, sizeof(float) * hw * (1 + 6 * 7)) == cudaSuccess;
   ok &= cudaMallocHost(&h->h_result, sizeof(double) * kResLen) == cudaSuccess;
-  ok &= cudaMallocHost(&h->h_status, sizeof(int) * 4) == cudaSuccess;
+  ok &= cudaMallocHost(&h->h_status, sizeof(int) * 8) == cudaSuccess;
   if (!ok) return cleanup(XSLAM_ENOMEM, "device or pinned allocation failed");
   *out = h;
   xslam_status st = xslam_reset(h);
@@ -217,6 +232,10 @@ extern "C" xslam_status xslam_destroy(xslam_t h) {
   cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp); cudaFree(h->hess_poses);
   cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.hit);
   cudaFree(b.tiles); cudaFree(b.tile_ctr);
+  cudaFree(h->q.pose_pp); cudaFree(h->q.candA); cudaFree(h->q.candB); cudaFree(h->q.judge); cudaFree(h->q.failA);
+  cudaFree(h->q.partial); cudaFree(h->q.ticket); cudaFree(h->q.row); cudaFree(h->q.prev); cudaFree(h->q.y);
+  for (int l = 0; l < 8; ++l) cudaFree(h->prop_act[l]);
+  cudaFree(h->prop_ws);
   for (int st = 0; st < XSLAM_NSTAGE; ++st)
     for (int i = 0; i < kProfRing; ++i)
       for (int k = 0; k < 2; ++k)
@@ -262,10 +281,13 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   CU(cudaMemsetAsync(h->b.model, 0, sizeof(float) * (size_t)h->p.W * h->p.H * (1 + 6 * Lmax), h->s));
   CU(cudaMemsetAsync(h->b.ticket, 0, sizeof(unsigned), h->s));
   CU(cudaMemsetAsync(h->b.partial, 0, sizeof(float) * (size_t)(h->nblk_max + 4) * kNT * kMaxLanes, h->s));
-  CU(cudaMemsetAsync(h->b.status, 0, sizeof(int) * 4, h->s));
+  CU(cudaMemsetAsync(h->b.status, 0, sizeof(int) * 8, h->s));
+  CU(cudaMemsetAsync(h->q.pose_pp, 0, sizeof(double) * 12 * kMaxLanes, h->s));
+  CU(cudaMemsetAsync(h->q.ticket, 0, sizeof(unsigned), h->s));
+  CU(cudaMemsetAsync(h->q.failA, 0, sizeof(int), h->s));
   CU(cudaMemsetAsync(h->b.pose + 12, 0, sizeof(double) * 12 * (kMaxLanes - 1), h->s));
   CU(cudaMemsetAsync(h->b.result, 0, sizeof(double) * kResLen, h->s));
-  CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * 2, h->s));
+  CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * kNStat, h->s));
   CU(cudaMemsetAsync(h->b.tile_ctr, 0, sizeof(unsigned) * 2, h->s));
   h->frame = 0;
   h->K = 0;
@@ -353,6 +375,8 @@ static void stage_end(xslam_t h, int st, int launches) {
   h->plaunch[st] += launches;
 }
 
+static bool uses_start(xslam_t h) { return h->cfg.icp_seed == 1 || h->mlp != nullptr; }
+
 static cudaError_t enqueue_first(xslam_t h) {
   cudaError_t e;
   const size_t hw = (size_t)h->p.W * h->p.H;
@@ -361,7 +385,18 @@ static cudaError_t enqueue_first(xslam_t h) {
   stage_end(h, XSLAM_STAGE_PREPARE, 1 + h->p.bilateral);
   stage_begin(h, XSLAM_STAGE_OTHER);
   if ((e = launch_seed_pose(h->p, h->b, h->d_kinds, h->d_index, h->s)) != cudaSuccess) return e;
-  stage_end(h, XSLAM_STAGE_OTHER, 1);
+  int n_other = 1;
+  if (uses_start(h)) {
+    if ((e = launch_prop_seed(h->p, h->b, h->q, h->prop_scale, 4, h->s)) != cudaSuccess) return e;
+    ++n_other;
+  }
+  if (h->mlp) {
+    if ((e = launch_features(h->b.depth_in, 1, h->p.W, h->p.H, h->p.depth_min, h->p.depth_max, h->q.row, 0, h->q.prev,
+                             h->s)) != cudaSuccess)
+      return e;
+    ++n_other;
+  }
+  stage_end(h, XSLAM_STAGE_OTHER, n_other);
   stage_begin(h, XSLAM_STAGE_INTEGRATE);
   if ((e = launch_integrate(h->p, h->b, h->s)) != cudaSuccess) return e;
   stage_end(h, XSLAM_STAGE_INTEGRATE, 1);
@@ -376,27 +411,64 @@ static cudaError_t enqueue_first(xslam_t h) {
   return e;
 }
 
+// ICP iterations of pyramid levels first .. last (first >= last), coarse to fine, on the current pose
+// lanes; close = the range's last iteration closes the frame (fallback to T_{k-1}, failure count)
+static cudaError_t enqueue_icp_levels(xslam_t h, int first, int last, bool close, int* n_icp) {
+  int last_level = -1;
+  for (int l = first; l >= last; --l)
+    if (h->cfg.icp_iters[l] > 0) last_level = l;
+  for (int l = first; l >= last; --l) {
+    for (int it = 0; it < h->cfg.icp_iters[l]; ++it) {
+      int flags = it == 0 ? kIcpFirst : 0;
+      if (close && l == last_level && it == h->cfg.icp_iters[l] - 1) flags |= kIcpLast;
+      cudaError_t e;
+      if (h->cfg.icp_newton)
+        e = launch_icp_newton(h->p, h->b, l, flags, icp_newton_blocks((h->p.W >> l) * (h->p.H >> l), h->nsm), h->s);
+      else
+        e = launch_icp(h->p, h->b, l, flags, h->nblk[l], h->s);
+      if (e != cudaSuccess) return e;
+      ++*n_icp;
+    }
+  }
+  return cudaSuccess;
+}
+
 static cudaError_t enqueue_track(xslam_t h) {
   cudaError_t e;
   const int levels = h->cfg.icp_levels;
   stage_begin(h, XSLAM_STAGE_PREPARE);
   if ((e = launch_prepare(h->p, h->b, levels, h->s)) != cudaSuccess) return e;
   stage_end(h, XSLAM_STAGE_PREPARE, levels + h->p.bilateral);
-  int last_level = -1, n_icp = 0;
-  for (int l = levels - 1; l >= 0; --l)
-    if (h->cfg.icp_iters[l] > 0) last_level = l;
+  if (uses_start(h)) {
+    // the proposal's forward pass and the start poses
+    stage_begin(h, XSLAM_STAGE_OTHER);
+    int n_other = 1;
+    if (h->mlp) {
+      if ((e = launch_features(h->b.depth_in, 1, h->p.W, h->p.H, h->p.depth_min, h->p.depth_max, h->q.row, 0,
+                               h->q.prev, h->s)) != cudaSuccess)
+        return e;
+      if ((e = mlp_enqueue_forward(h->mlp, h->q.row, 1, (__nv_bfloat16* const*)h->prop_act, h->prop_ws, h->q.y, 64, 6,
+                                   h->b.status + 4, h->s)) != cudaSuccess)
+        return e;
+      n_other += 1 + 2 * h->mlp->L;
+    }
+    const int mode = (h->cfg.icp_seed == 1 ? 1 : 0) | (h->mlp ? 2 : 0);
+    if ((e = launch_prop_seed(h->p, h->b, h->q, h->prop_scale, mode, h->s)) != cudaSuccess) return e;
+    stage_end(h, XSLAM_STAGE_OTHER, n_other);
+  }
+  int n_icp = 0;
   stage_begin(h, XSLAM_STAGE_ICP);
-  for (int l = levels - 1; l >= 0; --l) {
-    for (int it = 0; it < h->cfg.icp_iters[l]; ++it) {
-      int flags = 0;
-      if (l == last_level && it == h->cfg.icp_iters[l] - 1) flags |= kIcpLast;
-      if (h->cfg.icp_newton)
-        e = launch_icp_newton(h->p, h->b, l, flags, icp_newton_blocks((h->p.W >> l) * (h->p.H >> l), h->nsm), h->s);
-      else
-        e = launch_icp(h->p, h->b, l, flags, h->nblk[l], h->s);
-      if (e != cudaSuccess) return e;
+  if (h->mlp) {
+    const int J = std::min(h->judge_level, levels - 1);
+    for (int run = 0; run < 2; ++run) {
+      if ((e = enqueue_icp_levels(h, levels - 1, J, false, &n_icp)) != cudaSuccess) return e;
+      if ((e = launch_prop_judge(h->p, h->b, h->q, J, run, run == 1 && J == 0, h->judge_nblk, h->s)) != cudaSuccess)
+        return e;
       ++n_icp;
     }
+    if (J > 0 && (e = enqueue_icp_levels(h, J - 1, 0, true, &n_icp)) != cudaSuccess) return e;
+  } else {
+    if ((e = enqueue_icp_levels(h, levels - 1, 0, true, &n_icp)) != cudaSuccess) return e;
   }
   stage_end(h, XSLAM_STAGE_ICP, n_icp);
   stage_begin(h, XSLAM_STAGE_INTEGRATE);
@@ -489,9 +561,14 @@ extern "C" xslam_status xslam_frame(xslam_t h, const float* depth, int depth_on_
   const bool want = pose_out || dpose_out || dtwist_out;
   if (!want && depth_on_device) return leave(h);
   CU(cudaMemcpyAsync(h->h_result, h->b.result, sizeof(double) * kResSys, cudaMemcpyDeviceToHost, h->s));
-  CU(cudaMemcpyAsync(h->h_status, h->b.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->s));
+  CU(cudaMemcpyAsync(h->h_status, h->b.status, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->s));
   if ((st = leave(h)) != XSLAM_OK) return st;
   CU(cudaStreamSynchronize(h->s));
+  if (h->h_status[4]) {
+    CU(cudaMemsetAsync(h->b.status + 4, 0, sizeof(int), h->s));
+    CU(cudaStreamSynchronize(h->s));
+    return fail(h, XSLAM_ETIMEOUT, "a tensor-core wait of the proposal network ran out");
+  }
   if (pose_out) memcpy(pose_out, h->h_result, sizeof(double) * 12);
   if (dpose_out) memcpy(dpose_out, h->h_result + 12, sizeof(double) * 12 * h->K);
   if (dtwist_out) memcpy(dtwist_out, h->h_result + 12 + 12 * (kMaxLanes - 1), sizeof(double) * 6 * h->K);
@@ -506,10 +583,12 @@ extern "C" xslam_status xslam_frame(xslam_t h, const float* depth, int depth_on_
 
 extern "C" xslam_status xslam_sync(xslam_t h, int* n_failed) {
   if (!h) return XSLAM_EINVAL;
-  CU(cudaMemcpyAsync(h->h_status, h->b.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->s));
+  CU(cudaMemcpyAsync(h->h_status, h->b.status, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->s));
   CU(cudaMemsetAsync(h->b.status + 1, 0, sizeof(int), h->s));
+  CU(cudaMemsetAsync(h->b.status + 4, 0, sizeof(int), h->s));
   CU(cudaStreamSynchronize(h->s));
   if (n_failed) *n_failed = h->h_status[1];
+  if (h->h_status[4]) return fail(h, XSLAM_ETIMEOUT, "a tensor-core wait of the proposal network ran out");
   if (h->h_status[1] > 0) {
     h->err = "ICP failed to track on some frames";
     return XSLAM_ENOTRACK;
@@ -776,7 +855,7 @@ extern "C" xslam_status xslam_profile(xslam_t h, int enable) {
       h->plaunch[st] = 0;
     }
     h->pframes = 0;
-    CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * 2, h->s));
+    CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * kStatIcpIters, h->s));
   CU(cudaMemsetAsync(h->b.tile_ctr, 0, sizeof(unsigned) * 2, h->s));
   }
   if (!enable && h->profiling) {
@@ -807,3 +886,81 @@ extern "C" xslam_status xslam_profile_read(xslam_t h, double* ms, long long* lau
 }
 
 extern "C" const char* xslam_last_error(xslam_t h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+extern "C" xslam_status xslam_set_proposal(xslam_t h, xslam_mlp_t m, const float* scale, int judge_level) {
+  if (!h) return XSLAM_EINVAL;
+  if (m) {
+    if (!scale) return fail(h, XSLAM_EINVAL, "scale is NULL");
+    for (int k = 0; k < 6; ++k)
+      if (!std::isfinite(scale[k])) return fail(h, XSLAM_EINVAL, "scale has a non-finite entry");
+    if (m->n[0] != 2 * kFeat || m->n[m->L] != 6)
+      return fail(h, XSLAM_EINVAL, "the proposal network must map 9600 inputs to 6 outputs");
+    if (h->p.W % kFeatW || h->p.H % kFeatH) return fail(h, XSLAM_EINVAL, "the image size must be a multiple of 80 x 60");
+    if (h->cfg.icp_newton) return fail(h, XSLAM_EINVAL, "the proposal needs Gauss-Newton ICP");
+    if (judge_level < 0 || judge_level >= h->cfg.icp_levels)
+      return fail(h, XSLAM_EINVAL, "judge_level must be 0..icp_levels-1");
+  }
+  CU(cudaStreamSynchronize(h->s));
+  for (int l = 0; l < 8; ++l) {
+    cudaFree(h->prop_act[l]);
+    h->prop_act[l] = nullptr;
+  }
+  cudaFree(h->prop_ws);
+  cudaFree(h->q.row);
+  cudaFree(h->q.prev);
+  cudaFree(h->q.y);
+  h->prop_ws = nullptr;
+  h->q.row = h->q.prev = nullptr;
+  h->q.y = nullptr;
+  h->mlp = nullptr;
+  drop_graphs(h);
+  if (!m) return XSLAM_OK;
+  bool ok = true;
+  for (int l = 1; l < m->L; ++l)
+    ok &= cudaMalloc(&h->prop_act[l], sizeof(__nv_bfloat16) * m->np[l]) == cudaSuccess;
+  ok &= cudaMalloc(&h->prop_ws, sizeof(float) * std::max<size_t>(16, mlp_ws_floats(m, 1))) == cudaSuccess;
+  ok &= cudaMalloc(&h->q.row, sizeof(__nv_bfloat16) * 2 * kFeat) == cudaSuccess;
+  ok &= cudaMalloc(&h->q.prev, sizeof(__nv_bfloat16) * kFeat) == cudaSuccess;
+  ok &= cudaMalloc(&h->q.y, sizeof(float) * 64) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    for (int l = 0; l < 8; ++l) {
+      cudaFree(h->prop_act[l]);
+      h->prop_act[l] = nullptr;
+    }
+    cudaFree(h->prop_ws);
+    cudaFree(h->q.row);
+    cudaFree(h->q.prev);
+    cudaFree(h->q.y);
+    h->prop_ws = nullptr;
+    h->q.row = h->q.prev = nullptr;
+    h->q.y = nullptr;
+    return fail(h, XSLAM_ENOMEM, "proposal buffers");
+  }
+  CU(cudaMemsetAsync(h->q.row, 0, sizeof(__nv_bfloat16) * 2 * kFeat, h->s));
+  CU(cudaMemsetAsync(h->q.prev, 0, sizeof(__nv_bfloat16) * kFeat, h->s));
+  CU(cudaMemsetAsync(h->q.y, 0, sizeof(float) * 64, h->s));
+  CU(gemm_configure());
+  CU(cudaStreamSynchronize(h->s));
+  for (int k = 0; k < 6; ++k) h->prop_scale[k] = scale[k];
+  h->judge_level = judge_level;
+  h->mlp = m;
+  return XSLAM_OK;
+}
+
+extern "C" xslam_status xslam_counters(xslam_t h, unsigned long long* out, int reset) {
+  if (!h) return XSLAM_EINVAL;
+  unsigned long long c[kNStat] = {};
+  CU(cudaStreamSynchronize(h->s));
+  CU(cudaMemcpy(c, h->b.stats, sizeof(c), cudaMemcpyDeviceToHost));
+  if (out) {
+    out[0] = c[kStatIcpIters];
+    out[1] = c[kStatJudged];
+    out[2] = c[kStatAccepted];
+  }
+  if (reset) {
+    CU(cudaMemsetAsync(h->b.stats + kStatIcpIters, 0, sizeof(unsigned long long) * 3, h->s));
+    CU(cudaStreamSynchronize(h->s));
+  }
+  return XSLAM_OK;
+}

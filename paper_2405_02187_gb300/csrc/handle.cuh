@@ -28,6 +28,14 @@ struct xslam_s {
   float* model_q = nullptr;    // scratch model maps of xslam_grad (7 lanes)
   double* h_result = nullptr;  // pinned host staging
   int* h_status = nullptr;
+  // constant-velocity start and learned proposal (proposal.cu); the network is the caller's
+  xslam::PropBuffers q = {};
+  struct xslam_mlp_s* mlp = nullptr;
+  float prop_scale[6] = {};
+  int judge_level = 0;
+  int judge_nblk = 1;
+  void* prop_act[8] = {};   // BF16 hidden activations of the network's forward pass (1 row each)
+  float* prop_ws = nullptr; // its split-K workspace
   int nblk[3] = {1, 1, 1};
   int nblk_max = 1;
   cudaGraphExec_t g_first = nullptr, g_track = nullptr;

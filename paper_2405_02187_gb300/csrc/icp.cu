@@ -128,15 +128,35 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   __shared__ SeCoefF scf[kMaxLanes];
   __shared__ float sxs[kMaxLanes][6];
   __shared__ float sdl[kMaxLanes][12];
-  __shared__ int s_ncorr, s_fail;
+  __shared__ int s_ncorr, s_fail, s_conv;
   extern __shared__ float s_rec[];  // [rep][chunk of the group][field][pixel]: reps * L * kRec * 32 floats
 
-  if (threadIdx.x == 0) s_skip = b.status[0];
+  if (threadIdx.x == 0) {
+    s_skip = b.status[0];
+    // status[3]: the level converged (a step below p.icp_stop); only its first iteration ignores it
+    s_conv = (flags & (kIcpFirst | kIcpNoUpdate)) ? 0 : b.status[3];
+  }
   for (int i = threadIdx.x; i < L * 12; i += blockDim.x) {
     sT[i / 12][i % 12] = (float)b.pose[i];
     sP[i / 12][i % 12] = (float)b.pose_prev[i];
   }
   __syncthreads();
+  if ((s_skip || s_conv) && !(flags & kIcpNoUpdate)) {
+    // nothing to compute after a failure or after the level converged; the frame's last iteration
+    // still closes the frame: fall back to T_{k-1} on a failure and count it
+    if ((flags & kIcpLast) && blockIdx.x == 0) {
+      if (s_skip && threadIdx.x < 12 * L) b.pose[threadIdx.x] = b.pose_prev[threadIdx.x];
+      if (threadIdx.x == 0) {
+        if (s_skip) {
+          b.status[1] += 1;
+          b.status[2] = 0;
+        }
+        b.status[0] = 0;
+        b.status[3] = 0;
+      }
+    }
+    return;
+  }
 
   float acc[kNT];
 #pragma unroll
@@ -528,7 +548,15 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   }
   __syncthreads();
   if (go && t < 12 * L) b.pose[t] = tn;
-  if (threadIdx.x == 0 && s_fail && !s_skip) b.status[0] = 1;
+  if (threadIdx.x == 0) {
+    if (s_fail) b.status[0] = 1;
+    b.status[2] = s_ncorr;
+    double x2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) x2 += sx[0][k] * sx[0][k];
+    b.status[3] = (go && x2 < (double)p.icp_stop * (double)p.icp_stop) ? 1 : 0;
+    if (b.stats) b.stats[kStatIcpIters] += 1;
+  }
   if (flags & kIcpLast) {
     __syncthreads();
     const int failed = b.status[0];

@@ -41,6 +41,7 @@ struct Params {
   int bilateral;            // 1: bilateral filter of the gated raw depth before the pyramid
   float ray_step;           // dalpha in metres of camera depth
   float icp_newton_eta;     // Newton ICP: mean squared residual (m^2) below which the Hessian is used
+  float icp_stop;           // > 0: a level ends after a real step |x| below this (twist norm)
   int m0, m1;               // ray samples alpha_m = m * ray_step, m0 <= m <= m1
 };
 
@@ -59,11 +60,45 @@ struct Buffers {
   unsigned* ticket; // last-block-done counter
   int* status;      // [0] ICP failed in this frame, [1] frames failed since last sync, [2] last n_valid
   double* result;   // read-out: 12 (pose) + 12 K (dpose) + 6 K (dtwist) + 27 L (last system)
-  unsigned long long* stats;  // [0] voxels updated by fusion, [1] pixels with a ray-cast surface
+  unsigned long long* stats;  // kNStat counters (kStat* below); NULL in the allocation-free calls
   int* hit;                   // per pixel: index m of the first sample of the ray-cast hit pair, -1 = none
   int* tiles;                 // fusion: tiles the frame can touch (fuse_tile_count entries at most)
   unsigned* tile_ctr;         // fusion: [0] listed tiles, [1] finished blocks (both 0 between launches)
 };
+
+// device counters of a handle (Buffers::stats)
+enum : int {
+  kStatVoxels = 0,    // voxels updated by fusion
+  kStatHits = 1,      // pixels with a ray-cast surface
+  kStatIcpIters = 2,  // ICP iterations computed (not skipped after a failure or convergence)
+  kStatJudged = 3,    // frames whose learned proposal was judged
+  kStatAccepted = 4,  // ... and accepted
+  kNStat = 8
+};
+
+// Learned proposal and constant-velocity start (proposal.cu), per handle
+struct PropBuffers {
+  double* pose_pp;   // L x 12: T_{k-2} lanes (the pose before the model's)
+  double* candA;     // L x 12: the first ICP run's result while the second runs
+  double* candB;     // L x 12: the proposal's start pose
+  double* judge;     // [0] J of run A, [1] J of run B
+  int* failA;        // run A failed
+  double* partial;   // judge: per-block sums (2 per block)
+  unsigned* ticket;  // judge: last-block-done counter
+  void* row;         // BF16 network input [2 x 4800]: previous frame's features, then the current's
+  void* prev;        // BF16 previous frame's features [4800]
+  float* y;          // network output (padded to 64)
+};
+
+// GEMM launch plan (gemm.cu): K split into `splits` ranges of kb_per_split 64-wide slices
+struct GemmPlan {
+  int splits = 1, kb_per_split = 1;
+};
+GemmPlan gemm_plan(int M, int N, int K, int target_ctas);
+bool gemm_shape_ok(int M, int N, int K);
+cudaError_t gemm_configure();
+cudaError_t launch_gemm_bf16(const void* A, const void* B, int M, int N, int K, const GemmPlan& g, float* C, int* err,
+                             cudaStream_t s);
 
 __host__ __device__ inline size_t vox_count(const Params& p) {
   return (size_t)p.nx * p.ny * p.nz;
@@ -123,6 +158,21 @@ cudaError_t launch_loss(const Params& p, const Buffers& b, const float* depth, c
 int icp_blocks(int level_pixels, int L);
 int icp_reps(int L);
 cudaError_t icp_configure();
+
+// learned proposal / constant-velocity start (proposal.cu)
+constexpr int kFeatW = 80, kFeatH = 60, kFeat = kFeatW * kFeatH;
+// 80 x 60 block-mean features of n depth frames (frame f at D + f W H) into out + f out_stride (BF16);
+// with prev != NULL (n = 1): out[0..kFeat) = prev, out[kFeat..2 kFeat) = the features, prev = the features
+cudaError_t launch_features(const float* D, int n, int W, int H, float dmin, float dmax, void* out, size_t out_stride,
+                            void* prev, cudaStream_t s);
+// start poses: mode bit 0 constant velocity (else T_{k-1}), bit 1 proposal (T_{k-1} exp(scale y)),
+// bit 2 frame 0 (only records T_{k-2} := T_0)
+cudaError_t launch_prop_seed(const Params& p, const Buffers& b, const PropBuffers& q, const float* scale, int mode,
+                             cudaStream_t s);
+// judge of the current pose at `level`; phase 0 stores run A and starts run B, phase 1 selects; final:
+// phase 1 also closes the frame (fallback to T_{k-1} and failure count)
+cudaError_t launch_prop_judge(const Params& p, const Buffers& b, const PropBuffers& q, int level, int phase, int final_,
+                              int nblk, cudaStream_t s);
 
 // message of the last failed call made without a handle (returned by xslam_last_error(NULL))
 void set_handleless_error(const char* msg);

@@ -738,6 +738,8 @@ extern "C" xslam_status xslam_plain_create(xslam_plain_t* out, int nx, int ny, i
   else xslam_default_config(&c);
   if (c.icp_levels < 1 || c.icp_levels > 3) return pfail(h, XSLAM_EINVAL, "icp_levels must be in 1..3");
   if (c.icp_newton) return pfail(h, XSLAM_EINVAL, "the plain path runs Gauss-Newton ICP only");
+  if (c.icp_seed != 0 || c.icp_stop != 0.f)
+    return pfail(h, XSLAM_EINVAL, "the plain path starts ICP at the previous pose with fixed iteration counts");
   for (int l = 0; l < c.icp_levels; ++l)
     if (c.icp_iters[l] < 0 || c.icp_iters[l] > 100) return pfail(h, XSLAM_EINVAL, "icp_iters must be in 0..100");
   if (!(c.ray_step_vox > 0.f) || !(c.depth_max_m > c.depth_min_m) || !(c.depth_min_m > 0.f))

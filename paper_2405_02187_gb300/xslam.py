@@ -37,7 +37,7 @@ class Config(ctypes.Structure):
                 ("ray_step_vox", ctypes.c_float), ("depth_min_m", ctypes.c_float),
                 ("depth_max_m", ctypes.c_float), ("pyr_range_m", ctypes.c_float),
                 ("bilateral", ctypes.c_int), ("w_max", ctypes.c_float), ("icp_newton", ctypes.c_int),
-                ("icp_newton_eta", ctypes.c_float)]
+                ("icp_newton_eta", ctypes.c_float), ("icp_seed", ctypes.c_int), ("icp_stop", ctypes.c_float)]
 
 
 class XSlamError(RuntimeError):
@@ -102,6 +102,28 @@ SYMBOLS = [
     ("xslam_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _c_int_p,
                                             _c_float_p]),
     ("xslam_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    # include/xslam_mlp.h: the learned pose proposal
+    ("xslam_mlp_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _c_int_p, ctypes.c_int,
+                                        ctypes.c_void_p]),
+    ("xslam_mlp_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("xslam_mlp_param_count", ctypes.c_size_t, [ctypes.c_void_p]),
+    ("xslam_mlp_set_params", ctypes.c_int, [ctypes.c_void_p, _c_float_p]),
+    ("xslam_mlp_get_params", ctypes.c_int, [ctypes.c_void_p, _c_float_p]),
+    ("xslam_mlp_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("xslam_mlp_gradient", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _c_float_p,
+                                          _c_double_p]),
+    ("xslam_mlp_features", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                          ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+    ("xslam_mlp_pair_targets", ctypes.c_int, [_c_double_p, ctypes.c_int, _c_int_p, ctypes.c_int, _c_float_p,
+                                              _c_float_p]),
+    ("xslam_mlp_train", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                       ctypes.c_ulonglong, _c_float_p]),
+    ("xslam_gemm_bf16", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    ("xslam_set_proposal", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_float_p, ctypes.c_int]),
+    ("xslam_counters", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]),
+    ("xslam_mlp_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
 STAGES = ("prepare", "icp", "integrate", "raycast", "other")
 
@@ -327,6 +349,21 @@ class XSlam:
         T_prev = np.ascontiguousarray(T_prev, np.float64).reshape(-1)
         self._check(self.lib.xslam_set_model(self.h, _dev(depth), _dev(vmap), _dev(nmap), _dptr(T_prev)))
 
+    def set_proposal(self, mlp, scale=None, judge_level=2):
+        """Attach the learned proposal (an Mlp; None detaches) with its output scale (6 values)."""
+        if mlp is None:
+            self._check(self.lib.xslam_set_proposal(self.h, None, None, 0))
+            return
+        sc = np.ascontiguousarray(scale, np.float32).reshape(6)
+        self._check(self.lib.xslam_set_proposal(self.h, mlp.m, sc.ctypes.data_as(_c_float_p), int(judge_level)))
+        self._proposal = mlp  # must outlive the attachment
+
+    def counters(self, reset=False):
+        """dict: ICP iterations computed, proposals judged, proposals accepted."""
+        c = (ctypes.c_ulonglong * 3)()
+        self._check(self.lib.xslam_counters(self.h, c, int(bool(reset))))
+        return dict(icp_iterations=c[0], judged=c[1], accepted=c[2])
+
     def icp_system(self, level, Tj):
         Tj = np.ascontiguousarray(Tj, np.float64).reshape(-1)
         out = np.zeros(27 * (1 + self.K))
@@ -476,3 +513,144 @@ class XSlamBatch:
         ms = np.zeros(5, np.float32)
         self._check(self.lib.xslam_batch_autotune(self.b, arr, int(steps), ctypes.byref(d), ms.ctypes.data_as(_c_float_p)))
         return d.value, ms
+
+
+# ------------------------------------------------------------------------------------------------
+# include/xslam_mlp.h: the learned pose proposal
+# ------------------------------------------------------------------------------------------------
+def _bf16(t):
+    return _dev(t, "bfloat16")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    return ctypes.c_void_p(stream)
+
+
+def _mlp_raise(st, m=None):
+    lib = load()
+    raise XSlamError(st, lib.xslam_mlp_last_error(m).decode())
+
+
+def features(depth, depth_min, depth_max, out=None, stream=None):
+    """80 x 60 BF16 features of CUDA depth frames (n, H, W) or (H, W) into out (n, 4800)."""
+    import torch
+    lib = load()
+    d = depth if depth.dim() == 3 else depth[None]
+    n, H, W = d.shape
+    if out is None:
+        out = torch.empty((n, 4800), dtype=torch.bfloat16, device=d.device)
+    st = lib.xslam_mlp_features(_dev(d), int(n), int(W), int(H), float(depth_min), float(depth_max), _bf16(out),
+                                _stream_ptr(stream))
+    if st != OK:
+        _mlp_raise(st)
+    return out
+
+
+def pair_targets(poses, pairs, scale):
+    """log(T_i^-1 T_j) / scale for each pair (host; poses (n, 3, 4), pairs (P, 2)) -> (P, 6) float32."""
+    lib = load()
+    poses = np.ascontiguousarray(poses, np.float64).reshape(-1, 12)
+    pairs = np.ascontiguousarray(pairs, np.int32).reshape(-1, 2)
+    sc = np.ascontiguousarray(scale, np.float32).reshape(6)
+    out = np.zeros((pairs.shape[0], 6), np.float32)
+    st = lib.xslam_mlp_pair_targets(_dptr(poses), poses.shape[0], pairs.ctypes.data_as(_c_int_p), pairs.shape[0],
+                                    sc.ctypes.data_as(_c_float_p), out.ctypes.data_as(_c_float_p))
+    if st != OK:
+        _mlp_raise(st)
+    return out
+
+
+def gemm_bf16(A, B, C, splits=1, workspace=None, stream=None):
+    """C = A B^T on the tensor cores (A (M, K), B (N, K) CUDA bfloat16, C (M, N) CUDA float32)."""
+    lib = load()
+    M, K = A.shape
+    N = B.shape[0]
+    st = lib.xslam_gemm_bf16(_bf16(A), _bf16(B), int(M), int(N), int(K), _dev(C), int(splits), _dev(workspace),
+                             _stream_ptr(stream))
+    if st != OK:
+        _mlp_raise(st)
+    return C
+
+
+class Mlp:
+    """The proposal network (xslam_mlp_t): sizes (n_0, ..., n_L), batches of up to max_batch rows."""
+
+    def __init__(self, sizes, max_batch=256, stream=None):
+        self.lib = load()
+        self.sizes = tuple(int(s) for s in sizes)
+        arr = (ctypes.c_int * len(self.sizes))(*self.sizes)
+        m = ctypes.c_void_p()
+        st = self.lib.xslam_mlp_create(ctypes.byref(m), len(self.sizes) - 1, arr, int(max_batch), _stream_ptr(stream))
+        if st != OK:
+            _mlp_raise(st)
+        self.m = m
+        self.max_batch = max_batch
+        self.n_params = int(self.lib.xslam_mlp_param_count(m))
+
+    def _check(self, st):
+        if st != OK:
+            _mlp_raise(st, self.m)
+
+    def close(self):
+        if getattr(self, "m", None):
+            self.lib.xslam_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def flatten(params):
+        """[(W (out, in), b (out)), ...] -> the flat host layout."""
+        return np.concatenate([np.concatenate([np.asarray(W, np.float32).reshape(-1), np.asarray(b, np.float32)])
+                               for W, b in params])
+
+    def unflatten(self, flat):
+        out, k = [], 0
+        for n_in, n_out in zip(self.sizes[:-1], self.sizes[1:]):
+            W = flat[k:k + n_in * n_out].reshape(n_out, n_in)
+            k += n_in * n_out
+            out.append((W, flat[k:k + n_out]))
+            k += n_out
+        return out
+
+    def set_params(self, params):
+        flat = np.ascontiguousarray(self.flatten(params) if isinstance(params, (list, tuple)) else params, np.float32)
+        assert flat.size == self.n_params
+        self._check(self.lib.xslam_mlp_set_params(self.m, flat.ctypes.data_as(_c_float_p)))
+
+    def get_params(self):
+        flat = np.zeros(self.n_params, np.float32)
+        self._check(self.lib.xslam_mlp_get_params(self.m, flat.ctypes.data_as(_c_float_p)))
+        return self.unflatten(flat)
+
+    def forward(self, x, y=None):
+        """x: CUDA bfloat16 (B, n_0) -> CUDA float32 (B, n_L)."""
+        import torch
+        if y is None:
+            y = torch.empty((x.shape[0], self.sizes[-1]), dtype=torch.float32, device=x.device)
+        self._check(self.lib.xslam_mlp_forward(self.m, _bf16(x), int(x.shape[0]), _dev(y)))
+        return y
+
+    def gradient(self, x, targets):
+        """Loss and gradient (list of (dW, db)) of the batch x (CUDA bf16) with CUDA float32 targets."""
+        g = np.zeros(self.n_params, np.float32)
+        loss = ctypes.c_double(0)
+        self._check(self.lib.xslam_mlp_gradient(self.m, _bf16(x), _dev(targets), int(x.shape[0]),
+                                                g.ctypes.data_as(_c_float_p), ctypes.byref(loss)))
+        return loss.value, self.unflatten(g)
+
+    def train(self, feat, pairs, targets, epochs, batch=256, lr=1e-3, seed=1):
+        """Adam over the pairs (CUDA int32 (P, 2)) of feature rows feat (CUDA bf16 (n, 4800)) with CUDA
+        float32 targets (P, n_L); returns the per-epoch mean loss."""
+        losses = np.zeros(epochs, np.float32)
+        self._check(self.lib.xslam_mlp_train(self.m, _bf16(feat), int(feat.shape[0]), _dev(pairs, "int32"),
+                                             _dev(targets), int(pairs.shape[0]), int(batch), int(epochs), float(lr),
+                                             int(seed), losses.ctypes.data_as(_c_float_p)))
+        return losses

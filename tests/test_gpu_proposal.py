@@ -1,0 +1,162 @@
+"""ICP start poses, the stop tolerance and the learned proposal in the GPU frame chain, against the
+oracle (oracle/pipeline.py, oracle/proposal.py) on the 64^3 / 160x120 orbit, through the C ABI.
+
+Tolerances: pose 1e-5 m/rad, derivatives 1e-3 relative (Frobenius over the seeds' twist
+derivatives), as for the method without a proposal. The proposal cases are built so that the judge's
+decision is not a near tie (a clearly better or clearly worse start, or two identical runs), so that
+GPU and oracle take the same branch."""
+import numpy as np
+import pytest
+
+from gpu_helpers import H_GPU, gpu_seeds, rel_err, xslam_cfg
+from oracle import mlp as OM
+from oracle import pipeline as P
+from paper_2405_02187_gb300 import synth, xslam
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FRAMES = 5
+SEEDS = [P.Seed(P.POSE0, 0), P.Seed(P.POSE0, 4), P.Seed(P.TRUNC)]
+
+
+@pytest.fixture(scope="module")
+def orbit():
+    return synth.small_orbit(frames=FRAMES)
+
+
+def _gpu_run(wl, cfg, mlp=None, scale=None, judge_level=2, seeds=SEEDS, frames=FRAMES):
+    x = xslam.XSlam(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, cfg, max_lanes=len(seeds))
+    x.set_pose(wl.poses[0])
+    if mlp is not None:
+        x.set_proposal(mlp, scale, judge_level)
+    out = []
+    for k in range(frames):
+        pose, _, dtw, st = x.frame(torch.tensor(wl.depth[k], device="cuda"), gpu_seeds(seeds))
+        out.append((pose, dtw))
+    c = x.counters()
+    x.close()
+    return np.array([p for p, _ in out]), np.array([d for _, d in out]), c
+
+
+def _ora_run(wl, cfg):
+    r = P.run(wl, SEEDS, frames=FRAMES, cfg=cfg)
+    return r["pose"], r["dtwist"], r["runs"][0].stats
+
+
+def _cfgs(wl, icp_seed=0, icp_stop=0.0, iters=None):
+    c = xslam_cfg(wl)
+    c.icp_seed = icp_seed
+    c.icp_stop = icp_stop
+    it = tuple(wl.icp_iters) if iters is None else iters
+    for i, n in enumerate(it):
+        c.icp_iters[i] = n
+    o = P.Config(icp_iters=it, depth_min=wl.depth_min, depth_max=wl.depth_max, bilateral=wl.bilateral,
+                 icp_seed="cv" if icp_seed else "prev", icp_stop=icp_stop)
+    return c, o
+
+
+def _compare(gpu, ora):
+    gp, gd, _ = gpu
+    op, od, _ = ora
+    assert np.abs(gp - op).max() < 1e-5
+    for j in range(len(SEEDS)):
+        for k in range(1, FRAMES):
+            assert rel_err(gd[k, j], od[j, k]) < 1e-3, (j, k)
+
+
+def test_constant_velocity_start_parity(orbit):
+    c, o = _cfgs(orbit, icp_seed=1)
+    _compare(_gpu_run(orbit, c), _ora_run(orbit, o))
+
+
+def test_stop_tolerance_counts_and_parity(orbit):
+    levels = len(orbit.icp_iters)
+    c, _ = _cfgs(orbit, icp_stop=1e9)
+    _, _, cnt = _gpu_run(orbit, c)
+    assert cnt["icp_iterations"] == levels * (FRAMES - 1)
+    c, _ = _cfgs(orbit)
+    _, _, cnt = _gpu_run(orbit, c)
+    assert cnt["icp_iterations"] == sum(orbit.icp_iters) * (FRAMES - 1)
+    c, o = _cfgs(orbit, icp_stop=1e-6)
+    gpu, ora = _gpu_run(orbit, c), _ora_run(orbit, o)
+    _compare(gpu, ora)
+    assert gpu[2]["icp_iterations"] < sum(orbit.icp_iters) * (FRAMES - 1)
+    assert abs(gpu[2]["icp_iterations"] - ora[2]["iterations"]) <= 2
+
+
+def _net(rng, bias, hidden=64, w_scale=1e-3):
+    """A small network whose output is `bias` plus a small depth-dependent term."""
+    sizes = (9600, hidden, hidden, 6)
+    params = OM.init_params(sizes, rng)
+    params[-1] = (params[-1][0] * w_scale, np.asarray(bias, np.float64))
+    params = [(np.float32(W).astype(np.float64), np.float32(b).astype(np.float64)) for W, b in params]
+    m = xslam.Mlp(sizes, max_batch=64)
+    m.set_params(params)
+    return m, params
+
+
+def _motion(wl):
+    # the orbit turns by a constant step: the camera-frame motion between frames is the same each time
+    return OM.pair_target(wl.poses[1], wl.poses[2])
+
+
+def _proposal_case(wl, bias, icp_seed, iters, judge_level):
+    rng = np.random.default_rng(3)
+    scale = np.ones(6)
+    m, params = _net(rng, bias)
+    c, o = _cfgs(wl, icp_seed=icp_seed, iters=iters)
+    gpu = _gpu_run(wl, c, m, scale, judge_level)
+    o.proposal = P.Proposal(params, scale, judge_level)
+    ora = _ora_run(wl, o)
+    m.close()
+    return gpu, ora
+
+
+def test_true_motion_proposal_is_accepted_and_matches_oracle(orbit):
+    # one iteration at the coarsest level: from the previous pose run A is still far, run B starts right
+    gpu, ora = _proposal_case(orbit, _motion(orbit), 0, (10, 5, 1), 2)
+    _compare(gpu, ora)
+    assert gpu[2]["judged"] == FRAMES - 1 == ora[2]["judged"]
+    # the same decisions as the oracle, mostly for the proposal (one GN step from T_{k-1} can land as
+    # well as the exact start at this coarse level)
+    assert gpu[2]["accepted"] == ora[2]["accepted"] >= FRAMES - 2
+
+
+def test_far_proposal_is_rejected_and_matches_oracle(orbit):
+    far = np.array([0.0, 0.0, 0.0, 0.15, 0.0, 0.0])
+    gpu, ora = _proposal_case(orbit, far, 1, tuple(orbit.icp_iters), 2)
+    _compare(gpu, ora)
+    assert gpu[2]["accepted"] == ora[2]["accepted"] == 0
+    # and the result is the constant-velocity run's
+    c, _ = _cfgs(orbit, icp_seed=1)
+    ref = _gpu_run(orbit, c)
+    np.testing.assert_array_equal(gpu[0], ref[0])
+
+
+def test_zero_motion_proposal_changes_nothing(orbit):
+    sizes = (9600, 64, 6)
+    m = xslam.Mlp(sizes, max_batch=64)
+    m.set_params([(np.zeros((64, 9600)), np.zeros(64)), (np.zeros((6, 64)), np.zeros(6))])
+    c, _ = _cfgs(orbit)
+    for jl in (0, 1, 2):
+        gp, gd, cnt = _gpu_run(orbit, c, m, np.ones(6), jl)
+        rp, rd, _ = _gpu_run(orbit, c)
+        np.testing.assert_array_equal(gp, rp)
+        np.testing.assert_array_equal(gd, rd)
+        assert cnt["judged"] == cnt["accepted"] == FRAMES - 1
+    m.close()
+
+
+def test_proposal_argument_checks(orbit):
+    c, _ = _cfgs(orbit)
+    x = xslam.XSlam(orbit.dims, orbit.voxel, orbit.trunc, orbit.origin, orbit.intr, c, max_lanes=0)
+    bad = xslam.Mlp((9600, 64, 5), max_batch=1)
+    with pytest.raises(xslam.XSlamError):
+        x.set_proposal(bad, np.ones(6), 0)
+    good = xslam.Mlp((9600, 64, 6), max_batch=1)
+    with pytest.raises(xslam.XSlamError):
+        x.set_proposal(good, np.ones(6), 3)
+    x.set_proposal(good, np.ones(6), 2)
+    x.set_proposal(None)
+    x.close()
