@@ -220,6 +220,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_bf16_tflops():
+    """(dense bf16 TFLOP/s burst peak, "measured" | "fallback")."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
 KERNEL_SRC = {"integrate": "fuse.cu", "raycast": "raycast.cu", "icp": "icp.cu"}
 KERNEL_NAME = {"integrate": "k_integrate", "raycast": "k_march + k_refine", "icp": "k_icp"}
 
@@ -444,6 +455,7 @@ def run_ours(args, rank, world, local_rank):
     batched = None if args.no_batch else run_batch(args, dev, rank)
     second = None if args.no_second_order else run_second_order(args, dev, rank)
     newton = None if args.no_newton else run_newton_icp(args, dev, rank)
+    learned = None if args.no_learned else run_learned(args, dev, rank)
 
     # ---- CPU oracle on the host cores (rank 0, N = 1): frame 1 of the same sequence ----
     cpu = None
@@ -475,6 +487,7 @@ def run_ours(args, rank, world, local_rank):
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(round(launches_per_frame * K)),
                 clocks=clk, stage_ms_per_frame=stage_ms, grad_rel_err_vs_oracle=grad_err,
                 plain_fp64=plain, uncomplexified_fp32=real32, batched=batched, second_order=second, newton_icp=newton,
+                learned_proposal=learned,
                 per_frame=dict(fused_voxels=round(per_frame["fused"]), surface_pixels=round(per_frame["hits"])))
     if rank == 0:
         print(json.dumps(line))
@@ -693,6 +706,60 @@ def run_newton_icp(args, dev, rank):
 
 
 # ------------------------------------------------------------------------------------------------
+# learned pose proposal (include/xslam_mlp.h)
+# ------------------------------------------------------------------------------------------------
+def run_learned(args, dev, rank):
+    """Train the proposal network on frame pairs of room walks tracked by the method, then track a
+    1000-frame 640x480, 512^3 trajectory with K = 6 CSFD lanes from the constant-velocity start and from
+    the previous pose (the paper's start), each with and without the proposal as a second judged start:
+    frames/s, ICP iterations per frame (stop tolerance 1e-5), pose error against the ground truth,
+    failures, the proposal's acceptance and fallback rates, and how far each start lies from the true
+    motion."""
+    import torch
+    from paper_2405_02187_gb300 import learn, synth
+
+    ds = learn.make_dataset(n_traj=args.learned_rooms, frames=16, reverse=True, seed=20000 + 1000 * rank, device=dev)
+    P = int(ds.pairs.shape[0])
+    m, losses, ms = learn.train(ds, epochs=args.learned_epochs, lr=1e-3, mirror=True)
+    flops = learn.train_flops(P, 256, args.learned_epochs)
+    peak, peak_kind = measured_bf16_tflops()
+    tfl = flops / (ms * 1e9)
+    train = dict(pairs=P, frames=ds.n_frames, rooms=args.learned_rooms, epochs=args.learned_epochs, batch=256,
+                 lr=1e-3, mirror=True, data_s=round(ds.seconds, 1), train_ms=round(ms, 1),
+                 loss_first=round(float(losses[0]), 4), loss_last=round(float(losses[-1]), 4),
+                 gemm_tflop=round(flops / 1e12, 3), tflops_whole_steps=round(tfl, 2),
+                 tensor_frac_whole_steps=round(tfl / peak, 4), peak_tflops=peak,
+                 peak_note=f"whole training steps (GEMMs, reductions, loss, Adam, gather) against the {peak_kind} "
+                           "bf16 burst peak")
+    wl = synth.room_smooth(seed=31000 + rank, frames=args.learned_frames, dims=512, voxel=0.005, step_m=0.04,
+                           step_deg=3.0, jerk_every=10, device=dev)
+    starts = learn.start_errors(m, ds.scale, wl)
+    seeds = [(0, j, 1e-10) for j in range(6)]
+    arms = {}
+    for name, seed_mode, use in (("constant_velocity", 1, False), ("constant_velocity_proposal", 1, True),
+                                 ("previous_pose", 0, False), ("previous_pose_proposal", 0, True)):
+        r = learn.track(wl, learn.handle_config(wl, seed_mode, 1e-5), seeds, mlp=m if use else None,
+                        scale=ds.scale, judge_level=2)
+        dt, dr = learn.pose_errors(r["poses"], wl.poses)
+        c = r["counters"]
+        row = dict(fps=round(r["fps"], 1), icp_iterations_per_frame=round(c["icp_iterations"] / (len(dt) - 1), 2),
+                   failures=r["failures"], trans_err_cm_mean=round(float(dt.mean()) * 100, 3),
+                   trans_err_cm_max=round(float(dt.max()) * 100, 3), rot_err_deg_mean=round(float(dr.mean()), 4),
+                   rot_err_deg_max=round(float(dr.max()), 4))
+        if use:
+            row.update(judged=c["judged"], accepted=c["accepted"],
+                       fallback_rate=round(1.0 - c["accepted"] / max(c["judged"], 1), 4))
+        arms[name] = row
+    m.close()
+    return dict(workload=f"{args.learned_frames} frames of a 640x480 camera with inertia in the room (steps up to "
+                         "4 cm and 3 deg, rho = 0.9, a fresh motion every 10 frames), 512^3 x 0.5 cm, K = 6 "
+                         "(d pose / d pose0), ICP stop tolerance 1e-5, judge at the coarsest level",
+                train=train, network=f"{'-'.join(str(v) for v in learn.SIZES)} BF16, tcgen05 GEMMs",
+                start_error_sigma=dict((k, round(float(v.mean()), 3)) for k, v in starts.items()),
+                **arms)
+
+
+# ------------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle as it stands
 # ------------------------------------------------------------------------------------------------
 def _reference(args, rank):
@@ -741,6 +808,10 @@ def main():
     ap.add_argument("--reloc-eta", type=float, default=1e-3)
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-ICP frame-step comparison")
     ap.add_argument("--newton-frames", type=int, default=40)
+    ap.add_argument("--no-learned", action="store_true", help="skip training and evaluating the learned proposal")
+    ap.add_argument("--learned-rooms", type=int, default=100, help="room walks of 16 frames for the training pairs")
+    ap.add_argument("--learned-epochs", type=int, default=30)
+    ap.add_argument("--learned-frames", type=int, default=1000)
     ap.add_argument("--batch-n", type=int, default=32)
     ap.add_argument("--batch-min", type=int, default=50)
     ap.add_argument("--batch-max", type=int, default=400)

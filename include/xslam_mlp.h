@@ -85,11 +85,15 @@ xslam_status xslam_mlp_pair_targets(const double* poses, int n_poses, const int*
  * first), targets device FP32 [n_pairs x sizes[L]]. sizes[0] must be 9600. Each epoch visits the pairs
  * in an order drawn from seed (splitmix64 and Fisher-Yates on the host) in batches of `batch` rows
  * (a multiple of 64 up to max_batch; a last incomplete batch is skipped); one step per batch is a
- * replay of a CUDA graph of the whole step. epoch_loss (host, NULL allowed) receives each epoch's mean
- * batch loss. Allocates the device permutation (n_pairs ints) when it is larger than any before.
- * Synchronises. Errors: XSLAM_EINVAL, XSLAM_ENOMEM, XSLAM_ETIMEOUT, XSLAM_ECUDA. */
+ * replay of a CUDA graph of the whole step. mirror = 1 (6 outputs holding the twists of
+ * xslam_mlp_pair_targets, cameras whose principal point is the image centre): each visit of a pair
+ * reflects it at random left-right and/or top-bottom, both feature maps and the target (the twist of
+ * the reflected motion: phi_y, phi_z, rho_x negated left-right; phi_x, phi_z, rho_y top-bottom).
+ * epoch_loss (host, NULL allowed) receives each epoch's mean batch loss. Allocates the device
+ * permutation (n_pairs ints) when it is larger than any before. Synchronises. Errors: XSLAM_EINVAL
+ * (also a pair naming a frame outside the feature table), XSLAM_ENOMEM, XSLAM_ETIMEOUT, XSLAM_ECUDA. */
 xslam_status xslam_mlp_train(xslam_mlp_t m, const void* feat, int n_feat, const int* pairs, const float* targets,
-                             int n_pairs, int batch, int epochs, float lr, unsigned long long seed,
+                             int n_pairs, int batch, int epochs, float lr, unsigned long long seed, int mirror,
                              float* epoch_loss);
 
 /* One BF16 GEMM on the tensor cores: C[M x N] = A[M x K] B[N x K]^T, all device, A and B BF16

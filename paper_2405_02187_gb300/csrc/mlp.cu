@@ -125,7 +125,10 @@ __global__ void __launch_bounds__(256) k_colsum(const float* __restrict__ dz, in
 
 // training batch: rows [f_i, f_j] of the pairs idx[k B .. k B + B) with k = ctr[1], the step's batch
 // index (0 at the start of an epoch; the loss kernel of each step advances it), with the transposed
-// copy and the zero-padded targets
+// copy and the zero-padded targets. An entry of idx is (pair << 2) | mirror: mirror bit 0 reflects
+// both feature maps left-right (camera x -> -x), bit 1 top-bottom (y -> -y); a reflection M maps the
+// motion twist (phi, rho) to (-M phi, M rho), i.e. negates phi_y, phi_z, rho_x (left-right) or phi_x,
+// phi_z, rho_y (top-bottom)
 __global__ void __launch_bounds__(256) k_gather(const __nv_bfloat16* __restrict__ feat, const int* __restrict__ pairs,
                                                 const float* __restrict__ targets, const int* __restrict__ idx,
                                                 const int* __restrict__ ctr, int B, int nL, int npL, int n_feat,
@@ -137,17 +140,25 @@ __global__ void __launch_bounds__(256) k_gather(const __nv_bfloat16* __restrict_
   const size_t total = (size_t)B * n0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(e / n0), j = (int)(e % n0);
+    const int code = ib[b], mir = code & 3;
     const int second = j >= kFeat;
-    const int f = pairs[2 * ib[b] + second];
+    const int f = pairs[2 * (code >> 2) + second];
     const bool ok = f >= 0 && f < n_feat;  // a frame index outside the feature table reads zeros
     if (!ok) atomicOr(err, 2);
-    const __nv_bfloat16 v = ok ? feat[(size_t)f * kFeat + (j - second * kFeat)] : __float2bfloat16(0.f);
+    const int jj = j - second * kFeat;
+    int r = jj / kFeatW, c = jj % kFeatW;
+    if (mir & 1) c = kFeatW - 1 - c;
+    if (mir & 2) r = kFeatH - 1 - r;
+    const __nv_bfloat16 v = ok ? feat[(size_t)f * kFeat + r * kFeatW + c] : __float2bfloat16(0.f);
     X[e] = v;
     XT[(size_t)j * B + b] = v;
   }
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)B * npL; e += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(e / npL), c = (int)(e % npL);
-    tgt[e] = c < nL ? targets[(size_t)ib[b] * nL + c] : 0.f;
+    const int code = ib[b], mir = code & 3;
+    const int neg = (((mir & 1) ? 0x0E : 0) ^ ((mir & 2) ? 0x15 : 0)) >> c & 1;
+    const float t = c < nL ? targets[(size_t)(code >> 2) * nL + c] : 0.f;
+    tgt[e] = neg ? -t : t;
   }
 }
 
@@ -599,9 +610,12 @@ extern "C" xslam_status xslam_mlp_pair_targets(const double* poses, int n_poses,
 
 extern "C" xslam_status xslam_mlp_train(xslam_mlp_t m, const void* feat, int n_feat, const int* pairs,
                                         const float* targets, int n_pairs, int batch, int epochs, float lr,
-                                        unsigned long long seed, float* epoch_loss) {
+                                        unsigned long long seed, int mirror, float* epoch_loss) {
   if (!m || !feat || !pairs || !targets) return mfail(m, XSLAM_EINVAL, "NULL argument");
   if (m->n[0] != 2 * kFeat) return mfail(m, XSLAM_EINVAL, "training from frame pairs needs sizes[0] = 9600");
+  if (mirror != 0 && mirror != 1) return mfail(m, XSLAM_EINVAL, "mirror must be 0 or 1");
+  if (mirror && m->n[m->L] != 6) return mfail(m, XSLAM_EINVAL, "mirroring needs 6 twist outputs");
+  if (n_pairs > (1 << 28)) return mfail(m, XSLAM_EINVAL, "too many pairs");
   if (batch < 64 || batch % 64 || batch > m->max_batch)
     return mfail(m, XSLAM_EINVAL, "batch must be a multiple of 64 up to max_batch");
   if (n_pairs < batch || epochs < 1 || n_feat < 1 || !(lr > 0.f)) return mfail(m, XSLAM_EINVAL, "bad sizes or lr");
@@ -640,11 +654,13 @@ extern "C" xslam_status xslam_mlp_train(xslam_mlp_t m, const void* feat, int n_f
   const int nb = n_pairs / batch;
   uint64_t rs = seed;
   for (int ep = 0; ep < epochs && st == XSLAM_OK; ++ep) {
-    for (int i = 0; i < n_pairs; ++i) perm[i] = i;
+    for (int i = 0; i < n_pairs; ++i) perm[i] = i << 2;
     for (int i = n_pairs - 1; i > 0; --i) {
       const int j = (int)(splitmix64(rs) % (uint64_t)(i + 1));
       std::swap(perm[i], perm[j]);
     }
+    if (mirror)
+      for (int i = 0; i < n_pairs; ++i) perm[i] |= (int)(splitmix64(rs) & 3u);
     e = cudaMemcpyAsync(m->idx, perm.data(), sizeof(int) * (size_t)n_pairs, cudaMemcpyHostToDevice, m->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->ctr + 1, 0, sizeof(int), m->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->loss, 0, sizeof(double), m->s);

@@ -275,7 +275,7 @@ def _inward_ok(eye, R, c, r_lo, r_hi, y_lo, y_hi):
 
 def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 480, dims=256,
               voxel: float = 0.01, noise: bool = True, device="cpu", resident: bool = False,
-              n_prims: int = 12) -> Workload:
+              n_prims: int = 12, stride: int = 1) -> Workload:
     """Room of n_prims (12) random spheres/boxes in the central part of a (dims*voxel)^3 volume walled
     on all sides, seen at 640x480 (f=525, c=(319.5, 239.5)) by a camera that walks a ring around
     them facing inward (translation <= 2 cm, rotation <= 1.5 deg about a random axis per frame; the
@@ -284,7 +284,8 @@ def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 
 
     resident=True keeps the frames on ``device`` as one float32 torch tensor (frames, H, W) and draws
     the noise there from a torch generator seeded with ``seed`` (a different stream of normals than
-    the numpy one, for large batched workloads)."""
+    the numpy one, for large batched workloads). stride > 1 renders every stride-th pose of the walk
+    (frames rendered frames, stride walk steps apart: a faster camera on the same kind of path)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     s = width / 640.0
     intr = Intrinsics(525.0 * s, 525.0 * s, (width - 1) / 2.0, (height - 1) / 2.0, width, height)
@@ -310,7 +311,7 @@ def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 
     if resident:
         gen = torch.Generator(device=device)
         gen.manual_seed(seed)
-    for f in range(frames):
+    for f in range((frames - 1) * stride + 1):
         if f > 0:
             for _ in range(100):
                 step = rng.standard_normal(3)
@@ -324,6 +325,8 @@ def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 
                 if _inward_ok(ne, quat_to_matrix(nq) @ base, c, r_lo, r_hi, y_lo, y_hi):
                     eye, q = ne, nq
                     break
+        if f % stride:
+            continue
         R = quat_to_matrix(q) @ base
         T = np.concatenate([R, eye[:, None]], 1)
         if resident:
@@ -338,6 +341,81 @@ def room_walk(seed: int = 2, frames: int = 300, width: int = 640, height: int = 
             depth.append(add_noise(d, rng, sigma_quad=0.0015) if noise else d.astype(np.float32))
         poses.append(T)
     return Workload(f"room{dims}_{width}x{height}", intr, (dims, dims, dims), voxel, 4 * voxel,
+                    (0.0, 0.0, 0.0), np.array(poses), torch.stack(depth) if resident else np.array(depth), scene,
+                    seed, depth_min=0.3, depth_max=4.0, bilateral=True)
+
+
+def room_smooth(seed: int = 3, frames: int = 1000, width: int = 640, height: int = 480, dims=512,
+                voxel: float = 0.005, rho: float = 0.9, step_m: float = 0.02, step_deg: float = 1.5,
+                jerk_every: int = 25, noise: bool = True, device="cpu", resident: bool = True,
+                n_prims: int = 12) -> Workload:
+    """The room of room_walk (same geometry, intrinsics, noise and ring constraints) seen by a camera
+    with inertia: each frame's translation step and rotation vector are rho times the previous ones
+    plus sqrt(1 - rho^2) times a fresh draw of the random walk's step (translation uniform in a ball of
+    radius step_m, rotation up to step_deg about a random axis); every jerk_every frames, and whenever
+    a step would leave the ring constraints, the motion is drawn afresh (an abrupt change)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s = width / 640.0
+    intr = Intrinsics(525.0 * s, 525.0 * s, (width - 1) / 2.0, (height - 1) / 2.0, width, height)
+    side = dims * voxel
+    k = side / 2.56
+    margin = 0.06 * k
+    c = side / 2.0
+    r_lo, r_hi = 0.95 * k, 1.12 * k
+    y_lo, y_hi = 0.85 * k, 1.7 * k
+    scene = _room_scene(rng, side, margin, n_prims, 0.5 * k)
+    base = look_at(np.zeros(3), (0.0, 0.0, 1.0))[:, :3]
+    while True:
+        ang = rng.uniform(0, 2 * math.pi)
+        rad = rng.uniform(r_lo + 0.03 * k, r_hi - 0.03 * k)
+        eye = np.array([c + rad * math.cos(ang), rng.uniform(y_lo + 0.05 * k, y_hi - 0.05 * k), c + rad * math.sin(ang)])
+        yaw = math.atan2(c - eye[0], c - eye[2]) + rng.uniform(-0.3, 0.3)
+        q = axis_angle_quat((0.0, 1.0, 0.0), yaw)
+        if _inward_ok(eye, quat_to_matrix(q) @ base, c, r_lo, r_hi, y_lo, y_hi):
+            break
+
+    def draw():
+        st = rng.standard_normal(3)
+        st *= rng.uniform() ** (1 / 3) * step_m / np.linalg.norm(st)
+        ax = rng.standard_normal(3)
+        return st, ax / np.linalg.norm(ax) * math.radians(step_deg) * rng.uniform()
+
+    def qmul(a, b):
+        return np.array([a[0] * b[0] - a[1:] @ b[1:], *(a[0] * b[1:] + b[0] * a[1:] + np.cross(a[1:], b[1:]))])
+
+    v, w = draw()
+    poses, depth = [], []
+    if resident:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(seed)
+    a = math.sqrt(1.0 - rho * rho)
+    for f in range(frames):
+        if f > 0:
+            fresh = f % jerk_every == 0
+            for tries in range(100):
+                dv, dw = draw()
+                nv, nw = (dv, dw) if fresh or tries > 0 else (rho * v + a * dv, rho * w + a * dw)
+                ang = float(np.linalg.norm(nw))
+                dq = axis_angle_quat(nw / ang if ang > 0 else (1.0, 0.0, 0.0), ang)
+                nq = qmul(dq, q)
+                ne = eye + nv
+                if _inward_ok(ne, quat_to_matrix(nq) @ base, c, r_lo, r_hi, y_lo, y_hi):
+                    eye, q, v, w = ne, nq, nv, nw
+                    break
+        R = quat_to_matrix(q) @ base
+        T = np.concatenate([R, eye[:, None]], 1)
+        if resident:
+            d = render_depth_t(scene, intr, T, device)
+            if noise:
+                z = torch.randn(d.shape, generator=gen, dtype=torch.float64, device=d.device)
+                nd = d + z * (0.0015 * d * d)
+                d = torch.where((d > 0) & (nd > 0), nd, torch.zeros_like(nd))
+            depth.append(d.to(torch.float32))
+        else:
+            d = render_depth(scene, intr, T, device)
+            depth.append(add_noise(d, rng, sigma_quad=0.0015) if noise else d.astype(np.float32))
+        poses.append(T)
+    return Workload(f"roomsmooth{dims}_{width}x{height}", intr, (dims, dims, dims), voxel, 4 * voxel,
                     (0.0, 0.0, 0.0), np.array(poses), torch.stack(depth) if resident else np.array(depth), scene,
                     seed, depth_min=0.3, depth_max=4.0, bilateral=True)
 

@@ -118,7 +118,7 @@ SYMBOLS = [
                                               _c_float_p]),
     ("xslam_mlp_train", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
-                                       ctypes.c_ulonglong, _c_float_p]),
+                                       ctypes.c_ulonglong, ctypes.c_int, _c_float_p]),
     ("xslam_gemm_bf16", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("xslam_set_proposal", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_float_p, ctypes.c_int]),
@@ -646,11 +646,11 @@ class Mlp:
                                                 g.ctypes.data_as(_c_float_p), ctypes.byref(loss)))
         return loss.value, self.unflatten(g)
 
-    def train(self, feat, pairs, targets, epochs, batch=256, lr=1e-3, seed=1):
+    def train(self, feat, pairs, targets, epochs, batch=256, lr=1e-3, seed=1, mirror=False):
         """Adam over the pairs (CUDA int32 (P, 2)) of feature rows feat (CUDA bf16 (n, 4800)) with CUDA
-        float32 targets (P, n_L); returns the per-epoch mean loss."""
+        float32 targets (P, n_L), optionally with random reflections; returns the per-epoch mean loss."""
         losses = np.zeros(epochs, np.float32)
         self._check(self.lib.xslam_mlp_train(self.m, _bf16(feat), int(feat.shape[0]), _dev(pairs, "int32"),
                                              _dev(targets), int(pairs.shape[0]), int(batch), int(epochs), float(lr),
-                                             int(seed), losses.ctypes.data_as(_c_float_p)))
+                                             int(seed), int(bool(mirror)), losses.ctypes.data_as(_c_float_p)))
         return losses

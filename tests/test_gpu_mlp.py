@@ -175,3 +175,52 @@ def test_pair_targets_match_oracle():
         np.testing.assert_allclose(g, ref, rtol=1e-6, atol=1e-6)
     with pytest.raises(xslam.XSlamError):
         xslam.pair_targets(poses, np.array([[0, 8]], np.int32), scale)
+
+
+def _mirror_rows(x, g):
+    """Both 80 x 60 halves of the rows x (n, 9600) reflected left-right (g & 1) and/or top-bottom (g & 2)."""
+    v = x.reshape(-1, 2, 60, 80)
+    if g & 1:
+        v = v[..., ::-1]
+    if g & 2:
+        v = v[..., ::-1, :]
+    return np.ascontiguousarray(v).reshape(x.shape)
+
+
+# a reflection maps the motion twist (phi, rho) to (-M phi, M rho)
+_SIGN = {0: np.ones(6), 1: np.array([1, -1, -1, -1, 1, 1.0]), 2: np.array([-1, 1, -1, 1, -1, 1.0])}
+_SIGN[3] = _SIGN[1] * _SIGN[2]
+
+
+def test_mirror_augmentation_is_consistent():
+    """With more distinct inputs than a linear map can absorb (4800 feature rows: each half of the
+    input spans its whole 4800-dimensional space), a map that commutes with the reflections
+    (A P_g = S_g A) stays learnable under mirroring and a generic one does not; without mirroring
+    both are. A wrong reflection of the features or of the target signs breaks the first."""
+    rng = np.random.default_rng(51)
+    n_feat, P = 4800, 16384
+    feat = OM.bf16(rng.uniform(-1, 1, (n_feat, 4800)))  # zero mean: a well-conditioned least-squares fit
+    pairs = rng.integers(0, n_feat, (P, 2)).astype(np.int32)
+    A0 = rng.normal(0, 1, (6, 9600)) / np.sqrt(9600)
+    # A = 1/4 sum_g S_g A0 P_g, with (A0 P_g) x = A0 (P_g x)
+    A = sum(_SIGN[g][:, None] * _mirror_rows(A0, g) for g in range(4)) / 4
+    x4 = np.concatenate([feat[pairs[:4, 0]], feat[pairs[:4, 1]]], 1)
+    for g in range(4):
+        np.testing.assert_allclose(_mirror_rows(x4, g) @ A.T, (x4 @ A.T) * _SIGN[g], atol=1e-12)
+    dev_feat = _bf16_dev(feat)
+    dev_pairs = torch.tensor(pairs, device="cuda")
+    final = {}
+    for name, M, mirror in (("equivariant", A, True), ("generic", A0, True), ("generic_plain", A0, False)):
+        t = np.concatenate([feat[pairs[:, 0]], feat[pairs[:, 1]]], 1) @ M.T
+        m = xslam.Mlp((9600, 6), max_batch=256)
+        m.set_params([(np.zeros((6, 9600)), np.zeros(6))])
+        # Adam moves every weight by about lr per step, the output by about lr sum_i |x_i| = 4800 lr:
+        # lr = 1e-5 keeps that jitter near a tenth of the targets' spread (0.58)
+        losses = m.train(dev_feat, dev_pairs, torch.tensor(t.astype(np.float32), device="cuda"), epochs=60,
+                         batch=256, lr=1e-5, seed=3, mirror=mirror)
+        final[name] = (float(losses[0]), float(losses[-1]))
+        m.close()
+    print(final)
+    assert final["equivariant"][1] < 0.15 * final["equivariant"][0], final
+    assert final["generic_plain"][1] < 0.2 * final["generic_plain"][0], final
+    assert final["generic"][1] > 0.5 * final["generic"][0], final

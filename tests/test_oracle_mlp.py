@@ -164,3 +164,15 @@ def test_pair_target_is_motion_in_first_camera():
     Tj = se3.compose(Ti, se3.se3_exp(xi))
     np.testing.assert_allclose(mlp.pair_target(Ti, Tj), xi, rtol=1e-9, atol=1e-13)
     assert math.isclose(np.abs(mlp.pair_target(Ti, Ti)).max(), 0.0, abs_tol=1e-14)
+
+
+def test_reflected_motion_twist():
+    """The twist of a motion seen in a mirror: T -> M T M with M = diag(-1, 1, 1) or diag(1, -1, 1)
+    maps (phi, rho) to (-M phi, M rho)."""
+    rng = np.random.default_rng(10)
+    for M, sign in ((np.diag([-1.0, 1, 1]), [1, -1, -1, -1, 1, 1]), (np.diag([1.0, -1, 1]), [-1, 1, -1, 1, -1, 1])):
+        Ti = se3.se3_exp(rng.normal(0, 0.5, 6))
+        Tj = se3.compose(Ti, se3.se3_exp(rng.normal(0, 0.05, 6)))
+        refl = lambda T: np.concatenate([M @ T[:, :3] @ M, (M @ T[:, 3])[:, None]], 1)  # noqa: E731
+        np.testing.assert_allclose(mlp.pair_target(refl(Ti), refl(Tj)), np.array(sign) * mlp.pair_target(Ti, Tj),
+                                   atol=1e-12)
