@@ -169,3 +169,27 @@ def pose_errors(poses, truth):
     R = np.einsum("nij,nkj->nik", poses[:, :, :3], truth[:, :, :3])
     c = np.clip((np.trace(R, axis1=1, axis2=2) - 1) / 2, -1, 1)
     return dt, np.degrees(np.arccos(c))
+
+
+def main(argv=None):
+    """Build a training set, train, and print one JSON line (the small case the GEMM profiles use)."""
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="train the learned pose proposal")
+    ap.add_argument("--rooms", type=int, default=8)
+    ap.add_argument("--frames", type=int, default=16)
+    ap.add_argument("--epochs", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=256)
+    a = ap.parse_args(argv)
+    xslam.load()
+    ds = make_dataset(n_traj=a.rooms, frames=a.frames, reverse=True, seed=20000)
+    m, losses, ms = train(ds, epochs=a.epochs, batch=a.batch, mirror=True)
+    flops = train_flops(int(ds.pairs.shape[0]), a.batch, a.epochs)
+    print(json.dumps(dict(pairs=int(ds.pairs.shape[0]), epochs=a.epochs, batch=a.batch, train_ms=round(ms, 2),
+                          tflops=round(flops / (ms * 1e9), 2), loss=[round(float(v), 4) for v in losses])))
+    m.close()
+
+
+if __name__ == "__main__":
+    main()
