@@ -124,9 +124,10 @@ xslam_status xslam_set_proposal(xslam_t h, xslam_mlp_t m, const float* scale, in
 
 /*
  * Device counters of h since create or the last reset through this call (synchronises):
- * out[0] ICP iterations computed (iterations skipped after a failure or after their level converged,
- * cfg.icp_stop, are not counted), out[1] frames whose proposal was judged, out[2] proposals accepted.
- * reset = 1 zeroes the three counters after reading.
+ * out[0] Gauss-Newton ICP iterations computed, counted when a stop tolerance is set (cfg.icp_stop > 0;
+ * iterations skipped after a failure or after their level converged are not counted; without a
+ * tolerance every frame runs the fixed counts and this counter stays 0), out[1] frames whose proposal
+ * was judged, out[2] proposals accepted. reset = 1 zeroes the three counters after reading.
  */
 xslam_status xslam_counters(xslam_t h, unsigned long long* out, int reset);
 

@@ -93,8 +93,9 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   xslam_t h = nullptr;
   if (!out) return fail(h, XSLAM_EINVAL, "out is NULL");
   *out = nullptr;
-  if (nx < 2 || ny < 2 || nz < 2 || (size_t)nx * ny * nz >= ((size_t)1 << 31))
-    return fail(h, XSLAM_EINVAL, "volume dimensions must be >= 2 with fewer than 2^31 voxels");
+  if (nx < 2 || ny < 2 || nz < 2 ||
+      (size_t)((nx + 7) / 8) * ((ny + 7) / 8) * ((nz + 7) / 8) * 512 >= ((size_t)1 << 31))
+    return fail(h, XSLAM_EINVAL, "volume dimensions must be >= 2 with fewer than 2^31 voxels in whole 8^3 bricks");
   if (!(voxel_m > 0.f) || !(trunc_m > 0.f)) return fail(h, XSLAM_EINVAL, "voxel and truncation must be > 0");
   if (!origin_m || !K) return fail(h, XSLAM_EINVAL, "origin and intrinsics are required");
   if (max_lanes < 0 || max_lanes > kMaxLanes - 1) return fail(h, XSLAM_EINVAL, "max_lanes must be in 0..15");
@@ -126,6 +127,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   Params& p = h->p;
   memset(&p, 0, sizeof(p));
   p.nx = nx; p.ny = ny; p.nz = nz;
+  p.nbx = (nx + kBrick - 1) / kBrick; p.nby = (ny + kBrick - 1) / kBrick; p.nbz = (nz + kBrick - 1) / kBrick;
   p.voxel = voxel_m; p.mu = trunc_m;
   p.ox = origin_m[0]; p.oy = origin_m[1]; p.oz = origin_m[2];
   p.w_max = c.w_max;
@@ -160,7 +162,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
       cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess)
     return cleanup(XSLAM_ECUDA, "stream/event creation failed");
 
-  const size_t n = (size_t)nx * ny * nz, hw = (size_t)p.W * p.H;
+  const size_t n = vox_plane(p), hw = (size_t)p.W * p.H;
   const int Lmax = 1 + max_lanes;
   Buffers& b = h->b;
   memset(&b, 0, sizeof(b));
@@ -254,24 +256,33 @@ extern "C" xslam_status xslam_destroy(xslam_t h) {
 __global__ void k_fill(float* a, size_t n, float v) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] = v;
 }
-// lane-0 read-out: unobserved voxels read F = 1 (the sentinel is internal)
-__global__ void k_read_re(const float* a, float* o, size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    o[i] = a[i] > 1.f ? 1.f : a[i];
+// plane read-out into the linear layout x + nx (y + ny z): mode 0 = Re F (unobserved voxels read 1, the
+// sentinel is internal), 1 = scaled by s (imaginary lanes), 2 = as stored (weights)
+__global__ void k_read_plane(Params p, const float* a, float* o, int mode, double s) {
+  const size_t n = vox_count(p);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % p.nx), y = (int)((i / p.nx) % p.ny), z = (int)(i / ((size_t)p.nx * p.ny));
+    const float v = a[vox_index(p, x, y, z)];
+    o[i] = mode == 0 ? (v > 1.f ? 1.f : v) : (mode == 1 ? (float)((double)v * s) : v);
+  }
+}
+// plane write from the linear layout
+__global__ void k_write_plane(Params p, const float* in, float* a) {
+  const size_t n = vox_count(p);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % p.nx), y = (int)((i / p.nx) % p.ny), z = (int)(i / ((size_t)p.nx * p.ny));
+    a[vox_index(p, x, y, z)] = in[i];
+  }
 }
 // after W is written: voxels with W = 0 are unobserved
 __global__ void k_mark_unobserved(float* F, const float* W, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     if (!(W[i] > 0.f)) F[i] = kUnobserved;
 }
-__global__ void k_scale(const float* a, float* o, size_t n, double s) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    o[i] = (float)((double)a[i] * s);
-}
 
 extern "C" xslam_status xslam_reset(xslam_t h) {
   if (!h) return XSLAM_EINVAL;
-  const size_t n = vox_count(h->p);
+  const size_t n = vox_plane(h->p);
   const int Lmax = 1 + h->max_lanes;
   const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
   k_fill<<<g, 256, 0, h->s>>>(h->b.F, n, kUnobserved);
@@ -622,20 +633,17 @@ extern "C" xslam_status xslam_raycast(xslam_t h, const double* T, float* depth, 
 extern "C" xslam_status xslam_read_tsdf(xslam_t h, int lane, float* out) {
   if (!h || !out) return fail(h, XSLAM_EINVAL, "NULL argument");
   if (lane < -1 || lane > h->K) return fail(h, XSLAM_EINVAL, "lane must be -1..K");
-  const size_t n = vox_count(h->p);
+  const size_t n = vox_count(h->p), np = vox_plane(h->p);
   xslam_status st = enter(h);
   if (st != XSLAM_OK) return st;
-  if (lane == -1) {
-    CU(cudaMemcpyAsync(out, h->b.Wt, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->s));
-  } else if (lane == 0) {
-    const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
-    k_read_re<<<g, 256, 0, h->s>>>(h->b.F, out, n);
-    CU(cudaGetLastError());
-  } else {
-    const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
-    k_scale<<<g, 256, 0, h->s>>>(h->b.F + (size_t)lane * n, out, n, 1.0 / h->p.h[lane]);
-    CU(cudaGetLastError());
-  }
+  const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
+  if (lane == -1)
+    k_read_plane<<<g, 256, 0, h->s>>>(h->p, h->b.Wt, out, 2, 1.0);
+  else if (lane == 0)
+    k_read_plane<<<g, 256, 0, h->s>>>(h->p, h->b.F, out, 0, 1.0);
+  else
+    k_read_plane<<<g, 256, 0, h->s>>>(h->p, h->b.F + (size_t)lane * np, out, 1, 1.0 / h->p.h[lane]);
+  CU(cudaGetLastError());
   st = leave(h);
   CU(cudaStreamSynchronize(h->s));
   return st;
@@ -644,14 +652,16 @@ extern "C" xslam_status xslam_read_tsdf(xslam_t h, int lane, float* out) {
 extern "C" xslam_status xslam_write_tsdf(xslam_t h, int lane, const float* in) {
   if (!h || !in) return fail(h, XSLAM_EINVAL, "NULL argument");
   if (lane < -1 || lane > h->K) return fail(h, XSLAM_EINVAL, "lane must be -1..K");
-  const size_t n = vox_count(h->p);
+  const size_t n = vox_count(h->p), np = vox_plane(h->p);
   xslam_status st = enter(h);
   if (st != XSLAM_OK) return st;
-  float* dst = lane == -1 ? h->b.Wt : h->b.F + (size_t)lane * n;
-  CU(cudaMemcpyAsync(dst, in, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->s));
+  float* dst = lane == -1 ? h->b.Wt : h->b.F + (size_t)lane * np;
+  const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
+  k_write_plane<<<g, 256, 0, h->s>>>(h->p, in, dst);
+  CU(cudaGetLastError());
   if (lane == -1) {
-    const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
-    k_mark_unobserved<<<g, 256, 0, h->s>>>(h->b.F, h->b.Wt, n);
+    const unsigned gp = (unsigned)std::min<size_t>((np + 255) / 256, (size_t)h->nsm * 32);
+    k_mark_unobserved<<<gp, 256, 0, h->s>>>(h->b.F, h->b.Wt, np);
     CU(cudaGetLastError());
   }
 

@@ -8,28 +8,28 @@
 // so culled voxels cost no volume traffic. Imaginary lanes follow by the tangent rule through the
 // same arithmetic (pose lanes through p_c and x, TRUNC lanes through mu, DEPTH lanes through L).
 //
-// The volume is cut into 8 x 8 x 8 tiles. A first kernel lists the tiles the frame can touch (a tile
-// whose box lies entirely behind the camera or beyond one image edge cannot: exact, as the projection
-// of a convex set in front of the camera is the hull of its corners' projections); a fixed grid then
-// walks the list, a thread per voxel column of 8 along z (small tiles: at 640x480 in a 256^3 room an
-// 8^3 tile list holds about twice the updated voxels, a 32 x 8 x 8 one nearly four times). The update kernel is instantiated for each
-// lane count, so every lane of a voxel is loaded before any is stored (one memory round trip per
-// voxel rather than one per lane).
+// The volume is cut into 8 x 8 x 8 tiles, the bricks of the TSDF layout. A first kernel lists the
+// tiles the frame can touch (a tile whose box lies entirely behind the camera or beyond one image edge
+// cannot: exact, as the projection of a convex set in front of the camera is the hull of its corners'
+// projections); a fixed grid then walks the list, a block per tile and a thread per voxel, so each
+// tile is 2 KB of every plane read and written in full lines (small tiles: at 640x480 in a 256^3 room
+// an 8^3 tile list holds about twice the updated voxels, a 32 x 8 x 8 one nearly four times). The
+// update kernel is instantiated for each lane count, so every lane of a voxel is loaded before any is
+// stored (one memory round trip per voxel rather than one per lane).
 #include <algorithm>
 
 #include "internal.cuh"
 
 namespace xslam {
 
-constexpr int kBX = 8, kBY = 8, kBZ = 8;  // tile of voxels
-constexpr int kTPB = 4;                   // tiles per block iteration: 4 x 64 threads
+constexpr int kBX = 8, kBY = 8, kBZ = 8;  // tile of voxels: one brick of the TSDF layout
+constexpr int kFuseThreads = kBX * kBY * kBZ;  // a thread per voxel of a tile
 
 // Update voxel (i, j, k) if the frame observes it; returns whether it did. NL = 1 + K lanes.
 template <int NL>
 __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restrict__ D, const float (*sT)[12],
                                            float* __restrict__ F, float* __restrict__ Wt, int i, int j, int k,
-                                           size_t n) {
-  const size_t v = (size_t)i + (size_t)p.nx * ((size_t)j + (size_t)p.ny * k);
+                                           size_t n, size_t v) {
   const float* T = sT[0];
   const float dx = p.ox + (i + 0.5f) * p.voxel - T[3];
   const float dy = p.oy + (j + 0.5f) * p.voxel - T[7];
@@ -138,11 +138,12 @@ __global__ void __launch_bounds__(256) k_fuse_tiles(Params p, const double* __re
   }
 }
 
-// Fixed grid over the tile list; a block takes 4 tiles at a time, a thread per voxel column of a tile
-// (a warp covers 8 x 4 columns), each thread walking the tile's 8 voxels along z. The last block to
-// finish clears the list counters for the next launch.
+// Fixed grid over the tile list; a block takes one tile at a time, a thread per voxel: thread t of the
+// block is the brick's voxel t (x = t mod 8, y = t / 8 mod 8, z = t / 64), so a warp reads and writes
+// 128 consecutive bytes of every plane. The last block to finish clears the list counters for the next
+// launch.
 template <int NL>
-__global__ void __launch_bounds__(kBX * kBY * kTPB) k_integrate(Params p, const float* __restrict__ D,
+__global__ void __launch_bounds__(kFuseThreads) k_integrate(Params p, const float* __restrict__ D,
                                                         const double* __restrict__ pose, float* __restrict__ F,
                                                         float* __restrict__ Wt, unsigned long long* __restrict__ stats,
                                                         const int* __restrict__ tiles, unsigned* __restrict__ ctr) {
@@ -154,20 +155,14 @@ __global__ void __launch_bounds__(kBX * kBY * kTPB) k_integrate(Params p, const 
   __syncthreads();
   const unsigned count = ctr[0];
   const int ntx = (p.nx + kBX - 1) / kBX, nty = (p.ny + kBY - 1) / kBY;
-  const size_t n = vox_count(p);
-  const int sub = tid / (kBX * kBY), cx = tid % kBX, cy = (tid / kBX) % kBY;
+  const size_t n = vox_plane(p);
+  const int cx = tid & 7, cy = (tid >> 3) & 7, cz = tid >> 6;
   int cnt = 0;
-  for (unsigned q = blockIdx.x * kTPB + sub; q < count; q += gridDim.x * kTPB) {
+  for (unsigned q = blockIdx.x; q < count; q += gridDim.x) {
     const int t = tiles[q];
-    const int i = (t % ntx) * kBX + cx, j = ((t / ntx) % nty) * kBY + cy;
-    const int k0 = (t / (ntx * nty)) * kBZ;
-    if (i < p.nx && j < p.ny) {
-      for (int dk = 0; dk < kBZ; ++dk) {
-        const int k = k0 + dk;
-        if (k >= p.nz) break;
-        cnt += fuse_voxel<NL>(p, D, sT, F, Wt, i, j, k, n);
-      }
-    }
+    const int i = (t % ntx) * kBX + cx, j = ((t / ntx) % nty) * kBY + cy, k = (t / (ntx * nty)) * kBZ + cz;
+    // the tile is brick t, whose voxel tid sits at t 512 + tid
+    if (i < p.nx && j < p.ny && k < p.nz) cnt += fuse_voxel<NL>(p, D, sT, F, Wt, i, j, k, n, ((size_t)t << 9) + tid);
   }
   // updated-voxel count: warp sums, one atomic per warp
 #pragma unroll
@@ -187,7 +182,7 @@ __global__ void __launch_bounds__(kBX * kBY * kTPB) k_integrate(Params p, const 
 
 template <int NL>
 static cudaError_t launch_integrate_nl(const Params& p, const Buffers& b, int grid, cudaStream_t s) {
-  return launch_pdl(k_integrate<NL>, dim3(grid), dim3(kBX * kBY * kTPB), 0, s, p, b.pyr[0], b.pose, b.F, b.Wt, b.stats,
+  return launch_pdl(k_integrate<NL>, dim3(grid), dim3(kFuseThreads), 0, s, p, b.pyr[0], b.pose, b.F, b.Wt, b.stats,
                     b.tiles, b.tile_ctr);
 }
 
@@ -206,7 +201,7 @@ cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s) 
   cudaError_t e = launch_pdl(k_fuse_tiles, dim3(std::min((nt + 255) / 256, 4 * sms)), dim3(256), 0, s, p, b.pose,
                              b.tiles, b.tile_ctr);
   if (e != cudaSuccess) return e;
-  const int grid = std::max(1, std::min((nt + kTPB - 1) / kTPB, 4 * sms));
+  const int grid = std::max(1, std::min(nt, 4 * sms));
   switch (p.L) {
     case 1: return launch_integrate_nl<1>(p, b, grid, s);
     case 2: return launch_integrate_nl<2>(p, b, grid, s);

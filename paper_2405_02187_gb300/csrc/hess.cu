@@ -31,16 +31,16 @@ __device__ __forceinline__ bool load_cell(const Params& p, const float* __restri
   i = (int)gx;
   j = (int)gy;
   k = (int)gz;
-  const unsigned sy = (unsigned)p.nx, sz = (unsigned)p.nx * (unsigned)p.ny;
-  const unsigned b = (unsigned)i + sy * (unsigned)j + sz * (unsigned)k;
+  const CellAddr a = cell_addr(p, i, j, k);
+  const unsigned b = a.b, sx = a.dx, sy = a.dy, sz = a.dz;
   c[0] = __ldg(F + b);
-  c[1] = __ldg(F + b + 1);
+  c[1] = __ldg(F + b + sx);
   c[2] = __ldg(F + b + sy);
-  c[3] = __ldg(F + b + 1 + sy);
+  c[3] = __ldg(F + b + sx + sy);
   c[4] = __ldg(F + b + sz);
-  c[5] = __ldg(F + b + 1 + sz);
+  c[5] = __ldg(F + b + sx + sz);
   c[6] = __ldg(F + b + sy + sz);
-  c[7] = __ldg(F + b + 1 + sy + sz);
+  c[7] = __ldg(F + b + sx + sy + sz);
   float mx = c[0];
 #pragma unroll
   for (int q = 1; q < 8; ++q) mx = fmaxf(mx, c[q]);

@@ -109,6 +109,9 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// kStop: the stop tolerance p.icp_stop is in use (and the iteration counter): a launch after its level
+// converged returns at once. Without it the kernel is the fixed-count iteration of the method.
+template <bool kStop>
 __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int flags, int reps) {
   pdl_enter();
   const int L = p.L;
@@ -134,14 +137,14 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   if (threadIdx.x == 0) {
     s_skip = b.status[0];
     // status[3]: the level converged (a step below p.icp_stop); only its first iteration ignores it
-    s_conv = (flags & (kIcpFirst | kIcpNoUpdate)) ? 0 : b.status[3];
+    if (kStop) s_conv = (flags & (kIcpFirst | kIcpNoUpdate)) ? 0 : b.status[3];
   }
   for (int i = threadIdx.x; i < L * 12; i += blockDim.x) {
     sT[i / 12][i % 12] = (float)b.pose[i];
     sP[i / 12][i % 12] = (float)b.pose_prev[i];
   }
   __syncthreads();
-  if ((s_skip || s_conv) && !(flags & kIcpNoUpdate)) {
+  if (kStop && (s_skip || s_conv) && !(flags & kIcpNoUpdate)) {
     // nothing to compute after a failure or after the level converged; the frame's last iteration
     // still closes the frame: fall back to T_{k-1} on a failure and count it
     if ((flags & kIcpLast) && blockIdx.x == 0) {
@@ -548,14 +551,18 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   }
   __syncthreads();
   if (go && t < 12 * L) b.pose[t] = tn;
-  if (threadIdx.x == 0) {
-    if (s_fail) b.status[0] = 1;
-    b.status[2] = s_ncorr;
-    double x2 = 0.0;
+  if (kStop) {
+    if (threadIdx.x == 0) {
+      if (s_fail) b.status[0] = 1;
+      b.status[2] = s_ncorr;
+      double x2 = 0.0;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) x2 += sx[0][k] * sx[0][k];
-    b.status[3] = (go && x2 < (double)p.icp_stop * (double)p.icp_stop) ? 1 : 0;
-    if (b.stats) b.stats[kStatIcpIters] += 1;
+      for (int k = 0; k < 6; ++k) x2 += sx[0][k] * sx[0][k];
+      b.status[3] = (go && x2 < (double)p.icp_stop * (double)p.icp_stop) ? 1 : 0;
+      if (b.stats) b.stats[kStatIcpIters] += 1;
+    }
+  } else if (threadIdx.x == 0 && s_fail && !s_skip) {
+    b.status[0] = 1;
   }
   if (flags & kIcpLast) {
     __syncthreads();
@@ -573,7 +580,9 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
 static size_t icp_rec_bytes(int reps, int L) { return sizeof(float) * (size_t)reps * L * kRec * 32; }
 
 cudaError_t icp_configure() {
-  return cudaFuncSetAttribute(k_icp, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_icp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_icp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  return e;
 }
 
 int icp_reps(int L) {
@@ -607,7 +616,11 @@ cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int flags, 
   lv.cy = p.cy / lv.s;
   int reps = icp_reps(p.L);
   const int threads = 32 * p.L * reps;
-  const cudaError_t e = launch_pdl(k_icp, dim3(nblk), dim3(threads), icp_rec_bytes(reps, p.L), s, p, b, lv, flags, reps);
+  const cudaError_t e = p.icp_stop > 0.f
+                            ? launch_pdl(k_icp<true>, dim3(nblk), dim3(threads), icp_rec_bytes(reps, p.L), s, p, b, lv,
+                                         flags, reps)
+                            : launch_pdl(k_icp<false>, dim3(nblk), dim3(threads), icp_rec_bytes(reps, p.L), s, p, b, lv,
+                                         flags, reps);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -23,8 +23,9 @@ constexpr float kCellBias = 0.015625f;  // 2^-6 pixel: ICP bilinear-cell tie bre
 
 // Everything a kernel needs besides buffers; passed by value.
 struct Params {
-  // volume
+  // volume: nx x ny x nz voxels stored in nbx x nby x nbz bricks of 8 x 8 x 8 (vox_index)
   int nx, ny, nz;
+  int nbx, nby, nbz;
   float voxel, mu, ox, oy, oz;
   float w_max;              // <= 0: no cap
   // camera (level 0)
@@ -47,8 +48,8 @@ struct Params {
 
 // Device buffers owned by a handle.
 struct Buffers {
-  float* F;         // L planes of N: lane 0 = Re F (kUnobserved where W = 0), lane j = Im F (raw)
-  float* Wt;        // N
+  float* F;         // L planes of vox_plane floats: lane 0 = Re F (kUnobserved where W = 0), lane j = Im F (raw)
+  float* Wt;        // one plane
   float* depth_in;  // H*W raw input
   float* gated;     // H*W range-gated input (bilateral filter source)
   float* pyr[3];    // range-gated level 0 and its two coarser levels
@@ -102,6 +103,31 @@ cudaError_t launch_gemm_bf16(const void* A, const void* B, int M, int N, int K, 
 
 __host__ __device__ inline size_t vox_count(const Params& p) {
   return (size_t)p.nx * p.ny * p.nz;
+}
+
+// TSDF layout in HBM: bricks of 8 x 8 x 8 voxels, 512 consecutive floats each (x fastest, then y, then
+// z inside the brick), bricks in x-fastest order; a plane is padded to whole bricks (padding voxels
+// stay unobserved). A fusion tile is one brick (2 KB of one plane, read and written in full lines) and
+// a ray-cast cell's 8 corners lie in one brick unless it straddles a brick face.
+constexpr int kBrick = 8;
+__host__ __device__ inline size_t vox_plane(const Params& p) { return (size_t)p.nbx * p.nby * p.nbz * 512; }
+
+__host__ __device__ inline unsigned vox_index(const Params& p, int i, int j, int k) {
+  return ((((unsigned)(k >> 3) * (unsigned)p.nby + (unsigned)(j >> 3)) * (unsigned)p.nbx + (unsigned)(i >> 3)) << 9) +
+         ((unsigned)(k & 7) << 6) + ((unsigned)(j & 7) << 3) + (unsigned)(i & 7);
+}
+
+// index of voxel (i, j, k) and the offsets to (i + 1, j, k), (i, j + 1, k) and (i, j, k + 1)
+struct CellAddr {
+  unsigned b, dx, dy, dz;
+};
+__host__ __device__ inline CellAddr cell_addr(const Params& p, int i, int j, int k) {
+  CellAddr c;
+  c.b = vox_index(p, i, j, k);
+  c.dx = (i & 7) != 7 ? 1u : 512u - 7u;
+  c.dy = (j & 7) != 7 ? 8u : (unsigned)p.nbx * 512u - 56u;
+  c.dz = (k & 7) != 7 ? 64u : (unsigned)p.nbx * (unsigned)p.nby * 512u - 448u;
+  return c;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -47,41 +47,52 @@ xslam_status mfail(xslam_mlp_t m, xslam_status st, const std::string& msg) {
 
 int pad64(int n) { return (n + 63) / 64 * 64; }
 
-int grid_for(size_t n, int nsm) {
-  size_t g = (n + 255) / 256;
-  const size_t cap = (size_t)nsm * 8;
-  if (g > cap) g = cap;
-  return g < 1 ? 1 : (int)g;
-}
-
 // ---------------------------------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------------------------------
 
-// sum of the split-K partials, then the epilogue; i = r N + c over the M x N product
-__global__ void __launch_bounds__(256) k_reduce(const float* __restrict__ P, int splits, int M, int N,
-                                                const float* __restrict__ bias, int relu,
-                                                const __nv_bfloat16* __restrict__ mask, float* __restrict__ out32,
-                                                int ld32, int n32, __nv_bfloat16* __restrict__ out16,
-                                                __nv_bfloat16* __restrict__ out16T) {
+// The element-wise kernels work on 32 x 32 tiles with 32 x 8 threads: a row of a tile is read and
+// written with coalesced accesses, and a transposed copy goes through shared memory so that it is
+// written coalesced too.
+
+// sum of the split-K partials (in range order), then the epilogue, over the M x N product: one element
+// per thread (32 x 32 threads per tile), so that every partial load of the tile is in flight at once
+__global__ void __launch_bounds__(1024) k_reduce(const float* __restrict__ P, int splits, int M, int N,
+                                                 const float* __restrict__ bias, int relu,
+                                                 const __nv_bfloat16* __restrict__ mask, float* __restrict__ out32,
+                                                 int ld32, int n32, __nv_bfloat16* __restrict__ out16,
+                                                 __nv_bfloat16* __restrict__ out16T) {
   pdl_enter();
+  __shared__ __nv_bfloat16 tile[32][34];
   const size_t MN = (size_t)M * N;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < MN; i += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(i / N), c = (int)(i % N);
-    float v = 0.f;
-    for (int z = 0; z < splits; ++z) v += P[(size_t)z * MN + i];
-    if (bias) v += bias[c];
-    if (relu) v = fmaxf(v, 0.f);
-    if (mask && !(__bfloat162float(mask[i]) > 0.f)) v = 0.f;
-    if (out32 && c < n32) out32[(size_t)r * ld32 + c] = v;
-    const __nv_bfloat16 q = __float2bfloat16(v);
-    if (out16) out16[i] = q;
-    if (out16T) out16T[(size_t)c * M + r] = q;
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = blockIdx.y * 32 + k;
+    __nv_bfloat16 q = __float2bfloat16(0.f);
+    if (r < M && c < N) {
+      const size_t i = (size_t)r * N + c;
+      float v = 0.f;
+      for (int z = 0; z < splits; ++z) v += P[(size_t)z * MN + i];
+      if (bias) v += bias[c];
+      if (relu) v = fmaxf(v, 0.f);
+      if (mask && !(__bfloat162float(mask[i]) > 0.f)) v = 0.f;
+      if (out32 && c < n32) out32[(size_t)r * ld32 + c] = v;
+      q = __float2bfloat16(v);
+      if (out16) out16[i] = q;
+    }
+    tile[k][threadIdx.x] = q;
+  }
+  if (!out16T) return;
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int rt = blockIdx.x * 32 + k, ct = blockIdx.y * 32 + threadIdx.x;  // row of the transpose = column
+    if (rt < N && ct < M) out16T[(size_t)rt * M + ct] = tile[threadIdx.x][k];
   }
 }
 
 // dz_L = (y - t) / B on the first nL columns (0 on the padding), its BF16 copy and transpose, and the
-// batch loss sum |y - t|^2 / (2B) added to *loss; advances the Adam step and the batch index
+// batch loss sum |y - t|^2 / (2B) added to *loss (atomically: the loss is a report); block 0 advances the
+// Adam step and the batch index
 __global__ void __launch_bounds__(256) k_loss_grad(const float* __restrict__ y, const float* __restrict__ t, int B,
                                                    int np, int nL, float* __restrict__ dz32,
                                                    __nv_bfloat16* __restrict__ dzq, __nv_bfloat16* __restrict__ dzqT,
@@ -89,10 +100,11 @@ __global__ void __launch_bounds__(256) k_loss_grad(const float* __restrict__ y, 
   pdl_enter();
   __shared__ double s_red[8];
   double acc = 0.0;
-  for (int i = threadIdx.x; i < B * np; i += blockDim.x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B * np) {
     const int r = i / np, c = i % np;
     const float d = c < nL ? y[i] - t[i] : 0.f;
-    acc += (double)d * (double)d;
+    acc = (double)d * (double)d;
     const float g = d / (float)B;
     dz32[i] = g;
     const __nv_bfloat16 q = __float2bfloat16(g);
@@ -103,24 +115,31 @@ __global__ void __launch_bounds__(256) k_loss_grad(const float* __restrict__ y, 
   if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += s_red[w];
-    *loss += s / (2.0 * B);
-    if (ctr) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += s_red[w];
+    atomicAdd(loss, sum / (2.0 * B));
+    if (ctr && blockIdx.x == 0) {
       ctr[0] += 1;
       ctr[1] += 1;
     }
   }
 }
 
-// db = column sums of dz [B x N]
+// db = column sums of dz [B x N] (rows y, y + 8, ... per thread, then the 8 partial sums in order)
 __global__ void __launch_bounds__(256) k_colsum(const float* __restrict__ dz, int B, int N, float* __restrict__ out) {
   pdl_enter();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= N) return;
+  __shared__ float part[8][32];
+  const int c = blockIdx.x * 32 + threadIdx.x;
   float s = 0.f;
-  for (int r = 0; r < B; ++r) s += dz[(size_t)r * N + c];
-  out[c] = s;
+  if (c < N)
+    for (int r = threadIdx.y; r < B; r += 8) s += dz[(size_t)r * N + c];
+  part[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < N) {
+    float t = 0.f;
+    for (int k = 0; k < 8; ++k) t += part[k][threadIdx.x];
+    out[c] = t;
+  }
 }
 
 // training batch: rows [f_i, f_j] of the pairs idx[k B .. k B + B) with k = ctr[1], the step's batch
@@ -128,117 +147,158 @@ __global__ void __launch_bounds__(256) k_colsum(const float* __restrict__ dz, in
 // copy and the zero-padded targets. An entry of idx is (pair << 2) | mirror: mirror bit 0 reflects
 // both feature maps left-right (camera x -> -x), bit 1 top-bottom (y -> -y); a reflection M maps the
 // motion twist (phi, rho) to (-M phi, M rho), i.e. negates phi_y, phi_z, rho_x (left-right) or phi_x,
-// phi_z, rho_y (top-bottom)
+// phi_z, rho_y (top-bottom). Tile (blockIdx.y, blockIdx.x) = 32 rows x 32 input columns; the blocks of
+// the first tile column also write the rows' targets.
 __global__ void __launch_bounds__(256) k_gather(const __nv_bfloat16* __restrict__ feat, const int* __restrict__ pairs,
                                                 const float* __restrict__ targets, const int* __restrict__ idx,
                                                 const int* __restrict__ ctr, int B, int nL, int npL, int n_feat,
                                                 __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ XT,
                                                 float* __restrict__ tgt, int* __restrict__ err) {
   pdl_enter();
+  __shared__ __nv_bfloat16 tile[32][34];
   const int* ib = idx + (size_t)ctr[1] * B;
   const int n0 = 2 * kFeat;
-  const size_t total = (size_t)B * n0;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int b = (int)(e / n0), j = (int)(e % n0);
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int second = j >= kFeat;
+  const int jj = j - second * kFeat;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int b = blockIdx.y * 32 + k;
     const int code = ib[b], mir = code & 3;
-    const int second = j >= kFeat;
     const int f = pairs[2 * (code >> 2) + second];
     const bool ok = f >= 0 && f < n_feat;  // a frame index outside the feature table reads zeros
     if (!ok) atomicOr(err, 2);
-    const int jj = j - second * kFeat;
     int r = jj / kFeatW, c = jj % kFeatW;
     if (mir & 1) c = kFeatW - 1 - c;
     if (mir & 2) r = kFeatH - 1 - r;
     const __nv_bfloat16 v = ok ? feat[(size_t)f * kFeat + r * kFeatW + c] : __float2bfloat16(0.f);
-    X[e] = v;
-    XT[(size_t)j * B + b] = v;
+    X[(size_t)b * n0 + j] = v;
+    tile[k][threadIdx.x] = v;
+    if (blockIdx.x == 0)
+      for (int cc = threadIdx.x; cc < npL; cc += 32) {
+        const int neg = (((mir & 1) ? 0x0E : 0) ^ ((mir & 2) ? 0x15 : 0)) >> cc & 1;
+        const float tv = cc < nL ? targets[(size_t)(code >> 2) * nL + cc] : 0.f;
+        tgt[(size_t)b * npL + cc] = neg ? -tv : tv;
+      }
   }
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)B * npL; e += (size_t)gridDim.x * blockDim.x) {
-    const int b = (int)(e / npL), c = (int)(e % npL);
-    const int code = ib[b], mir = code & 3;
-    const int neg = (((mir & 1) ? 0x0E : 0) ^ ((mir & 2) ? 0x15 : 0)) >> c & 1;
-    const float t = c < nL ? targets[(size_t)(code >> 2) * nL + c] : 0.f;
-    tgt[e] = neg ? -t : t;
-  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8)
+    XT[(size_t)(blockIdx.x * 32 + k) * B + blockIdx.y * 32 + threadIdx.x] = tile[threadIdx.x][k];
 }
 
-// an explicit batch: x [B x n0] and targets [B x nL] into the batch buffers
+// an explicit batch: x [B x n0] and targets [B x nL] into the batch buffers (tiles as k_gather)
 __global__ void __launch_bounds__(256) k_load(const __nv_bfloat16* __restrict__ x, const float* __restrict__ targets,
                                               int B, int n0, int nL, int npL, __nv_bfloat16* __restrict__ X,
                                               __nv_bfloat16* __restrict__ XT, float* __restrict__ tgt) {
   pdl_enter();
-  const size_t total = (size_t)B * n0;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int b = (int)(e / n0), j = (int)(e % n0);
-    X[e] = x[e];
-    XT[(size_t)j * B + b] = x[e];
+  __shared__ __nv_bfloat16 tile[32][34];
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int b = blockIdx.y * 32 + k;
+    const __nv_bfloat16 v = x[(size_t)b * n0 + j];
+    X[(size_t)b * n0 + j] = v;
+    tile[k][threadIdx.x] = v;
+    if (blockIdx.x == 0)
+      for (int cc = threadIdx.x; cc < npL; cc += 32) tgt[(size_t)b * npL + cc] = cc < nL ? targets[(size_t)b * nL + cc] : 0.f;
   }
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)B * npL; e += (size_t)gridDim.x * blockDim.x) {
-    const int b = (int)(e / npL), c = (int)(e % npL);
-    tgt[e] = c < nL ? targets[(size_t)b * nL + c] : 0.f;
-  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8)
+    XT[(size_t)(blockIdx.x * 32 + k) * B + blockIdx.y * 32 + threadIdx.x] = tile[threadIdx.x][k];
 }
 
 struct LayerTab {
   int L;
-  unsigned long long offW[kMlpMaxLayers];
+  int ntiles;                            // 32 x 32 weight tiles of all layers
+  int tile_off[kMlpMaxLayers + 1];       // first tile of each layer
+  int bias_off[kMlpMaxLayers + 1];       // first bias of each layer in the biases' concatenation
+  unsigned long long offW[kMlpMaxLayers], offb[kMlpMaxLayers];
   int rows[kMlpMaxLayers], cols[kMlpMaxLayers];
   __nv_bfloat16* Wq[kMlpMaxLayers];
   __nv_bfloat16* WqT[kMlpMaxLayers];
 };
 
-// Adam on the FP32 masters (update = 1; step t = ctr[0]), then the BF16 copies of the weights
+__device__ __forceinline__ float adam_update(float* p, const float* g, float* m1, float* m2, size_t i, float lr,
+                                             float bc1, float bc2, int update) {
+  float w = p[i];
+  if (update) {
+    const float gi = g[i];
+    const float a = 0.9f * m1[i] + 0.1f * gi;
+    const float b = 0.999f * m2[i] + 0.001f * gi * gi;
+    m1[i] = a;
+    m2[i] = b;
+    w -= lr * (a / bc1) / (sqrtf(b / bc2) + 1e-8f);
+    p[i] = w;
+  }
+  return w;
+}
+
+// Adam on the FP32 masters (update = 1; step t = ctr[0]) and the BF16 copies of the weights and their
+// transposes: blocks [0, ntiles) take a 32 x 32 weight tile each, the rest 256 biases each
 __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
-                                              float* __restrict__ m2, size_t n, const int* __restrict__ ctr, float lr,
+                                              float* __restrict__ m2, const int* __restrict__ ctr, float lr,
                                               LayerTab tab, int update) {
   pdl_enter();
+  __shared__ __nv_bfloat16 tile[32][34];
   float bc1 = 1.f, bc2 = 1.f;
   if (update) {
     const float t = (float)ctr[0];
     bc1 = 1.f - powf(0.9f, t);
     bc2 = 1.f - powf(0.999f, t);
   }
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    float w = p[i];
-    if (update) {
-      const float gi = g[i];
-      const float a = 0.9f * m1[i] + 0.1f * gi;
-      const float b = 0.999f * m2[i] + 0.001f * gi * gi;
-      m1[i] = a;
-      m2[i] = b;
-      w -= lr * (a / bc1) / (sqrtf(b / bc2) + 1e-8f);
-      p[i] = w;
+  const int bid = blockIdx.x;
+  if (bid < tab.ntiles) {
+    int l = 0;
+    while (l + 1 < tab.L && bid >= tab.tile_off[l + 1]) ++l;
+    const int rows = tab.rows[l], cols = tab.cols[l];
+    const int local = bid - tab.tile_off[l], tcn = cols / 32;
+    const int r0 = (local / tcn) * 32, c0 = (local % tcn) * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+      const size_t e = (size_t)(r0 + k) * cols + c0 + threadIdx.x;
+      const float w = adam_update(p, g, m1, m2, tab.offW[l] + e, lr, bc1, bc2, update);
+      const __nv_bfloat16 q = __float2bfloat16(w);
+      tab.Wq[l][e] = q;
+      tile[k][threadIdx.x] = q;
     }
-    for (int l = 0; l < tab.L; ++l) {
-      const size_t o = tab.offW[l], sz = (size_t)tab.rows[l] * tab.cols[l];
-      if (i >= o && i < o + sz) {
-        const size_t k = i - o;
-        const int r = (int)(k / tab.cols[l]), c = (int)(k % tab.cols[l]);
-        const __nv_bfloat16 q = __float2bfloat16(w);
-        tab.Wq[l][k] = q;
-        tab.WqT[l][(size_t)c * tab.rows[l] + r] = q;
-      }
-    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8)
+      tab.WqT[l][(size_t)(c0 + k) * rows + r0 + threadIdx.x] = tile[threadIdx.x][k];
+    return;
   }
+  const int j = (bid - tab.ntiles) * 256 + threadIdx.y * 32 + threadIdx.x;
+  if (j >= tab.bias_off[tab.L]) return;
+  int l = 0;
+  while (l + 1 < tab.L && j >= tab.bias_off[l + 1]) ++l;
+  adam_update(p, g, m1, m2, tab.offb[l] + (j - tab.bias_off[l]), lr, bc1, bc2, update);
 }
 
 cudaError_t launch_reduce(const xslam_mlp_s* m, const float* P, int splits, int M, int N, const float* bias, int relu,
                           const __nv_bfloat16* mask, float* out32, int ld32, int n32, __nv_bfloat16* out16,
                           __nv_bfloat16* out16T, cudaStream_t s) {
-  return launch_pdl(k_reduce, dim3(grid_for((size_t)M * N, m->nsm)), dim3(256), 0, s, P, splits, M, N, bias, relu, mask,
+  (void)m;
+  // one row of threads per output row of the tile (a single-row product, the proposal's inference, uses one)
+  const int ty = M >= 32 ? 32 : M;
+  return launch_pdl(k_reduce, dim3((N + 31) / 32, (M + 31) / 32), dim3(32, ty), 0, s, P, splits, M, N, bias, relu, mask,
                     out32, ld32, n32, out16, out16T);
 }
 
 LayerTab layer_tab(const xslam_mlp_s* m) {
   LayerTab t = {};
   t.L = m->L;
+  int nt = 0, nb = 0;
   for (int l = 0; l < m->L; ++l) {
+    t.tile_off[l] = nt;
+    t.bias_off[l] = nb;
     t.offW[l] = m->offW[l];
+    t.offb[l] = m->offb[l];
     t.rows[l] = m->np[l + 1];
     t.cols[l] = m->np[l];
     t.Wq[l] = m->Wq[l];
     t.WqT[l] = m->WqT[l];
+    nt += (m->np[l + 1] / 32) * (m->np[l] / 32);
+    nb += m->np[l + 1];
   }
+  t.tile_off[m->L] = nt;
+  t.bias_off[m->L] = nb;
+  t.ntiles = nt;
   return t;
 }
 
@@ -259,15 +319,20 @@ cudaError_t enqueue_train_forward(xslam_mlp_s* m, int B, cudaStream_t s) {
 // count: the loss kernel advances the Adam step and the batch index (a training step)
 cudaError_t enqueue_backward(xslam_mlp_s* m, int B, bool count, cudaStream_t s) {
   const int npL = m->np[m->L];
-  KCU(launch_pdl(k_loss_grad, dim3(1), dim3(256), 0, s, (const float*)m->y, (const float*)m->tgt, B, npL, m->n[m->L],
-                 m->dz32, m->dzq, m->dzqT, m->loss, count ? m->ctr : nullptr));
+  KCU(launch_pdl(k_loss_grad, dim3((B * npL + 255) / 256), dim3(256), 0, s, (const float*)m->y, (const float*)m->tgt, B,
+                 npL, m->n[m->L], m->dz32, m->dzq, m->dzqT, m->loss, count ? m->ctr : nullptr));
   for (int l = m->L - 1; l >= 0; --l) {
     const int No = m->np[l + 1], Ni = m->np[l];
-    KCU(launch_pdl(k_colsum, dim3((No + 255) / 256), dim3(256), 0, s, (const float*)m->dz32, B, No,
+    KCU(launch_pdl(k_colsum, dim3((No + 31) / 32), dim3(32, 8), 0, s, (const float*)m->dz32, B, No,
                    m->grad + m->offb[l]));
     GemmPlan g = gemm_plan(No, Ni, B, m->nsm);
-    KCU(launch_gemm_bf16(m->dzqT, m->actT[l], No, Ni, B, g, m->ws, m->err, s));
-    KCU(launch_reduce(m, m->ws, g.splits, No, Ni, nullptr, 0, nullptr, m->grad + m->offW[l], Ni, Ni, nullptr, nullptr, s));
+    if (g.splits == 1) {  // the weight gradient [No x Ni] is the GEMM's own output: no reduction pass
+      KCU(launch_gemm_bf16(m->dzqT, m->actT[l], No, Ni, B, g, m->grad + m->offW[l], m->err, s));
+    } else {
+      KCU(launch_gemm_bf16(m->dzqT, m->actT[l], No, Ni, B, g, m->ws, m->err, s));
+      KCU(launch_reduce(m, m->ws, g.splits, No, Ni, nullptr, 0, nullptr, m->grad + m->offW[l], Ni, Ni, nullptr, nullptr,
+                        s));
+    }
     if (l > 0) {
       g = gemm_plan(B, Ni, No, m->nsm);
       KCU(launch_gemm_bf16(m->dzq, m->WqT[l], B, Ni, No, g, m->ws, m->err, s));
@@ -278,8 +343,10 @@ cudaError_t enqueue_backward(xslam_mlp_s* m, int B, bool count, cudaStream_t s) 
 }
 
 cudaError_t enqueue_adam(xslam_mlp_s* m, float lr, int update, cudaStream_t s) {
-  return launch_pdl(k_adam, dim3(grid_for(m->n_master, m->nsm)), dim3(256), 0, s, m->master, (const float*)m->grad,
-                    m->m1, m->m2, m->n_master, (const int*)m->ctr, lr, layer_tab(m), update);
+  const LayerTab t = layer_tab(m);
+  const int blocks = t.ntiles + (t.bias_off[m->L] + 255) / 256;
+  return launch_pdl(k_adam, dim3(blocks), dim3(32, 8), 0, s, m->master, (const float*)m->grad, m->m1, m->m2,
+                    (const int*)m->ctr, lr, t, update);
 }
 
 size_t gemm_ws(int M, int N, int K, int nsm) {
@@ -522,8 +589,8 @@ extern "C" xslam_status xslam_mlp_gradient(xslam_mlp_t m, const void* x, const f
   xslam_status st = enter(m);
   if (st != XSLAM_OK) return st;
   MCU(cudaMemsetAsync(m->loss, 0, sizeof(double), m->s));
-  MCU(launch_pdl(k_load, dim3(grid_for((size_t)B * m->np[0], m->nsm)), dim3(256), 0, m->s, (const __nv_bfloat16*)x,
-                 targets, B, m->np[0], m->n[m->L], m->np[m->L], m->act[0], m->actT[0], m->tgt));
+  MCU(launch_pdl(k_load, dim3(m->np[0] / 32, B / 32), dim3(32, 8), 0, m->s, (const __nv_bfloat16*)x, targets, B,
+                 m->np[0], m->n[m->L], m->np[m->L], m->act[0], m->actT[0], m->tgt));
   MCU(enqueue_train_forward(m, B, m->s));
   MCU(enqueue_backward(m, B, false, m->s));
   if ((st = leave_sync(m)) != XSLAM_OK) return st;
@@ -636,7 +703,7 @@ extern "C" xslam_status xslam_mlp_train(xslam_mlp_t m, const void* feat, int n_f
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   MCU(cudaStreamBeginCapture(m->s, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = launch_pdl(k_gather, dim3(grid_for((size_t)batch * m->np[0], m->nsm)), dim3(256), 0, m->s,
+  cudaError_t e = launch_pdl(k_gather, dim3(m->np[0] / 32, batch / 32), dim3(32, 8), 0, m->s,
                              (const __nv_bfloat16*)feat, pairs, targets, (const int*)m->idx, (const int*)m->ctr, batch,
                              m->n[m->L], m->np[m->L], n_feat, m->act[0], m->actT[0], m->tgt, m->err);
   if (e == cudaSuccess) e = enqueue_train_forward(m, batch, m->s);
@@ -696,15 +763,10 @@ extern "C" xslam_status xslam_gemm_bf16(const void* A, const void* B, int M, int
   g.splits = (K / 64 + g.kb_per_split - 1) / g.kb_per_split;
   if (e == cudaSuccess) e = gemm_configure();
   if (e == cudaSuccess) e = launch_gemm_bf16(A, B, M, N, K, g, g.splits == 1 ? C : workspace, err, s);
-  if (e == cudaSuccess && g.splits > 1) {
-    const size_t MN = (size_t)M * N;
-    int nsm = 148, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    e = launch_pdl(k_reduce, dim3(grid_for(MN, nsm)), dim3(256), 0, s, (const float*)workspace, g.splits, M, N,
-                   (const float*)nullptr, 0, (const __nv_bfloat16*)nullptr, C, N, N, (__nv_bfloat16*)nullptr,
+  if (e == cudaSuccess && g.splits > 1)
+    e = launch_pdl(k_reduce, dim3((N + 31) / 32, (M + 31) / 32), dim3(32, M >= 32 ? 32 : M), 0, s, (const float*)workspace, g.splits, M,
+                   N, (const float*)nullptr, 0, (const __nv_bfloat16*)nullptr, C, N, N, (__nv_bfloat16*)nullptr,
                    (__nv_bfloat16*)nullptr);
-  }
   int h_err = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) k_refine(Params p, const float* __restric
   if (u >= p.W || v >= p.H) return;
   const size_t hw = (size_t)p.W * p.H;
   const size_t pix = (size_t)v * p.W + u;
-  const size_t n = vox_count(p);
+  const size_t n = vox_plane(p);
   const float* T = sT[0];
   const Ray ry = make_ray(p, T, u, v);
   const float inv_vox = 1.f / p.voxel;

@@ -8,7 +8,7 @@
 namespace xslam {
 
 struct Tri {
-  unsigned base;   // linear index of the min corner
+  CellAddr a;      // brick index of the min corner and the steps to its neighbours
   float fx, fy, fz;
   float val;       // trilinear F (real lane)
   float g[3];      // d val / d g (continuous voxel coordinates)
@@ -22,11 +22,11 @@ __device__ __forceinline__ bool tri_real(const Params& p, const float* __restric
         gz < (float)(p.nz - 1)))
     return false;
   const int i = (int)gx, j = (int)gy, k = (int)gz;  // gx >= 0: truncation is floor
-  const unsigned sy = (unsigned)p.nx, sz = (unsigned)p.nx * (unsigned)p.ny;
-  const unsigned b = (unsigned)i + sy * (unsigned)j + sz * (unsigned)k;
-  const float c000 = __ldg(F + b), c100 = __ldg(F + b + 1), c010 = __ldg(F + b + sy), c110 = __ldg(F + b + 1 + sy);
-  const float c001 = __ldg(F + b + sz), c101 = __ldg(F + b + 1 + sz), c011 = __ldg(F + b + sy + sz),
-              c111 = __ldg(F + b + 1 + sy + sz);
+  const CellAddr a = cell_addr(p, i, j, k);
+  const unsigned b = a.b, sx = a.dx, sy = a.dy, sz = a.dz;
+  const float c000 = __ldg(F + b), c100 = __ldg(F + b + sx), c010 = __ldg(F + b + sy), c110 = __ldg(F + b + sx + sy);
+  const float c001 = __ldg(F + b + sz), c101 = __ldg(F + b + sx + sz), c011 = __ldg(F + b + sy + sz),
+              c111 = __ldg(F + b + sx + sy + sz);
   const float mx = fmaxf(fmaxf(fmaxf(c000, c100), fmaxf(c010, c110)), fmaxf(fmaxf(c001, c101), fmaxf(c011, c111)));
   if (!(mx <= 1.f)) return false;  // an unobserved corner
   const float fx = gx - i, fy = gy - j, fz = gz - k;
@@ -34,7 +34,7 @@ __device__ __forceinline__ bool tri_real(const Params& p, const float* __restric
   const float x01 = c001 + fx * (c101 - c001), x11 = c011 + fx * (c111 - c011);
   const float y0 = x00 + fy * (x10 - x00), y1 = x01 + fy * (x11 - x01);
   t.val = y0 + fz * (y1 - y0);
-  t.base = b;
+  t.a = a;
   t.fx = fx;
   t.fy = fy;
   t.fz = fz;
@@ -53,12 +53,11 @@ __device__ __forceinline__ float tri_lane(const Params& p, const float* __restri
                                           float gly, float glz) {
   float v = t.g[0] * glx + t.g[1] * gly + t.g[2] * glz;
   if (Fl) {
-    const unsigned sy = (unsigned)p.nx, sz = (unsigned)p.nx * (unsigned)p.ny;
-    const unsigned b = t.base;
-    const float x00 = __ldg(Fl + b) + t.fx * (__ldg(Fl + b + 1) - __ldg(Fl + b));
-    const float x10 = __ldg(Fl + b + sy) + t.fx * (__ldg(Fl + b + 1 + sy) - __ldg(Fl + b + sy));
-    const float x01 = __ldg(Fl + b + sz) + t.fx * (__ldg(Fl + b + 1 + sz) - __ldg(Fl + b + sz));
-    const float x11 = __ldg(Fl + b + sy + sz) + t.fx * (__ldg(Fl + b + 1 + sy + sz) - __ldg(Fl + b + sy + sz));
+    const unsigned b = t.a.b, sx = t.a.dx, sy = t.a.dy, sz = t.a.dz;
+    const float x00 = __ldg(Fl + b) + t.fx * (__ldg(Fl + b + sx) - __ldg(Fl + b));
+    const float x10 = __ldg(Fl + b + sy) + t.fx * (__ldg(Fl + b + sx + sy) - __ldg(Fl + b + sy));
+    const float x01 = __ldg(Fl + b + sz) + t.fx * (__ldg(Fl + b + sx + sz) - __ldg(Fl + b + sz));
+    const float x11 = __ldg(Fl + b + sy + sz) + t.fx * (__ldg(Fl + b + sx + sy + sz) - __ldg(Fl + b + sy + sz));
     const float y0 = x00 + t.fy * (x10 - x00), y1 = x01 + t.fy * (x11 - x01);
     v += y0 + t.fz * (y1 - y0);
   }

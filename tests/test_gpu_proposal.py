@@ -77,6 +77,9 @@ def test_stop_tolerance_counts_and_parity(orbit):
     assert cnt["icp_iterations"] == levels * (FRAMES - 1)
     c, _ = _cfgs(orbit)
     _, _, cnt = _gpu_run(orbit, c)
+    assert cnt["icp_iterations"] == 0  # fixed counts: the counter is not run
+    c, _ = _cfgs(orbit, icp_stop=1e-30)
+    _, _, cnt = _gpu_run(orbit, c)
     assert cnt["icp_iterations"] == sum(orbit.icp_iters) * (FRAMES - 1)
     c, o = _cfgs(orbit, icp_stop=1e-6)
     gpu, ora = _gpu_run(orbit, c), _ora_run(orbit, o)
