@@ -177,6 +177,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   bool ok = true;
   ok &= cudaMalloc(&b.F, sizeof(float) * n * Lmax) == cudaSuccess;
   ok &= cudaMalloc(&b.Wt, sizeof(float) * n) == cudaSuccess;
+  ok &= cudaMalloc(&b.F0lin, sizeof(float) * vox_count(p)) == cudaSuccess;
   ok &= cudaMalloc(&b.depth_in, sizeof(float) * hw) == cudaSuccess;
   ok &= cudaMalloc(&b.gated, sizeof(float) * hw) == cudaSuccess;
   for (int l = 0; l < 3; ++l) ok &= cudaMalloc(&b.pyr[l], sizeof(float) * (hw >> (2 * l))) == cudaSuccess;
@@ -229,7 +230,7 @@ extern "C" xslam_status xslam_destroy(xslam_t h) {
   if (h->s) cudaStreamSynchronize(h->s);
   drop_graphs(h);
   Buffers& b = h->b;
-  cudaFree(b.F); cudaFree(b.Wt); cudaFree(b.depth_in); cudaFree(b.gated);
+  cudaFree(b.F); cudaFree(b.Wt); cudaFree(b.F0lin); cudaFree(b.depth_in); cudaFree(b.gated);
   for (int l = 0; l < 3; ++l) cudaFree(b.pyr[l]);
   cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp); cudaFree(h->hess_poses);
   cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.hit);
@@ -274,10 +275,17 @@ __global__ void k_write_plane(Params p, const float* in, float* a) {
     a[vox_index(p, x, y, z)] = in[i];
   }
 }
-// after W is written: voxels with W = 0 are unobserved
+// after W is written: voxels with W = 0 are unobserved (the brick plane and the march's linear copy)
 __global__ void k_mark_unobserved(float* F, const float* W, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     if (!(W[i] > 0.f)) F[i] = kUnobserved;
+}
+__global__ void k_mark_unobserved_lin(Params p, float* Flin, const float* W) {
+  const size_t n = vox_count(p);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % p.nx), y = (int)((i / p.nx) % p.ny), z = (int)(i / ((size_t)p.nx * p.ny));
+    if (!(W[vox_index(p, x, y, z)] > 0.f)) Flin[i] = kUnobserved;
+  }
 }
 
 extern "C" xslam_status xslam_reset(xslam_t h) {
@@ -286,6 +294,8 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   const int Lmax = 1 + h->max_lanes;
   const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
   k_fill<<<g, 256, 0, h->s>>>(h->b.F, n, kUnobserved);
+  CU(cudaGetLastError());
+  k_fill<<<g, 256, 0, h->s>>>(h->b.F0lin, vox_count(h->p), kUnobserved);
   CU(cudaGetLastError());
   if (Lmax > 1) CU(cudaMemsetAsync(h->b.F + n, 0, sizeof(float) * n * (Lmax - 1), h->s));
   CU(cudaMemsetAsync(h->b.Wt, 0, sizeof(float) * n, h->s));
@@ -659,9 +669,12 @@ extern "C" xslam_status xslam_write_tsdf(xslam_t h, int lane, const float* in) {
   const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
   k_write_plane<<<g, 256, 0, h->s>>>(h->p, in, dst);
   CU(cudaGetLastError());
+  if (lane == 0) CU(cudaMemcpyAsync(h->b.F0lin, in, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->s));
   if (lane == -1) {
     const unsigned gp = (unsigned)std::min<size_t>((np + 255) / 256, (size_t)h->nsm * 32);
     k_mark_unobserved<<<gp, 256, 0, h->s>>>(h->b.F, h->b.Wt, np);
+    CU(cudaGetLastError());
+    k_mark_unobserved_lin<<<g, 256, 0, h->s>>>(h->p, h->b.F0lin, h->b.Wt);
     CU(cudaGetLastError());
   }
 

@@ -28,8 +28,8 @@ constexpr int kFuseThreads = kBX * kBY * kBZ;  // a thread per voxel of a tile
 // Update voxel (i, j, k) if the frame observes it; returns whether it did. NL = 1 + K lanes.
 template <int NL>
 __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restrict__ D, const float (*sT)[12],
-                                           float* __restrict__ F, float* __restrict__ Wt, int i, int j, int k,
-                                           size_t n, size_t v) {
+                                           float* __restrict__ F, float* __restrict__ Wt,
+                                           float* __restrict__ F0lin, int i, int j, int k, size_t n, size_t v) {
   const float* T = sT[0];
   const float dx = p.ox + (i + 0.5f) * p.voxel - T[3];
   const float dy = p.oy + (j + 0.5f) * p.voxel - T[7];
@@ -66,6 +66,7 @@ __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restr
   const float inv = 1.f / w1;
   const float Fn = (w * f0 + FD) / w1;  // an unobserved voxel (w = 0) takes F_D whatever its sentinel value
   F[v] = Fn;
+  F0lin[(size_t)i + (size_t)p.nx * ((size_t)j + (size_t)p.ny * k)] = Fn;
   Wt[v] = (p.w_max > 0.f) ? fminf(w1, p.w_max) : w1;
 
   // tangents of L with respect to the pixel coordinates
@@ -145,7 +146,8 @@ __global__ void __launch_bounds__(256) k_fuse_tiles(Params p, const double* __re
 template <int NL>
 __global__ void __launch_bounds__(kFuseThreads) k_integrate(Params p, const float* __restrict__ D,
                                                         const double* __restrict__ pose, float* __restrict__ F,
-                                                        float* __restrict__ Wt, unsigned long long* __restrict__ stats,
+                                                        float* __restrict__ Wt, float* __restrict__ F0lin,
+                                                        unsigned long long* __restrict__ stats,
                                                         const int* __restrict__ tiles, unsigned* __restrict__ ctr) {
   pdl_enter();
   __shared__ float sT[NL][12];
@@ -162,7 +164,8 @@ __global__ void __launch_bounds__(kFuseThreads) k_integrate(Params p, const floa
     const int t = tiles[q];
     const int i = (t % ntx) * kBX + cx, j = ((t / ntx) % nty) * kBY + cy, k = (t / (ntx * nty)) * kBZ + cz;
     // the tile is brick t, whose voxel tid sits at t 512 + tid
-    if (i < p.nx && j < p.ny && k < p.nz) cnt += fuse_voxel<NL>(p, D, sT, F, Wt, i, j, k, n, ((size_t)t << 9) + tid);
+    if (i < p.nx && j < p.ny && k < p.nz)
+      cnt += fuse_voxel<NL>(p, D, sT, F, Wt, F0lin, i, j, k, n, ((size_t)t << 9) + tid);
   }
   // updated-voxel count: warp sums, one atomic per warp
 #pragma unroll
@@ -182,8 +185,8 @@ __global__ void __launch_bounds__(kFuseThreads) k_integrate(Params p, const floa
 
 template <int NL>
 static cudaError_t launch_integrate_nl(const Params& p, const Buffers& b, int grid, cudaStream_t s) {
-  return launch_pdl(k_integrate<NL>, dim3(grid), dim3(kFuseThreads), 0, s, p, b.pyr[0], b.pose, b.F, b.Wt, b.stats,
-                    b.tiles, b.tile_ctr);
+  return launch_pdl(k_integrate<NL>, dim3(grid), dim3(kFuseThreads), 0, s, p, b.pyr[0], b.pose, b.F, b.Wt, b.F0lin,
+                    b.stats, b.tiles, b.tile_ctr);
 }
 
 int fuse_tile_count(const Params& p) {

@@ -50,6 +50,7 @@ struct Params {
 struct Buffers {
   float* F;         // L planes of vox_plane floats: lane 0 = Re F (kUnobserved where W = 0), lane j = Im F (raw)
   float* Wt;        // one plane
+  float* F0lin;     // Re F again, in the linear layout x + nx (y + ny z): the ray-cast march's copy
   float* depth_in;  // H*W raw input
   float* gated;     // H*W range-gated input (bilateral filter source)
   float* pyr[3];    // range-gated level 0 and its two coarser levels

@@ -52,10 +52,10 @@ __global__ void __launch_bounds__(256) k_march(Params p, const float* __restrict
   bool prev_valid = false, prev_pos = false;
   for (int m = m_lo; m <= m_hi; ++m) {
     const float al = m * p.ray_step;
-    Tri t;
-    const bool ok = tri_real(p, F, ry.g0x + al * ry.gdx, ry.g0y + al * ry.gdy, ry.g0z + al * ry.gdz, t, false);
+    float val = 0.f;
+    const bool ok = march_real(p, F, ry.g0x + al * ry.gdx, ry.g0y + al * ry.gdy, ry.g0z + al * ry.gdz, val);
     if (prev_valid && ok) {
-      const bool pos = t.val > 0.f;
+      const bool pos = val > 0.f;
       if (prev_pos && !pos) {
         m_hit = m - 1;
         break;
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_march(Params p, const float* __restrict
       if (!prev_pos && pos) break;
     }
     prev_valid = ok;
-    prev_pos = ok && t.val > 0.f;
+    prev_pos = ok && val > 0.f;
   }
   hit[(size_t)v * p.W + u] = m_hit;
 }
@@ -187,13 +187,13 @@ __global__ void __launch_bounds__(256) k_refine(Params p, const float* __restric
 
 cudaError_t launch_march(const Params& p, const Buffers& b, const double* pose, cudaStream_t s) {
   dim3 blk(32, 8), grd((p.W + 31) / 32, (p.H + 7) / 8);
-  return launch_pdl(k_march, grd, blk, 0, s, p, b.F, pose, b.hit);
+  return launch_pdl(k_march, grd, blk, 0, s, p, b.F0lin, pose, b.hit);
 }
 
 cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose, float* depth, float* vmap,
                            float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s) {
   dim3 blk(32, 8), grd((p.W + 31) / 32, (p.H + 7) / 8);
-  cudaError_t e = launch_pdl(k_march, grd, blk, 0, s, p, b.F, pose, b.hit);
+  cudaError_t e = launch_pdl(k_march, grd, blk, 0, s, p, b.F0lin, pose, b.hit);
   if (e != cudaSuccess) return e;
   return launch_pdl(k_refine, grd, blk, 0, s, p, b.F, pose, b.hit, depth, vmap, nmap, ignore_imag_volume ? 1 : 0,
                     set_prev ? b.pose_prev : nullptr, set_prev ? b.stats + 1 : nullptr);
