@@ -4,16 +4,21 @@
 // slices (split-K); range z writes its FP32 partial product P_z to C + z M N, and a reduction kernel
 // adds the partials and applies the layer's epilogue.
 //
-// One CTA of 128 threads per 128 x 128 output tile and K range. Per 64-wide slice of K the CTA copies
-// the A and B tiles (2 x 16 KB) into shared memory in the canonical K-major layout without swizzle:
-// 8-row x 16-byte core matrices, 128 bytes apart along K (leading byte offset) and 1024 bytes apart
-// along M/N (stride byte offset); two stages, so the copy of slice s + 1 overlaps the MMAs of slice s.
-// Rows past M or N are zero-filled in shared memory and never read from global memory. One thread
-// issues the four 128 x 128 x 16 MMAs of a slice into the 128-column TMEM accumulator and commits
-// them to the stage's mbarrier. After the last slice every warp reads its 32 TMEM lanes (rows) with
-// tcgen05.ld and stores the rows below M. Every mbarrier wait is bounded; on a timeout the CTA sets
-// *err, skips its stores and still releases its TMEM.
+// One CTA of 128 threads per 128 x 128 output tile and K range, warp-specialised:
+//   - thread 0 (producer) streams the A and B tiles of each 64-wide K slice with TMA
+//     (cp.async.bulk.tensor.2d, 128-byte swizzle: 128 rows x 128 bytes = 16 KB per operand) into a
+//     3-stage ring; a stage's "full" mbarrier expects the 32 KB of its two copies;
+//   - thread 32 (MMA issuer) waits for a stage to be full, issues four 128 x 128 x 16
+//     tcgen05.mma.kind::f16 into the 128-column TMEM accumulator and commits them to the stage's
+//     "empty" mbarrier, which the producer waits on before refilling that stage; after the last slice
+//     it commits once more to the "done" mbarrier;
+//   - all four warps wait for "done", read their 32 TMEM lanes (rows) with tcgen05.ld and store the
+//     rows below M.
+// TMA reads rows past M or N as zeros. Every mbarrier wait is bounded; on a timeout the thread sets
+// *err, the CTA skips its stores and still releases its TMEM.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "internal.cuh"
 
@@ -23,18 +28,21 @@ namespace {
 
 constexpr int kBM = 128, kBN = 128, kBK = 64;
 constexpr int kTileBytes = kBM * kBK * 2;  // 16 KB per operand tile
-constexpr int kStages = 2;
-constexpr unsigned kSpin = 1u << 22;  // try_wait polls before a wait gives up
+constexpr int kStages = 3;  // 97 KB of stages: two CTAs per SM
+constexpr unsigned kSpin = 1u << 22;        // try_wait polls before a wait gives up
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: K-major, no swizzle (layout type 0), version 1
-__device__ __forceinline__ unsigned long long make_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+// shared-memory matrix descriptor of a K-major operand tile written by TMA with 128-byte swizzle: rows of
+// 128 bytes, 8-row atoms of 1024 bytes (stride byte offset), leading byte offset unused (1), version 1,
+// layout type 2 (128-byte swizzle). The tile base is 1024-byte aligned.
+__device__ __forceinline__ unsigned long long make_desc_sw128(unsigned addr) {
   unsigned long long d = 0;
   d |= (unsigned long long)((addr >> 4) & 0x3FFFu);
-  d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 16;
+  d |= (unsigned long long)(1024 >> 4) << 32;
   d |= 1ull << 46;
+  d |= 2ull << 61;
   return d;
 }
 
@@ -57,48 +65,50 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
   return ok != 0;
 }
 
-// bounded wait; false on timeout
+// bounded wait for the completion of the phase with the given parity; false on timeout
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
   for (unsigned it = 0; it < kSpin; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
 
-__device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// copy the 128 x 64 BF16 tile starting at (row0, k0) of a row-major [rows, K] matrix into the core-matrix
-// layout at smem address dst (rows beyond `rows` are zero-filled)
-__device__ __forceinline__ void load_tile(unsigned dst, const __nv_bfloat16* __restrict__ src, int rows, int K, int row0,
-                                          int k0) {
-  for (int c = threadIdx.x; c < kBM * (kBK / 8); c += blockDim.x) {
-    const int r = c >> 3, kc = c & 7;
-    const unsigned off = (unsigned)((r >> 3) * 1024 + kc * 128 + (r & 7) * 16);
-    if (row0 + r < rows) {
-      cp_async16(dst + off, src + (size_t)(row0 + r) * K + k0 + kc * 8);
-    } else {
-      asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst + off), "r"(0) : "memory");
-    }
-  }
+// 2-D TMA load of the box at element coordinates (x = K index, y = row) into shared memory
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B,
-                                                  int M, int N, int K, int kb_per_split, float* __restrict__ C, int* err) {
+__global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ CUtensorMap tmA,
+                                                  const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
+                                                  int kb_per_split, float* __restrict__ C, int* err) {
   pdl_enter();
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) unsigned long long bars[kStages];
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], done;
   __shared__ unsigned s_tmem;
   __shared__ int s_bad;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-  const unsigned sbase = smem_u32(smem);
+  // the 128-byte swizzle atoms are 1024 bytes: align the stage ring to 1024
+  const unsigned sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
   if (threadIdx.x == 0) {
     s_bad = 0;
-    for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(&done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tmB)) : "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&s_tmem)) : "memory");
@@ -108,29 +118,43 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = s_tmem;
-  const unsigned idesc = make_idesc(kBM, kBN);
   const int kb0 = blockIdx.z * kb_per_split;
   const int nk = min(K / kBK - kb0, kb_per_split);  // >= 1 by construction of the grid
   const int kbase = kb0 * kBK;
-  unsigned phase[kStages] = {0, 0};
 
-  // prologue: slice 0 into stage 0
-  load_tile(sbase, A, M, K, m0, kbase);
-  load_tile(sbase + kTileBytes, B, N, K, n0, kbase);
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  for (int s = 0; s < nk; ++s) {
-    const int st = s & 1;
-    const unsigned a_s = sbase + st * 2 * kTileBytes, b_s = a_s + kTileBytes;
-    // the copies of slice s are complete and visible to the tensor core (async proxy)
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0 && !s_bad) {
+  if (threadIdx.x == 0) {
+    // producer: stage st = s mod S holds slice s; its k-th refill waits for the k-th "empty" phase
+    for (int s = 0; s < nk; ++s) {
+      const int st = s % kStages;
+      if (s >= kStages && !mbar_wait(smem_u32(&empty[st]), (unsigned)((s / kStages - 1) & 1))) {
+        s_bad = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      const unsigned a_s = sbase + st * 2 * kTileBytes, b_s = a_s + kTileBytes;
+      const unsigned bar = smem_u32(&full[st]);
+      mbar_expect_tx(bar, 2u * kTileBytes);
+      tma_load_2d(a_s, &tmA, kbase + s * kBK, m0, bar);
+      tma_load_2d(b_s, &tmB, kbase + s * kBK, n0, bar);
+    }
+  } else if (threadIdx.x == 32) {
+    // MMA issuer
+    const unsigned idesc = make_idesc(kBM, kBN);
+    bool ok = true;
+    for (int s = 0; s < nk; ++s) {
+      const int st = s % kStages;
+      if (!mbar_wait(smem_u32(&full[st]), (unsigned)((s / kStages) & 1))) {
+        ok = false;
+        atomicExch(err, 1);
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned a_s = sbase + st * 2 * kTileBytes, b_s = a_s + kTileBytes;
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {
-        const unsigned long long ad = make_desc(a_s + kk * 256, 128, 1024);
-        const unsigned long long bd = make_desc(b_s + kk * 256, 128, 1024);
+        // K step of 16 elements = 32 bytes inside the 128-byte swizzled rows
+        const unsigned long long ad = make_desc_sw128(a_s + kk * 32);
+        const unsigned long long bd = make_desc_sw128(b_s + kk * 32);
         const unsigned acc = (s > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -139,33 +163,22 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
             : "memory");
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&bars[st]))
+                       smem_u32(&empty[st]))
                    : "memory");
     }
-    // before stage st ^ 1 is refilled, the MMAs of slice s - 1 (which read it) must have completed
-    if (s + 1 < nk) {
-      if (s >= 1 && threadIdx.x == 0 && !s_bad) {
-        if (!mbar_wait(smem_u32(&bars[st ^ 1]), phase[st ^ 1])) s_bad = 1;
-      }
-      if (s >= 1) phase[st ^ 1] ^= 1u;
-      __syncthreads();
-      const unsigned a_n = sbase + (st ^ 1) * 2 * kTileBytes;
-      load_tile(a_n, A, M, K, m0, kbase + (s + 1) * kBK);
-      load_tile(a_n + kTileBytes, B, N, K, n0, kbase + (s + 1) * kBK);
-      asm volatile("cp.async.commit_group;" ::: "memory");
-    }
+    if (ok)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&done))
+                   : "memory");
+    else
+      s_bad = 1;
   }
-  // the last slice's commit (and with it every earlier MMA) has completed
-  if (threadIdx.x == 0 && !s_bad) {
-    const int last = (nk - 1) & 1;
-    if (!mbar_wait(smem_u32(&bars[last]), phase[last])) s_bad = 1;
-    // an earlier, still unconsumed commit of the other stage
-    if (nk >= 2 && !s_bad && !mbar_wait(smem_u32(&bars[last ^ 1]), phase[last ^ 1])) s_bad = 1;
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+  __syncwarp();
+  // every MMA of the CTA has completed once "done" completes its first phase
+  const bool fin = mbar_wait(smem_u32(&done), 0u);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!s_bad) {
+  if (!fin && threadIdx.x == 64) atomicExch(err, 1);
+  __syncthreads();
+  if (fin && !s_bad) {
     const int row = m0 + warp * 32 + lane;
     float* crow = C + (size_t)blockIdx.z * M * N + (size_t)row * N;
 #pragma unroll 1
@@ -193,8 +206,6 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
         }
       }
     }
-  } else if (threadIdx.x == 0) {
-    atomicExch(err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -203,6 +214,36 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __nv_bfloat16* __restri
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
   }
 }
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// tensor map of a row-major [rows x K] BF16 matrix, box 64 (K) x 128 (rows), 128-byte swizzle, zero fill
+cudaError_t make_map(CUtensorMap* map, const void* base, int rows, int K) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
 
 size_t gemm_smem_bytes() { return (size_t)kStages * 2 * kTileBytes + 1024; }
 
@@ -226,9 +267,12 @@ bool gemm_shape_ok(int M, int N, int K) { return M >= 1 && N >= 1 && K >= kBK &&
 
 cudaError_t launch_gemm_bf16(const void* A, const void* B, int M, int N, int K, const GemmPlan& g, float* C, int* err,
                              cudaStream_t s) {
+  alignas(64) CUtensorMap ta, tb;
+  cudaError_t e = make_map(&ta, A, M, K);
+  if (e == cudaSuccess) e = make_map(&tb, B, N, K);
+  if (e != cudaSuccess) return e;
   dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, g.splits);
-  return launch_pdl(k_gemm_bf16, grid, dim3(128), gemm_smem_bytes(), s, (const __nv_bfloat16*)A,
-                    (const __nv_bfloat16*)B, M, N, K, g.kb_per_split, C, err);
+  return launch_pdl(k_gemm_bf16, grid, dim3(128), gemm_smem_bytes(), s, ta, tb, M, N, K, g.kb_per_split, C, err);
 }
 
 }  // namespace xslam
