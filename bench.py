@@ -595,8 +595,10 @@ def run_batch(args, dev, rank):
 def run_second_order(args, dev, rank):
     """A 512^3 x 0.8 cm map of a 40-primitive scene built from a 500-frame walk; 100 query frames of
     that walk start from their true pose perturbed by up to 5 cm / 3 degrees and are relocalised by
-    gradient descent and by Newton's method with the eta switch (loss, gradient and Hessian from the
-    GPU). Also the time of one order-2 evaluation (21 second-order directions) and of one order-1."""
+    gradient descent, nonlinear conjugate gradients and Newton's method with the eta switch (loss,
+    gradient and Hessian from the GPU), with per-iteration curves of the three optimisers (Sec. 6's ICP
+    comparison). Also the time of one order-2 evaluation (21 second-order directions) and of one
+    order-1."""
     import torch
     from paper_2405_02187_gb300 import reloc, synth, xslam
 
@@ -622,7 +624,7 @@ def run_second_order(args, dev, rank):
                               rng.uniform(-1, 1, 3) * 0.05 / math.sqrt(3.0)])
         queries.append((k, reloc.compose(reloc.se3_exp(dxi), wl.poses[k])))
     out = {}
-    for method in ("gd", "newton"):
+    for method in ("gd", "nlcg", "newton"):
         errs, its, evals = [], [], 0
         t1 = time.perf_counter()
         for k, T0 in queries:
@@ -636,6 +638,22 @@ def run_second_order(args, dev, rank):
                            recall_1cm_1deg=round(float(np.mean((e[:, 0] < 0.01) & (e[:, 1] < 1.0))), 3),
                            mean_iterations=round(float(np.mean(its)), 2), evaluations=evals, wall_s=round(wall, 2))
     init = np.array([reloc.pose_error(T0, wl.poses[k]) for k, T0 in queries])
+    # Sec. 6's ICP optimiser comparison (translation error, rotation error and point-to-plane loss per
+    # iteration for gradient descent, nonlinear CG and Newton): medians over the first 10 queries
+    fig3 = {}
+    n_it = 30
+    for method in ("gd", "nlcg", "newton"):
+        curves = []
+        for k, T0 in queries[:10]:
+            tr = [(T0, float(x.grad(wl.depth[k], T0, order=1)[0]))]
+            reloc.relocalise(x, wl.depth[k], T0, method=method, eta=float("inf"), iters=n_it, tol=0.0, trace=tr)
+            while len(tr) < n_it + 1:
+                tr.append(tr[-1])
+            curves.append([(*reloc.pose_error(T, wl.poses[k]), E) for T, E in tr[:n_it + 1]])
+        c = np.median(np.array(curves), axis=0)
+        fig3[method] = dict(trans_cm=[round(float(v) * 100, 4) for v in c[:, 0]],
+                            rot_deg=[round(float(v), 4) for v in c[:, 1]],
+                            loss=[float(f"{v:.4g}") for v in c[:, 2]])
     # throughput of the derivative evaluations at one query
     k, T0 = queries[0]
     for order in (1, 2):
@@ -654,6 +672,8 @@ def run_second_order(args, dev, rank):
         workload=f"{wl.dims[0]}^3 x {wl.voxel * 100:.1f} cm map of a 40-primitive room from a {frames}-frame 640x480 walk; "
                  f"{len(queries)} queries at their true pose perturbed by up to 5 cm / 3 deg",
         map_ms_per_frame=round(map_ms / frames, 3), map_tracking_failures=int(n_fail),
+        optimiser_curves=dict(note="median over 10 queries of the translation error, rotation error and loss after "
+                                   "each iteration (index 0 = start); Newton without the eta switch", **fig3),
         initial=dict(median_cm=round(float(np.median(init[:, 0])) * 100, 3), median_deg=round(float(np.median(init[:, 1])), 4)),
         gradient_descent=out["gd"], newton_eta=dict(out["newton"], eta=args.reloc_eta),
         hessian=dict(ms_per_evaluation=round(times[2], 3), per_s=round(1000.0 / times[2], 1),

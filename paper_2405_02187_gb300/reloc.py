@@ -1,5 +1,6 @@
 """Camera relocalisation against a TSDF map (X-SLAM Sec. 5.2): minimise the point-to-plane loss E of
-a query depth frame over its pose, by gradient descent or by Newton's method with the paper's switch
+a query depth frame over its pose, by gradient descent, by nonlinear conjugate gradients (the three
+optimisers of Sec. 6's ICP comparison, "High order ICP") or by Newton's method with the paper's switch
 (gradient direction while E exceeds a threshold eta, Newton direction -H^-1 g below it).
 
 Every loss, gradient and Hessian comes from xslam_grad (orders 1 and 2, computed on the GPU); this
@@ -55,12 +56,63 @@ class Result:
     evaluations: int
 
 
-def relocalise(handle, depth, T_init, method="newton", eta=1e-3, iters=30, tol=1e-6, step0=0.01):
+def _nlcg(handle, depth, T, iters, tol, step0, trace):
+    """Polak-Ribiere+ conjugate directions (restarted when not a descent direction). The line search
+    along d evaluates a trial step a, fits the parabola through E(0), E'(0) = g.d and E(a), and takes
+    its minimiser if the Armijo condition E <= E(0) + 1e-4 a g.d holds there, else the trial step if it
+    holds, else halves the trial step. The next trial step is twice the last accepted one."""
+    E, g = handle.grad(depth, T, order=1)
+    evals = 1
+    d = -g
+    a = step0 / max(np.linalg.norm(g), 1e-30)
+    it = 0
+    for it in range(1, iters + 1):
+        gd = float(g @ d)
+        if gd >= 0.0:
+            d, gd = -g, -float(g @ g)
+        best = None
+        for _ in range(16):
+            Ta = compose(se3_exp(a * d), T)
+            Ea, ga = handle.grad(depth, Ta, order=1)
+            evals += 1
+            curv = (Ea - E - gd * a) / (a * a)
+            if curv > 0.0:
+                a2 = -gd / (2.0 * curv)
+                T2 = compose(se3_exp(a2 * d), T)
+                E2, g2 = handle.grad(depth, T2, order=1)
+                evals += 1
+                if E2 <= E + 1e-4 * a2 * gd and E2 <= Ea:
+                    best = (a2, T2, E2, g2)
+                    break
+            if Ea <= E + 1e-4 * a * gd:
+                best = (a, Ta, Ea, ga)
+                break
+            a *= 0.5
+        if best is None:
+            break
+        a, T1, E1, g1 = best
+        step = a * d
+        beta = max(0.0, float(g1 @ (g1 - g)) / max(float(g @ g), 1e-300))
+        T, E, g = T1, E1, g1
+        d = -g + beta * d
+        a *= 2.0
+        if trace is not None:
+            trace.append((T, float(E)))
+        if np.linalg.norm(step) < tol:
+            break
+    return Result(T, it, float(E), 0, evals)
+
+
+def relocalise(handle, depth, T_init, method="newton", eta=1e-3, iters=30, tol=1e-6, step0=0.01, trace=None):
     """Minimise E(T) from T_init. handle: an XSlam holding the map; depth: the query's CUDA depth.
     method "gd": steps -a g with a backtracking/expanding step size (a g at most step0 at first);
+    method "nlcg": nonlinear conjugate gradients (Polak-Ribiere+, Armijo backtracking);
     method "newton": -H^-1 g when E <= eta and H is positive definite (halved until E decreases),
-    otherwise the gradient step. Stops when a step's norm falls below tol."""
+    otherwise the gradient step. Stops when a step's norm falls below tol. trace (a list, optional)
+    receives (T, E) after every iteration."""
     T = np.asarray(T_init, np.float64)
+    if method == "nlcg":
+        return _nlcg(handle, depth, T, iters, tol, step0, trace)
     evals = 0
     if method == "newton":
         E, g, H = handle.grad(depth, T, order=2)
@@ -109,6 +161,8 @@ def relocalise(handle, depth, T_init, method="newton", eta=1e-3, iters=30, tol=1
                     accepted = True
                     break
                 alpha *= 0.5
+        if accepted and trace is not None:
+            trace.append((T, float(E)))
         if not accepted or np.linalg.norm(step) < tol:
             break
     return Result(T, it, float(E), n_newton, evals)

@@ -57,3 +57,26 @@ def test_newton_converges_faster_than_gradient_descent():
     # above eta the Newton method takes gradient steps only
     r = reloc.relocalise(_Quadratic(A, T_star), None, T0, method="newton", eta=0.0, iters=5)
     assert r.newton_steps == 0
+
+
+def test_conjugate_gradients_beat_gradient_descent_and_newton_beats_both():
+    """The ordering of Sec. 6's ICP optimiser comparison on an ill-conditioned quadratic: after the same
+    number of iterations Newton is exact, nonlinear CG is far closer than gradient descent."""
+    rng = np.random.default_rng(2)
+    Q = np.linalg.qr(rng.standard_normal((6, 6)))[0]
+    A = Q @ np.diag([1e-2, 3e-2, 0.1, 0.5, 1.0, 2.0]) @ Q.T
+    T_star = reloc.se3_exp(rng.standard_normal(6) * 0.3)
+    T0 = reloc.compose(reloc.se3_exp(np.array([0.03, -0.02, 0.01, 0.05, -0.04, 0.02])), T_star)
+    err = {}
+    traces = {}
+    for m in ("gd", "nlcg", "newton"):
+        tr = []
+        r = reloc.relocalise(_Quadratic(A, T_star), None, T0, method=m, eta=np.inf, iters=30, trace=tr)
+        err[m] = np.linalg.norm(_Quadratic(A, T_star)._d(r.T))
+        traces[m] = tr
+        assert len(tr) == r.iterations or len(tr) == r.iterations - 1
+        # every accepted iteration lowers the loss
+        losses = [e for _, e in tr]
+        assert all(b <= a + 1e-15 for a, b in zip(losses, losses[1:]))
+    assert err["newton"] < 1e-6
+    assert err["nlcg"] < 0.1 * err["gd"]
