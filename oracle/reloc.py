@@ -196,3 +196,93 @@ def hessian_bicomplex(F, Wt, T0, Dq, intr, dims, origin, voxel, depth_min=0.2, d
                 g[j] = float(Es.i1()) / h
                 E = float(Es.real)
     return E, g, H
+
+
+# ---------------------------------------------------------------------------------------------------
+# The paper's relocalisation loss (Sec. 5.2): the query frame fused into the reference volume at the
+# query pose, E(T) = sum_p (F_r(p) - F_q(p))^2 with (F_q, W_q) = surface_update(M_r, T, D_q). Only the
+# voxels the query updates differ; unobserved reference voxels hold F = 1, W = 0 (fusion.py's
+# convention). The derivatives with respect to a left twist of T follow the update's discrete
+# decisions (which voxels are updated, which are clamped at F_D = 1, the pixel cells) at the real pose.
+# ---------------------------------------------------------------------------------------------------
+def tsdf_loss(F, Wt, T, Dq, intr, dims, origin, voxel, mu, disc_gate=0.1):
+    """E(T) for a real or complex pose T (the reference volume F, Wt is real)."""
+    from . import fusion
+    T = np.asarray(T)
+    Fq = np.array(F, np.complex128 if np.iscomplexobj(T) else np.float64)
+    Wq = np.array(Wt, np.float64)
+    fusion.integrate(Fq, Wq, Dq, T, intr, dims, origin, voxel, mu, disc_gate)
+    d = np.asarray(F, np.float64) - Fq
+    return np.sum(d * d)
+
+
+def tsdf_gradient(F, Wt, T, Dq, intr, dims, origin, voxel, mu, h=1e-20, **kw):
+    """(E, dE/dxi), xi a left twist of T, by six complex runs."""
+    E = tsdf_loss(F, Wt, np.asarray(T, np.float64), Dq, intr, dims, origin, voxel, mu, **kw)
+    g = np.zeros(6)
+    for j in range(6):
+        g[j] = np.imag(tsdf_loss(F, Wt, se3.promote_pose(T, j, h), Dq, intr, dims, origin, voxel, mu, **kw)) / h
+    return float(E), g
+
+
+def tsdf_gradient_at(F, Wt, T0, xi, Dq, intr, dims, origin, voxel, mu, h=1e-20, **kw):
+    """The gradient with respect to the global twist xi of exp(xi) T0 (complex steps on xi)."""
+    g = np.zeros(6)
+    for j in range(6):
+        x = np.asarray(xi, np.complex128).copy()
+        x[j] += 1j * h
+        g[j] = np.imag(tsdf_loss(F, Wt, se3.compose(se3.se3_exp(x), T0), Dq, intr, dims, origin, voxel, mu,
+                                 **kw)) / h
+    return g
+
+
+def tsdf_decisions(F, Wt, T, Dq, intr, dims, origin, voxel, mu, disc_gate=0.1):
+    """The surface update's discrete decisions at the real pose T (update mask, clamp mask, cells)."""
+    from . import fusion
+    log = []
+    fusion.integrate(np.array(F, np.float64), np.array(Wt, np.float64), Dq, np.real(T), intr, dims, origin, voxel,
+                     mu, disc_gate, log=log)
+    return log
+
+
+def tsdf_hessian_bicomplex(F, Wt, T0, Dq, intr, dims, origin, voxel, mu, disc_gate=0.1, h=1e-20):
+    """(E, g, H) at T0 by the bicomplex step (Sec. 3): E(exp(h i1 e_j + h i2 e_k) T0) with the surface
+    update's decisions at the real pose, evaluated step by step as in fusion.integrate
+    (p_c = R^T (p - t), x = pi(K p_c), L(x) bilinear, sdf = L - |t - p| / |K^-1 x_dot|, F_D = sdf / mu
+    unless clamped, F_q = (W F_r + F_D) / (W + 1)); H_jk = the i1 i2 part / h^2, g_j the i1 part / h."""
+    from . import bicomplex as bc
+    from . import fusion
+    T0 = np.asarray(T0, np.float64)
+    keep, clamp, xc, yc = tsdf_decisions(F, Wt, T0, Dq, intr, dims, origin, voxel, mu, disc_gate)
+    E = float(tsdf_loss(F, Wt, T0, Dq, intr, dims, origin, voxel, mu, disc_gate))
+    g, H = np.zeros(6), np.zeros((6, 6))
+    sel = keep & ~clamp  # clamped voxels take F_D = 1 at every pose near T0: no derivative
+    idx = np.nonzero(sel)[0]
+    if idx.size == 0:
+        return E, g, H
+    p = fusion.voxel_centres(idx, dims, origin, voxel)
+    i0, j0 = xc[sel].astype(np.int64), yc[sel].astype(np.int64)
+    D = np.asarray(Dq, np.float64)
+    d00, d10, d01, d11 = D[j0, i0], D[j0, i0 + 1], D[j0 + 1, i0], D[j0 + 1, i0 + 1]
+    Fr = np.asarray(F, np.float64)[idx]
+    w = np.asarray(Wt, np.float64)[idx]
+    for j in range(6):
+        for k in range(j, 6):
+            T = bicomplex_pose(T0, j, k, h)
+            dv = [p[:, r] - T[r, 3] for r in range(3)]
+            pc = [T[0, c] * dv[0] + T[1, c] * dv[1] + T[2, c] * dv[2] for c in range(3)]
+            x = intr.fx * pc[0] / pc[2] + intr.cx
+            y = intr.fy * pc[1] / pc[2] + intr.cy
+            a, b = x - i0, y - j0
+            L = (1 - a) * (1 - b) * d00 + a * (1 - b) * d10 + (1 - a) * b * d01 + a * b * d11
+            lam = bc.sqrt(((x - intr.cx) / intr.fx) * ((x - intr.cx) / intr.fx)
+                          + ((y - intr.cy) / intr.fy) * ((y - intr.cy) / intr.fy) + 1.0)
+            dist = bc.sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2])
+            FD = (L - dist / lam) / mu
+            e = Fr - (w * Fr + FD) / (w + 1.0)
+            s = e * e
+            Es = bc.Bicomplex(np.sum(s.z1), np.sum(s.z2))
+            H[j, k] = H[k, j] = float(Es.i1i2()) / (h * h)
+            if j == k:
+                g[j] = float(Es.i1()) / h
+    return E, g, H
