@@ -201,9 +201,11 @@ def hessian_bicomplex(F, Wt, T0, Dq, intr, dims, origin, voxel, depth_min=0.2, d
 # ---------------------------------------------------------------------------------------------------
 # The paper's relocalisation loss (Sec. 5.2): the query frame fused into the reference volume at the
 # query pose, E(T) = sum_p (F_r(p) - F_q(p))^2 with (F_q, W_q) = surface_update(M_r, T, D_q). Only the
-# voxels the query updates differ; unobserved reference voxels hold F = 1, W = 0 (fusion.py's
-# convention). The derivatives with respect to a left twist of T follow the update's discrete
-# decisions (which voxels are updated, which are clamped at F_D = 1, the pixel cells) at the real pose.
+# voxels the query updates differ. The sum runs over the voxels the reference has observed (W_r > 0):
+# an unobserved voxel has no TSDF value to compare (its stored F = 1 is a convention of fusion.py), and
+# counting it would reward poses that see less of the map. The derivatives with respect to a left
+# twist of T follow the update's discrete decisions (which voxels are updated, which are clamped at
+# F_D = 1, the pixel cells) at the real pose.
 # ---------------------------------------------------------------------------------------------------
 def tsdf_loss(F, Wt, T, Dq, intr, dims, origin, voxel, mu, disc_gate=0.1):
     """E(T) for a real or complex pose T (the reference volume F, Wt is real)."""
@@ -212,7 +214,7 @@ def tsdf_loss(F, Wt, T, Dq, intr, dims, origin, voxel, mu, disc_gate=0.1):
     Fq = np.array(F, np.complex128 if np.iscomplexobj(T) else np.float64)
     Wq = np.array(Wt, np.float64)
     fusion.integrate(Fq, Wq, Dq, T, intr, dims, origin, voxel, mu, disc_gate)
-    d = np.asarray(F, np.float64) - Fq
+    d = (np.asarray(F, np.float64) - Fq)[np.asarray(Wt) > 0]
     return np.sum(d * d)
 
 
@@ -256,7 +258,8 @@ def tsdf_hessian_bicomplex(F, Wt, T0, Dq, intr, dims, origin, voxel, mu, disc_ga
     keep, clamp, xc, yc = tsdf_decisions(F, Wt, T0, Dq, intr, dims, origin, voxel, mu, disc_gate)
     E = float(tsdf_loss(F, Wt, T0, Dq, intr, dims, origin, voxel, mu, disc_gate))
     g, H = np.zeros(6), np.zeros((6, 6))
-    sel = keep & ~clamp  # clamped voxels take F_D = 1 at every pose near T0: no derivative
+    # clamped voxels take F_D = 1 at every pose near T0: no derivative; unobserved ones are not summed
+    sel = keep & ~clamp & (np.asarray(Wt) > 0)
     idx = np.nonzero(sel)[0]
     if idx.size == 0:
         return E, g, H

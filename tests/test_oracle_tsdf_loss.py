@@ -39,7 +39,7 @@ def test_zero_at_the_fusing_pose(setup):
     for j in range(6):
         Fq = np.array(F, np.complex128)
         fusion.integrate(Fq, np.array(W), D0, se3.promote_pose(T, j, H), *_args(wl))
-        e.append(np.imag(F - Fq) / H)
+        e.append(np.imag(F - Fq)[W > 0] / H)
     e = np.array(e)
     GN = 2.0 * e @ e.T
     _, gb, Hb = reloc.tsdf_hessian_bicomplex(F, W, T, D0, *_args(wl))
@@ -98,3 +98,27 @@ def test_bicomplex_hessian_matches_differences_of_the_gradient(setup):
         Hfd[:, k] = (gp - gm) / (2 * delta)
     np.testing.assert_allclose(Hb, Hfd, rtol=1e-4, atol=1e-5 * np.abs(Hfd).max())
     np.testing.assert_allclose(Hb, Hb.T, rtol=1e-12, atol=1e-12 * np.abs(Hb).max())
+
+
+def test_unobserved_voxels_do_not_count(setup):
+    """The sum runs over the voxels the reference has observed: whatever an unobserved voxel stores
+    leaves E, g and H unchanged, and forgetting observed voxels removes exactly their terms."""
+    wl, F, W, _ = setup
+    D1 = measure.range_gate(wl.depth[1].astype(np.float64), wl.depth_min, wl.depth_max)
+    T = wl.poses[1]
+    E, g, Hb = reloc.tsdf_hessian_bicomplex(F, W, T, D1, *_args(wl))
+    F2 = F.copy()
+    F2[W == 0] = -0.3
+    E2, g2, H2 = reloc.tsdf_hessian_bicomplex(F2, W, T, D1, *_args(wl))
+    assert E2 == E and np.array_equal(g2, g) and np.array_equal(H2, Hb)
+    # forget every other observed voxel: E drops by the forgotten voxels' squared changes
+    keep, clamp, xc, yc = reloc.tsdf_decisions(F, W, T, D1, *_args(wl))
+    Fq, Wq = F.copy(), W.copy()
+    fusion.integrate(Fq, Wq, D1, T, *_args(wl))
+    obs = np.nonzero(W > 0)[0]
+    W3 = W.copy()
+    W3[obs[::2]] = 0.0
+    E3 = reloc.tsdf_loss(F, W3, T, D1, *_args(wl))
+    d = (F - Fq)[obs[::2]]
+    assert E3 == pytest.approx(E - np.sum(d * d), rel=1e-12)
+    assert 0 < E3 < E
