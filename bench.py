@@ -637,6 +637,26 @@ def run_second_order(args, dev, rank):
         out[method] = dict(median_cm=round(float(np.median(e[:, 0])) * 100, 3), median_deg=round(float(np.median(e[:, 1])), 4),
                            recall_1cm_1deg=round(float(np.mean((e[:, 0] < 0.01) & (e[:, 1] < 1.0))), 3),
                            mean_iterations=round(float(np.mean(its)), 2), evaluations=evals, wall_s=round(wall, 2))
+    # the paper's TSDF-difference loss (the query's surface update against the map) on the first
+    # queries, Newton whenever the Hessian is positive definite (eta = inf: the loss is a sum over
+    # voxels, not on the point-to-plane scale)
+    out_tsdf = {}
+    nq = min(len(queries), args.reloc_tsdf_queries)
+    for method in ("gd", "nlcg", "newton"):
+        errs, its, evals = [], [], 0
+        t1 = time.perf_counter()
+        for k, T0 in queries[:nq]:
+            r = reloc.relocalise(x, wl.depth[k], T0, method=method, eta=float("inf"), iters=args.reloc_iters,
+                                 loss="tsdf")
+            errs.append(reloc.pose_error(r.T, wl.poses[k]))
+            its.append(r.iterations)
+            evals += r.evaluations
+        wall = time.perf_counter() - t1
+        e = np.array(errs)
+        out_tsdf[method] = dict(median_cm=round(float(np.median(e[:, 0])) * 100, 3),
+                                median_deg=round(float(np.median(e[:, 1])), 4),
+                                recall_1cm_1deg=round(float(np.mean((e[:, 0] < 0.01) & (e[:, 1] < 1.0))), 3),
+                                mean_iterations=round(float(np.mean(its)), 2), evaluations=evals, wall_s=round(wall, 2))
     init = np.array([reloc.pose_error(T0, wl.poses[k]) for k, T0 in queries])
     # Sec. 6's ICP optimiser comparison (translation error, rotation error and point-to-plane loss per
     # iteration for gradient descent, nonlinear CG and Newton): medians over the first 10 queries
@@ -667,6 +687,28 @@ def run_second_order(args, dev, rank):
         for _ in range(n):
             x.grad(wl.depth[k], T0, order=order)
         times[order] = (time.perf_counter() - t1) / n * 1e3
+    # the TSDF-difference loss at the same query
+    for _ in range(3):
+        x.grad_tsdf(wl.depth[k], T0, order=2)
+    tsdf_times = {}
+    for order in (1, 2):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        n = 20
+        for _ in range(n):
+            _, _, _, n_vox = x.grad_tsdf(wl.depth[k], T0, order=order)
+        tsdf_times[order] = (time.perf_counter() - t1) / n * 1e3
+    # the plain FP64 bicomplex path on the same query: time and the FP32 path's derivative error
+    x.grad_tsdf_plain64(wl.depth[k], T0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    n = 10
+    for _ in range(n):
+        E64, g64, H64, _ = x.grad_tsdf_plain64(wl.depth[k], T0)
+    ms64 = (time.perf_counter() - t1) / n * 1e3
+    E32, g32, H32, _ = x.grad_tsdf(wl.depth[k], T0, order=2)
+    err_g = float(np.linalg.norm(g32 - g64) / max(np.linalg.norm(g64), 1e-300))
+    err_H = float(np.linalg.norm(H32 - H64) / max(np.linalg.norm(H64), 1e-300))
     x.close()
     return dict(
         workload=f"{wl.dims[0]}^3 x {wl.voxel * 100:.1f} cm map of a 40-primitive room from a {frames}-frame 640x480 walk; "
@@ -675,10 +717,23 @@ def run_second_order(args, dev, rank):
         optimiser_curves=dict(note="median over 10 queries of the translation error, rotation error and loss after "
                                    "each iteration (index 0 = start); Newton without the eta switch", **fig3),
         initial=dict(median_cm=round(float(np.median(init[:, 0])) * 100, 3), median_deg=round(float(np.median(init[:, 1])), 4)),
-        gradient_descent=out["gd"], newton_eta=dict(out["newton"], eta=args.reloc_eta),
+        gradient_descent=out["gd"], nlcg=out["nlcg"], newton_eta=dict(out["newton"], eta=args.reloc_eta),
         hessian=dict(ms_per_evaluation=round(times[2], 3), per_s=round(1000.0 / times[2], 1),
                      directions=21, note="loss + gradient + 21 second-order directions over 640x480, host round trip included"),
         gradient=dict(ms_per_evaluation=round(times[1], 3), per_s=round(1000.0 / times[1], 1)),
+        tsdf_loss=dict(note=f"the paper's TSDF-difference loss on the first {nq} queries (Newton whenever H is "
+                            "positive definite); evaluation times at one query, host round trip included",
+                       updated_voxels=int(n_vox), gradient_descent=out_tsdf["gd"], nlcg=out_tsdf["nlcg"],
+                       newton=out_tsdf["newton"],
+                       hessian=dict(ms_per_evaluation=round(tsdf_times[2], 3), per_s=round(1000.0 / tsdf_times[2], 1),
+                                    voxel_direction_pairs_per_s=round(21 * n_vox / (tsdf_times[2] * 1e-3), 1)),
+                       gradient=dict(ms_per_evaluation=round(tsdf_times[1], 3), per_s=round(1000.0 / tsdf_times[1], 1)),
+                       plain_fp64=dict(note="Sec. 3's bicomplex step in FP64 with full products (h = 1e-20), same "
+                                            "voxels; the FP32 path's relative error against it",
+                                       ms_per_evaluation=round(ms64, 3), per_s=round(1000.0 / ms64, 1),
+                                       speedup_of_fp32=round(ms64 / tsdf_times[2], 2),
+                                       grad_rel_err_fp32=float(f"{err_g:.3g}"), hess_rel_err_fp32=float(f"{err_H:.3g}"),
+                                       loss_rel_diff=float(f"{abs(E32 - E64) / max(abs(E64), 1e-300):.3g}"))),
         generate_s=round(gen_s, 1))
 
 
@@ -824,6 +879,7 @@ def main():
     ap.add_argument("--no-second-order", action="store_true", help="skip the relocalisation / Hessian run")
     ap.add_argument("--reloc-frames", type=int, default=500)
     ap.add_argument("--reloc-queries", type=int, default=100)
+    ap.add_argument("--reloc-tsdf-queries", type=int, default=30)
     ap.add_argument("--reloc-iters", type=int, default=30)
     ap.add_argument("--reloc-eta", type=float, default=1e-3)
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-ICP frame-step comparison")

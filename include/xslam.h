@@ -164,6 +164,34 @@ xslam_status xslam_raycast(xslam_t h, const double* T, float* depth, float* vmap
 xslam_status xslam_grad(xslam_t h, const float* query_depth, const double T_q[12], int order, double* loss,
                         double grad[6], double* hess);
 
+/*
+ * The paper's relocalisation loss (Sec. 5.2, TSDF-difference reading) of a query depth frame and its
+ * derivatives with respect to the query pose: with (F_q, W_q) the handle's volume (F_r, W_r) after the
+ * surface update (Sec. 4.1) of the query frame at T_q, E(T_q) = sum over the observed voxels (W_r > 0)
+ * of (F_r - F_q)^2, which is the sum over the observed voxels the query updates of
+ * ((F_r - F_D) / (W_r + 1))^2. The volume itself is not changed. query_depth is a device pointer [H W]
+ * (range gated, and bilaterally filtered if the handle's configuration says so, as a frame's depth is).
+ * Derivatives are with respect to a left twist xi of T_q (phi then rho), from the bicomplex step of
+ * Sec. 3 in truncated arithmetic with the real pose's update decisions (voxels updated, voxels clamped
+ * at F_D = 1, which carry no derivative, and the pixel cells):
+ * order 1: *loss and grad[6] (hess gets the 6 diagonal entries, the rest 0);
+ * order 2: *loss, grad[6] and hess[21], the upper triangle row by row as in xslam_grad.
+ * *n_voxels = the number of observed voxels the query updates (the terms of the sum). Any handle; any
+ * output pointer may be NULL.
+ * Errors: XSLAM_EINVAL (NULL input, order not 1 or 2, non-finite T_q).
+ */
+xslam_status xslam_grad_tsdf(xslam_t h, const float* query_depth, const double T_q[12], int order, double* loss,
+                             double grad[6], double* hess, long long* n_voxels);
+
+/*
+ * The same loss, gradient and full Hessian (outputs as xslam_grad_tsdf order 2) by the plain FP64 path:
+ * Sec. 3's bicomplex step as printed, numbers a + b i1 + c i2 + d i1 i2 with i1^2 = i2^2 = -1 and every
+ * product kept, step h = 1e-20, the update's decisions taken in FP64. The comparison path of the FP32
+ * truncated arithmetic; the handle's volume (FP32) is read and not changed. Errors as xslam_grad_tsdf.
+ */
+xslam_status xslam_grad_tsdf_plain64(xslam_t h, const float* query_depth, const double T_q[12], double* loss,
+                                     double grad[6], double* hess, long long* n_voxels);
+
 /* Copy one plane of the volume to device array out[nx ny nz]: lane 0 = F (unobserved voxels read
  * 1), lane j >= 1 = Im F / h_j of lane j, lane -1 = the weight W. */
 xslam_status xslam_read_tsdf(xslam_t h, int lane, float* out);

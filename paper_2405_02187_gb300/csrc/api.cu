@@ -186,6 +186,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   ok &= cudaMalloc(&b.pose_prev, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&h->pose_tmp, sizeof(double) * 12 * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&h->hess_poses, sizeof(float) * 21 * 12 * 4) == cudaSuccess;
+  ok &= cudaMalloc(&h->hess_poses64, sizeof(double) * 21 * 12 * 4) == cudaSuccess;
   ok &= cudaMalloc(&b.partial, sizeof(float) * (size_t)(nblk_max + 4) * kNT * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&b.partial_n, sizeof(int) * nblk_max) == cudaSuccess;
   ok &= cudaMalloc(&b.ticket, sizeof(unsigned)) == cudaSuccess;
@@ -232,7 +233,7 @@ extern "C" xslam_status xslam_destroy(xslam_t h) {
   Buffers& b = h->b;
   cudaFree(b.F); cudaFree(b.Wt); cudaFree(b.F0lin); cudaFree(b.depth_in); cudaFree(b.gated);
   for (int l = 0; l < 3; ++l) cudaFree(b.pyr[l]);
-  cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp); cudaFree(h->hess_poses);
+  cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp); cudaFree(h->hess_poses); cudaFree(h->hess_poses64);
   cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.hit);
   cudaFree(b.tiles); cudaFree(b.tile_ctr);
   cudaFree(h->q.pose_pp); cudaFree(h->q.candA); cudaFree(h->q.candB); cudaFree(h->q.judge); cudaFree(h->q.failA);
@@ -760,8 +761,11 @@ extern "C" xslam_status xslam_icp_system(xslam_t h, int level, const double* Tj,
 
 // The 21 truncated-bicomplex start poses exp(e1 G_j + e2 G_k) T_q (j <= k) of the order-2 loss:
 // (I + e1 G_j + e2 G_k + e1 e2 (G_j G_k + G_k G_j) / 2) T_q, exact with e1^2 = e2^2 = 0; G_j the
-// generators of the left twist (phi then rho). Out: [pair][element][a, e1, e2, e1 e2] as float.
-static void hess_poses(const double* Tq, float* out) {
+// generators of the left twist (phi then rho). Out: [pair][element][a, e1, e2, e1 e2] in R, with the e1
+// and e2 parts scaled by the step h and the e1 e2 part by h^2 (h = 1 for the truncated FP32 arithmetic;
+// a tiny h for the full bicomplex FP64 path, whose dropped i1^2, i2^2 terms are O(h^2) in the real part).
+template <typename R>
+static void hess_poses(const double* Tq, R* out, double h = 1.0) {
   double G[6][4][4] = {};
   for (int j = 0; j < 3; ++j) {  // [e_j]x
     const int a = (j + 1) % 3, b = (j + 2) % 3;
@@ -794,11 +798,11 @@ static void hess_poses(const double* Tq, float* out) {
       mul(S, T, ST);
       for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 4; ++c) {
-          float* o = out + 4 * (12 * q + 4 * r + c);
-          o[0] = (float)T[r][c];
-          o[1] = (float)GjT[r][c];
-          o[2] = (float)GkT[r][c];
-          o[3] = (float)ST[r][c];
+          R* o = out + 4 * (12 * q + 4 * r + c);
+          o[0] = (R)T[r][c];
+          o[1] = (R)(h * GjT[r][c]);
+          o[2] = (R)(h * GkT[r][c]);
+          o[3] = (R)(h * h * ST[r][c]);
         }
     }
 }
@@ -862,6 +866,66 @@ extern "C" xslam_status xslam_grad(xslam_t h, const float* query_depth, const do
   if (loss) *loss = h->h_result[kResSys];
   if (grad)
     for (int j = 0; j < 6; ++j) grad[j] = h->h_result[kResSys + 1 + j];
+  return st;
+}
+
+extern "C" xslam_status xslam_grad_tsdf(xslam_t h, const float* query_depth, const double* T_q, int order,
+                                        double* loss, double* grad, double* hess, long long* n_voxels) {
+  if (!h || !query_depth || !T_q) return fail(h, XSLAM_EINVAL, "NULL argument");
+  if (order != 1 && order != 2) return fail(h, XSLAM_EINVAL, "order must be 1 or 2");
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(T_q[i])) return fail(h, XSLAM_EINVAL, "T_q has a non-finite entry");
+  float hp[21 * 12 * 4];
+  hess_poses(T_q, hp);
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  CU(cudaMemcpyAsync(h->hess_poses, hp, sizeof(hp), cudaMemcpyHostToDevice, h->s));
+  CU(cudaMemcpyAsync(h->pose_tmp, T_q, sizeof(double) * 12, cudaMemcpyHostToDevice, h->s));
+  if ((st = copy_depth(h, query_depth, 1)) != XSLAM_OK) return st;
+  CU(launch_prepare(h->p, h->b, 1, h->s));
+  const int nblk = std::max(1, std::min(fuse_tile_count(h->p), 4 * h->nsm));
+  CU(launch_tsdf_hess(h->p, h->b, h->b.pyr[0], h->pose_tmp, h->hess_poses, order, h->b.result + kResSys, nblk,
+                      h->s));
+  CU(cudaMemcpyAsync(h->h_result, h->b.result, sizeof(double) * kResLen, cudaMemcpyDeviceToHost, h->s));
+  st = leave(h);
+  CU(cudaStreamSynchronize(h->s));
+  const double* r = h->h_result + kResSys;
+  if (loss) *loss = r[0];
+  if (grad)
+    for (int j = 0; j < 6; ++j) grad[j] = r[1 + j];
+  if (hess)
+    for (int q = 0; q < 21; ++q) hess[q] = r[7 + q];
+  if (n_voxels) *n_voxels = (long long)r[28];
+  return st;
+}
+
+extern "C" xslam_status xslam_grad_tsdf_plain64(xslam_t h, const float* query_depth, const double* T_q,
+                                                double* loss, double* grad, double* hess, long long* n_voxels) {
+  if (!h || !query_depth || !T_q) return fail(h, XSLAM_EINVAL, "NULL argument");
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(T_q[i])) return fail(h, XSLAM_EINVAL, "T_q has a non-finite entry");
+  constexpr double kStep = 1e-20;
+  double hp[21 * 12 * 4];
+  hess_poses(T_q, hp, kStep);
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  CU(cudaMemcpyAsync(h->hess_poses64, hp, sizeof(hp), cudaMemcpyHostToDevice, h->s));
+  CU(cudaMemcpyAsync(h->pose_tmp, T_q, sizeof(double) * 12, cudaMemcpyHostToDevice, h->s));
+  if ((st = copy_depth(h, query_depth, 1)) != XSLAM_OK) return st;
+  CU(launch_prepare(h->p, h->b, 1, h->s));
+  const int nblk = std::max(1, std::min(fuse_tile_count(h->p), 4 * h->nsm));
+  CU(launch_tsdf_hess64(h->p, h->b, h->b.pyr[0], h->pose_tmp, h->hess_poses64, kStep, h->b.result + kResSys, nblk,
+                        h->s));
+  CU(cudaMemcpyAsync(h->h_result, h->b.result, sizeof(double) * kResLen, cudaMemcpyDeviceToHost, h->s));
+  st = leave(h);
+  CU(cudaStreamSynchronize(h->s));
+  const double* r = h->h_result + kResSys;
+  if (loss) *loss = r[0];
+  if (grad)
+    for (int j = 0; j < 6; ++j) grad[j] = r[1 + j];
+  if (hess)
+    for (int q = 0; q < 21; ++q) hess[q] = r[7 + q];
+  if (n_voxels) *n_voxels = (long long)r[28];
   return st;
 }
 

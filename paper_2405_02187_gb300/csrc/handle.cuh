@@ -25,6 +25,7 @@ struct xslam_s {
   int* d_index = nullptr;
   double* pose_tmp = nullptr;  // scratch pose lanes (raycast / grad)
   float* hess_poses = nullptr;  // the 21 truncated-bicomplex start poses of xslam_grad order 2
+  double* hess_poses64 = nullptr;  // the 21 bicomplex start poses (h = 1e-20) of the plain FP64 TSDF Hessian
   float* model_q = nullptr;    // scratch model maps of xslam_grad (7 lanes)
   double* h_result = nullptr;  // pinned host staging
   int* h_status = nullptr;

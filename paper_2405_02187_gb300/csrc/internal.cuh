@@ -165,6 +165,18 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // ---------------------------------------------------------------------------------------------
 cudaError_t launch_prepare(const Params& p, const Buffers& b, int levels, cudaStream_t s);
 cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s);
+// The fusion tile list (Buffers::tiles, tile_ctr) of the frame pose `pose` (device, 12 doubles); the
+// consumer of the list clears the counters.
+cudaError_t launch_fuse_tiles(const Params& p, const Buffers& b, const double* pose, cudaStream_t s);
+// The TSDF-difference relocalisation loss of the depth map `depth` fused at `pose`, with its gradient
+// and Hessian (order 2) or gradient (order 1) from the 21 truncated-bicomplex poses `poses`: out[29] =
+// E, g[6], H[21], updated-voxel count (tsdf_loss.cu).
+cudaError_t launch_tsdf_hess(const Params& p, const Buffers& b, const float* depth, const double* pose,
+                             const float* poses, int order, double* out, int nblk, cudaStream_t s);
+// The same loss, gradient and Hessian in the plain FP64 bicomplex arithmetic (full products, step h
+// folded into the 21 start poses `poses`).
+cudaError_t launch_tsdf_hess64(const Params& p, const Buffers& b, const float* depth, const double* pose,
+                               const double* poses, double h, double* out, int nblk, cudaStream_t s);
 int fuse_tile_count(const Params& p);
 cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose, float* depth,
                            float* vmap, float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s);

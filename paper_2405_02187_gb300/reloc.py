@@ -3,9 +3,10 @@ a query depth frame over its pose, by gradient descent, by nonlinear conjugate g
 optimisers of Sec. 6's ICP comparison, "High order ICP") or by Newton's method with the paper's switch
 (gradient direction while E exceeds a threshold eta, Newton direction -H^-1 g below it).
 
-Every loss, gradient and Hessian comes from xslam_grad (orders 1 and 2, computed on the GPU); this
-module holds only the host-side iteration: 6x6 solves, the SE(3) exponential of the step, and the
-step-size control.
+Two losses: the point-to-plane reading (xslam_grad) and the paper's TSDF difference, the sum of squared
+changes the query's surface update would make to the map (xslam_grad_tsdf). Every loss, gradient and
+Hessian comes from those calls (orders 1 and 2, computed on the GPU); this module holds only the
+host-side iteration: 6x6 solves, the SE(3) exponential of the step, and the step-size control.
 """
 from __future__ import annotations
 
@@ -56,12 +57,24 @@ class Result:
     evaluations: int
 
 
-def _nlcg(handle, depth, T, iters, tol, step0, trace):
+def _evaluator(handle, loss):
+    """(depth, T, order) -> (E, g) for order 1, (E, g, H) for order 2, of the named loss."""
+    if loss == "point_to_plane":
+        return handle.grad
+    if loss == "tsdf":
+        def ev(depth, T, order=1):
+            E, g, H, _ = handle.grad_tsdf(depth, T, order=order)
+            return (E, g) if order == 1 else (E, g, H)
+        return ev
+    raise ValueError(f"unknown loss {loss!r}")
+
+
+def _nlcg(ev, depth, T, iters, tol, step0, trace):
     """Polak-Ribiere+ conjugate directions (restarted when not a descent direction). The line search
     along d evaluates a trial step a, fits the parabola through E(0), E'(0) = g.d and E(a), and takes
     its minimiser if the Armijo condition E <= E(0) + 1e-4 a g.d holds there, else the trial step if it
     holds, else halves the trial step. The next trial step is twice the last accepted one."""
-    E, g = handle.grad(depth, T, order=1)
+    E, g = ev(depth, T, order=1)
     evals = 1
     d = -g
     a = step0 / max(np.linalg.norm(g), 1e-30)
@@ -73,13 +86,13 @@ def _nlcg(handle, depth, T, iters, tol, step0, trace):
         best = None
         for _ in range(16):
             Ta = compose(se3_exp(a * d), T)
-            Ea, ga = handle.grad(depth, Ta, order=1)
+            Ea, ga = ev(depth, Ta, order=1)
             evals += 1
             curv = (Ea - E - gd * a) / (a * a)
             if curv > 0.0:
                 a2 = -gd / (2.0 * curv)
                 T2 = compose(se3_exp(a2 * d), T)
-                E2, g2 = handle.grad(depth, T2, order=1)
+                E2, g2 = ev(depth, T2, order=1)
                 evals += 1
                 if E2 <= E + 1e-4 * a2 * gd and E2 <= Ea:
                     best = (a2, T2, E2, g2)
@@ -103,21 +116,25 @@ def _nlcg(handle, depth, T, iters, tol, step0, trace):
     return Result(T, it, float(E), 0, evals)
 
 
-def relocalise(handle, depth, T_init, method="newton", eta=1e-3, iters=30, tol=1e-6, step0=0.01, trace=None):
+def relocalise(handle, depth, T_init, method="newton", eta=1e-3, iters=30, tol=1e-6, step0=0.01, trace=None,
+               loss="point_to_plane"):
     """Minimise E(T) from T_init. handle: an XSlam holding the map; depth: the query's CUDA depth.
     method "gd": steps -a g with a backtracking/expanding step size (a g at most step0 at first);
     method "nlcg": nonlinear conjugate gradients (Polak-Ribiere+, Armijo backtracking);
     method "newton": -H^-1 g when E <= eta and H is positive definite (halved until E decreases),
     otherwise the gradient step. Stops when a step's norm falls below tol. trace (a list, optional)
-    receives (T, E) after every iteration."""
+    receives (T, E) after every iteration. loss: "point_to_plane" (mean squared point-to-plane residual
+    against the map ray cast at T) or "tsdf" (sum of squared TSDF changes of the query's surface update
+    at T; eta is then on that sum)."""
     T = np.asarray(T_init, np.float64)
+    ev = _evaluator(handle, loss)
     if method == "nlcg":
-        return _nlcg(handle, depth, T, iters, tol, step0, trace)
+        return _nlcg(ev, depth, T, iters, tol, step0, trace)
     evals = 0
     if method == "newton":
-        E, g, H = handle.grad(depth, T, order=2)
+        E, g, H = ev(depth, T, order=2)
     else:
-        E, g = handle.grad(depth, T, order=1)
+        E, g = ev(depth, T, order=1)
     evals += 1
     alpha = step0 / max(np.linalg.norm(g), 1e-30)
     n_newton = 0
@@ -135,7 +152,7 @@ def relocalise(handle, depth, T_init, method="newton", eta=1e-3, iters=30, tol=1
             s = 1.0
             for _ in range(6):
                 T1 = compose(se3_exp(s * direction), T)
-                E1, g1, H1 = handle.grad(depth, T1, order=2)
+                E1, g1, H1 = ev(depth, T1, order=2)
                 evals += 1
                 if E1 <= E:
                     step = s * direction
@@ -149,9 +166,9 @@ def relocalise(handle, depth, T_init, method="newton", eta=1e-3, iters=30, tol=1
                 step = -alpha * g
                 T1 = compose(se3_exp(step), T)
                 if method == "newton":
-                    E1, g1, H1 = handle.grad(depth, T1, order=2)
+                    E1, g1, H1 = ev(depth, T1, order=2)
                 else:
-                    E1, g1 = handle.grad(depth, T1, order=1)
+                    E1, g1 = ev(depth, T1, order=1)
                 evals += 1
                 if E1 <= E:
                     T, E, g = T1, E1, g1

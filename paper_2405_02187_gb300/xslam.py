@@ -63,6 +63,10 @@ SYMBOLS = [
     ("xslam_raycast", ctypes.c_int, [ctypes.c_void_p, _c_double_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("xslam_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_double_p, ctypes.c_int, _c_double_p,
                                   _c_double_p, _c_double_p]),
+    ("xslam_grad_tsdf", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_double_p, ctypes.c_int, _c_double_p,
+                                       _c_double_p, _c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
+    ("xslam_grad_tsdf_plain64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_double_p, _c_double_p,
+                                               _c_double_p, _c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
     ("xslam_read_tsdf", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("xslam_set_lanes", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Seed), ctypes.c_int]),
     ("xslam_set_pose_lanes", ctypes.c_int, [ctypes.c_void_p, _c_double_p]),
@@ -303,6 +307,38 @@ class XSlam:
             Hm[(iu[1], iu[0])] = H
             return loss.value, g, Hm
         return loss.value, g
+
+    def grad_tsdf(self, query_depth, T_q, order=2):
+        """TSDF-difference relocalisation loss (E, g[6], H 6x6 or None, observed voxels updated) at T_q."""
+        T_q = np.ascontiguousarray(T_q, np.float64).reshape(12)
+        loss = ctypes.c_double(0)
+        n = ctypes.c_longlong(0)
+        g = np.zeros(6)
+        H = np.zeros(21)
+        self._check(self.lib.xslam_grad_tsdf(self.h, _dev(query_depth), _dptr(T_q), int(order), ctypes.byref(loss),
+                                             _dptr(g), _dptr(H), ctypes.byref(n)))
+        Hm = None
+        if order == 2:
+            Hm = np.zeros((6, 6))
+            iu = np.triu_indices(6)
+            Hm[iu] = H
+            Hm[(iu[1], iu[0])] = H
+        return loss.value, g, Hm, n.value
+
+    def grad_tsdf_plain64(self, query_depth, T_q):
+        """The same (E, g, H, updated voxels) by the plain FP64 bicomplex path (full products, h = 1e-20)."""
+        T_q = np.ascontiguousarray(T_q, np.float64).reshape(12)
+        loss = ctypes.c_double(0)
+        n = ctypes.c_longlong(0)
+        g = np.zeros(6)
+        H = np.zeros(21)
+        self._check(self.lib.xslam_grad_tsdf_plain64(self.h, _dev(query_depth), _dptr(T_q), ctypes.byref(loss),
+                                                     _dptr(g), _dptr(H), ctypes.byref(n)))
+        Hm = np.zeros((6, 6))
+        iu = np.triu_indices(6)
+        Hm[iu] = H
+        Hm[(iu[1], iu[0])] = H
+        return loss.value, g, Hm, n.value
 
     def read_tsdf(self, lane, out):
         self._check(self.lib.xslam_read_tsdf(self.h, int(lane), _dev(out)))
