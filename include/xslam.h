@@ -174,7 +174,7 @@ xslam_status xslam_grad(xslam_t h, const float* query_depth, const double T_q[12
  * Derivatives are with respect to a left twist xi of T_q (phi then rho), from the bicomplex step of
  * Sec. 3 in truncated arithmetic with the real pose's update decisions (voxels updated, voxels clamped
  * at F_D = 1, which carry no derivative, and the pixel cells):
- * order 1: *loss and grad[6] (hess gets the 6 diagonal entries, the rest 0);
+ * order 1: *loss and grad[6] (hess gets zeros);
  * order 2: *loss, grad[6] and hess[21], the upper triangle row by row as in xslam_grad.
  * *n_voxels = the number of observed voxels the query updates (the terms of the sum). Any handle; any
  * output pointer may be NULL.

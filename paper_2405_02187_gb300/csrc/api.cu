@@ -883,7 +883,8 @@ extern "C" xslam_status xslam_grad_tsdf(xslam_t h, const float* query_depth, con
   CU(cudaMemcpyAsync(h->pose_tmp, T_q, sizeof(double) * 12, cudaMemcpyHostToDevice, h->s));
   if ((st = copy_depth(h, query_depth, 1)) != XSLAM_OK) return st;
   CU(launch_prepare(h->p, h->b, 1, h->s));
-  const int nblk = std::max(1, std::min(fuse_tile_count(h->p), 4 * h->nsm));
+  // two resident blocks per SM take tiles from the list by work stealing
+  const int nblk = std::max(1, std::min(fuse_tile_count(h->p), 2 * h->nsm));
   CU(launch_tsdf_hess(h->p, h->b, h->b.pyr[0], h->pose_tmp, h->hess_poses, order, h->b.result + kResSys, nblk,
                       h->s));
   CU(cudaMemcpyAsync(h->h_result, h->b.result, sizeof(double) * kResLen, cudaMemcpyDeviceToHost, h->s));

@@ -183,3 +183,51 @@ def relocalise(handle, depth, T_init, method="newton", eta=1e-3, iters=30, tol=1
         if not accepted or np.linalg.norm(step) < tol:
             break
     return Result(T, it, float(E), n_newton, evals)
+
+
+def main(argv=None):
+    """Evaluate the TSDF-difference loss with its Hessian on a room map (the command of its profile):
+    a dims^3 map from a frames-long 640x480 walk, the last frame as the query 1 cm / 0.5 degrees off."""
+    import argparse
+    import time
+
+    import torch
+
+    from . import synth, xslam
+
+    ap = argparse.ArgumentParser(description="evaluate the TSDF-difference relocalisation loss")
+    ap.add_argument("--dims", type=int, default=256)
+    ap.add_argument("--voxel", type=float, default=0.01)
+    ap.add_argument("--frames", type=int, default=20)
+    ap.add_argument("--evals", type=int, default=5)
+    ap.add_argument("--plain64", action="store_true", help="also evaluate the plain FP64 path once")
+    a = ap.parse_args(argv)
+    wl = synth.room_walk(seed=3, frames=a.frames, dims=a.dims, voxel=a.voxel, device="cuda", resident=True)
+    cfg = xslam.default_config()
+    cfg.icp_levels = len(wl.icp_iters)
+    for i, it in enumerate(wl.icp_iters):
+        cfg.icp_iters[i] = it
+    cfg.depth_min_m, cfg.depth_max_m, cfg.bilateral = wl.depth_min, wl.depth_max, int(wl.bilateral)
+    x = xslam.XSlam(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, cfg, max_lanes=0)
+    x.set_pose(wl.poses[0])
+    for k in range(a.frames - 1):
+        x.frame(wl.depth[k], [], outputs=False)
+    x.sync()
+    k = a.frames - 1
+    T = compose(se3_exp(np.array([0.005, -0.005, 0.0, 0.01, 0.0, 0.0])), wl.poses[k])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.evals):
+        E, g, H, n = x.grad_tsdf(wl.depth[k], T, order=2)
+    ms = (time.perf_counter() - t0) / a.evals * 1e3
+    print(f"E {E:.6g} |g| {np.linalg.norm(g):.6g} voxels {n} ms/evaluation {ms:.3f} (host round trip included)")
+    if a.plain64:
+        E64, g64, H64, n64 = x.grad_tsdf_plain64(wl.depth[k], T)
+        print(f"plain FP64: E {E64:.6g} voxels {n64} gradient rel err "
+              f"{np.linalg.norm(g - g64) / np.linalg.norm(g64):.3g} Hessian rel err "
+              f"{np.linalg.norm(H - H64) / np.linalg.norm(H64):.3g}")
+    x.close()
+
+
+if __name__ == "__main__":
+    main()
