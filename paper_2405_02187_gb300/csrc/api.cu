@@ -128,7 +128,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   memset(&p, 0, sizeof(p));
   p.nx = nx; p.ny = ny; p.nz = nz;
   p.nbx = (nx + kBrick - 1) / kBrick; p.nby = (ny + kBrick - 1) / kBrick; p.nbz = (nz + kBrick - 1) / kBrick;
-  p.voxel = voxel_m; p.mu = trunc_m;
+  p.voxel = voxel_m; p.mu = trunc_m; p.inv_mu = 1.f / trunc_m;
   p.ox = origin_m[0]; p.oy = origin_m[1]; p.oz = origin_m[2];
   p.w_max = c.w_max;
   p.fx = K->fx; p.fy = K->fy; p.cx = K->cx; p.cy = K->cy;

@@ -28,6 +28,7 @@ constexpr int kFuseThreads = kBX * kBY * kBZ;  // a thread per voxel of a tile
 // Update voxel (i, j, k) if the frame observes it; returns whether it did. NL = 1 + K lanes.
 template <int NL>
 __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restrict__ D, const float (*sT)[12],
+                                           const float (*sC)[3],
                                            float* __restrict__ F, float* __restrict__ Wt,
                                            float* __restrict__ F0lin, int i, int j, int k, size_t n, size_t v) {
   const float* T = sT[0];
@@ -75,16 +76,15 @@ __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restr
 #pragma unroll
   for (int l = 1; l < NL; ++l) {
     const float* Tl = sT[l];
-    // p_c' = dR^T (p - t) - R^T dt
-    const float ex = Tl[3], ey = Tl[7], ez = Tl[11];
-    const float pcx_l = Tl[0] * dx + Tl[4] * dy + Tl[8] * dz - (T[0] * ex + T[4] * ey + T[8] * ez);
-    const float pcy_l = Tl[1] * dx + Tl[5] * dy + Tl[9] * dz - (T[1] * ex + T[5] * ey + T[9] * ez);
-    const float pcz_l = Tl[2] * dx + Tl[6] * dy + Tl[10] * dz - (T[2] * ex + T[6] * ey + T[10] * ez);
+    // p_c' = dR^T (p - t) - R^T dt, the second term a per-lane constant
+    const float pcx_l = Tl[0] * dx + Tl[4] * dy + Tl[8] * dz + sC[l][0];
+    const float pcy_l = Tl[1] * dx + Tl[5] * dy + Tl[9] * dz + sC[l][1];
+    const float pcz_l = Tl[2] * dx + Tl[6] * dy + Tl[10] * dz + sC[l][2];
     const float x_l = p.fx * (pcx_l - qx * pcz_l) * invz;
     const float y_l = p.fy * (pcy_l - qy * pcz_l) * invz;
     const float L_l = dLda * x_l + dLdb * y_l + p.dD[l];
     const float sdf_l = L_l - pcz_l;
-    const float FD_l = clamp ? 0.f : (sdf_l - FD * p.dmu[l]) / p.mu;
+    const float FD_l = clamp ? 0.f : (sdf_l - FD * p.dmu[l]) * p.inv_mu;
     F[(size_t)l * n + v] = (w * fl[l] + FD_l) * inv;
   }
   return true;
@@ -144,16 +144,22 @@ __global__ void __launch_bounds__(256) k_fuse_tiles(Params p, const double* __re
 // 128 consecutive bytes of every plane. The last block to finish clears the list counters for the next
 // launch.
 template <int NL>
-__global__ void __launch_bounds__(kFuseThreads) k_integrate(Params p, const float* __restrict__ D,
+__global__ void __launch_bounds__(kFuseThreads, NL <= 9 ? 2 : 1) k_integrate(Params p, const float* __restrict__ D,
                                                         const double* __restrict__ pose, float* __restrict__ F,
                                                         float* __restrict__ Wt, float* __restrict__ F0lin,
                                                         unsigned long long* __restrict__ stats,
                                                         const int* __restrict__ tiles, unsigned* __restrict__ ctr) {
   pdl_enter();
   __shared__ float sT[NL][12];
+  __shared__ float sC[NL][3];  // -R^T dt of each lane: the voxel-independent part of its p_c tangent
   __shared__ bool s_last;
   const int tid = threadIdx.x;
   for (int i = tid; i < NL * 12; i += blockDim.x) sT[i / 12][i % 12] = (float)pose[i];
+  if (tid < NL * 3) {
+    const int l = tid / 3, c = tid % 3;
+    sC[l][c] = -((float)pose[c] * (float)pose[12 * l + 3] + (float)pose[4 + c] * (float)pose[12 * l + 7] +
+                 (float)pose[8 + c] * (float)pose[12 * l + 11]);
+  }
   __syncthreads();
   const unsigned count = ctr[0];
   const int ntx = (p.nx + kBX - 1) / kBX, nty = (p.ny + kBY - 1) / kBY;
@@ -165,7 +171,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_integrate(Params p, const floa
     const int i = (t % ntx) * kBX + cx, j = ((t / ntx) % nty) * kBY + cy, k = (t / (ntx * nty)) * kBZ + cz;
     // the tile is brick t, whose voxel tid sits at t 512 + tid
     if (i < p.nx && j < p.ny && k < p.nz)
-      cnt += fuse_voxel<NL>(p, D, sT, F, Wt, F0lin, i, j, k, n, ((size_t)t << 9) + tid);
+      cnt += fuse_voxel<NL>(p, D, sT, sC, F, Wt, F0lin, i, j, k, n, ((size_t)t << 9) + tid);
   }
   // updated-voxel count: warp sums, one atomic per warp
 #pragma unroll

@@ -44,6 +44,7 @@ struct Params {
   float icp_newton_eta;     // Newton ICP: mean squared residual (m^2) below which the Hessian is used
   float icp_stop;           // > 0: a level ends after a real step |x| below this (twist norm)
   int m0, m1;               // ray samples alpha_m = m * ray_step, m0 <= m <= m1
+  float inv_mu;             // 1 / mu (the lanes' tangents multiply by it)
 };
 
 // Device buffers owned by a handle.
