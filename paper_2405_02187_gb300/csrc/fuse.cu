@@ -70,9 +70,19 @@ __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restr
   F0lin[(size_t)i + (size_t)p.nx * ((size_t)j + (size_t)p.ny * k)] = Fn;
   Wt[v] = (p.w_max > 0.f) ? fminf(w1, p.w_max) : w1;
 
-  // tangents of L with respect to the pixel coordinates
+  if (clamp) {  // F_D = 1 whatever the lane: no tangent
+#pragma unroll
+    for (int l = 1; l < NL; ++l) F[(size_t)l * n + v] = w * fl[l] * inv;
+    return true;
+  }
+  // The tangent of sdf = L(x) - z_c is linear in the lane's p_c': with x' = fx (p_cx' - q_x p_cz') / z,
+  // y' = fy (p_cy' - q_y p_cz') / z and the bilinear L's slopes dL/da, dL/db,
+  // sdf' = c_x p_cx' + c_y p_cy' + c_z p_cz' + D', c_x = dL/da fx / z, c_y = dL/db fy / z,
+  // c_z = -(c_x q_x + c_y q_y) - 1.
   const float dLda = (1.f - bb) * (d10 - d00) + bb * (d11 - d01);
   const float dLdb = (1.f - a) * (d01 - d00) + a * (d11 - d10);
+  const float c_x = dLda * p.fx * invz, c_y = dLdb * p.fy * invz;
+  const float c_z = -(c_x * qx + c_y * qy) - 1.f;
 #pragma unroll
   for (int l = 1; l < NL; ++l) {
     const float* Tl = sT[l];
@@ -80,11 +90,8 @@ __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restr
     const float pcx_l = Tl[0] * dx + Tl[4] * dy + Tl[8] * dz + sC[l][0];
     const float pcy_l = Tl[1] * dx + Tl[5] * dy + Tl[9] * dz + sC[l][1];
     const float pcz_l = Tl[2] * dx + Tl[6] * dy + Tl[10] * dz + sC[l][2];
-    const float x_l = p.fx * (pcx_l - qx * pcz_l) * invz;
-    const float y_l = p.fy * (pcy_l - qy * pcz_l) * invz;
-    const float L_l = dLda * x_l + dLdb * y_l + p.dD[l];
-    const float sdf_l = L_l - pcz_l;
-    const float FD_l = clamp ? 0.f : (sdf_l - FD * p.dmu[l]) * p.inv_mu;
+    const float sdf_l = c_x * pcx_l + c_y * pcy_l + c_z * pcz_l + p.dD[l];
+    const float FD_l = (sdf_l - FD * p.dmu[l]) * p.inv_mu;
     F[(size_t)l * n + v] = (w * fl[l] + FD_l) * inv;
   }
   return true;
