@@ -385,6 +385,18 @@ def run_ours(args, rank, world, local_rank):
                     peak_source=f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
                     bytes_per_launch=round(bytes_launch), ms_per_launch=round(ms_launch, 5))
     stage_ms = {s: round(v[0] / nprof, 4) for s, v in stages.items()}
+    # the same roofline for each of the three stages (the dominant one is `roofline` itself)
+    roofline_stages = {}
+    for st in ("icp", "integrate", "raycast"):
+        n_units = stages[st][1] // 2 if st == "raycast" else stages[st][1]
+        if n_units <= 0 or stages[st][0] <= 0.0:
+            continue
+        ms_st = stages[st][0] / n_units
+        b_st = algorithmic_bytes(st, wl, L, per_frame)
+        a_st = b_st / (ms_st * 1e-3) / 1e9
+        roofline_stages[st] = dict(kernel=KERNEL_NAME[st], achieved=round(a_st, 1), frac=round(a_st / peak, 4),
+                                   traffic=ncu_traffic(st, wl.name), bytes_per_launch=round(b_st),
+                                   ms_per_launch=round(ms_st, 5))
 
     # ---- end to end: pinned host depth in, pose + derivative block out, every frame ----
     host = torch.empty((nf,) + tuple(wl.depth.shape[1:]), dtype=torch.float32, pin_memory=True)
@@ -485,7 +497,8 @@ def run_ours(args, rank, world, local_rank):
                                f"{np.prod(wl.dims) * 4 * (L + 1) / 1e6:.0f} MB",
                             tracking_failures=int(n_fail)),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(round(launches_per_frame * K)),
-                clocks=clk, stage_ms_per_frame=stage_ms, grad_rel_err_vs_oracle=grad_err,
+                clocks=clk, stage_ms_per_frame=stage_ms, roofline_stages=roofline_stages,
+                grad_rel_err_vs_oracle=grad_err,
                 plain_fp64=plain, uncomplexified_fp32=real32, batched=batched, second_order=second, newton_icp=newton,
                 learned_proposal=learned,
                 per_frame=dict(fused_voxels=round(per_frame["fused"]), surface_pixels=round(per_frame["hits"])))

@@ -176,8 +176,9 @@ xslam_status xslam_grad(xslam_t h, const float* query_depth, const double T_q[12
  * at F_D = 1, which carry no derivative, and the pixel cells):
  * order 1: *loss and grad[6] (hess gets zeros);
  * order 2: *loss, grad[6] and hess[21], the upper triangle row by row as in xslam_grad.
- * *n_voxels = the number of observed voxels the query updates (the terms of the sum). Any handle; any
- * output pointer may be NULL.
+ * *n_voxels = the number of observed voxels the query updates (the terms of the sum). The FP32 sums are
+ * taken in an order that depends on the blocks' scheduling: repeated calls agree to rounding, not bit for
+ * bit. Any handle; any output pointer may be NULL.
  * Errors: XSLAM_EINVAL (NULL input, order not 1 or 2, non-finite T_q).
  */
 xslam_status xslam_grad_tsdf(xslam_t h, const float* query_depth, const double T_q[12], int order, double* loss,

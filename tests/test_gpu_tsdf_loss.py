@@ -147,3 +147,52 @@ def test_plain_fp64_path(mapped, off):
     assert rel_err(g64, go) < 1e-4 and rel_err(H64, Ho) < 1e-4
     E, g, H, n = x.grad_tsdf(q, T, order=2)
     assert rel_err(g, g64) < 1e-3 and rel_err(H, H64) < 1e-3
+
+
+def test_ragged_volume_matches_oracle():
+    """A volume whose sides are not multiples of the 8^3 brick and a 44x36 image: partial bricks at
+    every face, the last pixel row and column."""
+    base = synth.tiny(frames=3, n=28, width=44, height=36)
+    dims = (28, 26, 25)
+    origin = tuple(-d * base.voxel / 2 for d in dims)
+    wl = synth.Workload(base.name + "_ragged", base.intr, dims, base.voxel, base.trunc, origin, base.poses,
+                        base.depth, base.scene, base.seed, icp_iters=base.icp_iters)
+    x = make_handle(wl, max_lanes=0)
+    x.set_pose(wl.poses[0])
+    for k in range(2):
+        x.frame(torch.tensor(wl.depth[k], device="cuda"), [])
+    buf = torch.empty(x.n_vox, device="cuda")
+    F = x.read_tsdf(0, buf).cpu().numpy().astype(np.float64)
+    W = x.read_tsdf(-1, buf).cpu().numpy().astype(np.float64)
+    q = torch.tensor(wl.depth[2], device="cuda")
+    T = se3.compose(se3.se3_exp(0.5 * OFFSETS[0]), wl.poses[2])
+    E, g, H, n = x.grad_tsdf(q, T, order=2)
+    E64, g64, H64, n64 = x.grad_tsdf_plain64(q, T)
+    x.close()
+    Eo, go, Ho, no = _oracle(wl, F, W, T, wl.depth[2])
+    print(E, Eo, n, no, rel_err(g, go), rel_err(H, Ho))
+    assert no > 100 and abs(n - no) <= 2 and abs(n64 - no) <= 2
+    assert abs(E - Eo) <= 2e-3 * Eo and rel_err(g, go) < 2e-3 and rel_err(H, Ho) < 2e-3
+    assert abs(E64 - Eo) <= 1e-4 * Eo and rel_err(g64, go) < 1e-4 and rel_err(H64, Ho) < 1e-4
+
+
+def test_degenerate_queries(mapped):
+    """A query with no valid depth, and a pose looking away from the map: nothing is updated, so the
+    loss, gradient and Hessian are exactly zero on both paths; the handle stays usable."""
+    wl, x, _, _ = mapped
+    empty = torch.zeros_like(torch.tensor(wl.depth[4], device="cuda"))
+    E, g, H, n = x.grad_tsdf(empty, wl.poses[4], order=2)
+    assert n == 0 and E == 0.0 and not g.any() and not H.any()
+    E64, g64, H64, n64 = x.grad_tsdf_plain64(empty, wl.poses[4])
+    assert n64 == 0 and E64 == 0.0 and not g64.any() and not H64.any()
+    # turned half a revolution about the vertical axis through the camera
+    away = se3.compose(wl.poses[4], np.concatenate([se3.se3_exp(np.array([0.0, np.pi, 0.0, 0.0, 0.0, 0.0]))[:, :3],
+                                                    np.zeros((3, 1))], 1))
+    q = torch.tensor(wl.depth[4], device="cuda")
+    E, g, H, n = x.grad_tsdf(q, away, order=2)
+    Ea, _, _, na = x.grad_tsdf(q, wl.poses[4], order=2)
+    assert na > 1000
+    assert n < 0.01 * na
+    # the handle is unchanged; blocks take tiles by work stealing, so FP32 sums may differ in rounding order
+    E2, g2, H2, n2 = x.grad_tsdf(q, wl.poses[4], order=2)
+    assert n2 == na and abs(E2 - Ea) <= 1e-6 * Ea
