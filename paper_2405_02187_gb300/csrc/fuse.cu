@@ -207,24 +207,18 @@ int fuse_tile_count(const Params& p) {
 }
 
 cudaError_t launch_fuse_tiles(const Params& p, const Buffers& b, const double* pose, cudaStream_t s) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  int dev = 0, sms = 0;  // the current device's SM count (queried per call: a handle may live on any device)
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int nt = fuse_tile_count(p);
   return launch_pdl(k_fuse_tiles, dim3(std::min((nt + 255) / 256, 4 * sms)), dim3(256), 0, s, p, pose, b.tiles,
                     b.tile_ctr);
 }
 
 cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  int dev = 0, sms = 0;  // the current device's SM count (queried per call: a handle may live on any device)
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int nt = fuse_tile_count(p);
   cudaError_t e = launch_fuse_tiles(p, b, b.pose, s);
   if (e != cudaSuccess) return e;

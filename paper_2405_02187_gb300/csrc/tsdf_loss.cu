@@ -455,12 +455,9 @@ cudaError_t launch_tsdf_hess(const Params& p, const Buffers& b, const float* dep
                              const float* poses, int order, double* out, int nblk, cudaStream_t s) {
   cudaError_t e = launch_fuse_tiles(p, b, pose, s);
   if (e != cudaSuccess) return e;
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(k_tsdf_hess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTsdfSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // per device, so set on every call (a host-side attribute write)
+  e = cudaFuncSetAttribute(k_tsdf_hess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTsdfSmem);
+  if (e != cudaSuccess) return e;
   return launch_pdl(k_tsdf_hess, dim3(nblk), dim3(kThreads), kTsdfSmem, s, p, depth, (const float*)b.F,
                     (const float*)b.Wt, poses, order, (const int*)b.tiles, b.tile_ctr, b.partial, b.ticket, out);
 }
