@@ -80,3 +80,30 @@ def test_conjugate_gradients_beat_gradient_descent_and_newton_beats_both():
         assert all(b <= a + 1e-15 for a, b in zip(losses, losses[1:]))
     assert err["newton"] < 1e-6
     assert err["nlcg"] < 0.1 * err["gd"]
+
+
+class _TsdfOnly(_Quadratic):
+    """The same quadratic served only through the TSDF-loss call (E, g, H or None, voxel count)."""
+
+    def grad(self, depth, T, order=1):
+        raise AssertionError("the point-to-plane loss was called")
+
+    def grad_tsdf(self, depth, T, order=2):
+        E, g, H = _Quadratic.grad(self, depth, T, order=2)
+        return E, g, (H if order == 2 else None), 1000
+
+
+def test_the_tsdf_loss_routes_through_grad_tsdf():
+    rng = np.random.default_rng(3)
+    A = np.diag([0.5, 1.0, 2.0, 1.0, 0.7, 1.5])
+    T_star = reloc.se3_exp(rng.standard_normal(6) * 0.3)
+    T0 = reloc.compose(reloc.se3_exp(np.array([0.02, -0.01, 0.01, 0.03, -0.02, 0.01])), T_star)
+    for m in ("gd", "nlcg", "newton"):
+        r = reloc.relocalise(_TsdfOnly(A, T_star), None, T0, method=m, eta=np.inf, iters=30, loss="tsdf")
+        assert reloc.pose_error(r.T, T_star)[0] < 1e-3
+    try:
+        reloc.relocalise(_TsdfOnly(A, T_star), None, T0, loss="sdf")
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("an unknown loss name was accepted")
