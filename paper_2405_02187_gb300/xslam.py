@@ -246,6 +246,18 @@ class XSlam:
     def n_vox(self):
         return self.dims[0] * self.dims[1] * self.dims[2]
 
+    def _depth(self, t):
+        """Device pointer of a CUDA depth map, checked to hold H x W floats (the library reads that many)."""
+        if t is not None and t.numel() != self.W * self.H:
+            raise ValueError(f"depth has {t.numel()} values, expected {self.H} x {self.W}")
+        return _dev(t)
+
+    def _out(self, t, n):
+        """Device pointer of a CUDA output buffer, checked to hold at least n floats."""
+        if t is not None and t.numel() < n:
+            raise ValueError(f"output buffer has {t.numel()} values, needs {n}")
+        return _dev(t)
+
     # -- sequence API ----------------------------------------------------------------------
     def reset(self):
         self._check(self.lib.xslam_reset(self.h))
@@ -260,6 +272,9 @@ class XSlam:
         Returns (pose (3,4), dpose (K,3,4), dtwist (K,6), status) or status if outputs is False."""
         K = len(seeds)
         sd = _seeds(seeds)
+        n = depth.size if isinstance(depth, np.ndarray) else depth.numel()
+        if n != self.W * self.H:
+            raise ValueError(f"depth has {n} values, expected {self.H} x {self.W}")
         if isinstance(depth, np.ndarray):
             depth = np.ascontiguousarray(depth, np.float32)
             ptr, on_dev = ctypes.c_void_p(depth.ctypes.data), 0
@@ -291,14 +306,16 @@ class XSlam:
         if T is not None:
             T = np.ascontiguousarray(T, np.float64).reshape(-1)
             Tp = _dptr(T)
-        self._check(self.lib.xslam_raycast(self.h, Tp, _dev(depth), _dev(vmap), _dev(nmap)))
+        hw = self.W * self.H
+        self._check(self.lib.xslam_raycast(self.h, Tp, self._out(depth, hw), self._out(vmap, 3 * (1 + self.K) * hw),
+                                           self._out(nmap, 3 * (1 + self.K) * hw)))
 
     def grad(self, query_depth, T_q, order=1):
         T_q = np.ascontiguousarray(T_q, np.float64).reshape(12)
         loss = ctypes.c_double(0)
         g = np.zeros(6)
         H = np.zeros(21)
-        self._check(self.lib.xslam_grad(self.h, _dev(query_depth), _dptr(T_q), int(order), ctypes.byref(loss),
+        self._check(self.lib.xslam_grad(self.h, self._depth(query_depth), _dptr(T_q), int(order), ctypes.byref(loss),
                                         _dptr(g), _dptr(H)))
         if order == 2:
             Hm = np.zeros((6, 6))
@@ -315,7 +332,7 @@ class XSlam:
         n = ctypes.c_longlong(0)
         g = np.zeros(6)
         H = np.zeros(21)
-        self._check(self.lib.xslam_grad_tsdf(self.h, _dev(query_depth), _dptr(T_q), int(order), ctypes.byref(loss),
+        self._check(self.lib.xslam_grad_tsdf(self.h, self._depth(query_depth), _dptr(T_q), int(order), ctypes.byref(loss),
                                              _dptr(g), _dptr(H), ctypes.byref(n)))
         Hm = None
         if order == 2:
@@ -332,7 +349,7 @@ class XSlam:
         n = ctypes.c_longlong(0)
         g = np.zeros(6)
         H = np.zeros(21)
-        self._check(self.lib.xslam_grad_tsdf_plain64(self.h, _dev(query_depth), _dptr(T_q), ctypes.byref(loss),
+        self._check(self.lib.xslam_grad_tsdf_plain64(self.h, self._depth(query_depth), _dptr(T_q), ctypes.byref(loss),
                                                      _dptr(g), _dptr(H), ctypes.byref(n)))
         Hm = np.zeros((6, 6))
         iu = np.triu_indices(6)
@@ -341,7 +358,7 @@ class XSlam:
         return loss.value, g, Hm, n.value
 
     def read_tsdf(self, lane, out):
-        self._check(self.lib.xslam_read_tsdf(self.h, int(lane), _dev(out)))
+        self._check(self.lib.xslam_read_tsdf(self.h, int(lane), self._out(out, self.n_vox)))
         return out
 
     def profile(self, enable=True):
@@ -372,18 +389,21 @@ class XSlam:
         return T.reshape(1 + self.K, 3, 4)
 
     def write_tsdf(self, lane, t):
-        self._check(self.lib.xslam_write_tsdf(self.h, int(lane), _dev(t)))
+        self._check(self.lib.xslam_write_tsdf(self.h, int(lane), self._out(t, self.n_vox)))
 
     def measure(self, depth, level=0, out=None):
-        self._check(self.lib.xslam_measure(self.h, _dev(depth), int(level), _dev(out)))
+        n_out = (self.W >> int(level)) * (self.H >> int(level)) if 0 <= int(level) < 3 else 0
+        self._check(self.lib.xslam_measure(self.h, self._depth(depth), int(level), self._out(out, n_out)))
         return out
 
     def integrate(self, depth):
-        self._check(self.lib.xslam_integrate(self.h, _dev(depth)))
+        self._check(self.lib.xslam_integrate(self.h, self._depth(depth)))
 
     def set_model(self, depth, vmap, nmap, T_prev):
         T_prev = np.ascontiguousarray(T_prev, np.float64).reshape(-1)
-        self._check(self.lib.xslam_set_model(self.h, _dev(depth), _dev(vmap), _dev(nmap), _dptr(T_prev)))
+        n_map = 3 * (1 + self.K) * self.W * self.H
+        self._check(self.lib.xslam_set_model(self.h, self._depth(depth), self._out(vmap, n_map), self._out(nmap, n_map),
+                                             _dptr(T_prev)))
 
     def set_proposal(self, mlp, scale=None, judge_level=2):
         """Attach the learned proposal (an Mlp; None detaches) with its output scale (6 values)."""
@@ -449,6 +469,18 @@ class XSlamPlain:
     def n_vox(self):
         return self.dims[0] * self.dims[1] * self.dims[2]
 
+    def _depth(self, t):
+        """Device pointer of a CUDA depth map, checked to hold H x W floats (the library reads that many)."""
+        if t is not None and t.numel() != self.W * self.H:
+            raise ValueError(f"depth has {t.numel()} values, expected {self.H} x {self.W}")
+        return _dev(t)
+
+    def _out(self, t, n):
+        """Device pointer of a CUDA output buffer, checked to hold at least n floats."""
+        if t is not None and t.numel() < n:
+            raise ValueError(f"output buffer has {t.numel()} values, needs {n}")
+        return _dev(t)
+
     def set_pose(self, T):
         T = np.ascontiguousarray(T, np.float64).reshape(12)
         self._check(self.lib.xslam_plain_set_pose(self.h, _dptr(T)))
@@ -456,6 +488,9 @@ class XSlamPlain:
     def frame(self, depth, seeds=()):
         """Run one frame of every run; returns (pose (3,4), dpose (K,3,4), dtwist (K,6), status)."""
         K = len(seeds)
+        n = depth.size if isinstance(depth, np.ndarray) else depth.numel()
+        if n != self.W * self.H:
+            raise ValueError(f"depth has {n} values, expected {self.H} x {self.W}")
         if isinstance(depth, np.ndarray):
             depth = np.ascontiguousarray(depth, np.float32)
             ptr, on_dev = ctypes.c_void_p(depth.ctypes.data), 0
