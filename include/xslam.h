@@ -257,8 +257,9 @@ xslam_status xslam_profile_read(xslam_t h, double* ms, long long* launches, doub
  *   cuda_stream  the stream the call is ordered on (NULL = legacy default); the call synchronises it
  * Limits: K_lanes <= 15 and at most 160 thread blocks (the grid this library picks on a GB300 is at
  * most one block per SM); larger requests return XSLAM_EINVAL with a message in
- * xslam_last_error(NULL). The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture. Calls share the
+ * xslam_last_error(NULL). Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress); the first lookup on a device may load the library's device code, so make
+ * the first call on each device before any stream capture. Calls share the
  * array: calls that overlap on the GPU (other streams, other host threads) race; the call clears the
  * scratch it needs cleared (ticket, status) itself. No cudaMalloc, cudaFree or allocating library
  * routine is called.

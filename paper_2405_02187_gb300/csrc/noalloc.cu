@@ -11,7 +11,6 @@
 // that overlap on the GPU race on it. Each call clears what must start at zero (ticket, status).
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/xslam.h"
 #include "internal.cuh"
@@ -33,24 +32,15 @@ constexpr size_t kNoAllocBytes = kOffResult + sizeof(double) * kResLen;  // ~290
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// device address of the array, looked up once per device (host code cannot use the symbol directly)
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
+// Device address of the array on the current device. Host code cannot use the symbol itself (in host
+// code it names a host-side stand-in), so every call looks the address up with the current device's
+// context current: a cached address would go stale once cudaDeviceReset rebuilds the context, and the
+// lookup after the first (which may load the module) is a host-side table read.
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

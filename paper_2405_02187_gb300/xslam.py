@@ -155,9 +155,20 @@ def icp_system_noalloc(depth, level, intr, model, Tj, T_prev, seeds=(), cfg: Con
     Returns ((1 + K, 27) array, n_valid)."""
     lib = load()
     K = len(seeds)
-    Kin = Intrinsics(float(intr.fx), float(intr.fy), float(intr.cx), float(intr.cy), int(intr.width), int(intr.height))
+    W, H = int(intr.width), int(intr.height)
+    Kin = Intrinsics(float(intr.fx), float(intr.fy), float(intr.cx), float(intr.cy), W, H)
     Tj = np.ascontiguousarray(Tj, np.float64).reshape(-1)
     T_prev = np.ascontiguousarray(T_prev, np.float64).reshape(-1)
+    # the C call reads (H >> level)(W >> level) depths, (1 + 6 (1 + K)) H W model floats and
+    # 12 (1 + K) doubles of each pose block: a shorter buffer would be read past its end
+    if Tj.size != 12 * (1 + K) or T_prev.size != 12 * (1 + K):
+        raise ValueError(f"Tj and T_prev must hold (1 + K) x 12 = {12 * (1 + K)} doubles")
+    if not 0 <= int(level) <= 2:
+        raise ValueError("level must be 0, 1 or 2")
+    if depth is None or depth.numel() != (H >> int(level)) * (W >> int(level)):
+        raise ValueError(f"depth must hold {(H >> int(level)) * (W >> int(level))} floats for level {level}")
+    if model is None or model.numel() < (1 + 6 * (1 + K)) * H * W:
+        raise ValueError(f"model must hold at least (1 + 6 (1 + K)) H W = {(1 + 6 * (1 + K)) * H * W} floats")
     out = np.zeros(27 * (1 + K))
     n = ctypes.c_int(0)
     if stream is None:

@@ -61,6 +61,29 @@ def rel_err(a, b):
     return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
 
 
+def assert_lanes_close(g, o, tol=1e-3, frac=0.999, max_err=1.0, frob=1e-3, what=""):
+    """Element-wise comparison of a derivative lane g (GPU) with the oracle's o over a compared set.
+
+    The lane's scale is max |o|. At least ``frac`` of the elements must lie within ``tol`` x scale of
+    the oracle, no element may be further than ``max_err`` x scale away (an element whose discrete
+    decision flipped between FP32 and FP64, e.g. a voxel clamped at F_D = 1 on one side only, can
+    differ by up to the lane's scale), and the Frobenius relative error stays below ``frob``."""
+    g = np.asarray(g, np.float64).ravel()
+    o = np.asarray(o, np.float64).ravel()
+    assert g.shape == o.shape and g.size > 0, what
+    assert np.all(np.isfinite(g)), what
+    scale = np.abs(o).max()
+    if scale == 0.0:
+        assert np.abs(g).max() == 0.0, what
+        return
+    err = np.abs(g - o) / scale
+    inside = (err <= tol).mean()
+    assert inside >= frac, f"{what}: {inside:.5f} of {g.size} elements within {tol} of the scale {scale:.3e}"
+    assert err.max() <= max_err, f"{what}: max error {err.max():.3e} of the scale"
+    fr = rel_err(g, o)
+    assert fr < frob, f"{what}: Frobenius relative error {fr:.3e}"
+
+
 def f32_params(wl):
     """The workload and oracle Config with every parameter rounded to float32 as the C ABI passes it
     (voxel size, truncation, origin, intrinsics, gates, depth range), for comparisons at FP64 rounding."""

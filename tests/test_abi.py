@@ -5,6 +5,8 @@ import os
 import re
 import shutil
 
+import numpy as np
+
 import pytest
 
 from paper_2405_02187_gb300 import xslam
@@ -116,3 +118,28 @@ def test_plain_null_handle_calls(lib):
     assert lib.xslam_plain_frame(None, None, 0, None, 0, None, None, None) == xslam.EINVAL
     assert lib.xslam_plain_set_pose(None, None) == xslam.EINVAL
     assert lib.xslam_plain_read_tsdf(None, 0, 0, None) == xslam.EINVAL
+
+
+def test_icp_system_noalloc_binding_checks_sizes(lib):
+    """The binding checks every buffer the C call reads before handing it over: a depth map of the
+    wrong level size, a model with too few planes and a short pose block raise ValueError."""
+    torch = pytest.importorskip("torch")
+    from paper_2405_02187_gb300 import synth
+
+    intr = synth.Intrinsics(100.0, 100.0, 31.5, 23.5, 64, 48)
+    seeds = [(xslam.POSE0, 0, 1e-10), (xslam.DEPTH, -1, 1e-10)]
+    L = 1 + len(seeds)
+    T = np.zeros((L, 3, 4))
+    good_d1 = torch.zeros(24 * 32)
+    good_m = torch.zeros((1 + 6 * L) * 48 * 64)
+    with pytest.raises(ValueError, match="depth"):
+        xslam.icp_system_noalloc(torch.zeros(48 * 64), 1, intr, good_m, T, T, seeds, stream=0)
+    with pytest.raises(ValueError, match="model"):
+        xslam.icp_system_noalloc(good_d1, 1, intr, torch.zeros(6 * L * 48 * 64), T, T, seeds, stream=0)
+    with pytest.raises(ValueError, match="doubles"):
+        xslam.icp_system_noalloc(good_d1, 1, intr, good_m, T[:2], T, seeds, stream=0)
+    with pytest.raises(ValueError, match="level"):
+        xslam.icp_system_noalloc(good_d1, 3, intr, good_m, T, T, seeds, stream=0)
+    # sizes right: the next check is the CUDA-tensor one, still before any library call
+    with pytest.raises(TypeError, match="CUDA"):
+        xslam.icp_system_noalloc(good_d1, 1, intr, good_m, T, T, seeds, stream=0)

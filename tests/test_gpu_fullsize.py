@@ -6,7 +6,7 @@ and the level-0 ICP normal equations against the GPU's ray-cast model."""
 import numpy as np
 import pytest
 
-from gpu_helpers import H_GPU, H_ORA, gpu_seeds, make_handle, oracle_cfg, rel_err
+from gpu_helpers import H_GPU, H_ORA, assert_lanes_close, gpu_seeds, make_handle, oracle_cfg, rel_err
 from oracle import fusion, icp, measure, raycast, se3
 from oracle import pipeline as P
 from paper_2405_02187_gb300 import synth
@@ -68,7 +68,7 @@ def test_fullsize_fusion_sampled(state):
         Wc = W0.copy()
         fusion.integrate(Fc, Wc, D, _complex_pose(T, j), wl.intr, wl.dims, wl.origin, wl.voxel, wl.trunc, idx=idx)
         upd_obs = obs[W1[obs] != W0[obs]]
-        assert rel_err(L1[j][upd_obs], Fc.imag[upd_obs] / H_ORA) < 1e-3, j
+        assert_lanes_close(L1[j][upd_obs], Fc.imag[upd_obs] / H_ORA, what=f"TSDF lane {j}")
 
 
 def test_fullsize_raycast_sampled(state):
@@ -98,8 +98,8 @@ def test_fullsize_raycast_sampled(state):
         _, cV, cN = raycast.raycast(Fc, W1, _complex_pose(T, j), *args, pix=pix)
         gvl = gv[3 * (j + 1):3 * (j + 2), pix].T[both] / H_GPU
         gnl = gn[3 * (j + 1):3 * (j + 2), pix].T[both] / H_GPU
-        assert rel_err(gvl, cV.imag[both] / H_ORA) < 1e-3, j
-        assert rel_err(gnl, cN.imag[both] / H_ORA) < 1e-3, j
+        assert_lanes_close(gvl, cV.imag[both] / H_ORA, what=f"vertex lane {j}")
+        assert_lanes_close(gnl, cN.imag[both] / H_ORA, what=f"normal lane {j}")
 
 
 def test_fullsize_icp_system(state):

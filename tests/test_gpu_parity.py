@@ -1,14 +1,17 @@
 """CUDA path vs the CPU oracle, stage by stage and end to end (X-SLAM Sec. 4.1), through the C ABI.
 
 Tolerances (FP32 lanes against the complex128 oracle): TSDF real part 1e-4 absolute where both
-sides observed the voxel with the same weight; pose 1e-5 m/rad; derivatives 1e-3 relative (Frobenius
-over the compared set). Discrete decisions taken in different precision may flip at knife edges
+sides observed the voxel with the same weight; pose 1e-5 m/rad; derivatives 1e-3 relative: a lane of
+a volume or a map passes if at least 99.9% of its elements lie within 1e-3 of the lane's scale (max
+|oracle|), none is further than the scale, and the Frobenius relative error is below 1e-3; the 27
+normal-equation sums and the 6-component twist blocks by their Frobenius relative error. Discrete decisions taken in different precision may flip at knife edges
 (a depth exactly at a gate, a TSDF sample at zero); their count is bounded and the values are
 compared where both sides took the same branch."""
 import numpy as np
 import pytest
 
-from gpu_helpers import (H_GPU, H_ORA, gpu_seeds, make_handle, oracle_cfg, pose_lanes, promote_seeds, rel_err)
+from gpu_helpers import (H_GPU, H_ORA, assert_lanes_close, gpu_seeds, make_handle, oracle_cfg, pose_lanes,
+                         promote_seeds, rel_err)
 from oracle import fusion, icp, measure, raycast, se3
 from oracle import pipeline as P
 from paper_2405_02187_gb300 import synth, xslam
@@ -88,7 +91,7 @@ def test_fusion_parity(orbit):
     for j in range(len(SEEDS_F)):
         gd = x.read_tsdf(j + 1, buf).cpu().numpy().astype(np.float64)
         od = Fc[j].imag / H_ORA
-        assert rel_err(gd[obs], od[obs]) < 1e-3, j
+        assert_lanes_close(gd[obs], od[obs], what=f"TSDF lane {j}")
         assert np.all(gd[~(W > 0) & agree] == 0)
 
 
@@ -136,8 +139,8 @@ def test_raycast_parity(orbit):
         _, cV, cN = raycast.raycast(Fcj, W, Tcs[j], *args)
         gvl = np.moveaxis(gv[3 * (j + 1):3 * (j + 2)], 0, -1)[both] / H_GPU
         gnl = np.moveaxis(gn[3 * (j + 1):3 * (j + 2)], 0, -1)[both] / H_GPU
-        assert rel_err(gvl, cV.imag[both] / H_ORA) < 1e-3, j
-        assert rel_err(gnl, cN.imag[both] / H_ORA) < 1e-3, j
+        assert_lanes_close(gvl, cV.imag[both] / H_ORA, what=f"vertex lane {j}")
+        assert_lanes_close(gnl, cN.imag[both] / H_ORA, what=f"normal lane {j}")
 
 
 # ---------------------------------------------------------------------------------------------

@@ -12,16 +12,28 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_icp_system_noalloc_matches_handle_call():
-    from gpu_helpers import H_GPU, gpu_seeds, make_handle, rel_err, xslam_cfg
+def _seed_set(n):
     from oracle import pipeline as P
+    if n == 3:
+        return [P.Seed(P.POSE0, 0), P.Seed(P.POSE0, 3), P.Seed(P.DEPTH, -1)]
+    # 15 lanes: the largest lane count, whose block is one replica of 16 warps (512 threads) and whose
+    # partial sums use the largest stride of the fixed array
+    s = [P.Seed(P.POSE0, j) for j in range(6)] + [P.Seed(P.TRUNC), P.Seed(P.DEPTH, -1)]
+    s += [P.Seed(P.POSE0, j, h=2e-20) for j in range(6)] + [P.Seed(P.TRUNC, h=3e-20)]
+    assert len(s) == 15
+    return s
+
+
+@pytest.mark.parametrize("n_seeds,levels", [(3, (0, 2)), (15, (0,))], ids=["4_lanes", "16_lanes"])
+def test_icp_system_noalloc_matches_handle_call(n_seeds, levels):
+    from gpu_helpers import H_GPU, gpu_seeds, make_handle, rel_err, xslam_cfg
     from oracle import se3
     from paper_2405_02187_gb300 import synth, xslam
 
     wl = synth.small_orbit(frames=5)
-    seeds = [P.Seed(P.POSE0, 0), P.Seed(P.POSE0, 3), P.Seed(P.DEPTH, -1)]
+    seeds = _seed_set(n_seeds)
     L = 1 + len(seeds)
-    x = make_handle(wl, max_lanes=6)
+    x = make_handle(wl, max_lanes=max(6, len(seeds)))
     x.set_pose(wl.poses[0])
     dev = [torch.tensor(wl.depth[k], device="cuda") for k in range(5)]
     for k in range(3):
@@ -38,7 +50,7 @@ def test_icp_system_noalloc_matches_handle_call():
     Tj = T_prev.copy()
     Tj[0] = se3.compose(se3.se3_exp(np.array([0.004, -0.002, 0.003, 0.005, 0.002, -0.004])), T_prev[0])
     cfg = xslam_cfg(wl)
-    for level in (0, 2):
+    for level in levels:
         lvl = torch.empty((H >> level, W >> level), device="cuda")
         x.measure(dev[3], level, lvl)
         ref, n_ref = x.icp_system(level, Tj)
