@@ -10,10 +10,18 @@ for the next frame.
 
 Seeds (which input carries the imaginary perturbation h i; one complex run per seed):
   POSE0 (kind 0, index 0..5): T_0* = exp(h i e_index) T_0 (Eq. lie), a left twist of frame 0's pose;
+  POSE (kind 1, index 0..5): frame k's own pose before ICP, T~_{k,0}* = exp(h i e_index) T~_{k,0}
+    (the start of ICP; T_0 itself at frame 0);
   TRUNC (kind 2): mu* = mu + h i;
   DEPTH (kind 3, index -1 for every pixel, else one linear pixel index): D_k* = D_k + h i at every
-    frame (Eq. csfd_depth).
-The derivative of any result X is Im(X*) / h (Eq. csfd).
+    frame (Eq. csfd_depth);
+  POSE_TRACKED (kind 4, index 0..5): frame k's tracked pose as the surface update and the ray cast use
+    it, T_{g,k}* = exp(h i e_index) T_{g,k} (Eq. lie, Eq. pvnpxi and the surface update's derivative
+    with respect to xi_k).
+The derivative of any result X is Im(X*) / h (Eq. csfd). The two per-frame pose kinds restart at every
+frame: before frame k > 0 the run drops the imaginary parts that earlier frames' perturbations left in
+its pose, TSDF and model maps, so that Im(X_k*) / h is the derivative of frame k's results with respect
+to frame k's pose alone (the paper's dF_k / dxi_{k,i}), not a sum over the frames.
 
 Readings: ICP starts each frame from the previous pose T_{k-1} (Sec. 4.1, "initialized with the
 previous frame pose"); on an ICP failure the frame is fused at T_{k-1} and the step reports it.
@@ -27,7 +35,8 @@ import numpy as np
 from . import fusion, icp, measure, mlp, proposal, raycast, se3
 from .csfd import H_ORACLE
 
-POSE0, POSE, TRUNC, DEPTH = 0, 1, 2, 3
+POSE0, POSE, TRUNC, DEPTH, POSE_TRACKED = 0, 1, 2, 3, 4
+PER_FRAME = (POSE, POSE_TRACKED)
 
 
 @dataclasses.dataclass
@@ -89,7 +98,7 @@ class XKinectFusion:
         self.W = np.zeros(n)
         self.mu = mu + (seed.delta if self.pert and seed.kind == TRUNC else 0)
         T0 = np.asarray(T0, np.float64)
-        if self.pert and seed.kind == POSE0:
+        if self.pert and seed.kind in (POSE0, POSE, POSE_TRACKED):  # frame 0: start = tracked = T_0
             self.T = se3.perturb_pose(T0, seed.index, seed.delta)
         else:
             self.T = T0.astype(dt)
@@ -114,10 +123,31 @@ class XKinectFusion:
             D = measure.bilateral(D)
         return measure.pyramid(D, len(self.cfg.icp_iters), self.cfg.pyr_range)
 
+    @property
+    def per_frame(self):
+        return self.pert and self.seed.kind in PER_FRAME
+
+    def restart_lane(self):
+        """A per-frame pose lane starts frame k from the real state: the imaginary parts that frame
+        k-1's perturbation left in the pose, the TSDF and the model maps are dropped."""
+        dt = self.T.dtype
+        self.T = np.real(self.T).astype(dt)
+        self.T_pp = np.real(self.T_pp).astype(dt)
+        self.F = np.real(self.F).astype(self.F.dtype)
+        self.model = {k: np.real(v) for k, v in self.model.items()}
+
+    def perturb(self, T):
+        """exp(h i e_index) T for the per-frame pose kinds (the identity for every other run)."""
+        if not self.per_frame:
+            return T
+        return se3.perturb_pose(np.real(T), self.seed.index, self.seed.delta)
+
     def frame(self, depth):
         c = self.cfg
         pyr = self.measure(depth)
         ok = True
+        if self.k > 0 and self.per_frame:
+            self.restart_lane()
         if self.k > 0:
             gates = dict(dist_gate=c.dist_gate, normal_gate_deg=c.normal_gate_deg, disc_gate=c.disc_gate)
             if c.icp_newton:
@@ -126,6 +156,8 @@ class XKinectFusion:
                                               c.min_corr_frac, eta=c.icp_newton_eta, **gates)
             else:
                 self.T, ok = self.track(pyr, depth, gates)
+            if self.pert and self.seed.kind == POSE_TRACKED:
+                self.T = self.perturb(self.T)
         if c.proposal is not None:
             self.feat_prev = mlp.features(np.real(np.asarray(depth, np.float64)), c.depth_min, c.depth_max)
         fusion.integrate(self.F, self.W, pyr[0], self.T, self.intr, self.dims, self.origin,
@@ -142,6 +174,8 @@ class XKinectFusion:
         c = self.cfg
         T1 = self.T
         seed_a = proposal.cv_seed(T1, self.T_pp) if c.icp_seed == "cv" else T1
+        if self.pert and self.seed.kind == POSE:
+            seed_a = self.perturb(seed_a)
         self.T_pp = T1
         kw = dict(stop_tol=c.icp_stop, stats=self.stats, **gates)
         levels = len(c.icp_iters)
@@ -155,6 +189,8 @@ class XKinectFusion:
         y, _ = mlp.forward(P.params, x, bf16_ops=True)
         xi = np.asarray(P.scale, np.float64) * y[0]
         seed_b = proposal.proposal_seed(T1, xi)
+        if self.pert and self.seed.kind == POSE:
+            seed_b = self.perturb(seed_b)
         jl = P.judge_level
         lintr = measure.level_intrinsics(self.intr, jl)
         res = []
