@@ -232,7 +232,7 @@ def measured_bf16_tflops():
 
 
 KERNEL_SRC = {"integrate": "fuse.cu", "raycast": "raycast.cu", "icp": "icp.cu"}
-KERNEL_NAME = {"integrate": "k_integrate", "raycast": "k_march + k_refine", "icp": "k_icp"}
+KERNEL_NAME = {"integrate": "k_integrate", "raycast": "k_march + k_refine", "icp": "k_icp_run"}
 
 
 def _src_hash(stage):
@@ -254,27 +254,110 @@ def ncu_traffic(stage, workload):
     return e.get("dram_bytes_per_launch")
 
 
-def algorithmic_bytes(stage, wl, K, per_frame):
+def icp_bytes_per_frame(wl, K):
+    """ICP's algorithmic bytes per frame at the scope table's per-unit figure: every iteration reads,
+    per pixel of its level, the pixel's own vertex and normal (24 B) and the model vertex and normal on
+    1 + K lanes at its correspondence (24 (1 + K) B): 192 B per pixel-iteration at K = 6."""
+    hw = wl.intr.width * wl.intr.height
+    return sum(iters * (hw >> (2 * level)) * (24 + 24 * (1 + K)) for level, iters in enumerate(wl.icp_iters))
+
+
+def algorithmic_bytes(stage, wl, K, per_frame, launches_per_frame=1.0):
     """Bytes a launch of the stage must move (see the kernels' headers):
     integrate: read + write of F (1 + K lanes) and W for every updated voxel, plus the depth map;
-    raycast:   the model outputs (depth + vertex and normal on 1 + K lanes) plus F and W of the
-               voxels in front of the surface that the rays cross (counted as the voxels the update
-               of the same pose touched) plus the K imaginary planes at the 8 cells of every hit;
-    icp:       per pixel of the level: its depth, and the model depth, vertex and normal (1 + K lanes)
-               at its correspondence."""
+    raycast:   the model outputs (depth + vertex and normal on 1 + K lanes) plus the distinct voxels
+               the march and the refinement read (per_frame["march_voxels"] of Re F, and
+               per_frame["refine_voxels"] of Re F and the K imaginary planes);
+    icp:       icp_bytes_per_frame / the ICP launches of a frame (one cooperative launch)."""
     L = 1 + K
     hw = wl.intr.width * wl.intr.height
     if stage == "integrate":
         return per_frame["fused"] * 2 * 4 * (L + 1) + 4 * hw
     if stage == "raycast":
-        return hw * 4 * (1 + 6 * L) + per_frame["fused"] * 8 + per_frame["hits"] * 8 * 8 * 4 * K
+        return hw * 4 * (1 + 6 * L) + per_frame["march_voxels"] * 4 + per_frame["refine_voxels"] * 4 * L
     if stage == "icp":
-        tot, launches = 0.0, 0
-        for level, iters in enumerate(wl.icp_iters):
-            tot += iters * (hw >> (2 * level)) * (4 + 4 + 24 * L)
-            launches += iters
-        return tot / launches
+        return icp_bytes_per_frame(wl, K) / launches_per_frame
     raise ValueError(stage)
+
+
+def raycast_voxel_reads(intr, T, hit_depth, dims, voxel, origin, step, m0, m1, chunk=2048):
+    """Distinct voxels the ray cast reads at pose T (3x4) given its per-pixel hit depth (camera z,
+    0 = no surface; a torch tensor H x W on any device), following the ray cast's sampling (samples at
+    alpha_m = m * step, m0 <= m <= m1, within the volume's slab, each reading the 8 corners of its
+    trilinear cell): the march reads every sample from the first in the volume to the second sample of
+    the hit pair (to the last in the volume without a hit); the refinement reads the cells of the hit
+    pair's two samples and of the six normal samples at the vertex +- one voxel per axis. Returns
+    (march voxels, refine voxels), each a count of distinct voxels."""
+    import torch
+    dev = hit_depth.device
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    H, W = hit_depth.shape
+    R = torch.tensor(np.asarray(T)[:, :3], dtype=torch.float64, device=dev)
+    t = torch.tensor(np.asarray(T)[:, 3], dtype=torch.float64, device=dev)
+    org = torch.tensor(origin, dtype=torch.float64, device=dev)
+    nn = torch.tensor([nx, ny, nz], dtype=torch.float64, device=dev)
+    v, u = torch.meshgrid(torch.arange(H, device=dev, dtype=torch.float64),
+                          torch.arange(W, device=dev, dtype=torch.float64), indexing="ij")
+    rc = torch.stack([(u - intr.cx) / intr.fx, (v - intr.cy) / intr.fy, torch.ones_like(u)], -1).reshape(-1, 3)
+    d = rc @ R.T                                  # world direction per unit camera depth
+    g0 = (t - org) / voxel - 0.5                  # grid coordinate at alpha = 0
+    gd = d / voxel
+    # slab: 0 <= g < n - 1 on every axis
+    t1 = (0.0 - g0) / gd
+    t2 = ((nn - 1.0) - g0) / gd
+    lo = torch.where(gd != 0, torch.minimum(t1, t2), torch.full_like(gd, -np.inf)).amax(1)
+    hi = torch.where(gd != 0, torch.maximum(t1, t2), torch.full_like(gd, np.inf)).amin(1)
+    inside = torch.where(gd == 0, (g0 >= 0) & (g0 < nn - 1), torch.ones_like(gd, dtype=torch.bool)).all(1)
+    hd = hit_depth.reshape(-1).to(torch.float64)
+    m_lo = torch.clamp(torch.floor(torch.clamp(lo, min=m0 * step) / step) - 1, min=m0)
+    m_hi = torch.clamp(torch.ceil(torch.clamp(hi, max=m1 * step) / step) + 1, max=m1)
+    m_end = torch.where(hd > 0, torch.floor(hd / step) + 1, m_hi)
+    march = torch.zeros(n, dtype=torch.bool, device=dev)
+    refine = torch.zeros(n, dtype=torch.bool, device=dev)
+    off = torch.tensor([[i, j, k] for k in (0, 1) for j in (0, 1) for i in (0, 1)], dtype=torch.int64, device=dev)
+
+    def mark(bitmap, g):
+        ok = ((g >= 0) & (g < nn - 1)).all(-1)
+        c = torch.floor(g[ok]).to(torch.int64)[:, None, :] + off[None]
+        idx = c[..., 0] + nx * (c[..., 1] + ny * c[..., 2])
+        bitmap[idx.reshape(-1)] = True
+
+    npx = H * W
+    for a in range(0, npx, chunk):
+        sl = slice(a, min(a + chunk, npx))
+        ok = inside[sl] & (m_end[sl] >= m_lo[sl])
+        if not bool(ok.any()):
+            continue
+        lo_c, end_c = m_lo[sl][ok], m_end[sl][ok]
+        M = int((end_c - lo_c).max().item()) + 1
+        m = lo_c[:, None] + torch.arange(M, device=dev, dtype=torch.float64)[None]
+        keep = m <= end_c[:, None]
+        g = g0 + (m * step)[..., None] * gd[sl][ok][:, None, :]
+        mark(march, g[keep])
+        hit = hd[sl] > 0
+        if bool(hit.any()):
+            a0 = hd[sl][hit]
+            mh = torch.floor(a0 / step)
+            gh = gd[sl][hit]
+            vtx = g0 + a0[:, None] * gh
+            e = torch.eye(3, dtype=torch.float64, device=dev)
+            pts = [g0 + (mh * step)[:, None] * gh, g0 + ((mh + 1) * step)[:, None] * gh]
+            pts += [vtx + s * e[i] for i in range(3) for s in (1.0, -1.0)]
+            mark(refine, torch.cat(pts, 0))
+    return int(march.sum().item()), int(refine.sum().item())
+
+
+def model_voxel_reads(x, wl, dev):
+    """raycast_voxel_reads of a handle's current model: its pose and the hit depth of a ray cast there."""
+    import torch
+    dep = torch.empty((wl.intr.height, wl.intr.width), device=dev)
+    x.raycast(None, dep, None, None)
+    T = x.get_pose_lanes()[0]
+    step = wl.voxel * 1.0  # ray_step_vox = 1
+    m0 = int(math.ceil(wl.depth_min / step - 1e-4))
+    m1 = int(math.floor(wl.depth_max / step + 1e-4))
+    return raycast_voxel_reads(wl.intr, T, dep, wl.dims, wl.voxel, wl.origin, step, m0, m1)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -368,15 +451,19 @@ def run_ours(args, rank, world, local_rank):
         x.frame(depth_dev[k], seeds, outputs=False)
     stages, counters = x.profile_read()
     x.profile(False)
-    x.close()
     nprof = counters["frames"]
     per_frame = dict(fused=counters["fused"] / nprof, hits=counters["hits"] / nprof)
+    # distinct voxels the ray cast reads, counted on the last frame's model (same pose, same volume)
+    per_frame["march_voxels"], per_frame["refine_voxels"] = model_voxel_reads(x, wl, dev)
+    x.close()
     launches_per_frame = sum(v[1] for v in stages.values()) / nprof
     cand = {s: stages[s][0] / nprof for s in ("integrate", "raycast", "icp")}
     dom = max(cand, key=cand.get)
-    units = stages[dom][1] // 2 if dom == "raycast" else stages[dom][1]  # a ray cast is a k_march + k_refine pair
-    ms_launch = stages[dom][0] / units
-    bytes_launch = algorithmic_bytes(dom, wl, L, per_frame)
+    # per stage: launches of its roofline kernel (a ray cast is a k_march + k_refine pair; the fusion
+    # stage's tile list, the integrate kernel and the restart clear count as one update)
+    n_units = dict(icp=stages["icp"][1] / nprof, integrate=1.0, raycast=1.0)
+    ms_launch = stages[dom][0] / nprof / n_units[dom]
+    bytes_launch = algorithmic_bytes(dom, wl, L, per_frame, launches_per_frame=n_units["icp"])
     peak, peak_src = measured_peaks()
     achieved = bytes_launch / (ms_launch * 1e-3) / 1e9
     traffic = ncu_traffic(dom, wl.name)
@@ -388,11 +475,10 @@ def run_ours(args, rank, world, local_rank):
     # the same roofline for each of the three stages (the dominant one is `roofline` itself)
     roofline_stages = {}
     for st in ("icp", "integrate", "raycast"):
-        n_units = stages[st][1] // 2 if st == "raycast" else stages[st][1]
-        if n_units <= 0 or stages[st][0] <= 0.0:
+        if stages[st][1] <= 0 or stages[st][0] <= 0.0:
             continue
-        ms_st = stages[st][0] / n_units
-        b_st = algorithmic_bytes(st, wl, L, per_frame)
+        ms_st = stages[st][0] / nprof / n_units[st]
+        b_st = algorithmic_bytes(st, wl, L, per_frame, launches_per_frame=n_units["icp"])
         a_st = b_st / (ms_st * 1e-3) / 1e9
         roofline_stages[st] = dict(kernel=KERNEL_NAME[st], achieved=round(a_st, 1), frac=round(a_st / peak, 4),
                                    traffic=ncu_traffic(st, wl.name), bytes_per_launch=round(b_st),
@@ -501,7 +587,9 @@ def run_ours(args, rank, world, local_rank):
                 grad_rel_err_vs_oracle=grad_err,
                 plain_fp64=plain, uncomplexified_fp32=real32, batched=batched, second_order=second, newton_icp=newton,
                 learned_proposal=learned,
-                per_frame=dict(fused_voxels=round(per_frame["fused"]), surface_pixels=round(per_frame["hits"])))
+                per_frame=dict(fused_voxels=round(per_frame["fused"]), surface_pixels=round(per_frame["hits"]),
+                               raycast_march_voxels=per_frame["march_voxels"],
+                               raycast_refine_voxels=per_frame["refine_voxels"]))
     if rank == 0:
         print(json.dumps(line))
 
@@ -550,8 +638,9 @@ def run_batch(args, dev, rank):
         L = 1 + len(lanes)
         hw = wl.intr.width * wl.intr.height
         per = dict(fused=cnt["fused"] / n, hits=cnt["hits"] / n)
+        per["march_voxels"], per["refine_voxels"] = model_voxel_reads(x, wl, dev)
         moved += n * (algorithmic_bytes("integrate", wl, len(lanes), per) + algorithmic_bytes("raycast", wl, len(lanes), per))
-        moved += (n - 1) * sum(it * (hw >> (2 * lv)) * (4 + 4 + 24 * L) for lv, it in enumerate(wl.icp_iters))
+        moved += (n - 1) * icp_bytes_per_frame(wl, len(lanes))
     # per-trajectory frame latency inside a step, from a second batch over the first steps
     batch.close()
     for (wl, lanes), x in zip(trajs, handles):

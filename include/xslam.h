@@ -41,19 +41,33 @@ typedef enum {
   XSLAM_ESTATE = 6    /* call not valid in the handle's current state               */
 } xslam_status;
 
-/* Which input a lane perturbs (X-SLAM Sec. 4.1). */
+/*
+ * Which input a lane perturbs (X-SLAM Sec. 4.1). The two per-frame pose kinds promote frame k's own pose
+ * (Eq. lie) and restart at every frame: before frame k > 0 the lane drops the imaginary parts earlier
+ * frames left in its pose lanes, its TSDF plane and its model maps, so that Im(X_k) / h is the
+ * derivative of frame k's results with respect to frame k's pose alone (the paper's dF_k / dxi_{k,i}
+ * and Eq. pvnpxi), not a sum over frames. At frame 0 both equal POSE0.
+ */
 typedef enum {
-  XSLAM_SEED_POSE0 = 0, /* index 0..5: left twist (phi then rho) of frame 0's pose, Eq. lie / pvnpxi */
-  XSLAM_SEED_POSE = 1,  /* reserved: per-frame pose twist; xslam_frame returns XSLAM_EINVAL        */
-  XSLAM_SEED_TRUNC = 2, /* the truncation distance mu (Sec. 4.1, Psi)                               */
-  XSLAM_SEED_DEPTH = 3  /* index -1: every valid pixel of every frame, D* = D + h i (Eq. csfd_depth);
-                           a single-pixel index is rejected with XSLAM_EINVAL                      */
+  XSLAM_SEED_POSE0 = 0, /* index 0..5: left twist (phi then rho) of frame 0's pose, Eq. lie / pvnpxi    */
+  XSLAM_SEED_POSE = 1,  /* index 0..5: left twist of frame k's pose before ICP, i.e. ICP's start (the
+                           previous pose, or the constant-velocity / proposal starts; both runs of the
+                           proposal are perturbed): dpose_out is d T_k / d xi_{k,0}, which ICP's
+                           contraction makes small once it converges                                  */
+  XSLAM_SEED_TRUNC = 2, /* the truncation distance mu (Sec. 4.1, Psi)                                   */
+  XSLAM_SEED_DEPTH = 3, /* index -1: every valid pixel of every frame, D* = D + h i (Eq. csfd_depth);
+                           index p in 0..W H - 1: level-0 pixel p of every frame (its perturbation
+                           passes through the bilateral filter and the pyramid like the depth)         */
+  XSLAM_SEED_POSE_TRACKED = 4 /* index 0..5: left twist of frame k's tracked pose T_{g,k} (the ICP result)
+                           as the surface update and the ray cast use it (Eq. lie, Eq. pvnpxi, and
+                           dF_k / dxi_{k,i} of the surface update): dpose_out is G_index T_k exactly;
+                           xslam_read_tsdf and the model maps carry the derivatives                   */
 } xslam_seed_kind;
 
 typedef struct {
-  int kind;   /* xslam_seed_kind                                   */
-  int index;  /* twist component 0..5 for POSE0; -1 for DEPTH      */
-  double h;   /* imaginary step; the read-out divides Im by h      */
+  int kind;   /* xslam_seed_kind                                                   */
+  int index;  /* twist component 0..5 (pose kinds); -1 or a pixel (DEPTH); 0 (TRUNC) */
+  double h;   /* imaginary step; the read-out divides Im by h                      */
 } xslam_seed;
 
 typedef struct {
@@ -116,7 +130,8 @@ xslam_status xslam_set_pose(xslam_t h, const double T_world_cam[12]);
 
 /*
  * One X-KinectFusion step (Sec. 4.1) on depth map `depth` (H x W float32; device pointer if
- * depth_on_device, else host): range gate, 3-level Gaussian pyramid, multi-level projective
+ * depth_on_device, else host): range gate, bilateral filter (if the configuration says so), 3-level
+ * Gaussian pyramid, multi-level projective
  * point-to-plane ICP from the previous pose against the previous frame's ray-cast model (frame 0
  * keeps its pose), TSDF update at the new pose, ray cast at the new pose; every step on 1 + K lanes.
  * seeds[K] (K <= max_lanes) define the lanes; they are fixed by the first frame after create/reset
@@ -251,8 +266,10 @@ xslam_status xslam_profile_read(xslam_t h, double* ms, long long* launches, doub
  *   model   device, level-0 model maps as (1 + 6 (1 + K_lanes)) planes of H x W: depth, vertex lanes,
  *           normal lanes (the layout of xslam_set_model / xslam_raycast)
  *   Tj, T_prev  host (1 + K_lanes) x 12 pose lanes (current estimate; pose the model was cast at)
- *   seeds   the K_lanes seeds (DEPTH seeds on every pixel enter the measured vertices; the others
- *           enter only through the pose lanes and the model); cfg may be NULL (defaults)
+ *   seeds   the K_lanes seeds (DEPTH seeds on every pixel enter the measured vertices; single-pixel
+ *           DEPTH seeds need a handle and are rejected; the per-frame pose kinds take no derivative
+ *           from T_prev's lanes or the model's; the others enter only through the pose lanes and the
+ *           model); cfg may be NULL (defaults)
  *   out     host (1 + K_lanes) x 27, as in xslam_icp_system; n_valid may be NULL
  *   cuda_stream  the stream the call is ordered on (NULL = legacy default); the call synchronises it
  * Limits: K_lanes <= 15 and at most 160 thread blocks (the grid this library picks on a GB300 is at

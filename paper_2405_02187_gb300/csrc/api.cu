@@ -124,6 +124,8 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   h->user = (cudaStream_t)cuda_stream;
   const char* env = getenv("XSLAM_GRAPHS");
   h->use_graphs = !(env && env[0] == '0');
+  const char* env2 = getenv("XSLAM_ICP_RUN");
+  h->icp_persistent = !(env2 && env2[0] == '0');
   Params& p = h->p;
   memset(&p, 0, sizeof(p));
   p.nx = nx; p.ny = ny; p.nz = nz;
@@ -134,6 +136,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   p.fx = K->fx; p.fy = K->fy; p.cx = K->cx; p.cy = K->cy;
   p.W = K->width; p.H = K->height;
   p.L = 1;
+  for (int l = 0; l < kMaxLanes; ++l) p.dpix[l] = -1;
   p.dist_gate2 = c.dist_gate_m * c.dist_gate_m;
   p.cos_normal_gate = (float)std::cos(c.normal_gate_deg * M_PI / 180.0);
   p.disc_gate = c.disc_gate_m;
@@ -173,6 +176,8 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
     nblk_max = std::max(nblk_max, h->nblk[l]);
   }
   nblk_max = std::max(nblk_max, 4 * h->nsm);  // k_loss grid
+  h->nblk_run = icp_run_blocks(Lmax);
+  nblk_max = std::max(nblk_max, 2 * h->nblk_run);  // the cooperative ICP's two partial buffers
   h->nblk_max = nblk_max;
   bool ok = true;
   ok &= cudaMalloc(&b.F, sizeof(float) * n * Lmax) == cudaSuccess;
@@ -190,6 +195,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   ok &= cudaMalloc(&b.partial, sizeof(float) * (size_t)(nblk_max + 4) * kNT * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&b.partial_n, sizeof(int) * nblk_max) == cudaSuccess;
   ok &= cudaMalloc(&b.ticket, sizeof(unsigned)) == cudaSuccess;
+  ok &= cudaMalloc(&b.grid_bar, sizeof(unsigned) * 4) == cudaSuccess;
   ok &= cudaMalloc(&b.status, sizeof(int) * 8) == cudaSuccess;
   ok &= cudaMalloc(&b.result, sizeof(double) * kResLen) == cudaSuccess;
   ok &= cudaMalloc(&b.stats, sizeof(unsigned long long) * kNStat) == cudaSuccess;
@@ -203,7 +209,9 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   ok &= cudaMalloc(&h->q.ticket, sizeof(unsigned)) == cudaSuccess;
   ok &= cudaMalloc(&b.hit, sizeof(int) * hw) == cudaSuccess;
   ok &= cudaMalloc(&b.tiles, sizeof(int) * (size_t)fuse_tile_count(p)) == cudaSuccess;
-  ok &= cudaMalloc(&b.tile_ctr, sizeof(unsigned) * 2) == cudaSuccess;
+  ok &= cudaMalloc(&b.tiles_prev, sizeof(int) * (size_t)fuse_tile_count(p)) == cudaSuccess;
+  ok &= cudaMalloc(&b.tile_ctr, sizeof(unsigned) * 4) == cudaSuccess;
+  if (max_lanes > 0) ok &= cudaMalloc(&b.dlane, sizeof(float) * dlane_stride(p) * max_lanes) == cudaSuccess;
   ok &= cudaMalloc(&h->d_kinds, sizeof(int) * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&h->d_index, sizeof(int) * kMaxLanes) == cudaSuccess;
   if (max_lanes >= 6) ok &= cudaMalloc(&h->model_q, sizeof(float) * hw * (1 + 6 * 7)) == cudaSuccess;
@@ -234,8 +242,8 @@ extern "C" xslam_status xslam_destroy(xslam_t h) {
   cudaFree(b.F); cudaFree(b.Wt); cudaFree(b.F0lin); cudaFree(b.depth_in); cudaFree(b.gated);
   for (int l = 0; l < 3; ++l) cudaFree(b.pyr[l]);
   cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp); cudaFree(h->hess_poses); cudaFree(h->hess_poses64);
-  cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.hit);
-  cudaFree(b.tiles); cudaFree(b.tile_ctr);
+  cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.grid_bar); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.hit);
+  cudaFree(b.tiles); cudaFree(b.tiles_prev); cudaFree(b.tile_ctr); cudaFree(b.dlane);
   cudaFree(h->q.pose_pp); cudaFree(h->q.candA); cudaFree(h->q.candB); cudaFree(h->q.judge); cudaFree(h->q.failA);
   cudaFree(h->q.partial); cudaFree(h->q.ticket); cudaFree(h->q.row); cudaFree(h->q.prev); cudaFree(h->q.y);
   for (int l = 0; l < 8; ++l) cudaFree(h->prop_act[l]);
@@ -302,6 +310,7 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   CU(cudaMemsetAsync(h->b.Wt, 0, sizeof(float) * n, h->s));
   CU(cudaMemsetAsync(h->b.model, 0, sizeof(float) * (size_t)h->p.W * h->p.H * (1 + 6 * Lmax), h->s));
   CU(cudaMemsetAsync(h->b.ticket, 0, sizeof(unsigned), h->s));
+  CU(cudaMemsetAsync(h->b.grid_bar, 0, sizeof(unsigned) * 4, h->s));
   CU(cudaMemsetAsync(h->b.partial, 0, sizeof(float) * (size_t)(h->nblk_max + 4) * kNT * kMaxLanes, h->s));
   CU(cudaMemsetAsync(h->b.status, 0, sizeof(int) * 8, h->s));
   CU(cudaMemsetAsync(h->q.pose_pp, 0, sizeof(double) * 12 * kMaxLanes, h->s));
@@ -310,7 +319,8 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   CU(cudaMemsetAsync(h->b.pose + 12, 0, sizeof(double) * 12 * (kMaxLanes - 1), h->s));
   CU(cudaMemsetAsync(h->b.result, 0, sizeof(double) * kResLen, h->s));
   CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * kNStat, h->s));
-  CU(cudaMemsetAsync(h->b.tile_ctr, 0, sizeof(unsigned) * 2, h->s));
+  CU(cudaMemsetAsync(h->b.tile_ctr, 0, sizeof(unsigned) * 4, h->s));
+  if (h->b.dlane) CU(cudaMemsetAsync(h->b.dlane, 0, sizeof(float) * dlane_stride(h->p) * h->max_lanes, h->s));
   h->frame = 0;
   h->K = 0;
   h->p.L = 1;
@@ -344,9 +354,11 @@ extern "C" xslam_status xslam_set_lanes(xslam_t h, const xslam_seed* seeds, int 
   int kinds[kMaxLanes] = {0}, index[kMaxLanes] = {0};
   Params p = h->p;
   p.L = 1 + K;
+  p.fresh = 0u;
   for (int l = 0; l < kMaxLanes; ++l) {
     p.dmu[l] = 0.f;
     p.dD[l] = 0.f;
+    p.dpix[l] = -1;
     p.h[l] = 1.0;
   }
   for (int j = 0; j < K; ++j) {
@@ -357,15 +369,25 @@ extern "C" xslam_status xslam_set_lanes(xslam_t h, const xslam_seed* seeds, int 
       case XSLAM_SEED_POSE0:
         if (s.index < 0 || s.index > 5) return fail(h, XSLAM_EINVAL, "POSE0 index must be 0..5");
         break;
+      case XSLAM_SEED_POSE:
+      case XSLAM_SEED_POSE_TRACKED:
+        if (s.index < 0 || s.index > 5) return fail(h, XSLAM_EINVAL, "POSE and POSE_TRACKED index must be 0..5");
+        p.fresh |= 1u << (j + 1);
+        break;
       case XSLAM_SEED_TRUNC:
         p.dmu[j + 1] = (float)s.h;
         break;
       case XSLAM_SEED_DEPTH:
-        if (s.index != -1) return fail(h, XSLAM_EINVAL, "only DEPTH seeds on every pixel (index -1) are built");
-        p.dD[j + 1] = (float)s.h;
+        if (s.index == -1) {
+          p.dD[j + 1] = (float)s.h;
+        } else if (s.index >= 0 && s.index < p.W * p.H) {
+          p.dpix[j + 1] = s.index;
+        } else {
+          return fail(h, XSLAM_EINVAL, "DEPTH index must be -1 (every pixel) or a pixel 0..W H - 1");
+        }
         break;
       default:
-        return fail(h, XSLAM_EINVAL, "seed kind not built (POSE0, TRUNC and DEPTH are)");
+        return fail(h, XSLAM_EINVAL, "unknown seed kind");
     }
     kinds[j + 1] = s.kind;
     index[j + 1] = s.index;
@@ -373,6 +395,8 @@ extern "C" xslam_status xslam_set_lanes(xslam_t h, const xslam_seed* seeds, int 
   }
   CU(cudaMemcpyAsync(h->d_kinds, kinds, sizeof(kinds), cudaMemcpyHostToDevice, h->s));
   CU(cudaMemcpyAsync(h->d_index, index, sizeof(index), cudaMemcpyHostToDevice, h->s));
+  // the single-pixel lanes' maps are zero outside their windows, which each frame rewrites
+  if (h->b.dlane) CU(cudaMemsetAsync(h->b.dlane, 0, sizeof(float) * dlane_stride(p) * h->max_lanes, h->s));
   CU(cudaStreamSynchronize(h->s));
   h->p = p;
   h->K = K;
@@ -398,13 +422,25 @@ static void stage_end(xslam_t h, int st, int launches) {
 }
 
 static bool uses_start(xslam_t h) { return h->cfg.icp_seed == 1 || h->mlp != nullptr; }
+static bool has_depth_lanes(xslam_t h) {
+  for (int l = 1; l < h->p.L; ++l)
+    if (h->p.dpix[l] >= 0) return true;
+  return false;
+}
+static bool has_kind(xslam_t h, int kind) {
+  for (int j = 0; j < h->K; ++j)
+    if (h->seeds[j].kind == kind) return true;
+  return false;
+}
 
 static cudaError_t enqueue_first(xslam_t h) {
   cudaError_t e;
   const size_t hw = (size_t)h->p.W * h->p.H;
   stage_begin(h, XSLAM_STAGE_PREPARE);
   if ((e = launch_prepare(h->p, h->b, 1, h->s)) != cudaSuccess) return e;
-  stage_end(h, XSLAM_STAGE_PREPARE, 1 + h->p.bilateral);
+  const bool dl = has_depth_lanes(h);
+  if (dl && (e = launch_depth_lanes(h->p, h->b, 1, h->s)) != cudaSuccess) return e;
+  stage_end(h, XSLAM_STAGE_PREPARE, 1 + h->p.bilateral + (dl ? 1 : 0));
   stage_begin(h, XSLAM_STAGE_OTHER);
   if ((e = launch_seed_pose(h->p, h->b, h->d_kinds, h->d_index, h->s)) != cudaSuccess) return e;
   int n_other = 1;
@@ -421,7 +457,7 @@ static cudaError_t enqueue_first(xslam_t h) {
   stage_end(h, XSLAM_STAGE_OTHER, n_other);
   stage_begin(h, XSLAM_STAGE_INTEGRATE);
   if ((e = launch_integrate(h->p, h->b, h->s)) != cudaSuccess) return e;
-  stage_end(h, XSLAM_STAGE_INTEGRATE, 1);
+  stage_end(h, XSLAM_STAGE_INTEGRATE, 2 + (h->p.fresh ? 1 : 0));
   stage_begin(h, XSLAM_STAGE_RAYCAST);
   if ((e = launch_raycast(h->p, h->b, h->b.pose, h->b.model, h->b.model + hw, h->b.model + hw * (1 + 3 * h->p.L),
                           false, true, h->s)) != cudaSuccess)
@@ -436,6 +472,14 @@ static cudaError_t enqueue_first(xslam_t h) {
 // ICP iterations of pyramid levels first .. last (first >= last), coarse to fine, on the current pose
 // lanes; close = the range's last iteration closes the frame (fallback to T_{k-1}, failure count)
 static cudaError_t enqueue_icp_levels(xslam_t h, int first, int last, bool close, int* n_icp) {
+  if (!h->cfg.icp_newton && h->icp_persistent) {
+    // every iteration of the range in one cooperative launch
+    int any = 0;
+    for (int l = first; l >= last; --l) any += h->cfg.icp_iters[l];
+    if (any == 0) return cudaSuccess;
+    *n_icp += 1;
+    return launch_icp_run(h->p, h->b, first, last, h->cfg.icp_iters, close, h->nblk_run, h->s);
+  }
   int last_level = -1;
   for (int l = first; l >= last; --l)
     if (h->cfg.icp_iters[l] > 0) last_level = l;
@@ -460,7 +504,20 @@ static cudaError_t enqueue_track(xslam_t h) {
   const int levels = h->cfg.icp_levels;
   stage_begin(h, XSLAM_STAGE_PREPARE);
   if ((e = launch_prepare(h->p, h->b, levels, h->s)) != cudaSuccess) return e;
-  stage_end(h, XSLAM_STAGE_PREPARE, levels + h->p.bilateral);
+  const bool dl = has_depth_lanes(h);
+  if (dl && (e = launch_depth_lanes(h->p, h->b, levels, h->s)) != cudaSuccess) return e;
+  stage_end(h, XSLAM_STAGE_PREPARE, levels + h->p.bilateral + (dl ? 1 : 0));
+  // per-frame pose lanes restart: the imaginary parts the last frame left in the pose lanes go, and
+  // (without a start-pose kernel to follow) ICP's start is perturbed at once
+  const bool fresh = h->p.fresh != 0u;
+  const bool start_kind = has_kind(h, XSLAM_SEED_POSE);
+  if (fresh) {
+    stage_begin(h, XSLAM_STAGE_OTHER);
+    const int mode = 1 | (uses_start(h) ? 0 : 2);
+    if ((e = launch_seed_frame(h->p, h->b, h->q.pose_pp, nullptr, h->d_kinds, h->d_index, mode, h->s)) != cudaSuccess)
+      return e;
+    stage_end(h, XSLAM_STAGE_OTHER, 1);
+  }
   if (uses_start(h)) {
     // the proposal's forward pass and the start poses
     stage_begin(h, XSLAM_STAGE_OTHER);
@@ -476,6 +533,12 @@ static cudaError_t enqueue_track(xslam_t h) {
     }
     const int mode = (h->cfg.icp_seed == 1 ? 1 : 0) | (h->mlp ? 2 : 0);
     if ((e = launch_prop_seed(h->p, h->b, h->q, h->prop_scale, mode, h->s)) != cudaSuccess) return e;
+    if (fresh && start_kind) {
+      if ((e = launch_seed_frame(h->p, h->b, nullptr, h->mlp ? h->q.candB : nullptr, h->d_kinds, h->d_index, 2,
+                                 h->s)) != cudaSuccess)
+        return e;
+      ++n_other;
+    }
     stage_end(h, XSLAM_STAGE_OTHER, n_other);
   }
   int n_icp = 0;
@@ -493,9 +556,15 @@ static cudaError_t enqueue_track(xslam_t h) {
     if ((e = enqueue_icp_levels(h, levels - 1, 0, true, &n_icp)) != cudaSuccess) return e;
   }
   stage_end(h, XSLAM_STAGE_ICP, n_icp);
+  if (has_kind(h, XSLAM_SEED_POSE_TRACKED)) {
+    // the tracked pose T_{g,k} enters the surface update and the ray cast perturbed
+    stage_begin(h, XSLAM_STAGE_OTHER);
+    if ((e = launch_seed_frame(h->p, h->b, nullptr, nullptr, h->d_kinds, h->d_index, 4, h->s)) != cudaSuccess) return e;
+    stage_end(h, XSLAM_STAGE_OTHER, 1);
+  }
   stage_begin(h, XSLAM_STAGE_INTEGRATE);
   if ((e = launch_integrate(h->p, h->b, h->s)) != cudaSuccess) return e;
-  stage_end(h, XSLAM_STAGE_INTEGRATE, 1);
+  stage_end(h, XSLAM_STAGE_INTEGRATE, 2 + (h->p.fresh ? 1 : 0));
   const size_t hw = (size_t)h->p.W * h->p.H;
   stage_begin(h, XSLAM_STAGE_RAYCAST);
   if ((e = launch_raycast(h->p, h->b, h->b.pose, h->b.model, h->b.model + hw, h->b.model + hw * (1 + 3 * h->p.L),
@@ -591,6 +660,11 @@ extern "C" xslam_status xslam_frame(xslam_t h, const float* depth, int depth_on_
     CU(cudaStreamSynchronize(h->s));
     return fail(h, XSLAM_ETIMEOUT, "a tensor-core wait of the proposal network ran out");
   }
+  if (h->h_status[5]) {
+    CU(cudaMemsetAsync(h->b.status + 5, 0, sizeof(int), h->s));
+    CU(cudaStreamSynchronize(h->s));
+    return fail(h, XSLAM_ETIMEOUT, "a grid barrier of the ICP launch ran out");
+  }
   if (pose_out) memcpy(pose_out, h->h_result, sizeof(double) * 12);
   if (dpose_out) memcpy(dpose_out, h->h_result + 12, sizeof(double) * 12 * h->K);
   if (dtwist_out) memcpy(dtwist_out, h->h_result + 12 + 12 * (kMaxLanes - 1), sizeof(double) * 6 * h->K);
@@ -607,10 +681,11 @@ extern "C" xslam_status xslam_sync(xslam_t h, int* n_failed) {
   if (!h) return XSLAM_EINVAL;
   CU(cudaMemcpyAsync(h->h_status, h->b.status, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->s));
   CU(cudaMemsetAsync(h->b.status + 1, 0, sizeof(int), h->s));
-  CU(cudaMemsetAsync(h->b.status + 4, 0, sizeof(int), h->s));
+  CU(cudaMemsetAsync(h->b.status + 4, 0, sizeof(int) * 2, h->s));
   CU(cudaStreamSynchronize(h->s));
   if (n_failed) *n_failed = h->h_status[1];
   if (h->h_status[4]) return fail(h, XSLAM_ETIMEOUT, "a tensor-core wait of the proposal network ran out");
+  if (h->h_status[5]) return fail(h, XSLAM_ETIMEOUT, "a grid barrier of the ICP launch ran out");
   if (h->h_status[1] > 0) {
     h->err = "ICP failed to track on some frames";
     return XSLAM_ENOTRACK;
@@ -944,7 +1019,8 @@ extern "C" xslam_status xslam_profile(xslam_t h, int enable) {
     }
     h->pframes = 0;
     CU(cudaMemsetAsync(h->b.stats, 0, sizeof(unsigned long long) * kStatIcpIters, h->s));
-  CU(cudaMemsetAsync(h->b.tile_ctr, 0, sizeof(unsigned) * 2, h->s));
+  CU(cudaMemsetAsync(h->b.tile_ctr, 0, sizeof(unsigned) * 4, h->s));
+  if (h->b.dlane) CU(cudaMemsetAsync(h->b.dlane, 0, sizeof(float) * dlane_stride(h->p) * h->max_lanes, h->s));
   }
   if (!enable && h->profiling) {
     xslam_status st = prof_accumulate(h);

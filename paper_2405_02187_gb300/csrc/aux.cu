@@ -5,17 +5,13 @@
 
 namespace xslam {
 
-// lanes j >= 1: Im exp(h_j i e_idx) T0 = h_j G_idx T0 (exact to O(h^3)); lane 0 untouched.
-__global__ void k_seed_pose(double* pose, int L, const int* kinds, const int* index, Params p) {
-  pdl_enter();
-  const int l = threadIdx.x;
-  if (l < 1 || l >= L) return;
-  const double* T0 = pose;
-  double* Tl = pose + 12 * l;
+// seed kinds (xslam_seed_kind)
+enum : int { kSeedPose0 = 0, kSeedPose = 1, kSeedTrunc = 2, kSeedDepth = 3, kSeedPoseTracked = 4 };
+
+// Tl = Im exp(h i e_idx) T0 = h G_idx T0 (exact to O(h^3)); G_idx the generator of the left twist
+// (phi then rho)
+__device__ void generator_times(int e, double h, const double* __restrict__ T0, double* __restrict__ Tl) {
   for (int i = 0; i < 12; ++i) Tl[i] = 0.0;
-  if (kinds[l] != 0) return;  // not a POSE0 lane
-  const int e = index[l];
-  const double h = p.h[l];
   if (e < 3) {
     // [e] T0: rows of the generator applied to every column of [R | t]
     for (int q = 0; q < 4; ++q) {
@@ -31,6 +27,46 @@ __global__ void k_seed_pose(double* pose, int L, const int* kinds, const int* in
   } else {
     Tl[4 * (e - 3) + 3] = h;
   }
+}
+
+// Frame 0: lanes of the pose kinds (POSE0, and the per-frame kinds, whose start and tracked pose are
+// T_0 itself at frame 0) get h G_idx T_0; every other lane is zero. Lane 0 untouched.
+__global__ void k_seed_pose(double* pose, int L, const int* kinds, const int* index, Params p) {
+  pdl_enter();
+  const int l = threadIdx.x;
+  if (l < 1 || l >= L) return;
+  const int k = kinds[l];
+  double* Tl = pose + 12 * l;
+  if (k == kSeedPose0 || k == kSeedPose || k == kSeedPoseTracked) {
+    generator_times(index[l], p.h[l], pose, Tl);
+  } else {
+    for (int i = 0; i < 12; ++i) Tl[i] = 0.0;
+  }
+}
+
+// Per-frame pose lanes of a tracked frame (X-SLAM Sec. 4.1, Eq. lie promoting frame k's own pose):
+// mode bit 0 restarts them (the imaginary parts earlier frames left in the pose, the previous pose and
+// T_{k-2} are dropped), bit 1 perturbs ICP's start (kind POSE; also the proposal's start candB), bit 2
+// the tracked pose (kind POSE_TRACKED). One thread per lane.
+__global__ void k_seed_frame(Params p, double* __restrict__ pose, double* __restrict__ pose_prev,
+                             double* __restrict__ pose_pp, double* __restrict__ candB, const int* __restrict__ kinds,
+                             const int* __restrict__ index, int mode) {
+  pdl_enter();
+  const int l = threadIdx.x;
+  if (l < 1 || l >= p.L || !((p.fresh >> l) & 1u)) return;
+  const int k = kinds[l];
+  if (mode & 1) {
+    for (int i = 0; i < 12; ++i) {
+      pose[12 * l + i] = 0.0;
+      pose_prev[12 * l + i] = 0.0;
+      if (pose_pp) pose_pp[12 * l + i] = 0.0;
+    }
+  }
+  if ((mode & 2) && k == kSeedPose) {
+    generator_times(index[l], p.h[l], pose, pose + 12 * l);
+    if (candB) generator_times(index[l], p.h[l], candB, candB + 12 * l);
+  }
+  if ((mode & 4) && k == kSeedPoseTracked) generator_times(index[l], p.h[l], pose, pose + 12 * l);
 }
 
 __global__ void k_readout(const double* __restrict__ pose, int L, Params p, double* __restrict__ out) {
@@ -142,6 +178,14 @@ __global__ void __launch_bounds__(256) k_loss(Params p, const float* __restrict_
 
 cudaError_t launch_seed_pose(const Params& p, const Buffers& b, const int* kinds, const int* index, cudaStream_t s) {
   const cudaError_t e = launch_pdl(k_seed_pose, dim3(1), dim3(32), 0, s, b.pose, p.L, kinds, index, p);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_frame(const Params& p, const Buffers& b, double* pose_pp, double* candB, const int* kinds,
+                              const int* index, int mode, cudaStream_t s) {
+  const cudaError_t e = launch_pdl(k_seed_frame, dim3(1), dim3(32), 0, s, p, b.pose, b.pose_prev, pose_pp, candB, kinds,
+                                   index, mode);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -47,6 +47,7 @@ struct xslam_batch_s {
   std::vector<std::vector<xslam_seed>> seeds;      // lanes recorded at create
   std::vector<std::array<double, 12>> pose0;       // frame-0 pose recorded at create
   std::vector<std::array<int, 3>> nblk0;           // default ICP grids
+  std::vector<char> persistent0;                   // the handles' ICP kernel choice, restored at destroy
   cudaStream_t s = nullptr, user = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_start = nullptr;
   std::vector<cudaEvent_t> ev_join;                // per trajectory, end of its chain (join edge)
@@ -88,6 +89,10 @@ static void drop_graph(xslam_batch_t b) {
 static void free_batch(xslam_batch_t b) {
   if (b->s) cudaStreamSynchronize(b->s);
   drop_graph(b);
+  for (size_t i = 0; i < b->persistent0.size(); ++i) {
+    b->hs[i]->icp_persistent = b->persistent0[i] != 0;
+    handle_drop_graphs(b->hs[i]);
+  }
   for (int r = 0; r < kRing; ++r) {
     if (b->h_src[r]) cudaFreeHost(b->h_src[r]);
     if (b->ev_slot[r]) cudaEventDestroy(b->ev_slot[r]);
@@ -153,6 +158,11 @@ extern "C" xslam_status xslam_batch_create(xslam_batch_t* out, int n, xslam_t co
     b->max_hw = std::max(b->max_hw, cnt[i]);
     b->seeds.emplace_back(h->seeds, h->seeds + h->K);
     b->nblk0.push_back({h->nblk[0], h->nblk[1], h->nblk[2]});
+    // the trajectories' chains run as concurrent graph branches: each ICP iteration is its own launch
+    // sized to its level (a cooperative launch holds a block on every SM for the whole ICP range)
+    b->persistent0.push_back(h->icp_persistent ? 1 : 0);
+    h->icp_persistent = false;
+    handle_drop_graphs(h);
     std::array<double, 12> T{};
     cudaStreamSynchronize(h->s);
     if (cudaMemcpy(T.data(), h->b.pose, sizeof(double) * 12, cudaMemcpyDeviceToHost) != cudaSuccess)

@@ -25,16 +25,16 @@ namespace xslam {
 constexpr int kBX = 8, kBY = 8, kBZ = 8;  // tile of voxels: one brick of the TSDF layout
 constexpr int kFuseThreads = kBX * kBY * kBZ;  // a thread per voxel of a tile
 
-// Update voxel (i, j, k) if the frame observes it; returns whether it did. NL = 1 + K lanes.
-template <int NL>
-__device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restrict__ D, const float (*sT)[12],
-                                           const float (*sC)[3],
-                                           float* __restrict__ F, float* __restrict__ Wt,
-                                           float* __restrict__ F0lin, int i, int j, int k, size_t n, size_t v) {
-  const float* T = sT[0];
-  const float dx = p.ox + (i + 0.5f) * p.voxel - T[3];
-  const float dy = p.oy + (j + 0.5f) * p.voxel - T[7];
-  const float dz = p.oz + (k + 0.5f) * p.voxel - T[11];
+// Real part of the update of voxel (i, j, k) at offset (dx, dy, dz) = centre - t from the camera centre:
+// whether the frame updates it, and what its lanes need. NL = 1 + K lanes.
+struct VoxDec {
+  float FD;             // F_D (real)
+  float cxl, cyl, czl;  // the sdf tangent as a linear form of the lane's p_c' (unclamped voxels)
+  bool clamp;           // F_D = 1 on every lane: no tangent
+};
+
+__device__ __forceinline__ bool fuse_decide(const Params& p, const float* __restrict__ D, const float* T, float dx,
+                                            float dy, float dz, VoxDec& o) {
   const float pcx = T[0] * dx + T[4] * dy + T[8] * dz;
   const float pcy = T[1] * dx + T[5] * dy + T[9] * dz;
   const float pcz = T[2] * dx + T[6] * dy + T[10] * dz;
@@ -53,48 +53,44 @@ __device__ __forceinline__ bool fuse_voxel(const Params& p, const float* __restr
   const float Lx = (1.f - a) * (1.f - bb) * d00 + a * (1.f - bb) * d10 + (1.f - a) * bb * d01 + a * bb * d11;
   const float sdf = Lx - pcz;
   if (sdf < -p.mu) return false;
-  const bool clamp = sdf >= p.mu;
-  const float FD = clamp ? 1.f : sdf / p.mu;
-
-  // every lane of the voxel is loaded before any is stored: the loads then leave together (one
-  // memory round trip per voxel) instead of one round trip per lane behind each store to F
-  const float w = Wt[v];
-  const float f0 = F[v];
-  float fl[NL];
-#pragma unroll
-  for (int l = 1; l < NL; ++l) fl[l] = F[(size_t)l * n + v];
-  const float w1 = w + 1.f;
-  const float inv = 1.f / w1;
-  const float Fn = (w * f0 + FD) / w1;  // an unobserved voxel (w = 0) takes F_D whatever its sentinel value
-  F[v] = Fn;
-  F0lin[(size_t)i + (size_t)p.nx * ((size_t)j + (size_t)p.ny * k)] = Fn;
-  Wt[v] = (p.w_max > 0.f) ? fminf(w1, p.w_max) : w1;
-
-  if (clamp) {  // F_D = 1 whatever the lane: no tangent
-#pragma unroll
-    for (int l = 1; l < NL; ++l) F[(size_t)l * n + v] = w * fl[l] * inv;
-    return true;
-  }
+  o.clamp = sdf >= p.mu;
+  o.FD = o.clamp ? 1.f : sdf / p.mu;
   // The tangent of sdf = L(x) - z_c is linear in the lane's p_c': with x' = fx (p_cx' - q_x p_cz') / z,
   // y' = fy (p_cy' - q_y p_cz') / z and the bilinear L's slopes dL/da, dL/db,
   // sdf' = c_x p_cx' + c_y p_cy' + c_z p_cz' + D', c_x = dL/da fx / z, c_y = dL/db fy / z,
   // c_z = -(c_x q_x + c_y q_y) - 1.
   const float dLda = (1.f - bb) * (d10 - d00) + bb * (d11 - d01);
   const float dLdb = (1.f - a) * (d01 - d00) + a * (d11 - d10);
-  const float c_x = dLda * p.fx * invz, c_y = dLdb * p.fy * invz;
-  const float c_z = -(c_x * qx + c_y * qy) - 1.f;
-#pragma unroll
-  for (int l = 1; l < NL; ++l) {
-    const float* Tl = sT[l];
-    // p_c' = dR^T (p - t) - R^T dt, the second term a per-lane constant
-    const float pcx_l = Tl[0] * dx + Tl[4] * dy + Tl[8] * dz + sC[l][0];
-    const float pcy_l = Tl[1] * dx + Tl[5] * dy + Tl[9] * dz + sC[l][1];
-    const float pcz_l = Tl[2] * dx + Tl[6] * dy + Tl[10] * dz + sC[l][2];
-    const float sdf_l = c_x * pcx_l + c_y * pcy_l + c_z * pcz_l + p.dD[l];
-    const float FD_l = (sdf_l - FD * p.dmu[l]) * p.inv_mu;
-    F[(size_t)l * n + v] = (w * fl[l] + FD_l) * inv;
-  }
+  o.cxl = dLda * p.fx * invz;
+  o.cyl = dLdb * p.fy * invz;
+  o.czl = -(o.cxl * qx + o.cyl * qy) - 1.f;
   return true;
+}
+
+// The lane-l tangent of F_D of an unclamped voxel: sdf' from the lane's p_c' = dR^T (p - t) - R^T dt
+// (the second term a per-lane constant sC) and D' (all-pixel DEPTH h, or the single-pixel lane's Im
+// depth map bilinear in the real cell), then F_D' = (sdf' - F_D mu') / mu.
+__device__ __forceinline__ float fuse_lane_FD(const Params& p, const float* __restrict__ dlane, const float* sT0,
+                                              const float* Tl, const float* C, int l, const VoxDec& o, float dx,
+                                              float dy, float dz) {
+  const float pcx_l = Tl[0] * dx + Tl[4] * dy + Tl[8] * dz + C[0];
+  const float pcy_l = Tl[1] * dx + Tl[5] * dy + Tl[9] * dz + C[1];
+  const float pcz_l = Tl[2] * dx + Tl[6] * dy + Tl[10] * dz + C[2];
+  float Dl = p.dD[l];
+  if (p.dpix[l] >= 0) {
+    // the projection again (the real pose's, as fuse_decide took it)
+    const float* T = sT0;
+    const float pcx = T[0] * dx + T[4] * dy + T[8] * dz;
+    const float pcy = T[1] * dx + T[5] * dy + T[9] * dz;
+    const float invz = 1.f / (T[2] * dx + T[6] * dy + T[10] * dz);
+    const float x = p.fx * (pcx * invz) + p.cx, y = p.fy * (pcy * invz) + p.cy;
+    const int i0 = (int)x, j0 = (int)y;
+    const float a = x - i0, bb = y - j0;
+    const float* m = dlane + dlane_offset(p, l, 0) + (size_t)j0 * p.W + i0;
+    Dl += (1.f - a) * (1.f - bb) * m[0] + a * (1.f - bb) * m[1] + (1.f - a) * bb * m[p.W] + a * bb * m[p.W + 1];
+  }
+  const float sdf_l = o.cxl * pcx_l + o.cyl * pcy_l + o.czl * pcz_l + Dl;
+  return (sdf_l - o.FD * p.dmu[l]) * p.inv_mu;
 }
 
 // One thread per 8 x 8 x 8 tile: a tile any of whose voxels the frame can update is appended to the
@@ -146,16 +142,24 @@ __global__ void __launch_bounds__(256) k_fuse_tiles(Params p, const double* __re
   }
 }
 
-// Fixed grid over the tile list; a block takes one tile at a time, a thread per voxel: thread t of the
-// block is the brick's voxel t (x = t mod 8, y = t / 8 mod 8, z = t / 64), so a warp reads and writes
-// 128 consecutive bytes of every plane. The last block to finish clears the list counters for the next
-// launch.
+// Fixed grid over the tile list; a block takes one tile at a time, a thread per 4 x-consecutive voxels of
+// a brick row: thread t holds voxels 4 (t mod 2) .. + 3 of row y = t / 2 mod 8, z = t / 16, so a warp's
+// 128-bit loads and stores cover 512 consecutive bytes of every plane. A thread first takes the real
+// decisions of its 4 voxels; if the frame updates any of them it loads W and every lane of all 4 (one
+// 16-byte load per plane, all issued before any store), updates the observed ones and stores the 4
+// (the others unchanged). The last block to finish clears the list counters for the next launch.
+constexpr int kQuadThreads = 128;
+
+// resident blocks of 128 threads per SM: register budgets of 64, 96 and 128 per thread by lane count
+__host__ __device__ constexpr int fuse_blocks_per_sm(int NL) { return NL <= 2 ? 8 : (NL <= 9 ? 5 : 4); }
+
 template <int NL>
-__global__ void __launch_bounds__(kFuseThreads, NL <= 9 ? 2 : 1) k_integrate(Params p, const float* __restrict__ D,
+__global__ void __launch_bounds__(kQuadThreads, fuse_blocks_per_sm(NL)) k_integrate(Params p, const float* __restrict__ D,
                                                         const double* __restrict__ pose, float* __restrict__ F,
                                                         float* __restrict__ Wt, float* __restrict__ F0lin,
                                                         unsigned long long* __restrict__ stats,
-                                                        const int* __restrict__ tiles, unsigned* __restrict__ ctr) {
+                                                        const int* __restrict__ tiles, unsigned* __restrict__ ctr,
+                                                        const float* __restrict__ dlane, int* __restrict__ tiles_prev) {
   pdl_enter();
   __shared__ float sT[NL][12];
   __shared__ float sC[NL][3];  // -R^T dt of each lane: the voxel-independent part of its p_c tangent
@@ -171,14 +175,72 @@ __global__ void __launch_bounds__(kFuseThreads, NL <= 9 ? 2 : 1) k_integrate(Par
   const unsigned count = ctr[0];
   const int ntx = (p.nx + kBX - 1) / kBX, nty = (p.ny + kBY - 1) / kBY;
   const size_t n = vox_plane(p);
-  const int cx = tid & 7, cy = (tid >> 3) & 7, cz = tid >> 6;
+  const int qx = (tid & 1) * 4, cy = (tid >> 1) & 7, cz = tid >> 4;
+  const int off = cz * 64 + cy * 8 + qx;  // the quad's first voxel in the brick
+  const bool lin4 = (p.nx & 3) == 0;      // the linear copy's rows keep 16-byte alignment
+  const float* T = sT[0];
   int cnt = 0;
   for (unsigned q = blockIdx.x; q < count; q += gridDim.x) {
     const int t = tiles[q];
-    const int i = (t % ntx) * kBX + cx, j = ((t / ntx) % nty) * kBY + cy, k = (t / (ntx * nty)) * kBZ + cz;
-    // the tile is brick t, whose voxel tid sits at t 512 + tid
-    if (i < p.nx && j < p.ny && k < p.nz)
-      cnt += fuse_voxel<NL>(p, D, sT, sC, F, Wt, F0lin, i, j, k, n, ((size_t)t << 9) + tid);
+    if (p.fresh && tid == 0) tiles_prev[q] = t;  // the next frame clears its restarted lanes here
+    const int i0 = (t % ntx) * kBX + qx, j = ((t / ntx) % nty) * kBY + cy, k = (t / (ntx * nty)) * kBZ + cz;
+    if (j >= p.ny || k >= p.nz) continue;
+    const float dy = p.oy + (j + 0.5f) * p.voxel - T[7];
+    const float dz = p.oz + (k + 0.5f) * p.voxel - T[11];
+    VoxDec dec[4];
+    unsigned upd = 0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float dx = p.ox + (i0 + v + 0.5f) * p.voxel - T[3];
+      if (i0 + v < p.nx && fuse_decide(p, D, T, dx, dy, dz, dec[v])) upd |= 1u << v;
+    }
+    if (!upd) continue;
+    const size_t base = ((size_t)t << 9) + off;
+    float4 w4 = *reinterpret_cast<const float4*>(Wt + base);
+    float4 f4[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) f4[l] = *reinterpret_cast<const float4*>(F + (size_t)l * n + base);
+    float w[4] = {w4.x, w4.y, w4.z, w4.w};
+    float f[NL][4];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      f[l][0] = f4[l].x;
+      f[l][1] = f4[l].y;
+      f[l][2] = f4[l].z;
+      f[l][3] = f4[l].w;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (!((upd >> v) & 1u)) continue;
+      const float w0 = w[v];
+      const float w1 = w0 + 1.f;
+      const float inv = 1.f / w1;
+      f[0][v] = (w0 * f[0][v] + dec[v].FD) / w1;  // an unobserved voxel (w = 0) takes F_D whatever its sentinel
+      w[v] = (p.w_max > 0.f) ? fminf(w1, p.w_max) : w1;
+      if (dec[v].clamp) {  // F_D = 1 whatever the lane: no tangent
+#pragma unroll
+        for (int l = 1; l < NL; ++l) f[l][v] = w0 * f[l][v] * inv;
+      } else {
+        const float dx = p.ox + (i0 + v + 0.5f) * p.voxel - T[3];
+#pragma unroll
+        for (int l = 1; l < NL; ++l)
+          f[l][v] = (w0 * f[l][v] + fuse_lane_FD(p, dlane, T, sT[l], sC[l], l, dec[v], dx, dy, dz)) * inv;
+      }
+    }
+    *reinterpret_cast<float4*>(Wt + base) = make_float4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+    for (int l = 0; l < NL; ++l)
+      *reinterpret_cast<float4*>(F + (size_t)l * n + base) = make_float4(f[l][0], f[l][1], f[l][2], f[l][3]);
+    // the march's linear copy of Re F (unchanged voxels rewrite the value they hold in both layouts)
+    const size_t li = (size_t)i0 + (size_t)p.nx * ((size_t)j + (size_t)p.ny * k);
+    if (lin4 && i0 + 3 < p.nx) {
+      *reinterpret_cast<float4*>(F0lin + li) = make_float4(f[0][0], f[0][1], f[0][2], f[0][3]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if ((upd >> v) & 1u) F0lin[li + v] = f[0][v];
+    }
+    cnt += __popc(upd);
   }
   // updated-voxel count: warp sums, one atomic per warp
 #pragma unroll
@@ -191,15 +253,32 @@ __global__ void __launch_bounds__(kFuseThreads, NL <= 9 ? 2 : 1) k_integrate(Par
   }
   __syncthreads();
   if (s_last && tid == 0) {
+    ctr[2] = p.fresh ? count : 0u;
     ctr[0] = 0u;
     ctr[1] = 0u;
   }
 }
 
+// Restarted lanes (per-frame pose seeds): before frame k's update their TSDF planes must hold no
+// imaginary part, so that Im F_k is frame k's derivative alone. Only the bricks of the last update can
+// hold one: a block per brick of that list zeroes those lanes' planes there.
+__global__ void __launch_bounds__(kFuseThreads) k_clear_fresh(Params p, float* __restrict__ F,
+                                                               const int* __restrict__ tiles_prev,
+                                                               const unsigned* __restrict__ ctr) {
+  pdl_enter();
+  const unsigned count = ctr[2];
+  const size_t n = vox_plane(p);
+  for (unsigned q = blockIdx.x; q < count; q += gridDim.x) {
+    const size_t v = ((size_t)tiles_prev[q] << 9) + threadIdx.x;
+    for (int l = 1; l < p.L; ++l)
+      if ((p.fresh >> l) & 1u) F[(size_t)l * n + v] = 0.f;
+  }
+}
+
 template <int NL>
 static cudaError_t launch_integrate_nl(const Params& p, const Buffers& b, int grid, cudaStream_t s) {
-  return launch_pdl(k_integrate<NL>, dim3(grid), dim3(kFuseThreads), 0, s, p, b.pyr[0], b.pose, b.F, b.Wt, b.F0lin,
-                    b.stats, b.tiles, b.tile_ctr);
+  return launch_pdl(k_integrate<NL>, dim3(grid), dim3(kQuadThreads), 0, s, p, b.pyr[0], b.pose, b.F, b.Wt, b.F0lin,
+                    b.stats, b.tiles, b.tile_ctr, (const float*)b.dlane, b.tiles_prev);
 }
 
 int fuse_tile_count(const Params& p) {
@@ -215,14 +294,24 @@ cudaError_t launch_fuse_tiles(const Params& p, const Buffers& b, const double* p
                     b.tile_ctr);
 }
 
+cudaError_t launch_clear_fresh(const Params& p, const Buffers& b, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return launch_pdl(k_clear_fresh, dim3(std::max(1, std::min(fuse_tile_count(p), 4 * sms))), dim3(kFuseThreads), 0, s,
+                    p, b.F, (const int*)b.tiles_prev, (const unsigned*)b.tile_ctr);
+}
+
 cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s) {
   int dev = 0, sms = 0;  // the current device's SM count (queried per call: a handle may live on any device)
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int nt = fuse_tile_count(p);
-  cudaError_t e = launch_fuse_tiles(p, b, b.pose, s);
+  cudaError_t e = cudaSuccess;
+  if (p.fresh && (e = launch_clear_fresh(p, b, s)) != cudaSuccess) return e;
+  e = launch_fuse_tiles(p, b, b.pose, s);
   if (e != cudaSuccess) return e;
-  const int grid = std::max(1, std::min(nt, 4 * sms));
+  const int grid = std::max(1, std::min(nt, fuse_blocks_per_sm(p.L) * sms));  // the resident blocks
   switch (p.L) {
     case 1: return launch_integrate_nl<1>(p, b, grid, s);
     case 2: return launch_integrate_nl<2>(p, b, grid, s);

@@ -39,6 +39,8 @@ struct xslam_s {
   float* prop_ws = nullptr; // its split-K workspace
   int nblk[3] = {1, 1, 1};
   int nblk_max = 1;
+  int nblk_run = 1;             // blocks of the cooperative ICP launch
+  bool icp_persistent = true;   // the frame chain runs each ICP range in one cooperative launch
   cudaGraphExec_t g_first = nullptr, g_track = nullptr;
   bool use_graphs = true;
   // stage profiling (xslam_profile): one event pair per stage and frame, accumulated on read

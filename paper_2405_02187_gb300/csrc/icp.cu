@@ -26,7 +26,7 @@ constexpr int kMaxPartials = 256;  // upper bound of the grid size (partials per
 __host__ __device__ __forceinline__ int icp_pstride(int nblk) { return (nblk + 3) & ~3; }
 
 struct Lvl {
-  int W, H, s;
+  int W, H, s, level;
   float fx, fy, cx, cy;
 };
 
@@ -109,83 +109,39 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// kStop: the stop tolerance p.icp_stop is in use (and the iteration counter): a launch after its level
-// converged returns at once. Without it the kernel is the fixed-count iteration of the method.
-template <bool kStop>
-__global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int flags, int reps) {
-  pdl_enter();
-  const int L = p.L;
-  const int warp = threadIdx.x >> 5, lid = threadIdx.x & 31;
-  const int ln = warp % L, rep = warp / L;
-  __shared__ float sT[kMaxLanes][12];
-  __shared__ float sP[kMaxLanes][12];
-  __shared__ int s_skip, s_last;
-  __shared__ float s_red[kNT * kMaxLanes];  // [rep][lane][27]; reps * L <= 16 by construction
-  __shared__ int s_cnt[32];
-  __shared__ double sA[kMaxLanes * kNT];
-  __shared__ double sx[kMaxLanes][6];
-  __shared__ Ldl32 s_ldl;
-  __shared__ double s_half[2 * kNT * kMaxLanes];
-  __shared__ float sAf[kNT * kMaxLanes];
-  __shared__ float sxf[kMaxLanes][6], srf[kMaxLanes][6], sdf[kMaxLanes][6];
-  __shared__ SeCoefF scf[kMaxLanes];
-  __shared__ float sxs[kMaxLanes][6];
-  __shared__ float sdl[kMaxLanes][12];
-  __shared__ int s_ncorr, s_fail, s_conv;
-  extern __shared__ float s_rec[];  // [rep][chunk of the group][field][pixel]: reps * L * kRec * 32 floats
+// Shared memory of the ICP kernels (static part; the per-pixel records are dynamic).
+struct IcpShared {
+  float sT[kMaxLanes][12];   // pose lanes of the current iterate (FP32 copy for the pixel work)
+  float sP[kMaxLanes][12];   // pose lanes the model was ray cast at
+  float sZero[12];
+  float s_red[kNT * kMaxLanes];  // [rep][lane][27]; reps * L <= 16 by construction
+  int s_cnt[32];
+  double sA[kMaxLanes * kNT];
+  double sx[kMaxLanes][6];
+  Ldl32 s_ldl;
+  double s_half[2 * kNT * kMaxLanes];
+  float sAf[kNT * kMaxLanes];
+  float sxf[kMaxLanes][6], srf[kMaxLanes][6], sdf[kMaxLanes][6];
+  SeCoefF scf[kMaxLanes];
+  float sxs[kMaxLanes][6];
+  float sdl[kMaxLanes][12];
+  int s_ncorr, s_fail;
+};
 
-  if (threadIdx.x == 0) {
-    s_skip = b.status[0];
-    // status[3]: the level converged (a step below p.icp_stop); only its first iteration ignores it
-    if (kStop) s_conv = (flags & (kIcpFirst | kIcpNoUpdate)) ? 0 : b.status[3];
-  }
-  for (int i = threadIdx.x; i < L * 12; i += blockDim.x) {
-    sT[i / 12][i % 12] = (float)b.pose[i];
-    sP[i / 12][i % 12] = (float)b.pose_prev[i];
-  }
-  __syncthreads();
-  if (kStop && (s_skip || s_conv) && !(flags & kIcpNoUpdate)) {
-    // nothing to compute after a failure or after the level converged; the frame's last iteration
-    // still closes the frame: fall back to T_{k-1} on a failure and count it
-    if ((flags & kIcpLast) && blockIdx.x == 0) {
-      if (s_skip && threadIdx.x < 12 * L) b.pose[threadIdx.x] = b.pose_prev[threadIdx.x];
-      if (threadIdx.x == 0) {
-        if (s_skip) {
-          b.status[1] += 1;
-          b.status[2] = 0;
-        }
-        b.status[0] = 0;
-        b.status[3] = 0;
-      }
-    }
-    return;
-  }
-
-  float acc[kNT];
-#pragma unroll
-  for (int q = 0; q < kNT; ++q) acc[q] = 0.f;
-  int cnt = 0;
-
-  // Work unit: a group of L chunks of 32 pixels per replica. Every warp of the replica computes the
-  // real part of one chunk of the group (correspondence, residual, Jacobian, bilinear derivatives) into
-  // a shared-memory record; after a named barrier every warp reads all L records and adds the sums of
-  // its own lane: lane 0 the real normal equations, lane l > 0 their tangent, for which it loads only
-  // lane l's model taps. A second barrier frees the records for the next group.
-  int nloop = 0, gbase = 0, gstride = 1;
-  const int npx = lv.W * lv.H;
-  const int nchunk = (npx + 31) >> 5;
-  {
-    const int ngroup = (nchunk + L - 1) / L;
-    gbase = blockIdx.x * reps + rep;
-    gstride = gridDim.x * reps;
-    nloop = (!s_skip && gbase < ngroup) ? (ngroup - gbase + gstride - 1) / gstride : 0;
-  }
+// Level-l pixel chunks of this replica: groups gbase, gbase + gstride, ... of L chunks of 32 pixels.
+// Every warp of the replica computes the real part of one chunk of the group (correspondence, residual,
+// Jacobian, bilinear derivatives) into a shared-memory record; after a named barrier every warp reads
+// all L records and adds the sums of its own lane: lane 0 the real normal equations, lane l > 0 their
+// tangent, for which it loads only lane l's model taps. A second barrier frees the records.
+__device__ __forceinline__ void icp_pixels(const Params& p, const Buffers& b, const Lvl& lv, const IcpShared& S,
+                                           float* __restrict__ recs, int L, int ln, int lid, int rep, int gbase,
+                                           int gstride, int nloop, float* acc, int& cnt) {
   const float* D = lv.s == 1 ? b.pyr[0] : (lv.s == 2 ? b.pyr[1] : b.pyr[2]);
   const size_t hw0 = (size_t)p.W * p.H;
   const float* mdep = b.model;
   const float* mV = b.model + hw0;
   const float* mN = b.model + hw0 * (1 + 3 * L);
-  float* recs = s_rec + (size_t)rep * L * kRec * 32;
+  const int npx = lv.W * lv.H;
   for (int it = 0; it < nloop; ++it) {
     const int ch = (gbase + it * gstride) * L + ln;
     {
@@ -202,8 +158,8 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
         dyp = D[px + lv.W];
       }
       ok = ok && d0 > 0.f && dxp > 0.f && dyp > 0.f;
-      const float* T = sT[0];
-      const float* P = sP[0];
+      const float* T = S.sT[0];
+      const float* P = S.sP[0];
       const float rx = (u - lv.cx) / lv.fx, ry = (v - lv.cy) / lv.fy;
       const float rx1 = (u + 1 - lv.cx) / lv.fx, ry1 = (v + 1 - lv.cy) / lv.fy;
       const float V[3] = {d0 * rx, d0 * ry, d0};
@@ -270,7 +226,7 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
                           nn[0], nn[1], nn[2]};
       {
         float* R_ = rec + lid;
-        R_[RV * 32] = __int_as_float(ok ? 1 : 0);
+        R_[RV * 32] = __int_as_float(ok ? px + 1 : 0);  // 0: no correspondence; else the pixel + 1
         if (ok) {
           R_[RD * 32] = d0;
           R_[RRX * 32] = rx;
@@ -314,13 +270,17 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
         const float hJ[6] = {0.5f * J[0], 0.5f * J[1], 0.5f * J[2], 0.5f * J[3], 0.5f * J[4], 0.5f * J[5]};
         accum(acc, hJ, 0.5f * res, J, res);
       } else {
-        const float* T = sT[0];
-        const float* P = sP[0];
-        const float* Tl = sT[ln];
-        const float* Pl = sP[ln];
+        const float* T = S.sT[0];
+        const float* P = S.sP[0];
+        const float* Tl = S.sT[ln];
+        // a restarted lane (per-frame pose seed) carries no derivative in the previous pose or the model
+        const bool fresh = (p.fresh >> ln) & 1u;
+        const float* Pl = fresh ? S.sZero : S.sP[ln];
         const float d0 = R_[RD * 32], rx = R_[RRX * 32], ry = R_[RRY * 32];
         const float V[3] = {d0 * rx, d0 * ry, d0};
-        const float dDl = p.dD[ln];
+        float dDl = p.dD[ln];
+        if (p.dpix[ln] >= 0)  // single-pixel DEPTH lane: the level's Im depth map at this pixel
+          dDl += b.dlane[dlane_offset(p, ln, lv.level) + (__float_as_int(R_[RV * 32]) - 1)];
         const float Vl[3] = {dDl * rx, dDl * ry, dDl};
         const float e0 = R_[RE * 32], e1 = R_[(RE + 1) * 32], e2 = R_[(RE + 2) * 32];
         const float qx = R_[RQX * 32], qy = R_[RQY * 32], iz = R_[RIZ * 32];
@@ -354,12 +314,17 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
         float ql[3], nl[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-          const float* Vpl = mVl + (size_t)r * hw0;
-          const float* Npl = mNl + (size_t)r * hw0;
-          ql[r] = R_[(RDQA + r) * 32] * al + R_[(RDQB + r) * 32] * bl + w00 * Vpl[t00] + w10 * Vpl[t10] +
-                  w01 * Vpl[t01] + w11 * Vpl[t11];
-          nl[r] = R_[(RDNA + r) * 32] * al + R_[(RDNB + r) * 32] * bl + w00 * Npl[t00] + w10 * Npl[t10] +
-                  w01 * Npl[t01] + w11 * Npl[t11];
+          ql[r] = R_[(RDQA + r) * 32] * al + R_[(RDQB + r) * 32] * bl;
+          nl[r] = R_[(RDNA + r) * 32] * al + R_[(RDNB + r) * 32] * bl;
+        }
+        if (!fresh) {
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const float* Vpl = mVl + (size_t)r * hw0;
+            const float* Npl = mNl + (size_t)r * hw0;
+            ql[r] += w00 * Vpl[t00] + w10 * Vpl[t10] + w01 * Vpl[t01] + w11 * Vpl[t11];
+            nl[r] += w00 * Npl[t00] + w10 * Npl[t10] + w01 * Npl[t01] + w11 * Npl[t11];
+          }
         }
         const float dfl[3] = {ppl[0] - ql[0], ppl[1] - ql[1], ppl[2] - ql[2]};
         const float resl = dfl[0] * nn[0] + dfl[1] * nn[1] + dfl[2] * nn[2] + df[0] * nl[0] + df[1] * nl[1] + df[2] * nl[2];
@@ -372,8 +337,15 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
     }
     named_barrier(1 + rep, 32 * L);
   }
+}
 
-  // ---------------- block reduction ----------------
+// Block reduction of the threads' sums: warp shuffles, then the replicas of a lane added in shared
+// memory; the block's 27 L sums go to column `col` of the value-major partials ([value][stride], so that
+// the cross-block sum reads each value's row with coalesced loads) and its correspondence count to
+// partial_n[col]. The last column of a launch pads its rows with zeros up to the stride.
+__device__ __forceinline__ void icp_block_sums(IcpShared& S, float* acc, int cnt, int L, int reps, int ln, int rep,
+                                               int warp, int lid, float* __restrict__ partial, int pst, int col,
+                                               int ncol, int* __restrict__ partial_n) {
 #pragma unroll
   for (int q = 0; q < kNT; ++q) {
     float x = acc[q];
@@ -385,66 +357,53 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   if (lid == 0) {
 #pragma unroll
-    for (int q = 0; q < kNT; ++q) s_red[(rep * L + ln) * kNT + q] = acc[q];
-    s_cnt[warp] = cnt;
+    for (int q = 0; q < kNT; ++q) S.s_red[(rep * L + ln) * kNT + q] = acc[q];
+    S.s_cnt[warp] = cnt;
   }
   __syncthreads();
-  // partials are stored value-major ([value][block]) so that the last block reads each value's
-  // per-block sums with coalesced warp loads
-  const int pst = icp_pstride(gridDim.x);
   for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) {
     float s = 0.f;
-    for (int r = 0; r < reps; ++r) s += s_red[r * L * kNT + i];
-    b.partial[(size_t)i * pst + blockIdx.x] = s;
-    if (blockIdx.x == gridDim.x - 1)  // the row padding of this launch's stride reads as zero
-      for (int k = gridDim.x; k < pst; ++k) b.partial[(size_t)i * pst + k] = 0.f;
+    for (int r = 0; r < reps; ++r) s += S.s_red[r * L * kNT + i];
+    partial[(size_t)i * pst + col] = s;
+    if (col == ncol - 1)  // the row padding of this launch's stride reads as zero
+      for (int k = ncol; k < pst; ++k) partial[(size_t)i * pst + k] = 0.f;
   }
   if (threadIdx.x == 0) {
     int c = 0;
-    for (int r = 0; r < reps; ++r) c += s_cnt[r * L];
-    b.partial_n[blockIdx.x] = c;
+    for (int r = 0; r < reps; ++r) c += S.s_cnt[r * L];
+    partial_n[col] = c;
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned t = atomicAdd(b.ticket, 1u);
-    s_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
+}
 
-  // ---------------- last block: FP64 cross-block sum ----------------
-  // value v is summed by two threads, one per half of its row of block partials: all float4 loads of a
-  // half (up to 20, i.e. grids of up to 160 blocks) issued together, so the read costs one L2 round
-  // trip; FP32 sums of 16 partials, FP64 accumulation of those sums, FP64 add of the two halves.
-  // Different values sit in different lanes, so each FP64 warp instruction adds 32 values.
+// FP64 cross-block sum of the partials of `ncol` blocks into S.sA (27 L values) and S.s_ncorr. Value v
+// is summed by two threads, one per half of its row: all float4 loads of a half (up to 20, i.e. up to
+// 160 columns) issued together, FP32 sums of 16 partials, FP64 accumulation of those sums, FP64 add of
+// the two halves. Different values sit in different lanes, so each FP64 warp instruction adds 32 values.
+// The order is fixed by the column count alone: every block that runs it gets the same bits.
+__device__ __forceinline__ void icp_cross_sum(IcpShared& S, const float* __restrict__ partial, int pst, int ncol,
+                                              const int* __restrict__ partial_n, int L, int warp, int lid) {
   const int NV = L * kNT;
-  const int pstride = icp_pstride(gridDim.x);
   if (warp == (int)(blockDim.x >> 5) - 1) {
     // the last warp adds the per-block correspondence counts: 8 loads per lane in flight at once
     int c = 0;
-    for (int k0 = 0; k0 < (int)gridDim.x; k0 += 256) {
+    for (int k0 = 0; k0 < ncol; k0 += 256) {
       int q[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int k = k0 + lid + 32 * j;
-        q[j] = k < (int)gridDim.x ? __ldcg(&b.partial_n[k]) : 0;
+        q[j] = k < ncol ? __ldcg(&partial_n[k]) : 0;
       }
 #pragma unroll
       for (int j = 0; j < 8; ++j) c += q[j];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lid == 0) {
-      s_ncorr = c;
-      *b.ticket = 0u;  // ready for the next launch
-    }
+    if (lid == 0) S.s_ncorr = c;
   }
-  const int n4 = pstride >> 2, h4 = (n4 + 1) >> 1;
+  const int n4 = pst >> 2, h4 = (n4 + 1) >> 1;
   for (int t = threadIdx.x; t < 2 * NV; t += blockDim.x) {
     const int v = t >> 1, half = t & 1;
-    const float4* row = reinterpret_cast<const float4*>(b.partial + (size_t)v * pstride) + half * h4;
+    const float4* row = reinterpret_cast<const float4*>(partial + (size_t)v * pst) + half * h4;
     const int cnt = half ? n4 - h4 : h4;
     double acc = 0.0;
     for (int c0 = 0; c0 < cnt; c0 += 20) {
@@ -459,120 +418,364 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
         acc += (double)f;
       }
     }
-    s_half[t] = acc;
+    S.s_half[t] = acc;
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < NV; v += blockDim.x) sA[v] = s_half[2 * v] + s_half[2 * v + 1];
+  for (int v = threadIdx.x; v < NV; v += blockDim.x) S.sA[v] = S.s_half[2 * v] + S.s_half[2 * v + 1];
   __syncthreads();
+}
 
-  const bool update = !s_skip && !(flags & kIcpNoUpdate);
-  if (flags & kIcpNoUpdate) {
-    for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) b.result[kResSys + i] = sA[i];
-    if (threadIdx.x == 0) b.status[2] = s_ncorr;
-    return;
-  }
-  // factor the real 6x6 A once, then x_0 = A^-1 (-g_0) and x_l = A^-1 (-g_l - A_l x_0)
+// The 6x6 solve of the summed normal equations: factor the real A once, x_0 = A^-1 (-g_0) and
+// x_l = A^-1 (-g_l - A_l x_0) on every lane, each refined once with FP64 residuals. Sets S.s_fail (too
+// few correspondences, A not positive definite, or `skip`) and S.sx.
+__device__ __forceinline__ void icp_solve(const Params& p, IcpShared& S, int L, int npx, bool skip, bool update) {
+  const int NV = L * kNT;
   const int t = threadIdx.x;
-  for (int v = t; v < NV; v += blockDim.x) sAf[v] = (float)sA[v];
+  for (int v = t; v < NV; v += blockDim.x) S.sAf[v] = (float)S.sA[v];
   __syncthreads();
   if (t == 0) {
-    int fail = s_skip;
-    if (!fail && (float)s_ncorr < p.min_corr_frac * (float)(lv.W * lv.H)) fail = 1;
-    if (!fail && !ldl32(sAf, s_ldl)) fail = 1;
+    int fail = skip;
+    if (!fail && (float)S.s_ncorr < p.min_corr_frac * (float)npx) fail = 1;
+    if (!fail && !ldl32(S.sAf, S.s_ldl)) fail = 1;
     if (!fail) {
       float b0[6];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) b0[i] = -sAf[21 + i];
-      subst32(s_ldl, b0, sxf[0]);
+      for (int i = 0; i < 6; ++i) b0[i] = -S.sAf[21 + i];
+      subst32(S.s_ldl, b0, S.sxf[0]);
     }
-    s_fail = fail;
+    S.s_fail = fail;
   }
   __syncthreads();
-  const bool go = update && !s_fail;
+  const bool go = update && !S.s_fail;
   // real lane: residual in FP64 (thread i = row), FP32 correction
   if (go && t < 6) {
-    double r = -sA[21 + t];
+    double r = -S.sA[21 + t];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) r = fma(-sA[t <= k ? up6(t, k) : up6(k, t)], (double)sxf[0][k], r);
-    srf[0][t] = (float)r;
+    for (int k = 0; k < 6; ++k) r = fma(-S.sA[t <= k ? up6(t, k) : up6(k, t)], (double)S.sxf[0][k], r);
+    S.srf[0][t] = (float)r;
   }
   __syncthreads();
-  if (go && t == 0) subst32(s_ldl, srf[0], sdf[0]);
+  if (go && t == 0) subst32(S.s_ldl, S.srf[0], S.sdf[0]);
   __syncthreads();
-  if (go && t < 6) sx[0][t] = (double)sxf[0][t] + (double)sdf[0][t];
+  if (go && t < 6) S.sx[0][t] = (double)S.sxf[0][t] + (double)S.sdf[0][t];
   __syncthreads();
   // imaginary lanes: right-hand sides in FP64, thread (l, i)
   const int ls = 1 + t / 6, li = t % 6;
   const bool lane_thread = go && t < 6 * (L - 1);
   double rhs = 0.0;
   if (lane_thread) {
-    const double* Al = sA + ls * kNT;
+    const double* Al = S.sA + ls * kNT;
     rhs = -Al[21 + li];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) rhs = fma(-Al[li <= k ? up6(li, k) : up6(k, li)], sx[0][k], rhs);
-    srf[ls][li] = (float)rhs;
+    for (int k = 0; k < 6; ++k) rhs = fma(-Al[li <= k ? up6(li, k) : up6(k, li)], S.sx[0][k], rhs);
+    S.srf[ls][li] = (float)rhs;
   }
   __syncthreads();
-  if (go && t >= 1 && t < L) subst32(s_ldl, srf[t], sxf[t]);
+  if (go && t >= 1 && t < L) subst32(S.s_ldl, S.srf[t], S.sxf[t]);
   __syncthreads();
   if (lane_thread) {
     double r = rhs;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) r = fma(-sA[li <= k ? up6(li, k) : up6(k, li)], (double)sxf[ls][k], r);
-    srf[ls][li] = (float)r;
+    for (int k = 0; k < 6; ++k) r = fma(-S.sA[li <= k ? up6(li, k) : up6(k, li)], (double)S.sxf[ls][k], r);
+    S.srf[ls][li] = (float)r;
   }
   __syncthreads();
-  if (go && t >= 1 && t < L) subst32(s_ldl, srf[t], sdf[t]);
+  if (go && t >= 1 && t < L) subst32(S.s_ldl, S.srf[t], S.sdf[t]);
   __syncthreads();
-  if (lane_thread) sx[ls][li] = (double)sxf[ls][li] + (double)sdf[ls][li];
+  if (lane_thread) S.sx[ls][li] = (double)S.sxf[ls][li] + (double)S.sdf[ls][li];
   __syncthreads();
+}
 
-  // pose update T <- exp(x) T on every lane: delta = exp(x) - I in FP32 (coefficients once per lane,
-  // then one thread per (lane, element)), T + delta T composed in FP64 one element per thread
-  if (go && t < 6 * L) sxs[t / 6][t % 6] = (float)sx[t / 6][t % 6];
+// Pose update T <- exp(x) T on every lane of the pose lanes at `pose` (in place): delta = exp(x) - I in
+// FP32 (coefficients once per lane, then one thread per (lane, element)), T + delta T composed in FP64
+// one element per thread.
+__device__ __forceinline__ void icp_update(IcpShared& S, int L, double* pose) {
+  const int t = threadIdx.x;
+  if (t < 6 * L) S.sxs[t / 6][t % 6] = (float)S.sx[t / 6][t % 6];
   __syncthreads();
-  if (go && t < L) se3_coef_lane_f(sxs[0], sxs[t], scf[t]);
+  if (t < L) se3_coef_lane_f(S.sxs[0], S.sxs[t], S.scf[t]);
   __syncthreads();
-  if (go && t < 12 * L) {
+  if (t < 12 * L) {
     const int l = t / 12, e = t % 12;
-    sdl[l][e] = se3_delta_element(sxs[0], sxs[l], scf[l], l > 0, e);
+    S.sdl[l][e] = se3_delta_element(S.sxs[0], S.sxs[l], S.scf[l], l > 0, e);
   }
   __syncthreads();
   double tn = 0.0;
-  if (go && t < 12 * L) {
+  if (t < 12 * L) {
     const int l = t / 12, e = t % 12, r = e >> 2, c = e & 3;
-    const double* T0 = b.pose;
-    const double* Tl = b.pose + 12 * l;
+    const double* T0 = pose;
+    const double* Tl = pose + 12 * l;
     // lane 0: T0 + d0 T0; lane l: Tl + dl T0 + d0 Tl (translation column adds the delta's own column)
-    tn = Tl[e] + (double)sdl[l][4 * r] * T0[c] + (double)sdl[l][4 * r + 1] * T0[4 + c] +
-         (double)sdl[l][4 * r + 2] * T0[8 + c] + (c == 3 ? (double)sdl[l][4 * r + 3] : 0.0);
+    tn = Tl[e] + (double)S.sdl[l][4 * r] * T0[c] + (double)S.sdl[l][4 * r + 1] * T0[4 + c] +
+         (double)S.sdl[l][4 * r + 2] * T0[8 + c] + (c == 3 ? (double)S.sdl[l][4 * r + 3] : 0.0);
     if (l > 0)
-      tn += (double)sdl[0][4 * r] * Tl[c] + (double)sdl[0][4 * r + 1] * Tl[4 + c] + (double)sdl[0][4 * r + 2] * Tl[8 + c];
+      tn += (double)S.sdl[0][4 * r] * Tl[c] + (double)S.sdl[0][4 * r + 1] * Tl[4 + c] +
+            (double)S.sdl[0][4 * r + 2] * Tl[8 + c];
   }
   __syncthreads();
-  if (go && t < 12 * L) b.pose[t] = tn;
+  if (t < 12 * L) pose[t] = tn;
+  __syncthreads();
+}
+
+// kStop: the stop tolerance p.icp_stop is in use (and the iteration counter): a launch after its level
+// converged returns at once. Without it the kernel is the fixed-count iteration of the method.
+// One launch per iteration; the last block to finish (ticket counter) sums, solves and updates. The
+// frame chain runs k_icp_run instead; this kernel serves the stage calls (kIcpNoUpdate).
+template <bool kStop>
+__global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int flags, int reps) {
+  pdl_enter();
+  const int L = p.L;
+  const int warp = threadIdx.x >> 5, lid = threadIdx.x & 31;
+  const int ln = warp % L, rep = warp / L;
+  __shared__ IcpShared S;
+  __shared__ int s_skip, s_last, s_conv;
+  extern __shared__ float s_rec[];  // [rep][chunk of the group][field][pixel]: reps * L * kRec * 32 floats
+
+  if (threadIdx.x == 0) {
+    s_skip = b.status[0];
+    // status[3]: the level converged (a step below p.icp_stop); only its first iteration ignores it
+    if (kStop) s_conv = (flags & (kIcpFirst | kIcpNoUpdate)) ? 0 : b.status[3];
+  }
+  for (int i = threadIdx.x; i < L * 12; i += blockDim.x) {
+    S.sT[i / 12][i % 12] = (float)b.pose[i];
+    S.sP[i / 12][i % 12] = (float)b.pose_prev[i];
+  }
+  if (threadIdx.x < 12) S.sZero[threadIdx.x] = 0.f;
+  __syncthreads();
+  if (kStop && (s_skip || s_conv) && !(flags & kIcpNoUpdate)) {
+    // nothing to compute after a failure or after the level converged; the frame's last iteration
+    // still closes the frame: fall back to T_{k-1} on a failure and count it
+    if ((flags & kIcpLast) && blockIdx.x == 0) {
+      if (s_skip && threadIdx.x < 12 * L) b.pose[threadIdx.x] = b.pose_prev[threadIdx.x];
+      if (threadIdx.x == 0) {
+        if (s_skip) {
+          b.status[1] += 1;
+          b.status[2] = 0;
+        }
+        b.status[0] = 0;
+        b.status[3] = 0;
+      }
+    }
+    return;
+  }
+
+  float acc[kNT];
+#pragma unroll
+  for (int q = 0; q < kNT; ++q) acc[q] = 0.f;
+  int cnt = 0;
+  const int npx = lv.W * lv.H;
+  const int nchunk = (npx + 31) >> 5;
+  const int ngroup = (nchunk + L - 1) / L;
+  const int gbase = blockIdx.x * reps + rep, gstride = gridDim.x * reps;
+  const int nloop = (!s_skip && gbase < ngroup) ? (ngroup - gbase + gstride - 1) / gstride : 0;
+  icp_pixels(p, b, lv, S, s_rec + (size_t)rep * L * kRec * 32, L, ln, lid, rep, gbase, gstride, nloop, acc, cnt);
+
+  const int pst = icp_pstride(gridDim.x);
+  icp_block_sums(S, acc, cnt, L, reps, ln, rep, warp, lid, b.partial, pst, blockIdx.x, gridDim.x, b.partial_n);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(b.ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) *b.ticket = 0u;  // ready for the next launch
+
+  // ---------------- last block: FP64 cross-block sum, solve, update ----------------
+  icp_cross_sum(S, b.partial, pst, gridDim.x, b.partial_n, L, warp, lid);
+  if (flags & kIcpNoUpdate) {
+    for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) b.result[kResSys + i] = S.sA[i];
+    if (threadIdx.x == 0) b.status[2] = S.s_ncorr;
+    return;
+  }
+  icp_solve(p, S, L, npx, s_skip, true);
+  const bool go = !S.s_fail;
+  if (go) icp_update(S, L, b.pose);
   if (kStop) {
     if (threadIdx.x == 0) {
-      if (s_fail) b.status[0] = 1;
-      b.status[2] = s_ncorr;
+      if (S.s_fail) b.status[0] = 1;
+      b.status[2] = S.s_ncorr;
       double x2 = 0.0;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) x2 += sx[0][k] * sx[0][k];
+      for (int k = 0; k < 6; ++k) x2 += S.sx[0][k] * S.sx[0][k];
       b.status[3] = (go && x2 < (double)p.icp_stop * (double)p.icp_stop) ? 1 : 0;
       if (b.stats) b.stats[kStatIcpIters] += 1;
     }
-  } else if (threadIdx.x == 0 && s_fail && !s_skip) {
+  } else if (threadIdx.x == 0 && S.s_fail && !s_skip) {
     b.status[0] = 1;
   }
   if (flags & kIcpLast) {
     __syncthreads();
     const int failed = b.status[0];
+    const int t = threadIdx.x;
     if (failed && t < 12 * L) b.pose[t] = b.pose_prev[t];
     __syncthreads();
     if (threadIdx.x == 0) {
       if (failed) b.status[1] += 1;
       b.status[0] = 0;
-      b.status[2] = s_ncorr;
+      b.status[2] = S.s_ncorr;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// All the iterations of a range of pyramid levels in one cooperative launch (every block resident):
+// per iteration each block adds its pixels into its column of the partial sums (two buffers, used
+// alternately), the grid meets at a barrier, and every block then takes the same FP64 cross-block sum,
+// solve and update itself, keeping the pose lanes in its own shared memory, so no second barrier is
+// needed: the next iteration's partials go to the other buffer, which no block can still be reading
+// (a block writes iteration j + 1's partials only after every block arrived at iteration j's
+// barrier, i.e. finished reading iteration j - 1's). Block 0 writes the pose lanes and the status at
+// the end. Every wait is bounded: a barrier that does not fill within its poll budget sets status[5]
+// and the blocks leave the launch.
+// ---------------------------------------------------------------------------------------------------
+constexpr unsigned kBarrierPolls = 1u << 22;  // ~0.3 s at the poll interval below
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* a) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+
+// returns false if the barrier timed out
+__device__ __forceinline__ bool grid_barrier(unsigned* arrive, unsigned target, int* timeout_flag) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(arrive, 1u);
+    unsigned polls = 0;
+    int ok = 1;
+    while (ld_acquire_gpu(arrive) < target) {
+      if (++polls > kBarrierPolls) {
+        ok = 0;
+        atomicExch(timeout_flag, 1);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+struct IcpRange {
+  int first, last;   // pyramid levels, coarse (first) to fine (last)
+  int iters[3];      // iterations per level
+  int close;         // the range's last iteration closes the frame (fallback to T_{k-1}, failure count)
+};
+
+template <bool kStop>
+__global__ void __launch_bounds__(512, 1) k_icp_run(Params p, Buffers b, IcpRange rg, int reps) {
+  // no launch_dependents: the next kernel must not take SM resources while this grid is resident
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int L = p.L;
+  const int warp = threadIdx.x >> 5, lid = threadIdx.x & 31;
+  const int ln = warp % L, rep = warp / L;
+  __shared__ IcpShared S;
+  __shared__ double sTd[kMaxLanes * 12];  // this block's copy of the pose lanes (FP64)
+  extern __shared__ float s_rec[];
+  float* recs = s_rec + (size_t)rep * L * kRec * 32;
+  const int nblk = gridDim.x;
+  const int pst = icp_pstride(nblk);
+  const size_t pbuf = (size_t)kNT * L * pst;  // floats of one partial buffer
+
+  for (int i = threadIdx.x; i < L * 12; i += blockDim.x) {
+    sTd[i] = b.pose[i];
+    S.sT[i / 12][i % 12] = (float)sTd[i];
+    S.sP[i / 12][i % 12] = (float)b.pose_prev[i];
+  }
+  if (threadIdx.x < 12) S.sZero[threadIdx.x] = 0.f;
+  bool skip = b.status[0] != 0;           // the frame failed in an earlier range
+  bool conv = kStop && b.status[3] != 0;  // the level converged in an earlier range
+  int ncorr_last = b.status[2];
+  unsigned gen = 0;                       // barriers passed
+  bool timed_out = false;
+  __syncthreads();
+
+  for (int l = rg.first; l >= rg.last && !timed_out; --l) {
+    Lvl lv;
+    lv.s = 1 << l;
+    lv.level = l;
+    lv.W = p.W >> l;
+    lv.H = p.H >> l;
+    lv.fx = p.fx / lv.s;
+    lv.fy = p.fy / lv.s;
+    lv.cx = p.cx / lv.s;
+    lv.cy = p.cy / lv.s;
+    const int npx = lv.W * lv.H;
+    const int nchunk = (npx + 31) >> 5;
+    const int ngroup = (nchunk + L - 1) / L;
+    const int gbase = blockIdx.x * reps + rep, gstride = nblk * reps;
+    for (int it = 0; it < rg.iters[l]; ++it) {
+      const bool last = rg.close && l == rg.last && it == rg.iters[l] - 1;
+      if (it == 0) conv = false;
+      if (!(skip || (kStop && conv))) {
+        float acc[kNT];
+#pragma unroll
+        for (int q = 0; q < kNT; ++q) acc[q] = 0.f;
+        int cnt = 0;
+        const int nloop = gbase < ngroup ? (ngroup - gbase + gstride - 1) / gstride : 0;
+        icp_pixels(p, b, lv, S, recs, L, ln, lid, rep, gbase, gstride, nloop, acc, cnt);
+        float* part = b.partial + (gen & 1u) * pbuf;
+        int* part_n = b.partial_n + (gen & 1u) * nblk;
+        icp_block_sums(S, acc, cnt, L, reps, ln, rep, warp, lid, part, pst, blockIdx.x, nblk, part_n);
+        ++gen;
+        if (!grid_barrier(b.grid_bar, gen * (unsigned)nblk, b.status + 5)) {
+          timed_out = true;
+          break;
+        }
+        icp_cross_sum(S, part, pst, nblk, part_n, L, warp, lid);
+        icp_solve(p, S, L, npx, false, true);
+        ncorr_last = S.s_ncorr;
+        if (S.s_fail) {
+          skip = true;
+        } else {
+          icp_update(S, L, sTd);
+          for (int i = threadIdx.x; i < L * 12; i += blockDim.x) S.sT[i / 12][i % 12] = (float)sTd[i];
+        }
+        if (kStop) {
+          double x2 = 0.0;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) x2 += S.sx[0][k] * S.sx[0][k];
+          conv = !S.s_fail && x2 < (double)p.icp_stop * (double)p.icp_stop;
+          if (blockIdx.x == 0 && threadIdx.x == 0 && b.stats) b.stats[kStatIcpIters] += 1;
+        }
+        __syncthreads();
+      }
+      if (last) {
+        // close the frame: a failed frame falls back to T_{k-1} on every lane and is counted
+        if (skip) {
+          for (int i = threadIdx.x; i < L * 12; i += blockDim.x) sTd[i] = b.pose_prev[i];
+          if (blockIdx.x == 0 && threadIdx.x == 0) b.status[1] += 1;
+          ncorr_last = 0;
+        }
+        skip = false;
+        conv = false;
+        __syncthreads();
+      }
+    }
+  }
+  if (blockIdx.x == 0 && !timed_out) {
+    for (int i = threadIdx.x; i < L * 12; i += blockDim.x) b.pose[i] = sTd[i];
+    if (threadIdx.x == 0) {
+      b.status[0] = skip ? 1 : 0;
+      b.status[2] = ncorr_last;
+      b.status[3] = conv ? 1 : 0;
+    }
+  }
+  // leave: the last block out resets the barrier counter for the next launch (every block has
+  // passed its last barrier when it counts itself out)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(b.grid_bar + 1, 1u) == (unsigned)nblk - 1) {
+      b.grid_bar[0] = 0u;
+      b.grid_bar[1] = 0u;
     }
   }
 }
@@ -582,6 +785,10 @@ static size_t icp_rec_bytes(int reps, int L) { return sizeof(float) * (size_t)re
 cudaError_t icp_configure() {
   cudaError_t e = cudaFuncSetAttribute(k_icp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_icp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_icp_run<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_icp_run<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   return e;
 }
 
@@ -608,6 +815,7 @@ int icp_blocks(int level_pixels, int L) {
 cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int flags, int nblk, cudaStream_t s) {
   Lvl lv;
   lv.s = 1 << level;
+  lv.level = level;
   lv.W = p.W >> level;
   lv.H = p.H >> level;
   lv.fx = p.fx / lv.s;
@@ -621,6 +829,44 @@ cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int flags, 
                                          flags, reps)
                             : launch_pdl(k_icp<false>, dim3(nblk), dim3(threads), icp_rec_bytes(reps, p.L), s, p, b, lv,
                                          flags, reps);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// blocks of the cooperative ICP launch: as many as are resident at once (one per SM), at most
+// kMaxPartials (the partial buffers' column bound)
+int icp_run_blocks(int L) {
+  const int reps = icp_reps(L);
+  const size_t smem = icp_rec_bytes(reps, L);
+  int dev = 0, sms = 148, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp_run<false>, 32 * L * reps, smem) != cudaSuccess)
+    per_sm = 1;
+  int n = sms * (per_sm < 1 ? 1 : per_sm);
+  return n > kMaxPartials ? kMaxPartials : n;
+}
+
+cudaError_t launch_icp_run(const Params& p, const Buffers& b, int first, int last, const int* iters, bool close,
+                           int nblk, cudaStream_t s) {
+  IcpRange rg;
+  rg.first = first;
+  rg.last = last;
+  for (int l = 0; l < 3; ++l) rg.iters[l] = iters[l];
+  rg.close = close ? 1 : 0;
+  const int reps = icp_reps(p.L);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblk);
+  cfg.blockDim = dim3(32 * p.L * reps);
+  cfg.dynamicSmemBytes = icp_rec_bytes(reps, p.L);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = p.icp_stop > 0.f ? cudaLaunchKernelEx(&cfg, k_icp_run<true>, p, b, rg, reps)
+                                         : cudaLaunchKernelEx(&cfg, k_icp_run<false>, p, b, rg, reps);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

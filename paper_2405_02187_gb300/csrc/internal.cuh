@@ -35,6 +35,10 @@ struct Params {
   int L;
   float dmu[kMaxLanes];     // Im mu of each lane (TRUNC seeds), lane 0 unused
   float dD[kMaxLanes];      // Im D of each lane (DEPTH seeds on every pixel), lane 0 unused
+  int dpix[kMaxLanes];      // single-pixel DEPTH seed: its level-0 pixel (the lane's Im depth maps
+                            // Buffers::dlane hold the perturbation at every level); -1 otherwise
+  unsigned fresh;           // bit l: lane l restarts at every frame (per-frame pose seeds): its earlier
+                            // imaginary parts of the previous pose and the model maps do not enter ICP
   double h[kMaxLanes];      // step of each lane for the read-out
   // gates and ranges
   float dist_gate2, cos_normal_gate, disc_gate, min_corr_frac;
@@ -61,13 +65,30 @@ struct Buffers {
   float* partial;   // ICP per-block partial sums: nblk x L x 27
   int* partial_n;   // ICP per-block correspondence counts
   unsigned* ticket; // last-block-done counter
-  int* status;      // [0] ICP failed in this frame, [1] frames failed since last sync, [2] last n_valid
+  unsigned* grid_bar;  // cooperative ICP: [0] barrier arrivals, [1] blocks out (both 0 between launches)
+  int* status;      // [0] ICP failed in this frame, [1] frames failed since last sync, [2] last n_valid,
+                    // [3] level converged, [4] tensor-core wait timed out, [5] ICP grid barrier timed out
   double* result;   // read-out: 12 (pose) + 12 K (dpose) + 6 K (dtwist) + 27 L (last system)
   unsigned long long* stats;  // kNStat counters (kStat* below); NULL in the allocation-free calls
   int* hit;                   // per pixel: index m of the first sample of the ray-cast hit pair, -1 = none
   int* tiles;                 // fusion: tiles the frame can touch (fuse_tile_count entries at most)
-  unsigned* tile_ctr;         // fusion: [0] listed tiles, [1] finished blocks (both 0 between launches)
+  unsigned* tile_ctr;         // fusion: [0] listed tiles, [1] finished blocks (both 0 between launches),
+                              // [2] tiles of the last update (tiles_prev), kept for the restarted lanes
+  int* tiles_prev;            // fusion: the tiles of the last update (written when Params::fresh != 0)
+  float* dlane;               // single-pixel DEPTH lanes: Im D at levels 0, 1, 2 (dlane_offset), lane l
+                              // at (l - 1) dlane_stride; zero outside the seed's windows
 };
+
+// Im depth map of lane l (single-pixel DEPTH seed) at pyramid level `level`
+__host__ __device__ inline size_t dlane_stride(const Params& p) {
+  const size_t hw = (size_t)p.W * p.H;
+  return hw + (hw >> 2) + (hw >> 4);
+}
+__host__ __device__ inline size_t dlane_offset(const Params& p, int lane, int level) {
+  const size_t hw = (size_t)p.W * p.H;
+  const size_t lo = level == 0 ? 0 : (level == 1 ? hw : hw + (hw >> 2));
+  return (size_t)(lane - 1) * dlane_stride(p) + lo;
+}
 
 // device counters of a handle (Buffers::stats)
 enum : int {
@@ -188,6 +209,15 @@ cudaError_t launch_icp_newton(const Params& p, const Buffers& b, int level, int 
 int icp_newton_blocks(int level_pixels, int sms);
 cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int iter_flags, int nblk, cudaStream_t s);
 cudaError_t launch_seed_pose(const Params& p, const Buffers& b, const int* kinds, const int* index, cudaStream_t s);
+// Per-frame pose lanes (aux.cu). mode bit 0: restart (zero the lanes of Params::fresh in the pose, the
+// previous pose and T_{k-2}); bit 1: ICP's start, lanes of kind POSE = h G_index Re(pose) (and of
+// candB, the proposal's start, if not NULL); bit 2: the tracked pose, lanes of kind POSE_TRACKED.
+cudaError_t launch_seed_frame(const Params& p, const Buffers& b, double* pose_pp, double* candB, const int* kinds,
+                              const int* index, int mode, cudaStream_t s);
+// Im depth maps of the single-pixel DEPTH lanes at every level of the pyramid (measure.cu)
+cudaError_t launch_depth_lanes(const Params& p, const Buffers& b, int levels, cudaStream_t s);
+// zero the restarted lanes' TSDF planes over the tiles of the last update (fuse.cu)
+cudaError_t launch_clear_fresh(const Params& p, const Buffers& b, cudaStream_t s);
 cudaError_t launch_readout(const Params& p, const Buffers& b, cudaStream_t s);
 // relocalisation loss, gradient and Hessian (hess.cu); poses: 21 x 12 truncated-bicomplex pose
 // elements (4 floats each), out: [E, g(6), H upper (21), count]
@@ -196,6 +226,11 @@ cudaError_t launch_hess(const Params& p, const Buffers& b, const float* depth, c
 cudaError_t launch_loss(const Params& p, const Buffers& b, const float* depth, const float* model,
                         const double* pose, double* out, int nblk, cudaStream_t s);
 int icp_blocks(int level_pixels, int L);
+// all iterations of pyramid levels first .. last (coarse to fine, iters[l] each) in one cooperative
+// launch of nblk resident blocks (icp_run_blocks); close: the last iteration closes the frame
+cudaError_t launch_icp_run(const Params& p, const Buffers& b, int first, int last, const int* iters, bool close,
+                           int nblk, cudaStream_t s);
+int icp_run_blocks(int L);
 int icp_reps(int L);
 cudaError_t icp_configure();
 

@@ -5,9 +5,13 @@
 // Level l+1 at pixel u is the 5x5 binomial ([1 4 6 4 1]/16 per axis) average of level l around
 // pixel 2u over the taps that are valid and within pyr_range of the centre depth; invalid where the
 // centre is invalid ("A coarser level depth is computed by applying Gaussian smoothing over D_k(u)").
-// Depth lanes are not stored: the only depth seed on the GPU perturbs every valid pixel by the same
-// h; the bilateral weights depend only on depth differences and the pyramid weights are constant,
-// and both averages are normalised, so the perturbation stays h at every valid pixel of every level.
+// A DEPTH seed on every pixel needs no stored lane: it perturbs every valid pixel by the same h, the
+// bilateral weights depend only on depth differences and the pyramid weights are constant, and both
+// averages are normalised, so the perturbation stays h at every valid pixel of every level. A DEPTH seed
+// on one pixel s has an Im depth map per level (k_depth_lanes): at level 0 the tangent of the bilateral
+// filter (its range weights now move with the perturbation) over the 7x7 window around s, at levels 1
+// and 2 the pyramid's average of the finer level's map with the real part's weights ("The perturbed hi
+// is also Gaussian smoothed"); outside those windows the maps stay zero.
 #include "internal.cuh"
 
 namespace xslam {
@@ -79,6 +83,113 @@ __global__ void k_pyr_down(const float* __restrict__ src, int Ws, int Hs, float*
     out = acc / wsum;  // wsum >= 36/256 (the centre tap)
   }
   dst[v * Wd + u] = out;
+}
+
+// Im depth maps of single-pixel DEPTH lanes, one block per lane (blockIdx.x + 1). The seed pixel s carries
+// h if its range-gated depth is valid. Level 0 with the filter on: at output u (valid) with real input
+// D, filtered value D'(u) and weights w_t = exp(-|t - u|^2 / 2 ss^2 - (D_t - D_u)^2 / 2 sr^2), the
+// tangent is [sum_t w_t dD_t - sum_t w_t (D_t - D_u) / sr^2 (dD_t - dD_u) (D_t - D'(u))] / sum_t w_t
+// with dD_t = h [t = s]; without the filter the map is h at s. Level l + 1 at u: the pyramid's
+// normalised average of level l's map over the taps the real average used.
+__global__ void k_depth_lanes(Params p, const float* __restrict__ src0, const float* __restrict__ pyr0,
+                              const float* __restrict__ pyr1, const float* __restrict__ pyr2, float* __restrict__ dlane,
+                              int levels) {
+  pdl_enter();
+  const int l = blockIdx.x + 1;
+  if (l >= p.L || p.dpix[l] < 0) return;
+  const int W = p.W, H = p.H;
+  const int sx = p.dpix[l] % W, sy = p.dpix[l] / W;
+  const float h = (float)p.h[l];
+  const bool seed_ok = src0[p.dpix[l]] > 0.f;
+  // level 0
+  const int R0 = p.bilateral ? 3 : 0;
+  int lox = max(sx - R0, 0), hix = min(sx + R0, W - 1), loy = max(sy - R0, 0), hiy = min(sy + R0, H - 1);
+  float* d0 = dlane + dlane_offset(p, l, 0);
+  const int n0 = (hix - lox + 1) * (hiy - loy + 1);
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+    const int u = lox + i % (hix - lox + 1), v = loy + i / (hix - lox + 1);
+    const float c = src0[v * W + u];
+    float out = 0.f;
+    if (seed_ok && c > 0.f) {
+      if (!p.bilateral) {
+        out = (u == sx && v == sy) ? h : 0.f;
+      } else {
+        const float inv2ss = 1.f / (2.f * 4.5f * 4.5f), inv2sr = 1.f / (2.f * 0.03f * 0.03f);
+        const float isr2 = 1.f / (0.03f * 0.03f);
+        const float Df = pyr0[v * W + u];
+        const float dDu = (u == sx && v == sy) ? h : 0.f;
+        float num = 0.f, wsum = 0.f;
+        for (int dy = -3; dy <= 3; ++dy) {
+          const int y = v + dy;
+          if (y < 0 || y >= H) continue;
+          for (int dx = -3; dx <= 3; ++dx) {
+            const int x = u + dx;
+            if (x < 0 || x >= W) continue;
+            const float t = src0[y * W + x];
+            if (!(t > 0.f)) continue;
+            const float d = t - c;
+            const float w = expf(-(float)(dx * dx + dy * dy) * inv2ss - d * d * inv2sr);
+            const float dDt = (x == sx && y == sy) ? h : 0.f;
+            num += w * dDt - w * d * isr2 * (dDt - dDu) * (t - Df);
+            wsum += w;
+          }
+        }
+        out = num / wsum;
+      }
+    }
+    d0[v * W + u] = out;
+  }
+  __syncthreads();
+  // levels 1 and 2: the windows of the pixels whose 5x5 taps around 2u reach the finer window
+  const float k5[5] = {1.f / 16, 4.f / 16, 6.f / 16, 4.f / 16, 1.f / 16};
+  const float* fine = pyr0;
+  const float* dfine = d0;
+  for (int lv = 1; lv < levels; ++lv) {
+    const int Wf = W >> (lv - 1), Hf = H >> (lv - 1), Wc = W >> lv, Hc = H >> lv;
+    const float* coarse = lv == 1 ? pyr1 : pyr2;
+    float* dc = dlane + dlane_offset(p, l, lv);
+    const int nlox = max((lox - 2 + 1) >> 1, 0), nhix = min((hix + 2) >> 1, Wc - 1);
+    const int nloy = max((loy - 2 + 1) >> 1, 0), nhiy = min((hiy + 2) >> 1, Hc - 1);
+    const int n = (nhix - nlox + 1) * (nhiy - nloy + 1);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int u = nlox + i % (nhix - nlox + 1), v = nloy + i / (nhix - nlox + 1);
+      float out = 0.f;
+      if (coarse[v * Wc + u] > 0.f) {
+        const float c = fine[(2 * v) * Wf + 2 * u];
+        float num = 0.f, wsum = 0.f;
+        for (int dy = -2; dy <= 2; ++dy) {
+          const int y = 2 * v + dy;
+          if (y < 0 || y >= Hf) continue;
+          for (int dx = -2; dx <= 2; ++dx) {
+            const int x = 2 * u + dx;
+            if (x < 0 || x >= Wf) continue;
+            const float t = fine[y * Wf + x];
+            if (t > 0.f && fabsf(t - c) < p.pyr_range) {
+              const float w = k5[dy + 2] * k5[dx + 2];
+              num += w * dfine[y * Wf + x];
+              wsum += w;
+            }
+          }
+        }
+        out = num / wsum;
+      }
+      dc[v * Wc + u] = out;
+    }
+    __syncthreads();
+    fine = coarse;
+    dfine = dc;
+    lox = nlox;
+    hix = nhix;
+    loy = nloy;
+    hiy = nhiy;
+  }
+}
+
+cudaError_t launch_depth_lanes(const Params& p, const Buffers& b, int levels, cudaStream_t s) {
+  if (p.L < 2) return cudaSuccess;
+  const float* src0 = p.bilateral ? b.gated : b.pyr[0];
+  return launch_pdl(k_depth_lanes, dim3(p.L - 1), dim3(256), 0, s, p, src0, b.pyr[0], b.pyr[1], b.pyr[2], b.dlane,
+                    levels);
 }
 
 cudaError_t launch_prepare(const Params& p, const Buffers& b, int levels, cudaStream_t s) {

@@ -75,12 +75,17 @@ extern "C" xslam_status xslam_icp_system_noalloc(const float* depth, int level, 
   p.W = K->width;
   p.H = K->height;
   p.L = 1 + K_lanes;
-  for (int l = 0; l < kMaxLanes; ++l) p.h[l] = 1.0;
+  for (int l = 0; l < kMaxLanes; ++l) {
+    p.h[l] = 1.0;
+    p.dpix[l] = -1;
+  }
   for (int j = 0; j < K_lanes; ++j) {
     if (seeds[j].kind == XSLAM_SEED_DEPTH) {
-      if (seeds[j].index != -1) return fail(XSLAM_EINVAL, "only DEPTH seeds on every pixel (index -1) are built");
+      if (seeds[j].index != -1)
+        return fail(XSLAM_EINVAL, "single-pixel DEPTH seeds need a handle (xslam_icp_system); index must be -1 here");
       p.dD[j + 1] = (float)seeds[j].h;
     }
+    if (seeds[j].kind == XSLAM_SEED_POSE || seeds[j].kind == XSLAM_SEED_POSE_TRACKED) p.fresh |= 1u << (j + 1);
     p.h[j + 1] = seeds[j].h;
   }
   p.dist_gate2 = c.dist_gate_m * c.dist_gate_m;

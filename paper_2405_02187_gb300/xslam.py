@@ -11,7 +11,7 @@ import os
 
 import numpy as np
 
-POSE0, POSE, TRUNC, DEPTH = 0, 1, 2, 3
+POSE0, POSE, TRUNC, DEPTH, POSE_TRACKED = 0, 1, 2, 3, 4
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTRACK, ESTATE = range(7)
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTRACK", 6: "ESTATE"}
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libxslam.so")

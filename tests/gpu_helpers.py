@@ -102,3 +102,35 @@ def f32_params(wl):
                    bilateral=wl.bilateral)
     assert math.isinf(cfg.w_max)
     return w, cfg
+
+
+def _oracle_run_worker(args):
+    """One oracle run (real when seed is None) over the first `frames` frames: its pose per frame."""
+    wl, seed, frames, cfg = args
+    r = P.XKinectFusion(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, wl.poses[0], cfg, seed)
+    poses, oks = [], []
+    for k in range(frames):
+        T, ok = r.frame(wl.depth[k])
+        poses.append(np.array(T))
+        oks.append(ok)
+    return poses, oks
+
+
+def oracle_runs_parallel(wl, seeds, frames, cfg=None):
+    """The real oracle run and one complex run per seed, each in its own spawned process (started
+    with `spawn`, so a process that already holds a CUDA context is never forked). Returns a dict
+    like oracle.pipeline.run's: pose (F, 3, 4), ok (F,), dtwist (K, F, 6)."""
+    import concurrent.futures
+    import multiprocessing
+
+    cfg = cfg or oracle_cfg(wl)
+    jobs = [(wl, None, frames, cfg)] + [(wl, s, frames, cfg) for s in seeds]
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(max_workers=len(jobs), mp_context=ctx) as ex:
+        res = list(ex.map(_oracle_run_worker, jobs))
+    pose = np.stack(res[0][0])
+    dtwist = np.zeros((len(seeds), frames, 6))
+    for j, s in enumerate(seeds):
+        for k in range(frames):
+            dtwist[j, k] = se3.readout(res[j + 1][0][k], s.h)[2]
+    return dict(pose=pose, ok=np.array(res[0][1]), dtwist=dtwist)

@@ -1,12 +1,14 @@
 """Host-side measurement logic of bench.py without a GPU: the algorithmic bytes per launch of each
-frame stage against their closed forms at the 640x480, K = 6 workload, and the rule that an ncu traffic
-record counts only while the kernel source it was taken on is unchanged."""
+frame stage against their closed forms at the 640x480, K = 6 workload, the ray cast's distinct voxel
+reads against a brute-force count, and the rule that an ncu traffic record counts only while the kernel
+source it was taken on is unchanged."""
 import hashlib
 import json
 import os
 import sys
 import types
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -18,12 +20,15 @@ def _wl(width=640, height=480, iters=(10, 5, 4)):
     return types.SimpleNamespace(intr=types.SimpleNamespace(width=width, height=height), icp_iters=list(iters))
 
 
-def test_icp_bytes_are_176_per_pixel_averaged_over_the_launches():
-    # 4 B own depth + 4 B model depth + 24 B model vertex and normal on each of 7 lanes
+def test_icp_bytes_are_192_per_pixel_iteration():
+    # the scope table's figure: 24 B own vertex and normal + 24 B model vertex and normal on each of 7 lanes
     px = 10 * 640 * 480 + 5 * 320 * 240 + 4 * 160 * 120
-    assert bench.algorithmic_bytes("icp", _wl(), 6, {}) == pytest.approx(px * 176 / 19, rel=1e-12)
-    # one lane: 8 + 24 B per pixel
-    assert bench.algorithmic_bytes("icp", _wl(iters=(1, 0, 0)), 0, {}) == 640 * 480 * 32
+    assert bench.icp_bytes_per_frame(_wl(), 6) == px * 192
+    # one cooperative launch per frame carries all of it; 19 launches share it
+    assert bench.algorithmic_bytes("icp", _wl(), 6, {}) == px * 192
+    assert bench.algorithmic_bytes("icp", _wl(), 6, {}, launches_per_frame=19) == pytest.approx(px * 192 / 19)
+    # one lane: 24 + 24 B per pixel
+    assert bench.algorithmic_bytes("icp", _wl(iters=(1, 0, 0)), 0, {}) == 640 * 480 * 48
 
 
 def test_fusion_bytes_are_64_per_updated_voxel_at_six_lanes():
@@ -34,11 +39,64 @@ def test_fusion_bytes_are_64_per_updated_voxel_at_six_lanes():
 
 def test_raycast_bytes():
     hw = 640 * 480
-    got = bench.algorithmic_bytes("raycast", _wl(), 6, {"fused": 2e6, "hits": 3e5})
-    # outputs: depth + 6 floats on 7 lanes; F and W of the crossed voxels; 6 imaginary planes at 8 cells per hit
-    assert got == hw * 4 * 43 + 2e6 * 8 + 3e5 * 8 * 8 * 4 * 6
+    got = bench.algorithmic_bytes("raycast", _wl(), 6, {"march_voxels": 2e6, "refine_voxels": 3e5})
+    # outputs: depth + 6 floats on 7 lanes; Re F of the marched voxels; all 7 lanes of the refined ones
+    assert got == hw * 4 * 43 + 2e6 * 4 + 3e5 * 4 * 7
     with pytest.raises(ValueError):
         bench.algorithmic_bytes("march", _wl(), 6, {})
+
+
+def _brute_voxel_reads(intr, T, hit, dims, voxel, origin, step, m0, m1):
+    """The same sets by explicit per-ray loops over every sample alpha_m with m0 <= m <= m1."""
+    nx, ny, nz = dims
+    R, t = np.asarray(T)[:, :3], np.asarray(T)[:, 3]
+    march, refine = set(), set()
+
+    def cell(g):
+        if all(0 <= g[i] < dims[i] - 1 for i in range(3)):
+            i, j, k = (int(np.floor(c)) for c in g)
+            return {(i + a) + nx * ((j + b) + ny * (k + c)) for a in (0, 1) for b in (0, 1) for c in (0, 1)}
+        return set()
+
+    for v in range(intr.height):
+        for u in range(intr.width):
+            d = R @ np.array([(u - intr.cx) / intr.fx, (v - intr.cy) / intr.fy, 1.0])
+            gp = lambda a: (t + a * d - np.asarray(origin)) / voxel - 0.5  # noqa: E731
+            h = float(hit[v, u])
+            ins = [m for m in range(m0, m1 + 1) if cell(gp(m * step))]
+            if not ins:
+                continue
+            end = int(np.floor(h / step)) + 1 if h > 0 else ins[-1]
+            for m in range(ins[0], end + 1):
+                march |= cell(gp(m * step))
+            if h > 0:
+                mh = int(np.floor(h / step))
+                pts = [gp(mh * step), gp((mh + 1) * step)]
+                vt = gp(h)
+                for i in range(3):
+                    for sgn in (1.0, -1.0):
+                        q = vt.copy()
+                        q[i] += sgn
+                        pts.append(q)
+                for q in pts:
+                    refine |= cell(q)
+    return len(march), len(refine)
+
+
+def test_raycast_voxel_reads_match_brute_force():
+    torch = pytest.importorskip("torch")
+    from paper_2405_02187_gb300 import synth
+    intr = synth.Intrinsics(6.0, 6.0, 3.5, 2.5, 8, 6)
+    dims, voxel, origin, step = (12, 10, 14), 0.05, (-0.3, -0.25, 0.05), 0.05
+    c, s_ = np.cos(0.2), np.sin(0.2)
+    T = np.array([[c, 0.0, s_, 0.01], [0.0, 1.0, 0.0, -0.02], [-s_, 0.0, c, 0.0]])
+    rng = np.random.default_rng(0)
+    hit = rng.uniform(0.2, 0.6, (6, 8))
+    hit[rng.random((6, 8)) < 0.3] = 0.0
+    m0, m1 = 2, 20
+    got = bench.raycast_voxel_reads(intr, T, torch.tensor(hit), dims, voxel, origin, step, m0, m1, chunk=7)
+    assert got == _brute_voxel_reads(intr, T, hit, dims, voxel, origin, step, m0, m1)
+    assert got[0] > 100 and got[1] > 20
 
 
 def test_traffic_counts_only_for_the_source_it_was_taken_on(tmp_path, monkeypatch):

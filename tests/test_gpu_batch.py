@@ -30,11 +30,13 @@ def _handle(wl, seeds):
     return x
 
 
-def test_batch_matches_single_handles():
+def test_batch_matches_single_handles(monkeypatch):
     wls, seeds = _workloads()
     lengths = [4, 6, 5]
     dev = [torch.tensor(w.depth, device="cuda") for w in wls]
-    # reference: each trajectory alone through xslam_frame
+    # reference: each trajectory alone through xslam_frame, with the ICP kernel a batch runs (one
+    # launch per iteration; XSLAM_ICP_RUN=0 selects it for a handle created alone)
+    monkeypatch.setenv("XSLAM_ICP_RUN", "0")
     ref = []
     for wl, sd, d, n in zip(wls, seeds, dev, lengths):
         x = make_handle(wl, max_lanes=max(1, len(sd)))

@@ -85,7 +85,7 @@ def test_argument_and_state_errors():
     wl = synth.tiny(frames=2)
     x = make_handle(wl, max_lanes=2)
     d = torch.tensor(wl.depth[0], device="cuda")
-    for bad in ([(xslam.POSE, 0, H_GPU)], [(xslam.DEPTH, 5, H_GPU)], [(xslam.POSE0, 0, 0.0)],
+    for bad in ([(xslam.POSE, 6, H_GPU)], [(xslam.DEPTH, 10 ** 8, H_GPU)], [(xslam.POSE0, 0, 0.0)],
                 [(xslam.POSE0, 7, H_GPU)], [(xslam.POSE0, 0, H_GPU)] * 3):
         with pytest.raises(xslam.XSlamError) as e:
             x.frame(d, bad)
