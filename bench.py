@@ -232,7 +232,8 @@ def measured_bf16_tflops():
 
 
 KERNEL_SRC = {"integrate": "fuse.cu", "raycast": "raycast.cu", "icp": "icp.cu"}
-KERNEL_NAME = {"integrate": "k_integrate", "raycast": "k_march + k_refine", "icp": "k_icp_run"}
+KERNEL_NAME = {"integrate": "k_integrate", "raycast": "k_march + k_refine",
+               "icp": "k_icp_run" if os.environ.get("XSLAM_ICP_RUN") == "1" else "k_icp"}
 
 
 def _src_hash(stage):

@@ -15,7 +15,10 @@
 //   - all four warps wait for "done", read their 32 TMEM lanes (rows) with tcgen05.ld and store the
 //     rows below M.
 // TMA reads rows past M or N as zeros. Every mbarrier wait is bounded; on a timeout the thread sets
-// *err, the CTA skips its stores and still releases its TMEM.
+// *err and the CTA skips its stores, but it leaves no asynchronous work behind before it frees its
+// TMEM and exits: the MMA issuer commits to "done" whether or not it finished (a commit completes once
+// every tcgen05.mma the thread issued before it has completed), and the producer waits (bounded) for
+// the TMA copies of the last stages it filled to land.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -124,6 +127,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ CUten
 
   if (threadIdx.x == 0) {
     // producer: stage st = s mod S holds slice s; its k-th refill waits for the k-th "empty" phase
+    int issued = 0;
     for (int s = 0; s < nk; ++s) {
       const int st = s % kStages;
       if (s >= kStages && !mbar_wait(smem_u32(&empty[st]), (unsigned)((s / kStages - 1) & 1))) {
@@ -136,7 +140,12 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ CUten
       mbar_expect_tx(bar, 2u * kTileBytes);
       tma_load_2d(a_s, &tmA, kbase + s * kBK, m0, bar);
       tma_load_2d(b_s, &tmB, kbase + s * kBK, n0, bar);
+      issued = s + 1;
     }
+    // the copies into the last stages may still be in flight if the MMA issuer stopped early: the CTA
+    // must not exit while TMA still writes its shared memory (each stage's last use is its final phase)
+    for (int s = issued > kStages ? issued - kStages : 0; s < issued; ++s)
+      if (!mbar_wait(smem_u32(&full[s % kStages]), (unsigned)((s / kStages) & 1))) atomicExch(err, 1);
   } else if (threadIdx.x == 32) {
     // MMA issuer
     const unsigned idesc = make_idesc(kBM, kBN);
@@ -166,14 +175,15 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ CUten
                        smem_u32(&empty[st]))
                    : "memory");
     }
-    if (ok)
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&done))
-                   : "memory");
-    else
-      s_bad = 1;
+    // commit to "done" on every path: it completes when all MMAs issued above have completed, so the
+    // wait below also covers an issuer that stopped early
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&done))
+                 : "memory");
+    if (!ok) s_bad = 1;
   }
   __syncwarp();
-  // every MMA of the CTA has completed once "done" completes its first phase
+  // every MMA of the CTA has completed once "done" completes its first phase; the commit above is
+  // issued on every path and MMAs wait on nothing, so this wait ends unless the issuer never ran
   const bool fin = mbar_wait(smem_u32(&done), 0u);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (!fin && threadIdx.x == 64) atomicExch(err, 1);

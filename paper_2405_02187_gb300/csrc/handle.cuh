@@ -40,7 +40,7 @@ struct xslam_s {
   int nblk[3] = {1, 1, 1};
   int nblk_max = 1;
   int nblk_run = 1;             // blocks of the cooperative ICP launch
-  bool icp_persistent = true;   // the frame chain runs each ICP range in one cooperative launch
+  bool icp_persistent = false;  // the frame chain runs each ICP range in one cooperative launch
   cudaGraphExec_t g_first = nullptr, g_track = nullptr;
   bool use_graphs = true;
   // stage profiling (xslam_profile): one event pair per stage and frame, accumulated on read

@@ -243,8 +243,8 @@ def test_deterministic_and_graph_equals_direct(orbit, monkeypatch):
 
 @pytest.mark.parametrize("stop", [0.0, 1e-5])
 def test_cooperative_icp_matches_per_iteration_launches(orbit, monkeypatch, stop):
-    """The frame chain's ICP runs every iteration of a frame in one cooperative launch; with
-    XSLAM_ICP_RUN=0 it runs one launch per iteration. Both add the same per-pixel terms and differ only
+    """The frame chain's ICP runs one launch per iteration; with XSLAM_ICP_RUN=1 it runs every
+    iteration of a range in one cooperative launch. Both add the same per-pixel terms and differ only
     in how the FP32 block partials are grouped: poses agree to 1e-6, twist blocks to 1e-4 relative."""
     seeds = [P.Seed(P.POSE0, 0), P.Seed(P.POSE0, 4), P.Seed(P.TRUNC), P.Seed(P.DEPTH, -1)]
 
@@ -258,6 +258,7 @@ def test_cooperative_icp_matches_per_iteration_launches(orbit, monkeypatch, stop
         x.close()
         return out, it
 
+    monkeypatch.setenv("XSLAM_ICP_RUN", "1")
     a, ia = run()
     monkeypatch.setenv("XSLAM_ICP_RUN", "0")
     b, ib = run()
