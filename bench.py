@@ -21,9 +21,12 @@ twist of the first pose). Prints one JSON line (rank 0):
   batched      32 independent trajectories of 50-400 frames (mixed image sizes, grids and lane
                counts) advanced together through include/xslam_batch.h: aggregate frames/s and the
                per-trajectory frame latency;
-  second_order relocalisation on a 512^3 map: gradient descent vs Newton's method with the Hessian
-               from xslam_grad order 2, and the time of one Hessian evaluation;
-  newton_icp   tracking failures and error of Gauss-Newton vs Newton ICP as the frame step grows.
+  second_order relocalisation on a 512^3 map: gradient descent, nonlinear CG and Newton's method with
+               the Hessian from xslam_grad order 2, the time of one Hessian evaluation, and the plain FP64
+               bicomplex path beside it;
+  learned_proposal  the learned pose proposal: training time and the tracking comparison.
+
+The line carries these as compact summaries; --details PATH writes every figure to a JSON file.
 
 --impl reference times the oracle alone on sampled steps of the same workload (see _reference).
 Multi-GPU (torchrun): every rank runs its own independent sequence (replicas, no collective in the
@@ -83,10 +86,16 @@ def xslam_cfg(wl):
 # ------------------------------------------------------------------------------------------------
 # CPU oracle legs (run in spawned processes: no CUDA state is inherited)
 # ------------------------------------------------------------------------------------------------
+def oracle_pool(procs):
+    """A pool of `procs` fresh interpreters (spawned, so no CUDA context is ever forked), each running the
+    oracle on one thread: the math libraries' thread pools are set to one thread before they start."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    return mp.get_context("spawn").Pool(procs)
+
+
 def _oracle_frames(task):
     """One complex lane of the oracle: frame 0 untimed, frame 1 timed. Returns (seconds, dtwist)."""
-    import os as _os
-    _os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import pipeline as P
     from oracle import se3
     wl, seed = task
@@ -153,6 +162,19 @@ def _wl_payload(wl, frames=2):
     return dict(dims=wl.dims, voxel=wl.voxel, trunc=wl.trunc, origin=wl.origin, intr=wl.intr,
                 pose0=wl.poses[0], depth=wl.depth[:frames], icp_iters=wl.icp_iters, depth_min=wl.depth_min,
                 depth_max=wl.depth_max, bilateral=wl.bilateral)
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else the platform's processor string)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
 
 
 # ------------------------------------------------------------------------------------------------
@@ -232,8 +254,7 @@ def measured_bf16_tflops():
 
 
 KERNEL_SRC = {"integrate": "fuse.cu", "raycast": "raycast.cu", "icp": "icp.cu"}
-KERNEL_NAME = {"integrate": "k_integrate", "raycast": "k_march + k_refine",
-               "icp": "k_icp_run" if os.environ.get("XSLAM_ICP_RUN") == "1" else "k_icp"}
+KERNEL_NAME = {"integrate": "k_integrate", "raycast": "k_march + k_refine", "icp": "k_icp"}
 
 
 def _src_hash(stage):
@@ -396,7 +417,7 @@ def run_ours(args, rank, world, local_rank):
     pool = None
     cpu_lanes = min(args.lanes, 6)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        pool = mp.get_context("spawn").Pool(cpu_lanes)
+        pool = oracle_pool(cpu_lanes)
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -553,7 +574,6 @@ def run_ours(args, rank, world, local_rank):
 
     batched = None if args.no_batch else run_batch(args, dev, rank)
     second = None if args.no_second_order else run_second_order(args, dev, rank)
-    newton = None if args.no_newton else run_newton_icp(args, dev, rank)
     learned = None if args.no_learned else run_learned(args, dev, rank)
 
     # ---- CPU oracle on the host cores (rank 0, N = 1): frame 1 of the same sequence ----
@@ -568,6 +588,7 @@ def run_ours(args, rank, world, local_rank):
         pool.close()
         lane_s = max(r[0] for r in res)
         cpu = dict(value=round(1.0 / lane_s * cpu_lanes / L, 5), unit="frames/s", cores=cpu_lanes, kind="oracle",
+                   cpu_model=cpu_model(), host_cores=os.cpu_count(),
                    sample=f"frame 1 (ICP 19 iterations, fusion, ray cast) of the same {wl.name} sequence after an "
                           f"untimed frame 0; {cpu_lanes} complex128 lanes, one process per lane, slowest lane "
                           f"{lane_s:.1f} s (wall incl. frame 0: {wall:.0f} s)")
@@ -576,23 +597,71 @@ def run_ours(args, rank, world, local_rank):
             gpu = dtw_frame1[:cpu_lanes]
             grad_err = float(np.linalg.norm(gpu - ref) / np.linalg.norm(ref))
 
+    # the metric's companions as top-level scalars first; the experiments beside the headline as short
+    # summaries (every figure goes to --details)
+    companions = dict(
+        grad_rel_err_vs_oracle=grad_err,
+        plain_fp64_frames_per_s=plain["value"] if plain else None,
+        speedup_vs_plain_fp64=plain["speedup_of_value"] if plain else None,
+        grad_rel_err_vs_plain_fp64=float(f"{plain['grad_rel_err_fp32_lanes_vs_plain']:.3g}") if plain else None,
+        uncomplexified_fp32_frames_per_s=real32["value"],
+        lanes_cost_vs_uncomplexified=round(real32["value"] / value, 3))
     line = dict(metric=METRIC, value=round(value, 2), unit="frames/s", n_gpus=world, steps=K, warmup=W,
                 ms_per_step=round(ms / K, 4), higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f32", data="synthetic",
+                dtype="f32", data="synthetic", **companions,
                 config=dict(wl_desc(wl, L), parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                             l2="inputs larger than L2: the TSDF state alone is "
                                f"{np.prod(wl.dims) * 4 * (L + 1) / 1e6:.0f} MB",
                             tracking_failures=int(n_fail)),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(round(launches_per_frame * K)),
                 clocks=clk, stage_ms_per_frame=stage_ms, roofline_stages=roofline_stages,
-                grad_rel_err_vs_oracle=grad_err,
-                plain_fp64=plain, uncomplexified_fp32=real32, batched=batched, second_order=second, newton_icp=newton,
-                learned_proposal=learned,
                 per_frame=dict(fused_voxels=round(per_frame["fused"]), surface_pixels=round(per_frame["hits"]),
                                raycast_march_voxels=per_frame["march_voxels"],
-                               raycast_refine_voxels=per_frame["refine_voxels"]))
+                               raycast_refine_voxels=per_frame["refine_voxels"]),
+                batched=_batched_summary(batched), second_order=_second_summary(second),
+                learned_proposal=_learned_summary(learned))
+    details = dict(line, plain_fp64=plain, uncomplexified_fp32=real32, batched=batched, second_order=second,
+                   learned_proposal=learned)
     if rank == 0:
+        if args.details:
+            with open(args.details, "w") as f:
+                json.dump(details, f, indent=1)
         print(json.dumps(line))
+
+
+def _batched_summary(b):
+    if not b:
+        return None
+    return dict(value=b["value"], unit=b["unit"], frames=b["frames"], speedup_vs_sequential=b["speedup_vs_sequential"],
+                latency_ms_median=b["latency_ms_per_frame"]["median"], roofline_frac=b["roofline"]["frac"],
+                tracking_failures=b["tracking_failures"])
+
+
+def _second_summary(s2):
+    if not s2:
+        return None
+    h = s2["hessian"]
+    t = s2["tsdf_loss"]
+    return dict(newton_recall=s2["newton_eta"].get("recall_1cm_1deg"), newton_median_cm=s2["newton_eta"]["median_cm"],
+                nlcg_median_cm=s2["nlcg"]["median_cm"], gd_median_cm=s2["gradient_descent"]["median_cm"],
+                hessian_ms=h["ms_per_evaluation"], hessian_plain_fp64_ms=h["plain_fp64"]["ms_per_evaluation"],
+                hessian_speedup_vs_plain_fp64=h["plain_fp64"]["speedup_of_fp32"],
+                hessian_rel_err_vs_plain_fp64=h["plain_fp64"]["hess_rel_err_fp32"],
+                tsdf_hessian_ms=t["hessian"]["ms_per_evaluation"],
+                tsdf_hessian_plain_fp64_ms=t["plain_fp64"]["ms_per_evaluation"],
+                tsdf_hessian_rel_err_vs_plain_fp64=t["plain_fp64"]["hess_rel_err_fp32"])
+
+
+def _learned_summary(lp):
+    if not lp:
+        return None
+    out = dict(train_ms=lp["train"]["train_ms"], pairs=lp["train"]["pairs"], start_error_sigma=lp["start_error_sigma"])
+    for k in ("constant_velocity", "constant_velocity_proposal", "previous_pose", "previous_pose_proposal"):
+        if k in lp:
+            r = lp[k]
+            out[k] = dict(fps=r["fps"], failures=r["failures"], trans_err_cm_mean=r["trans_err_cm_mean"],
+                          fallback_rate=r.get("fallback_rate"))
+    return out
 
 
 # ------------------------------------------------------------------------------------------------
@@ -600,7 +669,7 @@ def run_ours(args, rank, world, local_rank):
 # ------------------------------------------------------------------------------------------------
 def run_batch(args, dev, rank):
     """Many trajectories of uneven length, image size, grid and lane count, advanced together: one
-    CUDA graph per step. The ICP grid is picked by the library's autotuner on the first steps; the
+    CUDA graph per step. The launch shapes are picked by the library's autotuner on the first steps; the
     timed pass then runs every trajectory from frame 0 to its end. Returns the JSON object."""
     import torch
     from paper_2405_02187_gb300 import synth, xslam
@@ -620,7 +689,7 @@ def run_batch(args, dev, rank):
     batch = xslam.XSlamBatch(handles)
     tune_steps = 6
     frames = [[d[k] if k < n else None for d, n in zip(depth, lens)] for k in range(tune_steps)]
-    divisor, tune_ms = batch.autotune(frames, tune_steps)
+    choice, tune_ms = batch.autotune(frames, tune_steps)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = max(lens)
@@ -649,11 +718,20 @@ def run_batch(args, dev, rank):
         x.set_lanes([(k, j, H_GPU) for k, j in lanes])
         x.set_pose(wl.poses[0])
     batch = xslam.XSlamBatch(handles)
+    batch.set_shapes(choice)
     lat = []
     for k in range(min(12, min(lens))):
         batch.step([d[k] for d in depth])
         if k >= 2:
             lat.append(batch.latency())
+    # where a segmented step's time goes: one profiled step (events between the launches)
+    batch.set_shapes(dict(choice, mode="segmented"))
+    batch.profile(True)
+    kp = min(12, min(lens))
+    batch.step([d[kp] for d in depth])
+    stage_ms = {}
+    for stage, _, _, t in batch.profile_read():
+        stage_ms[stage] = stage_ms.get(stage, 0.0) + t
     batch.close()
     lat = np.mean(np.array(lat), 0) if lat else np.zeros(len(lens))
     # the same trajectories one at a time (their own graphs, default grids): frames 2..7 of each
@@ -685,7 +763,11 @@ def run_batch(args, dev, rank):
         roofline=dict(bound="hbm", achieved=round(moved / (ms * 1e-3) / 1e9, 1), peak=peak, unit="GB/s",
                       frac=round(moved / (ms * 1e-3) / 1e9 / peak, 4), algorithmic_gb=round(moved / 1e9, 2),
                       note="algorithmic bytes of every ICP, fusion and ray-cast launch of the run / its time"),
-        icp_grid_divisor=divisor, autotune_ms_per_step={str(d): round(float(m), 3) for d, m in zip((1, 2, 4, 8, 16), tune_ms)},
+        autotune=dict(choice=choice, ms_per_step=[round(float(m), 3) for m in tune_ms],
+                      candidates="mode segmented, branches; ICP grid / 1, 2, 4, 8; then in segmented mode fusion "
+                                 "blocks per SM default, 1, 2, 4 and ray tile 32x8, 16x16, 64x4 (one coordinate at a "
+                                 "time, each with the best of the ones before)"),
+        segmented_step_ms_by_stage={k: round(v, 3) for k, v in stage_ms.items()},
         latency_ms_per_frame=dict(min=round(float(lat.min()), 3), median=round(float(np.median(lat)), 3),
                                   max=round(float(lat.max()), 3)),
         state_gb=round(sum(v * 4 * (2 + len(l)) for v, (_, l) in zip(vox, trajs)) / 1e9, 2),
@@ -812,6 +894,22 @@ def run_second_order(args, dev, rank):
     E32, g32, H32, _ = x.grad_tsdf(wl.depth[k], T0, order=2)
     err_g = float(np.linalg.norm(g32 - g64) / max(np.linalg.norm(g64), 1e-300))
     err_H = float(np.linalg.norm(H32 - H64) / max(np.linalg.norm(H64), 1e-300))
+    # the point-to-plane loss of xslam_grad by the plain FP64 bicomplex path (xslam_grad_plain64)
+    x.grad_plain64(wl.depth[k], T0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    n = 5
+    for _ in range(n):
+        Ep, gp, Hp = x.grad_plain64(wl.depth[k], T0)
+    ms_p64 = (time.perf_counter() - t1) / n * 1e3
+    Ef, gf, Hf = x.grad(wl.depth[k], T0, order=2)
+    p2p64 = dict(note="Sec. 3's bicomplex step in FP64 with full products (h = 1e-20), its own FP64 march and "
+                      "decisions, one thread per pixel; the FP32 truncated path's relative error against it",
+                 ms_per_evaluation=round(ms_p64, 3), per_s=round(1000.0 / ms_p64, 2),
+                 speedup_of_fp32=round(ms_p64 / times[2], 1),
+                 grad_rel_err_fp32=float(f"{np.linalg.norm(gf - gp) / max(np.linalg.norm(gp), 1e-300):.3g}"),
+                 hess_rel_err_fp32=float(f"{np.linalg.norm(Hf - Hp) / max(np.linalg.norm(Hp), 1e-300):.3g}"),
+                 loss_rel_diff=float(f"{abs(Ef - Ep) / max(abs(Ep), 1e-300):.3g}"))
     x.close()
     return dict(
         workload=f"{wl.dims[0]}^3 x {wl.voxel * 100:.1f} cm map of a 40-primitive room from a {frames}-frame 640x480 walk; "
@@ -822,7 +920,8 @@ def run_second_order(args, dev, rank):
         initial=dict(median_cm=round(float(np.median(init[:, 0])) * 100, 3), median_deg=round(float(np.median(init[:, 1])), 4)),
         gradient_descent=out["gd"], nlcg=out["nlcg"], newton_eta=dict(out["newton"], eta=args.reloc_eta),
         hessian=dict(ms_per_evaluation=round(times[2], 3), per_s=round(1000.0 / times[2], 1),
-                     directions=21, note="loss + gradient + 21 second-order directions over 640x480, host round trip included"),
+                     directions=21, note="loss + gradient + 21 second-order directions over 640x480, host round trip included",
+                     plain_fp64=p2p64),
         gradient=dict(ms_per_evaluation=round(times[1], 3), per_s=round(1000.0 / times[1], 1)),
         tsdf_loss=dict(note=f"the paper's TSDF-difference loss on the first {nq} queries (Newton whenever H is "
                             "positive definite); evaluation times at one query, host round trip included",
@@ -840,51 +939,6 @@ def run_second_order(args, dev, rank):
         generate_s=round(gen_s, 1))
 
 
-# ------------------------------------------------------------------------------------------------
-# Newton ICP against Gauss-Newton as the frame step grows
-# ------------------------------------------------------------------------------------------------
-def run_newton_icp(args, dev, rank):
-    """The room sequence tracked with every s-th frame (s = 1, 2, 4, 6, 8) by Gauss-Newton, by Newton
-    ICP with the eta switch (eta = 1e-4 m^2) and by Newton steps only (real pose, K = 0): tracking
-    failures, the translation RMSE against the ground truth, and the device time per frame."""
-    import torch
-    from paper_2405_02187_gb300 import synth, xslam
-
-    n = args.newton_frames
-    steps = (1, 2, 4, 6, 8)
-    wl = synth.room_walk(seed=21 + rank, frames=n * max(steps), device=dev, resident=True)
-    out = {}
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for method in ("gauss_newton", "newton", "newton_only"):
-        rows = {}
-        for s in steps:
-            cfg = xslam_cfg(wl)
-            cfg.icp_newton = 0 if method == "gauss_newton" else 1
-            cfg.icp_newton_eta = float("inf") if method == "newton_only" else 1e-4
-            x = xslam.XSlam(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, cfg, max_lanes=0)
-            x.set_pose(wl.poses[0])
-            idx = list(range(0, n * s, s))
-            poses = []
-            torch.cuda.synchronize()
-            e0.record()
-            for k in idx:
-                pose, _, _, st = x.frame(wl.depth[k], [])
-                poses.append(pose)
-            e1.record()
-            torch.cuda.synchronize()
-            _, fails = x.sync()
-            err = np.array([np.linalg.norm(pz[:, 3] - wl.poses[k][:, 3]) for pz, k in zip(poses, idx)])
-            rows[str(s)] = dict(failures=int(fails), rmse_cm=round(float(np.sqrt(np.mean(err ** 2))) * 100, 3),
-                                final_cm=round(float(err[-1]) * 100, 3), ms_per_frame=round(e0.elapsed_time(e1) / len(idx), 3))
-            x.close()
-        out[method] = rows
-    return dict(workload=f"{n} frames of the 640x480 room walk taken every s-th frame, 256^3 x 1 cm, K = 0; "
-                         "ms_per_frame includes the pose read-back per frame",
-                frame_step=list(steps), **out)
-
-
-# ------------------------------------------------------------------------------------------------
-# learned pose proposal (include/xslam_mlp.h)
 # ------------------------------------------------------------------------------------------------
 def run_learned(args, dev, rank):
     """Train the proposal network on frame pairs of room walks tracked by the method, then track a
@@ -948,7 +1002,7 @@ def _reference(args, rank):
     procs = min(L, 6)
     wl = make_workload(args.workload, 2, 2, "cpu")
     payload = _wl_payload(wl, 2)
-    with mp.get_context("spawn").Pool(procs) as pool:
+    with oracle_pool(procs) as pool:
         res = pool.map(_oracle_shard_steps, [(payload, (0, j % 6), R, args.warmup, args.steps) for j in range(procs)])
     step_s = np.max(np.stack([np.asarray(r) for r in res]), 0)  # the slowest lane per step
     frame_s = step_s.mean() * R * L / procs
@@ -958,6 +1012,7 @@ def _reference(args, rank):
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="c128", data="synthetic",
                 config=dict(wl_desc(wl, L), parallelism="host cores"),
                 cpu_baseline=dict(kind="oracle", cores=procs, value=round(value, 6), unit="frames/s",
+                                  cpu_model=cpu_model(), host_cores=os.cpu_count(),
                                   sample=f"each step is shard s = step mod {R} of frame 1 of {wl.name}: 1/{R} of the "
                                          f"ICP pixels (19 iterations), of the voxels and of the ray-cast pixels, plus "
                                          f"1/{R} of the once-timed measurement (filter, pyramid, vertex and normal "
@@ -985,8 +1040,6 @@ def main():
     ap.add_argument("--reloc-tsdf-queries", type=int, default=30)
     ap.add_argument("--reloc-iters", type=int, default=30)
     ap.add_argument("--reloc-eta", type=float, default=1e-3)
-    ap.add_argument("--no-newton", action="store_true", help="skip the Newton-ICP frame-step comparison")
-    ap.add_argument("--newton-frames", type=int, default=40)
     ap.add_argument("--no-learned", action="store_true", help="skip training and evaluating the learned proposal")
     ap.add_argument("--learned-rooms", type=int, default=100, help="room walks of 16 frames for the training pairs")
     ap.add_argument("--learned-epochs", type=int, default=30)
@@ -994,7 +1047,8 @@ def main():
     ap.add_argument("--batch-n", type=int, default=32)
     ap.add_argument("--batch-min", type=int, default=50)
     ap.add_argument("--batch-max", type=int, default=400)
-    ap.add_argument("--ref-shards", type=int, default=128)
+    ap.add_argument("--ref-shards", type=int, default=32)
+    ap.add_argument("--details", default=None, help="write every measured figure to this JSON file")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -180,6 +180,18 @@ xslam_status xslam_grad(xslam_t h, const float* query_depth, const double T_q[12
                         double grad[6], double* hess);
 
 /*
+ * The loss, gradient and Hessian of xslam_grad order 2 (outputs as there) by the plain FP64 path: Sec. 3's
+ * bicomplex step as printed, numbers a + b i1 + c i2 + d i1 i2 with i1^2 = i2^2 = -1 and every product
+ * kept, step h = 1e-20 in each of the 21 start poses exp(h i1 G_j + h i2 G_k) T_q, one thread per pixel,
+ * and every decision in FP64 (the pixel's own march with the ray cast's sampling rules, the cells of
+ * the hit pair and of the gradient samples, the distance gate). The comparison path of the FP32
+ * truncated arithmetic; the handle's volume is read and not changed. Any handle.
+ * Errors: XSLAM_EINVAL (NULL input, non-finite T_q).
+ */
+xslam_status xslam_grad_plain64(xslam_t h, const float* query_depth, const double T_q[12], double* loss,
+                                double grad[6], double* hess);
+
+/*
  * The paper's relocalisation loss (Sec. 5.2, TSDF-difference reading) of a query depth frame and its
  * derivatives with respect to the query pose: with (F_q, W_q) the handle's volume (F_r, W_r) after the
  * surface update (Sec. 4.1) of the query frame at T_q, E(T_q) = sum over the observed voxels (W_r > 0)

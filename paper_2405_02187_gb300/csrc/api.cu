@@ -124,11 +124,6 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   h->user = (cudaStream_t)cuda_stream;
   const char* env = getenv("XSLAM_GRAPHS");
   h->use_graphs = !(env && env[0] == '0');
-  // ICP kernel of the frame chain: one launch per iteration (default), or with XSLAM_ICP_RUN=1 every
-  // iteration of a range in one cooperative launch (measured slower on the 640x480 room: each of its
-  // 152 blocks repeats the cross-block sum and the solve, against one last block per launch)
-  const char* env2 = getenv("XSLAM_ICP_RUN");
-  h->icp_persistent = env2 && env2[0] == '1';
   Params& p = h->p;
   memset(&p, 0, sizeof(p));
   p.nx = nx; p.ny = ny; p.nz = nz;
@@ -179,8 +174,6 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
     nblk_max = std::max(nblk_max, h->nblk[l]);
   }
   nblk_max = std::max(nblk_max, 4 * h->nsm);  // k_loss grid
-  h->nblk_run = icp_run_blocks(Lmax);
-  nblk_max = std::max(nblk_max, 2 * h->nblk_run);  // the cooperative ICP's two partial buffers
   h->nblk_max = nblk_max;
   bool ok = true;
   ok &= cudaMalloc(&b.F, sizeof(float) * n * Lmax) == cudaSuccess;
@@ -198,7 +191,6 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   ok &= cudaMalloc(&b.partial, sizeof(float) * (size_t)(nblk_max + 4) * kNT * kMaxLanes) == cudaSuccess;
   ok &= cudaMalloc(&b.partial_n, sizeof(int) * nblk_max) == cudaSuccess;
   ok &= cudaMalloc(&b.ticket, sizeof(unsigned)) == cudaSuccess;
-  ok &= cudaMalloc(&b.grid_bar, sizeof(unsigned) * 4) == cudaSuccess;
   ok &= cudaMalloc(&b.status, sizeof(int) * 8) == cudaSuccess;
   ok &= cudaMalloc(&b.result, sizeof(double) * kResLen) == cudaSuccess;
   ok &= cudaMalloc(&b.stats, sizeof(unsigned long long) * kNStat) == cudaSuccess;
@@ -245,7 +237,7 @@ extern "C" xslam_status xslam_destroy(xslam_t h) {
   cudaFree(b.F); cudaFree(b.Wt); cudaFree(b.F0lin); cudaFree(b.depth_in); cudaFree(b.gated);
   for (int l = 0; l < 3; ++l) cudaFree(b.pyr[l]);
   cudaFree(b.model); cudaFree(b.pose); cudaFree(b.pose_prev); cudaFree(h->pose_tmp); cudaFree(h->hess_poses); cudaFree(h->hess_poses64);
-  cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.grid_bar); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.hit);
+  cudaFree(b.partial); cudaFree(b.partial_n); cudaFree(b.ticket); cudaFree(b.status); cudaFree(b.result); cudaFree(b.stats); cudaFree(b.hit);
   cudaFree(b.tiles); cudaFree(b.tiles_prev); cudaFree(b.tile_ctr); cudaFree(b.dlane);
   cudaFree(h->q.pose_pp); cudaFree(h->q.candA); cudaFree(h->q.candB); cudaFree(h->q.judge); cudaFree(h->q.failA);
   cudaFree(h->q.partial); cudaFree(h->q.ticket); cudaFree(h->q.row); cudaFree(h->q.prev); cudaFree(h->q.y);
@@ -313,7 +305,6 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   CU(cudaMemsetAsync(h->b.Wt, 0, sizeof(float) * n, h->s));
   CU(cudaMemsetAsync(h->b.model, 0, sizeof(float) * (size_t)h->p.W * h->p.H * (1 + 6 * Lmax), h->s));
   CU(cudaMemsetAsync(h->b.ticket, 0, sizeof(unsigned), h->s));
-  CU(cudaMemsetAsync(h->b.grid_bar, 0, sizeof(unsigned) * 4, h->s));
   CU(cudaMemsetAsync(h->b.partial, 0, sizeof(float) * (size_t)(h->nblk_max + 4) * kNT * kMaxLanes, h->s));
   CU(cudaMemsetAsync(h->b.status, 0, sizeof(int) * 8, h->s));
   CU(cudaMemsetAsync(h->q.pose_pp, 0, sizeof(double) * 12 * kMaxLanes, h->s));
@@ -475,14 +466,6 @@ static cudaError_t enqueue_first(xslam_t h) {
 // ICP iterations of pyramid levels first .. last (first >= last), coarse to fine, on the current pose
 // lanes; close = the range's last iteration closes the frame (fallback to T_{k-1}, failure count)
 static cudaError_t enqueue_icp_levels(xslam_t h, int first, int last, bool close, int* n_icp) {
-  if (!h->cfg.icp_newton && h->icp_persistent) {
-    // every iteration of the range in one cooperative launch
-    int any = 0;
-    for (int l = first; l >= last; --l) any += h->cfg.icp_iters[l];
-    if (any == 0) return cudaSuccess;
-    *n_icp += 1;
-    return launch_icp_run(h->p, h->b, first, last, h->cfg.icp_iters, close, h->nblk_run, h->s);
-  }
   int last_level = -1;
   for (int l = first; l >= last; --l)
     if (h->cfg.icp_iters[l] > 0) last_level = l;
@@ -663,11 +646,6 @@ extern "C" xslam_status xslam_frame(xslam_t h, const float* depth, int depth_on_
     CU(cudaStreamSynchronize(h->s));
     return fail(h, XSLAM_ETIMEOUT, "a tensor-core wait of the proposal network ran out");
   }
-  if (h->h_status[5]) {
-    CU(cudaMemsetAsync(h->b.status + 5, 0, sizeof(int), h->s));
-    CU(cudaStreamSynchronize(h->s));
-    return fail(h, XSLAM_ETIMEOUT, "a grid barrier of the ICP launch ran out");
-  }
   if (pose_out) memcpy(pose_out, h->h_result, sizeof(double) * 12);
   if (dpose_out) memcpy(dpose_out, h->h_result + 12, sizeof(double) * 12 * h->K);
   if (dtwist_out) memcpy(dtwist_out, h->h_result + 12 + 12 * (kMaxLanes - 1), sizeof(double) * 6 * h->K);
@@ -684,11 +662,10 @@ extern "C" xslam_status xslam_sync(xslam_t h, int* n_failed) {
   if (!h) return XSLAM_EINVAL;
   CU(cudaMemcpyAsync(h->h_status, h->b.status, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->s));
   CU(cudaMemsetAsync(h->b.status + 1, 0, sizeof(int), h->s));
-  CU(cudaMemsetAsync(h->b.status + 4, 0, sizeof(int) * 2, h->s));
+  CU(cudaMemsetAsync(h->b.status + 4, 0, sizeof(int), h->s));
   CU(cudaStreamSynchronize(h->s));
   if (n_failed) *n_failed = h->h_status[1];
   if (h->h_status[4]) return fail(h, XSLAM_ETIMEOUT, "a tensor-core wait of the proposal network ran out");
-  if (h->h_status[5]) return fail(h, XSLAM_ETIMEOUT, "a grid barrier of the ICP launch ran out");
   if (h->h_status[1] > 0) {
     h->err = "ICP failed to track on some frames";
     return XSLAM_ENOTRACK;
@@ -944,6 +921,33 @@ extern "C" xslam_status xslam_grad(xslam_t h, const float* query_depth, const do
   if (loss) *loss = h->h_result[kResSys];
   if (grad)
     for (int j = 0; j < 6; ++j) grad[j] = h->h_result[kResSys + 1 + j];
+  return st;
+}
+
+extern "C" xslam_status xslam_grad_plain64(xslam_t h, const float* query_depth, const double* T_q, double* loss,
+                                           double* grad, double* hess) {
+  if (!h || !query_depth || !T_q) return fail(h, XSLAM_EINVAL, "NULL argument");
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(T_q[i])) return fail(h, XSLAM_EINVAL, "T_q has a non-finite entry");
+  const double step = 1e-20;
+  double hp[21 * 12 * 4];
+  hess_poses(T_q, hp, step);
+  xslam_status st = enter(h);
+  if (st != XSLAM_OK) return st;
+  CU(cudaMemcpyAsync(h->hess_poses64, hp, sizeof(hp), cudaMemcpyHostToDevice, h->s));
+  if ((st = copy_depth(h, query_depth, 1)) != XSLAM_OK) return st;
+  CU(launch_prepare(h->p, h->b, 1, h->s));
+  const int nblk = std::min((int)((size_t)h->p.W * h->p.H + 127) / 128, 4 * h->nsm);
+  CU(launch_hess64(h->p, h->b, h->b.pyr[0], h->hess_poses64, step, h->b.result + kResSys, nblk, h->s));
+  CU(cudaMemcpyAsync(h->h_result, h->b.result, sizeof(double) * kResLen, cudaMemcpyDeviceToHost, h->s));
+  st = leave(h);
+  CU(cudaStreamSynchronize(h->s));
+  const double* r = h->h_result + kResSys;
+  if (loss) *loss = r[0];
+  if (grad)
+    for (int j = 0; j < 6; ++j) grad[j] = r[1 + j];
+  if (hess)
+    for (int q = 0; q < 21; ++q) hess[q] = r[7 + q];
   return st;
 }
 

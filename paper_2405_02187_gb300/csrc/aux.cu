@@ -31,8 +31,8 @@ __device__ void generator_times(int e, double h, const double* __restrict__ T0, 
 
 // Frame 0: lanes of the pose kinds (POSE0, and the per-frame kinds, whose start and tracked pose are
 // T_0 itself at frame 0) get h G_idx T_0; every other lane is zero. Lane 0 untouched.
-__global__ void k_seed_pose(double* pose, int L, const int* kinds, const int* index, Params p) {
-  pdl_enter();
+__device__ __forceinline__ void seed_pose_body(double* pose, int L, const int* kinds, const int* index,
+                                               const Params& p) {
   const int l = threadIdx.x;
   if (l < 1 || l >= L) return;
   const int k = kinds[l];
@@ -42,6 +42,11 @@ __global__ void k_seed_pose(double* pose, int L, const int* kinds, const int* in
   } else {
     for (int i = 0; i < 12; ++i) Tl[i] = 0.0;
   }
+}
+
+__global__ void k_seed_pose(double* pose, int L, const int* kinds, const int* index, Params p) {
+  pdl_enter();
+  seed_pose_body(pose, L, kinds, index, p);
 }
 
 // Per-frame pose lanes of a tracked frame (X-SLAM Sec. 4.1, Eq. lie promoting frame k's own pose):
@@ -69,8 +74,8 @@ __global__ void k_seed_frame(Params p, double* __restrict__ pose, double* __rest
   if ((mode & 4) && k == kSeedPoseTracked) generator_times(index[l], p.h[l], pose, pose + 12 * l);
 }
 
-__global__ void k_readout(const double* __restrict__ pose, int L, Params p, double* __restrict__ out) {
-  pdl_enter();
+__device__ __forceinline__ void readout_body(const double* __restrict__ pose, int L, const Params& p,
+                                             double* __restrict__ out) {
   const int l = threadIdx.x;
   if (l == 0)
     for (int i = 0; i < 12; ++i) out[i] = pose[i];
@@ -96,6 +101,23 @@ __global__ void k_readout(const double* __restrict__ pose, int L, Params p, doub
   tw[3] = dT[3] - (w1 * t2 - w2 * t1);
   tw[4] = dT[7] - (w2 * t0 - w0 * t2);
   tw[5] = dT[11] - (w0 * t1 - w1 * t0);
+}
+
+__global__ void k_readout(const double* __restrict__ pose, int L, Params p, double* __restrict__ out) {
+  pdl_enter();
+  readout_body(pose, L, p, out);
+}
+
+// one 32-thread block per segment: mode 0 seeds frame 0's pose lanes, mode 1 reads the frame out
+__global__ void __launch_bounds__(32) k_lanes_seg(SegTable st, int mode) {
+  pdl_enter();
+  const TrajDesc& d = st.desc[st.seg[blockIdx.x].traj];
+  if (mode == 0) seed_pose_body(d.b.pose, d.p.L, d.kinds, d.index, d.p);
+  else readout_body(d.b.pose, d.p.L, d.p, d.b.result);
+}
+
+cudaError_t launch_lanes_seg(const SegTable& t, int mode, cudaStream_t s) {
+  return launch_pdl(k_lanes_seg, dim3(t.nseg), dim3(32), 0, s, t, mode);
 }
 
 // Relocalisation loss E = mean_u r_u^2, r_u = (T V_q(u) - V_g(u)) . N_g(u), model ray cast at T itself

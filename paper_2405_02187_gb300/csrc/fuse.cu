@@ -97,15 +97,15 @@ __device__ __forceinline__ float fuse_lane_FD(const Params& p, const float* __re
 // list (warp-aggregated atomics). The test is the exact corner test: the tile's box (padded by half a
 // voxel around the voxel centres) is skipped if all 8 corners lie behind the camera or beyond the
 // same image edge.
-__global__ void __launch_bounds__(256) k_fuse_tiles(Params p, const double* __restrict__ pose, int* __restrict__ tiles,
-                                                   unsigned* __restrict__ ctr) {
-  pdl_enter();
+// bx, gx: this block's index in its trajectory's grid and that grid's size
+__device__ __forceinline__ void fuse_tiles_body(const Params& p, const double* __restrict__ pose,
+                                                int* __restrict__ tiles, unsigned* __restrict__ ctr, int bx, int gx) {
   const int ntx = (p.nx + kBX - 1) / kBX, nty = (p.ny + kBY - 1) / kBY, ntz = (p.nz + kBZ - 1) / kBZ;
   const int nt = ntx * nty * ntz;
   float T[12];
 #pragma unroll
   for (int e = 0; e < 12; ++e) T[e] = (float)pose[e];
-  for (int t0 = blockIdx.x * blockDim.x; t0 < nt; t0 += gridDim.x * blockDim.x) {
+  for (int t0 = bx * blockDim.x; t0 < nt; t0 += gx * blockDim.x) {
     const int t = t0 + threadIdx.x;
     bool keep = false;
     if (t < nt) {
@@ -142,6 +142,19 @@ __global__ void __launch_bounds__(256) k_fuse_tiles(Params p, const double* __re
   }
 }
 
+__global__ void __launch_bounds__(256) k_fuse_tiles(Params p, const double* __restrict__ pose, int* __restrict__ tiles,
+                                                   unsigned* __restrict__ ctr) {
+  pdl_enter();
+  fuse_tiles_body(p, pose, tiles, ctr, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) k_fuse_tiles_seg(SegTable st) {
+  pdl_enter();
+  const Seg sg = st.seg[seg_find(st, blockIdx.x)];
+  const TrajDesc& d = st.desc[sg.traj];
+  fuse_tiles_body(d.p, d.b.pose, d.b.tiles, d.b.tile_ctr, blockIdx.x - sg.block0, sg.nblk);
+}
+
 // Fixed grid over the tile list; a block takes one tile at a time, a thread per 4 x-consecutive voxels of
 // a brick row: thread t holds voxels 4 (t mod 2) .. + 3 of row y = t / 2 mod 8, z = t / 16, so a warp's
 // 128-bit loads and stores cover 512 consecutive bytes of every plane. A thread first takes the real
@@ -154,13 +167,12 @@ constexpr int kQuadThreads = 128;
 __host__ __device__ constexpr int fuse_blocks_per_sm(int NL) { return NL <= 2 ? 8 : (NL <= 9 ? 5 : 4); }
 
 template <int NL>
-__global__ void __launch_bounds__(kQuadThreads, fuse_blocks_per_sm(NL)) k_integrate(Params p, const float* __restrict__ D,
-                                                        const double* __restrict__ pose, float* __restrict__ F,
-                                                        float* __restrict__ Wt, float* __restrict__ F0lin,
-                                                        unsigned long long* __restrict__ stats,
-                                                        const int* __restrict__ tiles, unsigned* __restrict__ ctr,
-                                                        const float* __restrict__ dlane, int* __restrict__ tiles_prev) {
-  pdl_enter();
+__device__ __forceinline__ void integrate_body(const Params& p, const float* __restrict__ D,
+                                               const double* __restrict__ pose, float* __restrict__ F,
+                                               float* __restrict__ Wt, float* __restrict__ F0lin,
+                                               unsigned long long* __restrict__ stats, const int* __restrict__ tiles,
+                                               unsigned* __restrict__ ctr, const float* __restrict__ dlane,
+                                               int* __restrict__ tiles_prev, int bx, int gx) {
   __shared__ float sT[NL][12];
   __shared__ float sC[NL][3];  // -R^T dt of each lane: the voxel-independent part of its p_c tangent
   __shared__ bool s_last;
@@ -180,7 +192,7 @@ __global__ void __launch_bounds__(kQuadThreads, fuse_blocks_per_sm(NL)) k_integr
   const bool lin4 = (p.nx & 3) == 0;      // the linear copy's rows keep 16-byte alignment
   const float* T = sT[0];
   int cnt = 0;
-  for (unsigned q = blockIdx.x; q < count; q += gridDim.x) {
+  for (unsigned q = bx; q < count; q += gx) {
     const int t = tiles[q];
     if (p.fresh && tid == 0) tiles_prev[q] = t;  // the next frame clears its restarted lanes here
     const int i0 = (t % ntx) * kBX + qx, j = ((t / ntx) % nty) * kBY + cy, k = (t / (ntx * nty)) * kBZ + cz;
@@ -249,7 +261,7 @@ __global__ void __launch_bounds__(kQuadThreads, fuse_blocks_per_sm(NL)) k_integr
   __syncthreads();
   if (tid == 0) {
     __threadfence();
-    s_last = atomicAdd(ctr + 1, 1u) == gridDim.x - 1;
+    s_last = atomicAdd(ctr + 1, 1u) == (unsigned)gx - 1;
   }
   __syncthreads();
   if (s_last && tid == 0) {
@@ -257,6 +269,28 @@ __global__ void __launch_bounds__(kQuadThreads, fuse_blocks_per_sm(NL)) k_integr
     ctr[0] = 0u;
     ctr[1] = 0u;
   }
+}
+
+template <int NL>
+__global__ void __launch_bounds__(kQuadThreads, fuse_blocks_per_sm(NL)) k_integrate(Params p, const float* __restrict__ D,
+                                                        const double* __restrict__ pose, float* __restrict__ F,
+                                                        float* __restrict__ Wt, float* __restrict__ F0lin,
+                                                        unsigned long long* __restrict__ stats,
+                                                        const int* __restrict__ tiles, unsigned* __restrict__ ctr,
+                                                        const float* __restrict__ dlane, int* __restrict__ tiles_prev) {
+  pdl_enter();
+  integrate_body<NL>(p, D, pose, F, Wt, F0lin, stats, tiles, ctr, dlane, tiles_prev, blockIdx.x, gridDim.x);
+}
+
+// every segment's trajectory has NL lanes
+template <int NL>
+__global__ void __launch_bounds__(kQuadThreads, fuse_blocks_per_sm(NL)) k_integrate_seg(SegTable st) {
+  pdl_enter();
+  const Seg sg = st.seg[seg_find(st, blockIdx.x)];
+  const TrajDesc& d = st.desc[sg.traj];
+  const Buffers& b = d.b;
+  integrate_body<NL>(d.p, b.pyr[0], b.pose, b.F, b.Wt, b.F0lin, b.stats, b.tiles, b.tile_ctr, b.dlane, b.tiles_prev,
+                     blockIdx.x - sg.block0, sg.nblk);
 }
 
 // Restarted lanes (per-frame pose seeds): before frame k's update their TSDF planes must hold no
@@ -285,52 +319,62 @@ int fuse_tile_count(const Params& p) {
   return ((p.nx + kBX - 1) / kBX) * ((p.ny + kBY - 1) / kBY) * ((p.nz + kBZ - 1) / kBZ);
 }
 
-cudaError_t launch_fuse_tiles(const Params& p, const Buffers& b, const double* pose, cudaStream_t s) {
-  int dev = 0, sms = 0;  // the current device's SM count (queried per call: a handle may live on any device)
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int nt = fuse_tile_count(p);
-  return launch_pdl(k_fuse_tiles, dim3(std::min((nt + 255) / 256, 4 * sms)), dim3(256), 0, s, p, pose, b.tiles,
-                    b.tile_ctr);
-}
-
-cudaError_t launch_clear_fresh(const Params& p, const Buffers& b, cudaStream_t s) {
+static int device_sms() {  // the current device's SM count (queried per call: a handle may live on any device)
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return launch_pdl(k_clear_fresh, dim3(std::max(1, std::min(fuse_tile_count(p), 4 * sms))), dim3(kFuseThreads), 0, s,
-                    p, b.F, (const int*)b.tiles_prev, (const unsigned*)b.tile_ctr);
+  return sms;
+}
+
+int fuse_tiles_grid(const Params& p) { return std::max(1, std::min((fuse_tile_count(p) + 255) / 256, 4 * device_sms())); }
+
+int integrate_grid(const Params& p) {
+  return std::max(1, std::min(fuse_tile_count(p), fuse_blocks_per_sm(p.L) * device_sms()));  // the resident blocks
+}
+
+cudaError_t launch_fuse_tiles(const Params& p, const Buffers& b, const double* pose, cudaStream_t s) {
+  return launch_pdl(k_fuse_tiles, dim3(fuse_tiles_grid(p)), dim3(256), 0, s, p, pose, b.tiles, b.tile_ctr);
+}
+
+cudaError_t launch_clear_fresh(const Params& p, const Buffers& b, cudaStream_t s) {
+  return launch_pdl(k_clear_fresh, dim3(std::max(1, std::min(fuse_tile_count(p), 4 * device_sms()))),
+                    dim3(kFuseThreads), 0, s, p, b.F, (const int*)b.tiles_prev, (const unsigned*)b.tile_ctr);
+}
+
+template <int NL>
+static cudaError_t launch_integrate_seg_nl(const SegTable& t, int nblocks, cudaStream_t s) {
+  return launch_pdl(k_integrate_seg<NL>, dim3(nblocks), dim3(kQuadThreads), 0, s, t);
+}
+
+cudaError_t launch_fuse_tiles_seg(const SegTable& t, int nblocks, cudaStream_t s) {
+  return launch_pdl(k_fuse_tiles_seg, dim3(nblocks), dim3(256), 0, s, t);
+}
+
+#define XSLAM_LANE_SWITCH(L, CALL)                                                                   \
+  switch (L) {                                                                                       \
+    case 1: return CALL(1); case 2: return CALL(2); case 3: return CALL(3); case 4: return CALL(4);  \
+    case 5: return CALL(5); case 6: return CALL(6); case 7: return CALL(7); case 8: return CALL(8);  \
+    case 9: return CALL(9); case 10: return CALL(10); case 11: return CALL(11);                      \
+    case 12: return CALL(12); case 13: return CALL(13); case 14: return CALL(14);                    \
+    case 15: return CALL(15); case 16: return CALL(16);                                              \
+    default: return cudaErrorInvalidValue;                                                           \
+  }
+
+cudaError_t launch_integrate_seg(const SegTable& t, int nblocks, int L, cudaStream_t s) {
+#define XSLAM_SEG(NL) launch_integrate_seg_nl<NL>(t, nblocks, s)
+  XSLAM_LANE_SWITCH(L, XSLAM_SEG)
+#undef XSLAM_SEG
 }
 
 cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s) {
-  int dev = 0, sms = 0;  // the current device's SM count (queried per call: a handle may live on any device)
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int nt = fuse_tile_count(p);
   cudaError_t e = cudaSuccess;
   if (p.fresh && (e = launch_clear_fresh(p, b, s)) != cudaSuccess) return e;
   e = launch_fuse_tiles(p, b, b.pose, s);
   if (e != cudaSuccess) return e;
-  const int grid = std::max(1, std::min(nt, fuse_blocks_per_sm(p.L) * sms));  // the resident blocks
-  switch (p.L) {
-    case 1: return launch_integrate_nl<1>(p, b, grid, s);
-    case 2: return launch_integrate_nl<2>(p, b, grid, s);
-    case 3: return launch_integrate_nl<3>(p, b, grid, s);
-    case 4: return launch_integrate_nl<4>(p, b, grid, s);
-    case 5: return launch_integrate_nl<5>(p, b, grid, s);
-    case 6: return launch_integrate_nl<6>(p, b, grid, s);
-    case 7: return launch_integrate_nl<7>(p, b, grid, s);
-    case 8: return launch_integrate_nl<8>(p, b, grid, s);
-    case 9: return launch_integrate_nl<9>(p, b, grid, s);
-    case 10: return launch_integrate_nl<10>(p, b, grid, s);
-    case 11: return launch_integrate_nl<11>(p, b, grid, s);
-    case 12: return launch_integrate_nl<12>(p, b, grid, s);
-    case 13: return launch_integrate_nl<13>(p, b, grid, s);
-    case 14: return launch_integrate_nl<14>(p, b, grid, s);
-    case 15: return launch_integrate_nl<15>(p, b, grid, s);
-    case 16: return launch_integrate_nl<16>(p, b, grid, s);
-    default: return cudaErrorInvalidValue;
-  }
+  const int grid = integrate_grid(p);
+#define XSLAM_ONE(NL) launch_integrate_nl<NL>(p, b, grid, s)
+  XSLAM_LANE_SWITCH(p.L, XSLAM_ONE)
+#undef XSLAM_ONE
 }
 
 }  // namespace xslam

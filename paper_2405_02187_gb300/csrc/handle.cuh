@@ -38,9 +38,8 @@ struct xslam_s {
   void* prop_act[8] = {};   // BF16 hidden activations of the network's forward pass (1 row each)
   float* prop_ws = nullptr; // its split-K workspace
   int nblk[3] = {1, 1, 1};
+  bool in_batch = false;      // grouped by a live xslam_batch (which may change nblk until it is destroyed)
   int nblk_max = 1;
-  int nblk_run = 1;             // blocks of the cooperative ICP launch
-  bool icp_persistent = false;  // the frame chain runs each ICP range in one cooperative launch
   cudaGraphExec_t g_first = nullptr, g_track = nullptr;
   bool use_graphs = true;
   // stage profiling (xslam_profile): one event pair per stage and frame, accumulated on read

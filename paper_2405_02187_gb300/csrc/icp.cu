@@ -7,12 +7,16 @@
 // normal equations A = sum J J^T, g = sum J r (Eq. icp, Eq. "icp approx") are reduced, A x = -g is
 // solved and T_{j+1} = exp(x) T_j.
 //
-// GB300 mapping: a block holds L = 1 + K warps per replica; warp `lane` of a replica computes the
-// real part of its 32 pixels and, if lane > 0, the tangent of that lane, accumulating only 27 FP32
-// sums per thread; replicas of a block share pixel chunks through L1. Warp shuffles and shared
-// memory reduce each block to one FP32 partial per lane; the last block to finish (ticket counter,
-// no grid-wide wait) adds the partials in FP64, factors the real 6x6 matrix by Cholesky (FP64), solves
-// the K + 1 right-hand sides (x_0 from the real part, x_j = A^-1 (-g_j - A_j x_0) for each lane) and
+// GB300 mapping: one launch per Gauss-Newton iteration, blocks of 16 warps, at most one block per SM.
+// A warp takes one chunk of 32 consecutive pixels of the level at a time (a pixel per thread) and
+// computes its real part once, then every lane's tangent in turn from the lane's affine map of the
+// camera-frame point (formed once per launch from the pose lanes) and the lane's own model taps. The 27
+// terms of each lane are summed over the warp right away by a transpose reduction (thread t ends with
+// value t), so a thread holds no accumulators across chunks and warps never wait for each other; the
+// warps' sums go to shared memory, the block's to value-major partials. The last block to finish
+// (ticket counter, no grid-wide wait) adds the partials in FP64, factors the real 6x6 matrix (FP32
+// square-root-free Cholesky with one FP64-residual refinement of every right-hand side), solves the
+// K + 1 right-hand sides (x_0 from the real part, x_j = A^-1 (-g_j - A_j x_0) for each lane) and
 // composes exp(x) T_j on every lane in FP64.
 #include "internal.cuh"
 #include "se3.cuh"
@@ -86,36 +90,30 @@ __device__ __forceinline__ void subst32(const Ldl32& f, const float* b, float* x
   }
 }
 
-__device__ __forceinline__ void accum(float* acc, const float* Ja, const float ra, const float* Jb, const float rb) {
-  // acc += Ja Jb^T + Jb Ja^T (upper triangle) and Ja rb + Jb ra; called with (J, r, J, r) * 0.5 for
-  // the real lane and with (J, r, J_l, r_l) for a tangent lane.
-  int q = 0;
-#pragma unroll
-  for (int r = 0; r < 6; ++r)
-#pragma unroll
-    for (int c = r; c < 6; ++c) acc[q++] += Ja[r] * Jb[c] + Jb[r] * Ja[c];
-#pragma unroll
-  for (int r = 0; r < 6; ++r) acc[21 + r] += Ja[r] * rb + Jb[r] * ra;
-}
-
-// fields of the per-pixel record handed from the real warp to the lane warps (SoA, [field][32])
-enum : int {
-  RV = 0, RD, RRX, RRY, RE, RQX = RE + 3, RQY, RIZ, RA, RB, RT, RPP, RN = RPP + 3, RDF = RN + 3, RDQA = RDF + 3,
-  RDQB = RDQA + 3, RDNA = RDQB + 3, RDNB = RDNA + 3, RJ = RDNB + 3, RRES = RJ + 6, kRec
-};
-constexpr int kMaxReps = 4;
-
-__device__ __forceinline__ void named_barrier(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 // Shared memory of the ICP kernels (static part; the per-pixel records are dynamic).
+constexpr int kIcpThreads = 512;  // 16 warps; a warp takes one chunk of 32 pixels at a time
+constexpr int kIcpWarps = kIcpThreads / 32;
+// dynamic shared memory of the ICP kernels for L lanes: the warps' sums [warp][lane][27]
+__host__ __device__ __forceinline__ int icp_dyn_bytes(int L) { return (int)sizeof(float) * kIcpWarps * L * kNT; }
+
+
+// The tangent of a lane's camera-frame point is affine in the pixel's vertex V: with the pose lanes
+// (T, T_l) and the model's pose lanes (P, P_l),
+//   p_c' = P_l^T (T V + t - t_P) + P^T (T_l V + t_l - t_Pl + T V_l) = A_l V + b_l + P^T T V_l,
+// A_l = P_l^T T + P^T T_l, b_l = P_l^T (t - t_P) + P^T (t_l - t_Pl), and V_l = dD_l (rx, ry, 1) for a
+// DEPTH lane, whose P^T T V_l = dD_l (p_c - b_0) / d with b_0 = P^T (t - t_P). Per launch, per lane.
+struct IcpLane {
+  float A[9];
+  float b[3];
+};
+
+// Shared memory of the ICP kernels.
 struct IcpShared {
   float sT[kMaxLanes][12];   // pose lanes of the current iterate (FP32 copy for the pixel work)
   float sP[kMaxLanes][12];   // pose lanes the model was ray cast at
-  float sZero[12];
-  float s_red[kNT * kMaxLanes];  // [rep][lane][27]; reps * L <= 16 by construction
-  int s_cnt[32];
+  IcpLane sL[kMaxLanes];     // per-lane affine maps of the camera-frame tangent
+  float sb0[3];
+  int s_cnt[kIcpWarps];
   double sA[kMaxLanes * kNT];
   double sx[kMaxLanes][6];
   Ldl32 s_ldl;
@@ -128,249 +126,258 @@ struct IcpShared {
   int s_ncorr, s_fail;
 };
 
-// Level-l pixel chunks of this replica: groups gbase, gbase + gstride, ... of L chunks of 32 pixels.
-// Every warp of the replica computes the real part of one chunk of the group (correspondence, residual,
-// Jacobian, bilinear derivatives) into a shared-memory record; after a named barrier every warp reads
-// all L records and adds the sums of its own lane: lane 0 the real normal equations, lane l > 0 their
-// tangent, for which it loads only lane l's model taps. A second barrier frees the records.
-__device__ __forceinline__ void icp_pixels(const Params& p, const Buffers& b, const Lvl& lv, const IcpShared& S,
-                                           float* __restrict__ recs, int L, int ln, int lid, int rep, int gbase,
-                                           int gstride, int nloop, float* acc, int& cnt) {
-  const float* D = lv.s == 1 ? b.pyr[0] : (lv.s == 2 ? b.pyr[1] : b.pyr[2]);
-  const size_t hw0 = (size_t)p.W * p.H;
-  const float* mdep = b.model;
-  const float* mV = b.model + hw0;
-  const float* mN = b.model + hw0 * (1 + 3 * L);
-  const int npx = lv.W * lv.H;
-  for (int it = 0; it < nloop; ++it) {
-    const int ch = (gbase + it * gstride) * L + ln;
-    {
-      // ---------------- real part (every warp produces one chunk's records) ----------------
-      float* rec = recs + ln * kRec * 32;
-      const int px = (ch << 5) + lid;
-      bool ok = px < npx;
-      const int u = ok ? px % lv.W : 0, v = ok ? px / lv.W : 0;
-      ok = ok && u < lv.W - 1 && v < lv.H - 1;
-      float d0 = 0.f, dxp = 0.f, dyp = 0.f;
-      if (ok) {
-        d0 = D[px];
-        dxp = D[px + 1];
-        dyp = D[px + lv.W];
-      }
-      ok = ok && d0 > 0.f && dxp > 0.f && dyp > 0.f;
-      const float* T = S.sT[0];
-      const float* P = S.sP[0];
-      const float rx = (u - lv.cx) / lv.fx, ry = (v - lv.cy) / lv.fy;
-      const float rx1 = (u + 1 - lv.cx) / lv.fx, ry1 = (v + 1 - lv.cy) / lv.fy;
-      const float V[3] = {d0 * rx, d0 * ry, d0};
-      const float ex[3] = {dxp * rx1 - V[0], dxp * ry - V[1], dxp - V[2]};
-      const float ey[3] = {dyp * rx - V[0], dyp * ry1 - V[1], dyp - V[2]};
-      const float c[3] = {ex[1] * ey[2] - ex[2] * ey[1], ex[2] * ey[0] - ex[0] * ey[2], ex[0] * ey[1] - ex[1] * ey[0]};
-      const float n2m = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
-      ok = ok && n2m > 0.f;
-      const float inm = ok ? 1.f / sqrtf(n2m) : 0.f;
-      const float Nm[3] = {c[0] * inm, c[1] * inm, c[2] * inm};
-      float pp[3];
+// Load the pose lanes into S and form the lanes' affine maps; zero the warps' sums (wacc). A restarted
+// lane (per-frame pose seed) carries no derivative in the model's pose: its P_l is taken as zero.
+__device__ __forceinline__ void icp_prologue(const Params& p, const double* __restrict__ pose,
+                                             const double* __restrict__ pose_prev, IcpShared& S, int L,
+                                             float* __restrict__ wacc) {
+  for (int i = threadIdx.x; i < L * 12; i += blockDim.x) {
+    S.sT[i / 12][i % 12] = (float)pose[i];
+    const bool fresh = (i >= 12) && ((p.fresh >> (i / 12)) & 1u);
+    S.sP[i / 12][i % 12] = fresh ? 0.f : (float)pose_prev[i];
+  }
+  for (int i = threadIdx.x; i < kIcpWarps * L * kNT; i += blockDim.x) wacc[i] = 0.f;
+  __syncthreads();
+  const float* T = S.sT[0];
+  const float* P = S.sP[0];
+  const int t = threadIdx.x;
+  if (t < 3) S.sb0[t] = P[t] * (T[3] - P[3]) + P[4 + t] * (T[7] - P[7]) + P[8 + t] * (T[11] - P[11]);
+  if (t >= 32 && t < 32 + 12 * (L - 1)) {
+    const int l = 1 + (t - 32) / 12, e = (t - 32) % 12;
+    const float* Tl = S.sT[l];
+    const float* Pl = S.sP[l];
+    if (e < 9) {
+      const int r = e / 3, c = e % 3;  // A[r][c] = sum_k Pl[k][r] T[k][c] + P[k][r] Tl[k][c]
+      float a = 0.f;
 #pragma unroll
-      for (int r = 0; r < 3; ++r) pp[r] = T[4 * r] * V[0] + T[4 * r + 1] * V[1] + T[4 * r + 2] * V[2] + T[4 * r + 3];
-      const float e0 = pp[0] - P[3], e1 = pp[1] - P[7], e2 = pp[2] - P[11];
-      const float pcx = P[0] * e0 + P[4] * e1 + P[8] * e2;
-      const float pcy = P[1] * e0 + P[5] * e1 + P[9] * e2;
-      const float pcz = P[2] * e0 + P[6] * e1 + P[10] * e2;
-      ok = ok && pcz > 0.f;
-      const float iz = ok ? 1.f / pcz : 0.f;
-      const float qx = pcx * iz, qy = pcy * iz;
-      const float ux = lv.fx * qx + lv.cx, uy = lv.fy * qy + lv.cy;
-      const float ci = floorf(ux + kCellBias), cj = floorf(uy + kCellBias);
-      ok = ok && ci >= 0.f && ci <= (float)(lv.W - 2) && cj >= 0.f && cj <= (float)(lv.H - 2);
-      const int i0 = ok ? (int)ci : 0, j0 = ok ? (int)cj : 0;
-      const float a = ux - ci, bb = uy - cj;
-      const size_t t00 = (size_t)(j0 * lv.s) * p.W + (size_t)(i0 * lv.s);
-      const size_t t10 = t00 + lv.s, t01 = t00 + (size_t)lv.s * p.W, t11 = t01 + lv.s;
-      float g00 = 0.f, g10 = 0.f, g01 = 0.f, g11 = 0.f;
-      if (ok) {
-        g00 = mdep[t00];
-        g10 = mdep[t10];
-        g01 = mdep[t01];
-        g11 = mdep[t11];
-      }
-      ok = ok && g00 > 0.f && g10 > 0.f && g01 > 0.f && g11 > 0.f;
-      ok = ok && fabsf(g10 - g00) + fabsf(g01 - g00) + fabsf(g11 - g00) < p.disc_gate;
-      const float w00 = (1.f - a) * (1.f - bb), w10 = a * (1.f - bb), w01 = (1.f - a) * bb, w11 = a * bb;
-      float q[3] = {0.f, 0.f, 0.f}, nn[3] = {0.f, 0.f, 0.f};
-      float dqa[3] = {0.f, 0.f, 0.f}, dqb[3] = {0.f, 0.f, 0.f}, dna[3] = {0.f, 0.f, 0.f}, dnb[3] = {0.f, 0.f, 0.f};
-      if (ok) {
+      for (int k = 0; k < 3; ++k) a += Pl[4 * k + r] * T[4 * k + c] + P[4 * k + r] * Tl[4 * k + c];
+      S.sL[l].A[e] = a;
+    } else {
+      const int r = e - 9;
+      float bv = 0.f;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const float* Vp = mV + (size_t)r * hw0;
-          const float* Np = mN + (size_t)r * hw0;
-          const float v00 = Vp[t00], v10 = Vp[t10], v01 = Vp[t01], v11 = Vp[t11];
-          const float m00 = Np[t00], m10 = Np[t10], m01 = Np[t01], m11 = Np[t11];
-          q[r] = w00 * v00 + w10 * v10 + w01 * v01 + w11 * v11;
-          nn[r] = w00 * m00 + w10 * m10 + w01 * m01 + w11 * m11;
-          dqa[r] = (1.f - bb) * (v10 - v00) + bb * (v11 - v01);
-          dqb[r] = (1.f - a) * (v01 - v00) + a * (v11 - v10);
-          dna[r] = (1.f - bb) * (m10 - m00) + bb * (m11 - m01);
-          dnb[r] = (1.f - a) * (m01 - m00) + a * (m11 - m10);
-        }
-      }
-      const float df[3] = {pp[0] - q[0], pp[1] - q[1], pp[2] - q[2]};
-      ok = ok && df[0] * df[0] + df[1] * df[1] + df[2] * df[2] <= p.dist_gate2;
-      float nw[3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) nw[r] = T[4 * r] * Nm[0] + T[4 * r + 1] * Nm[1] + T[4 * r + 2] * Nm[2];
-      const float nl2 = nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2];
-      ok = ok && fabsf(nw[0] * nn[0] + nw[1] * nn[1] + nw[2] * nn[2]) >= p.cos_normal_gate * sqrtf(nl2);
-      const float res = df[0] * nn[0] + df[1] * nn[1] + df[2] * nn[2];
-      const float J[6] = {pp[1] * nn[2] - pp[2] * nn[1], pp[2] * nn[0] - pp[0] * nn[2], pp[0] * nn[1] - pp[1] * nn[0],
-                          nn[0], nn[1], nn[2]};
-      {
-        float* R_ = rec + lid;
-        R_[RV * 32] = __int_as_float(ok ? px + 1 : 0);  // 0: no correspondence; else the pixel + 1
-        if (ok) {
-          R_[RD * 32] = d0;
-          R_[RRX * 32] = rx;
-          R_[RRY * 32] = ry;
-          R_[RE * 32] = e0;
-          R_[(RE + 1) * 32] = e1;
-          R_[(RE + 2) * 32] = e2;
-          R_[RQX * 32] = qx;
-          R_[RQY * 32] = qy;
-          R_[RIZ * 32] = iz;
-          R_[RA * 32] = a;
-          R_[RB * 32] = bb;
-          R_[RT * 32] = __int_as_float((int)t00);
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            R_[(RPP + r) * 32] = pp[r];
-            R_[(RN + r) * 32] = nn[r];
-            R_[(RDF + r) * 32] = df[r];
-            R_[(RDQA + r) * 32] = dqa[r];
-            R_[(RDQB + r) * 32] = dqb[r];
-            R_[(RDNA + r) * 32] = dna[r];
-            R_[(RDNB + r) * 32] = dnb[r];
-          }
-#pragma unroll
-          for (int r = 0; r < 6; ++r) R_[(RJ + r) * 32] = J[r];
-          R_[RRES * 32] = res;
-        }
-      }
+      for (int k = 0; k < 3; ++k)
+        bv += Pl[4 * k + r] * (T[4 * k + 3] - P[4 * k + 3]) + P[4 * k + r] * (Tl[4 * k + 3] - Pl[4 * k + 3]);
+      S.sL[l].b[r] = bv;
     }
-    named_barrier(1 + rep, 32 * L);
-    for (int j = 0; j < L; ++j) {
-      // ---------------- lane `ln` of the records of chunk j (consumer) ----------------
-      const float* R_ = recs + j * kRec * 32 + lid;
-      if (!__float_as_int(R_[RV * 32])) continue;
-      if (ln == 0) {
-        ++cnt;
-        float J[6];
+  }
+  __syncthreads();
+}
+
+// Sum over the warp of 32 values per thread such that thread t ends with the sum of value t: five
+// exchange steps, each sending half of the values still held to the partner lane and keeping the half
+// that belongs to this lane's bit (31 shuffles for the 32 values).
+template <int N>
+__device__ __forceinline__ void transpose_step(float* v, int lid) {
+  const bool hi = (lid & N) != 0;
 #pragma unroll
-        for (int r = 0; r < 6; ++r) J[r] = R_[(RJ + r) * 32];
-        const float res = R_[RRES * 32];
-        const float hJ[6] = {0.5f * J[0], 0.5f * J[1], 0.5f * J[2], 0.5f * J[3], 0.5f * J[4], 0.5f * J[5]};
-        accum(acc, hJ, 0.5f * res, J, res);
-      } else {
-        const float* T = S.sT[0];
-        const float* P = S.sP[0];
-        const float* Tl = S.sT[ln];
-        // a restarted lane (per-frame pose seed) carries no derivative in the previous pose or the model
-        const bool fresh = (p.fresh >> ln) & 1u;
-        const float* Pl = fresh ? S.sZero : S.sP[ln];
-        const float d0 = R_[RD * 32], rx = R_[RRX * 32], ry = R_[RRY * 32];
-        const float V[3] = {d0 * rx, d0 * ry, d0};
-        float dDl = p.dD[ln];
-        if (p.dpix[ln] >= 0)  // single-pixel DEPTH lane: the level's Im depth map at this pixel
-          dDl += b.dlane[dlane_offset(p, ln, lv.level) + (__float_as_int(R_[RV * 32]) - 1)];
-        const float Vl[3] = {dDl * rx, dDl * ry, dDl};
-        const float e0 = R_[RE * 32], e1 = R_[(RE + 1) * 32], e2 = R_[(RE + 2) * 32];
-        const float qx = R_[RQX * 32], qy = R_[RQY * 32], iz = R_[RIZ * 32];
-        const float a = R_[RA * 32], bb = R_[RB * 32];
-        const size_t t00 = (size_t)__float_as_int(R_[RT * 32]);
-        const size_t t10 = t00 + lv.s, t01 = t00 + (size_t)lv.s * p.W, t11 = t01 + lv.s;
-        float pp[3], nn[3], df[3], J[6];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          pp[r] = R_[(RPP + r) * 32];
-          nn[r] = R_[(RN + r) * 32];
-          df[r] = R_[(RDF + r) * 32];
-        }
-#pragma unroll
-        for (int r = 0; r < 6; ++r) J[r] = R_[(RJ + r) * 32];
-        const float res = R_[RRES * 32];
-        float ppl[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-          ppl[r] = Tl[4 * r] * V[0] + Tl[4 * r + 1] * V[1] + Tl[4 * r + 2] * V[2] + Tl[4 * r + 3] +
-                   T[4 * r] * Vl[0] + T[4 * r + 1] * Vl[1] + T[4 * r + 2] * Vl[2];
-        const float el0 = ppl[0] - Pl[3], el1 = ppl[1] - Pl[7], el2 = ppl[2] - Pl[11];
-        const float pcxl = Pl[0] * e0 + Pl[4] * e1 + Pl[8] * e2 + P[0] * el0 + P[4] * el1 + P[8] * el2;
-        const float pcyl = Pl[1] * e0 + Pl[5] * e1 + Pl[9] * e2 + P[1] * el0 + P[5] * el1 + P[9] * el2;
-        const float pczl = Pl[2] * e0 + Pl[6] * e1 + Pl[10] * e2 + P[2] * el0 + P[6] * el1 + P[10] * el2;
-        const float al = lv.fx * (pcxl - qx * pczl) * iz;
-        const float bl = lv.fy * (pcyl - qy * pczl) * iz;
-        const float w00 = (1.f - a) * (1.f - bb), w10 = a * (1.f - bb), w01 = (1.f - a) * bb, w11 = a * bb;
-        const float* mVl = mV + (size_t)(3 * ln) * hw0;
-        const float* mNl = mN + (size_t)(3 * ln) * hw0;
-        float ql[3], nl[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          ql[r] = R_[(RDQA + r) * 32] * al + R_[(RDQB + r) * 32] * bl;
-          nl[r] = R_[(RDNA + r) * 32] * al + R_[(RDNB + r) * 32] * bl;
-        }
-        if (!fresh) {
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            const float* Vpl = mVl + (size_t)r * hw0;
-            const float* Npl = mNl + (size_t)r * hw0;
-            ql[r] += w00 * Vpl[t00] + w10 * Vpl[t10] + w01 * Vpl[t01] + w11 * Vpl[t11];
-            nl[r] += w00 * Npl[t00] + w10 * Npl[t10] + w01 * Npl[t01] + w11 * Npl[t11];
-          }
-        }
-        const float dfl[3] = {ppl[0] - ql[0], ppl[1] - ql[1], ppl[2] - ql[2]};
-        const float resl = dfl[0] * nn[0] + dfl[1] * nn[1] + dfl[2] * nn[2] + df[0] * nl[0] + df[1] * nl[1] + df[2] * nl[2];
-        const float Jl[6] = {ppl[1] * nn[2] - ppl[2] * nn[1] + pp[1] * nl[2] - pp[2] * nl[1],
-                             ppl[2] * nn[0] - ppl[0] * nn[2] + pp[2] * nl[0] - pp[0] * nl[2],
-                             ppl[0] * nn[1] - ppl[1] * nn[0] + pp[0] * nl[1] - pp[1] * nl[0],
-                             nl[0], nl[1], nl[2]};
-        accum(acc, J, res, Jl, resl);
-      }
-    }
-    named_barrier(1 + rep, 32 * L);
+  for (int i = 0; i < N; ++i) {
+    const float send = hi ? v[i] : v[i + N];
+    const float keep = hi ? v[i + N] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, N);
   }
 }
 
-// Block reduction of the threads' sums: warp shuffles, then the replicas of a lane added in shared
-// memory; the block's 27 L sums go to column `col` of the value-major partials ([value][stride], so that
-// the cross-block sum reads each value's row with coalesced loads) and its correspondence count to
-// partial_n[col]. The last column of a launch pads its rows with zeros up to the stride.
-__device__ __forceinline__ void icp_block_sums(IcpShared& S, float* acc, int cnt, int L, int reps, int ln, int rep,
-                                               int warp, int lid, float* __restrict__ partial, int pst, int col,
-                                               int ncol, int* __restrict__ partial_n) {
+__device__ __forceinline__ float warp_transpose_sum(float* v, int lid) {
+  transpose_step<16>(v, lid);
+  transpose_step<8>(v, lid);
+  transpose_step<4>(v, lid);
+  transpose_step<2>(v, lid);
+  transpose_step<1>(v, lid);
+  return v[0];
+}
+
+// The level's chunks c0, c0 + cstride, ... of 32 pixels for this warp (lane `lid` = pixel). For each
+// pixel: the real part (V = D K_l^-1 u, the measured normal for the gate, p' = T V, the projection
+// u_hat = pi(K_l P^-1 p'), the bilinear model vertex q and normal n at u_hat with their slopes in the
+// cell, the gates, r = (p' - q) . n, J = [(p' x n)^T, n^T]); then for every lane its tangent of r and
+// J from the lane's affine map, its depth perturbation and its own model taps. Each lane's 27 terms
+// (J J^T upper triangle, J r; the tangent lanes J J_l^T + J_l J^T and J r_l + J_l r) are summed over
+// the warp at once (warp_transpose_sum) and added to this warp's sums wacc[lane][27] in shared memory;
+// cnt counts the correspondences.
+__device__ __forceinline__ void icp_chunks(const Params& p, const Buffers& b, const Lvl& lv, IcpShared& S, int L,
+                                           int warp, int lid, int c0, int cstride, int nchunk, int& cnt,
+                                           float* __restrict__ wacc) {
+  const float* D = lv.s == 1 ? b.pyr[0] : (lv.s == 2 ? b.pyr[1] : b.pyr[2]);
+  const unsigned hw0 = (unsigned)p.W * (unsigned)p.H;
+  const float* mdep = b.model;
+  const float* mV = b.model + hw0;
+  const float* mN = b.model + (size_t)hw0 * (1 + 3 * L);
+  const int npx = lv.W * lv.H;
+  const float* T = S.sT[0];
+  const float* P = S.sP[0];
+  for (int ch = c0; ch < nchunk; ch += cstride) {
+    const int px = (ch << 5) + lid;
+    bool ok = px < npx;
+    const int u = ok ? px % lv.W : 0, v = ok ? px / lv.W : 0;
+    ok = ok && u < lv.W - 1 && v < lv.H - 1;
+    float d0 = 0.f, dxp = 0.f, dyp = 0.f;
+    if (ok) {
+      d0 = D[px];
+      dxp = D[px + 1];
+      dyp = D[px + lv.W];
+    }
+    ok = ok && d0 > 0.f && dxp > 0.f && dyp > 0.f;
+    const float rx = (u - lv.cx) / lv.fx, ry = (v - lv.cy) / lv.fy;
+    const float rx1 = (u + 1 - lv.cx) / lv.fx, ry1 = (v + 1 - lv.cy) / lv.fy;
+    const float V[3] = {d0 * rx, d0 * ry, d0};
+    const float ex[3] = {dxp * rx1 - V[0], dxp * ry - V[1], dxp - V[2]};
+    const float ey[3] = {dyp * rx - V[0], dyp * ry1 - V[1], dyp - V[2]};
+    const float c[3] = {ex[1] * ey[2] - ex[2] * ey[1], ex[2] * ey[0] - ex[0] * ey[2], ex[0] * ey[1] - ex[1] * ey[0]};
+    const float n2m = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    ok = ok && n2m > 0.f;
+    const float inm = ok ? 1.f / sqrtf(n2m) : 0.f;
+    const float Nm[3] = {c[0] * inm, c[1] * inm, c[2] * inm};
+    float pp[3];
 #pragma unroll
-  for (int q = 0; q < kNT; ++q) {
-    float x = acc[q];
+    for (int r = 0; r < 3; ++r) pp[r] = T[4 * r] * V[0] + T[4 * r + 1] * V[1] + T[4 * r + 2] * V[2] + T[4 * r + 3];
+    const float e0 = pp[0] - P[3], e1 = pp[1] - P[7], e2 = pp[2] - P[11];
+    const float pc[3] = {P[0] * e0 + P[4] * e1 + P[8] * e2, P[1] * e0 + P[5] * e1 + P[9] * e2,
+                         P[2] * e0 + P[6] * e1 + P[10] * e2};
+    ok = ok && pc[2] > 0.f;
+    const float iz = ok ? 1.f / pc[2] : 0.f;
+    const float qx = pc[0] * iz, qy = pc[1] * iz;
+    const float ux = lv.fx * qx + lv.cx, uy = lv.fy * qy + lv.cy;
+    const float ci = floorf(ux + kCellBias), cj = floorf(uy + kCellBias);
+    ok = ok && ci >= 0.f && ci <= (float)(lv.W - 2) && cj >= 0.f && cj <= (float)(lv.H - 2);
+    const int i0 = ok ? (int)ci : 0, j0 = ok ? (int)cj : 0;
+    const float a = ok ? ux - ci : 0.f, bb = ok ? uy - cj : 0.f;
+    // the four taps of the cell in the level-0 model maps (32-bit offsets)
+    const unsigned t00 = (unsigned)(j0 * lv.s) * (unsigned)p.W + (unsigned)(i0 * lv.s);
+    const unsigned t10 = t00 + lv.s, t01 = t00 + (unsigned)lv.s * (unsigned)p.W, t11 = t01 + lv.s;
+    float g00 = 0.f, g10 = 0.f, g01 = 0.f, g11 = 0.f;
+    if (ok) {
+      g00 = mdep[t00];
+      g10 = mdep[t10];
+      g01 = mdep[t01];
+      g11 = mdep[t11];
+    }
+    ok = ok && g00 > 0.f && g10 > 0.f && g01 > 0.f && g11 > 0.f;
+    ok = ok && fabsf(g10 - g00) + fabsf(g01 - g00) + fabsf(g11 - g00) < p.disc_gate;
+    const float w00 = (1.f - a) * (1.f - bb), w10 = a * (1.f - bb), w01 = (1.f - a) * bb, w11 = a * bb;
+    float q[3], nn[3], dqa[3], dqb[3], dna[3], dnb[3];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    acc[q] = x;
+    for (int r = 0; r < 3; ++r) {
+      const float* Vp = mV + r * hw0;
+      const float* Np = mN + r * hw0;
+      const float v00 = Vp[t00], v10 = Vp[t10], v01 = Vp[t01], v11 = Vp[t11];
+      const float m00 = Np[t00], m10 = Np[t10], m01 = Np[t01], m11 = Np[t11];
+      q[r] = w00 * v00 + w10 * v10 + w01 * v01 + w11 * v11;
+      nn[r] = w00 * m00 + w10 * m10 + w01 * m01 + w11 * m11;
+      dqa[r] = (1.f - bb) * (v10 - v00) + bb * (v11 - v01);
+      dqb[r] = (1.f - a) * (v01 - v00) + a * (v11 - v10);
+      dna[r] = (1.f - bb) * (m10 - m00) + bb * (m11 - m01);
+      dnb[r] = (1.f - a) * (m01 - m00) + a * (m11 - m10);
+    }
+    const float df[3] = {pp[0] - q[0], pp[1] - q[1], pp[2] - q[2]};
+    ok = ok && df[0] * df[0] + df[1] * df[1] + df[2] * df[2] <= p.dist_gate2;
+    float nw[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) nw[r] = T[4 * r] * Nm[0] + T[4 * r + 1] * Nm[1] + T[4 * r + 2] * Nm[2];
+    const float nl2 = nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2];
+    ok = ok && fabsf(nw[0] * nn[0] + nw[1] * nn[1] + nw[2] * nn[2]) >= p.cos_normal_gate * sqrtf(nl2);
+    if (!__any_sync(0xffffffffu, ok)) continue;
+    cnt += ok ? 1 : 0;
+    // a pixel without a correspondence adds zeros: its J and r are zero and its lanes stay finite
+    const float m = ok ? 1.f : 0.f;
+    const float res = m * (df[0] * nn[0] + df[1] * nn[1] + df[2] * nn[2]);
+    const float J[6] = {m * (pp[1] * nn[2] - pp[2] * nn[1]), m * (pp[2] * nn[0] - pp[0] * nn[2]),
+                        m * (pp[0] * nn[1] - pp[1] * nn[0]), m * nn[0], m * nn[1], m * nn[2]};
+    float cv[32];
+    {
+      int k = 0;
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int cc = r; cc < 6; ++cc) cv[k++] = J[r] * J[cc];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) cv[21 + r] = J[r] * res;
+#pragma unroll
+      for (int r = 27; r < 32; ++r) cv[r] = 0.f;
+    }
+    {
+      const float sum = warp_transpose_sum(cv, lid);
+      if (lid < kNT) wacc[lid] += sum;
+    }
+    if (L < 2) continue;
+    // what the lanes share: the model pose's P^T T ray for DEPTH lanes, T ray likewise
+    const float id0 = ok ? 1.f / d0 : 0.f;
+    const float Cray[3] = {(pc[0] - S.sb0[0]) * id0, (pc[1] - S.sb0[1]) * id0, (pc[2] - S.sb0[2]) * id0};
+    const float Tray[3] = {(pp[0] - T[3]) * id0, (pp[1] - T[7]) * id0, (pp[2] - T[11]) * id0};
+    for (int l = 1; l < L; ++l) {
+      const float* Tl = S.sT[l];
+      const IcpLane& LA = S.sL[l];
+      float dDl = p.dD[l];
+      if (p.dpix[l] >= 0 && ok) dDl += b.dlane[dlane_offset(p, l, lv.level) + px];
+      float ppl[3], pcl[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        ppl[r] = Tl[4 * r] * V[0] + Tl[4 * r + 1] * V[1] + Tl[4 * r + 2] * V[2] + Tl[4 * r + 3] + dDl * Tray[r];
+        pcl[r] = LA.A[3 * r] * V[0] + LA.A[3 * r + 1] * V[1] + LA.A[3 * r + 2] * V[2] + LA.b[r] + dDl * Cray[r];
+      }
+      const float al = lv.fx * (pcl[0] - qx * pcl[2]) * iz;
+      const float bl = lv.fy * (pcl[1] - qy * pcl[2]) * iz;
+      float ql[3], nl[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        ql[r] = dqa[r] * al + dqb[r] * bl;
+        nl[r] = dna[r] * al + dnb[r] * bl;
+      }
+      if (!((p.fresh >> l) & 1u)) {
+        const float* mVl = mV + (unsigned)(3 * l) * hw0;
+        const float* mNl = mN + (unsigned)(3 * l) * hw0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const float* Vpl = mVl + r * hw0;
+          const float* Npl = mNl + r * hw0;
+          ql[r] += w00 * Vpl[t00] + w10 * Vpl[t10] + w01 * Vpl[t01] + w11 * Vpl[t11];
+          nl[r] += w00 * Npl[t00] + w10 * Npl[t10] + w01 * Npl[t01] + w11 * Npl[t11];
+        }
+      }
+      const float dfl[3] = {ppl[0] - ql[0], ppl[1] - ql[1], ppl[2] - ql[2]};
+      const float resl = m * (dfl[0] * nn[0] + dfl[1] * nn[1] + dfl[2] * nn[2] + df[0] * nl[0] + df[1] * nl[1] +
+                              df[2] * nl[2]);
+      const float Jl[6] = {m * (ppl[1] * nn[2] - ppl[2] * nn[1] + pp[1] * nl[2] - pp[2] * nl[1]),
+                           m * (ppl[2] * nn[0] - ppl[0] * nn[2] + pp[2] * nl[0] - pp[0] * nl[2]),
+                           m * (ppl[0] * nn[1] - ppl[1] * nn[0] + pp[0] * nl[1] - pp[1] * nl[0]),
+                           m * nl[0], m * nl[1], m * nl[2]};
+      int k = 0;
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int cc = r; cc < 6; ++cc, ++k) cv[k] = J[r] * Jl[cc] + Jl[r] * J[cc];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) cv[21 + r] = J[r] * resl + Jl[r] * res;
+#pragma unroll
+      for (int r = 27; r < 32; ++r) cv[r] = 0.f;
+      const float sum = warp_transpose_sum(cv, lid);
+      if (lid < kNT) wacc[l * kNT + lid] += sum;
+    }
   }
+}
+
+// Block sums: the warps' sums (wacc [warp][lane][27]) added in warp order into column `col` of the
+// value-major partials ([value][stride], so that the cross-block sum reads each value's row with
+// coalesced loads), the correspondence count into partial_n[col]. The last column of a launch pads its
+// rows with zeros up to the stride.
+__device__ __forceinline__ void icp_block_sums(IcpShared& S, int cnt, int L, int warp, int lid,
+                                               const float* __restrict__ wacc, float* __restrict__ partial,
+                                               int pst, int col, int ncol, int* __restrict__ partial_n) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if (lid == 0) {
-#pragma unroll
-    for (int q = 0; q < kNT; ++q) S.s_red[(rep * L + ln) * kNT + q] = acc[q];
-    S.s_cnt[warp] = cnt;
-  }
+  if (lid == 0) S.s_cnt[warp] = cnt;
   __syncthreads();
   for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) {
     float s = 0.f;
-    for (int r = 0; r < reps; ++r) s += S.s_red[r * L * kNT + i];
+#pragma unroll
+    for (int w = 0; w < kIcpWarps; ++w) s += wacc[w * L * kNT + i];
     partial[(size_t)i * pst + col] = s;
     if (col == ncol - 1)  // the row padding of this launch's stride reads as zero
       for (int k = ncol; k < pst; ++k) partial[(size_t)i * pst + k] = 0.f;
   }
   if (threadIdx.x == 0) {
     int c = 0;
-    for (int r = 0; r < reps; ++r) c += S.s_cnt[r * L];
+    for (int w = 0; w < kIcpWarps; ++w) c += S.s_cnt[w];
     partial_n[col] = c;
   }
 }
@@ -517,35 +524,42 @@ __device__ __forceinline__ void icp_update(IcpShared& S, int L, double* pose) {
   __syncthreads();
 }
 
-// kStop: the stop tolerance p.icp_stop is in use (and the iteration counter): a launch after its level
-// converged returns at once. Without it the kernel is the fixed-count iteration of the method.
-// One launch per iteration; the last block to finish (ticket counter) sums, solves and updates. The
-// frame chain runs k_icp_run instead; this kernel serves the stage calls (kIcpNoUpdate).
+// the pyramid level's image size and intrinsics
+__device__ __forceinline__ Lvl icp_level(const Params& p, int level) {
+  Lvl lv;
+  lv.s = 1 << level;
+  lv.level = level;
+  lv.W = p.W >> level;
+  lv.H = p.H >> level;
+  lv.fx = p.fx / lv.s;
+  lv.fy = p.fy / lv.s;
+  lv.cx = p.cx / lv.s;
+  lv.cy = p.cy / lv.s;
+  return lv;
+}
+
+// One Gauss-Newton iteration; (bx, gx): this block in its trajectory's grid. The last block to finish
+// (ticket counter) sums, solves and updates. kStop: the stop tolerance p.icp_stop is in use (and the
+// iteration counter): a launch after its level converged returns at once. Without it the kernel is the
+// fixed-count iteration of the method.
 template <bool kStop>
-__global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int flags, int reps) {
-  pdl_enter();
+__device__ __forceinline__ void icp_body(const Params& p, const Buffers& b, const Lvl& lv, int flags, int bx, int gx) {
   const int L = p.L;
   const int warp = threadIdx.x >> 5, lid = threadIdx.x & 31;
-  const int ln = warp % L, rep = warp / L;
   __shared__ IcpShared S;
   __shared__ int s_skip, s_last, s_conv;
-  extern __shared__ float s_rec[];  // [rep][chunk of the group][field][pixel]: reps * L * kRec * 32 floats
+  extern __shared__ __align__(16) float icp_wacc[];  // icp_dyn_bytes(L): the warps' sums
 
   if (threadIdx.x == 0) {
     s_skip = b.status[0];
     // status[3]: the level converged (a step below p.icp_stop); only its first iteration ignores it
     if (kStop) s_conv = (flags & (kIcpFirst | kIcpNoUpdate)) ? 0 : b.status[3];
   }
-  for (int i = threadIdx.x; i < L * 12; i += blockDim.x) {
-    S.sT[i / 12][i % 12] = (float)b.pose[i];
-    S.sP[i / 12][i % 12] = (float)b.pose_prev[i];
-  }
-  if (threadIdx.x < 12) S.sZero[threadIdx.x] = 0.f;
-  __syncthreads();
+  icp_prologue(p, b.pose, b.pose_prev, S, L, icp_wacc);
   if (kStop && (s_skip || s_conv) && !(flags & kIcpNoUpdate)) {
     // nothing to compute after a failure or after the level converged; the frame's last iteration
     // still closes the frame: fall back to T_{k-1} on a failure and count it
-    if ((flags & kIcpLast) && blockIdx.x == 0) {
+    if ((flags & kIcpLast) && bx == 0) {
       if (s_skip && threadIdx.x < 12 * L) b.pose[threadIdx.x] = b.pose_prev[threadIdx.x];
       if (threadIdx.x == 0) {
         if (s_skip) {
@@ -559,24 +573,20 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
     return;
   }
 
-  float acc[kNT];
-#pragma unroll
-  for (int q = 0; q < kNT; ++q) acc[q] = 0.f;
   int cnt = 0;
   const int npx = lv.W * lv.H;
   const int nchunk = (npx + 31) >> 5;
-  const int ngroup = (nchunk + L - 1) / L;
-  const int gbase = blockIdx.x * reps + rep, gstride = gridDim.x * reps;
-  const int nloop = (!s_skip && gbase < ngroup) ? (ngroup - gbase + gstride - 1) / gstride : 0;
-  icp_pixels(p, b, lv, S, s_rec + (size_t)rep * L * kRec * 32, L, ln, lid, rep, gbase, gstride, nloop, acc, cnt);
+  if (!s_skip)
+    icp_chunks(p, b, lv, S, L, warp, lid, bx * kIcpWarps + warp, gx * kIcpWarps, nchunk, cnt,
+               icp_wacc + warp * L * kNT);
 
-  const int pst = icp_pstride(gridDim.x);
-  icp_block_sums(S, acc, cnt, L, reps, ln, rep, warp, lid, b.partial, pst, blockIdx.x, gridDim.x, b.partial_n);
+  const int pst = icp_pstride(gx);
+  icp_block_sums(S, cnt, L, warp, lid, icp_wacc, b.partial, pst, bx, gx, b.partial_n);
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned t = atomicAdd(b.ticket, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == gx - 1);
   }
   __syncthreads();
   if (!s_last) return;
@@ -584,7 +594,7 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   if (threadIdx.x == 0) *b.ticket = 0u;  // ready for the next launch
 
   // ---------------- last block: FP64 cross-block sum, solve, update ----------------
-  icp_cross_sum(S, b.partial, pst, gridDim.x, b.partial_n, L, warp, lid);
+  icp_cross_sum(S, b.partial, pst, gx, b.partial_n, L, warp, lid);
   if (flags & kIcpNoUpdate) {
     for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) b.result[kResSys + i] = S.sA[i];
     if (threadIdx.x == 0) b.status[2] = S.s_ncorr;
@@ -620,192 +630,48 @@ __global__ void __launch_bounds__(512, 1) k_icp(Params p, Buffers b, Lvl lv, int
   }
 }
 
-// ---------------------------------------------------------------------------------------------------
-// All the iterations of a range of pyramid levels in one cooperative launch (every block resident):
-// per iteration each block adds its pixels into its column of the partial sums (two buffers, used
-// alternately), the grid meets at a barrier, and every block then takes the same FP64 cross-block sum,
-// solve and update itself, keeping the pose lanes in its own shared memory, so no second barrier is
-// needed: the next iteration's partials go to the other buffer, which no block can still be reading
-// (a block writes iteration j + 1's partials only after every block arrived at iteration j's
-// barrier, i.e. finished reading iteration j - 1's). Block 0 writes the pose lanes and the status at
-// the end. Every wait is bounded: a barrier that does not fill within its poll budget sets status[5]
-// and the blocks leave the launch.
-// ---------------------------------------------------------------------------------------------------
-constexpr unsigned kBarrierPolls = 1u << 22;  // ~0.3 s at the poll interval below
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* a) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
-  return v;
-}
-
-// returns false if the barrier timed out
-__device__ __forceinline__ bool grid_barrier(unsigned* arrive, unsigned target, int* timeout_flag) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(arrive, 1u);
-    unsigned polls = 0;
-    int ok = 1;
-    while (ld_acquire_gpu(arrive) < target) {
-      if (++polls > kBarrierPolls) {
-        ok = 0;
-        atomicExch(timeout_flag, 1);
-        break;
-      }
-      __nanosleep(64);
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-struct IcpRange {
-  int first, last;   // pyramid levels, coarse (first) to fine (last)
-  int iters[3];      // iterations per level
-  int close;         // the range's last iteration closes the frame (fallback to T_{k-1}, failure count)
-};
-
 template <bool kStop>
-__global__ void __launch_bounds__(512, 1) k_icp_run(Params p, Buffers b, IcpRange rg, int reps) {
-  // no launch_dependents: the next kernel must not take SM resources while this grid is resident
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  const int L = p.L;
-  const int warp = threadIdx.x >> 5, lid = threadIdx.x & 31;
-  const int ln = warp % L, rep = warp / L;
-  __shared__ IcpShared S;
-  __shared__ double sTd[kMaxLanes * 12];  // this block's copy of the pose lanes (FP64)
-  extern __shared__ float s_rec[];
-  float* recs = s_rec + (size_t)rep * L * kRec * 32;
-  const int nblk = gridDim.x;
-  const int pst = icp_pstride(nblk);
-  const size_t pbuf = (size_t)kNT * L * pst;  // floats of one partial buffer
-
-  for (int i = threadIdx.x; i < L * 12; i += blockDim.x) {
-    sTd[i] = b.pose[i];
-    S.sT[i / 12][i % 12] = (float)sTd[i];
-    S.sP[i / 12][i % 12] = (float)b.pose_prev[i];
-  }
-  if (threadIdx.x < 12) S.sZero[threadIdx.x] = 0.f;
-  bool skip = b.status[0] != 0;           // the frame failed in an earlier range
-  bool conv = kStop && b.status[3] != 0;  // the level converged in an earlier range
-  int ncorr_last = b.status[2];
-  unsigned gen = 0;                       // barriers passed
-  bool timed_out = false;
-  __syncthreads();
-
-  for (int l = rg.first; l >= rg.last && !timed_out; --l) {
-    Lvl lv;
-    lv.s = 1 << l;
-    lv.level = l;
-    lv.W = p.W >> l;
-    lv.H = p.H >> l;
-    lv.fx = p.fx / lv.s;
-    lv.fy = p.fy / lv.s;
-    lv.cx = p.cx / lv.s;
-    lv.cy = p.cy / lv.s;
-    const int npx = lv.W * lv.H;
-    const int nchunk = (npx + 31) >> 5;
-    const int ngroup = (nchunk + L - 1) / L;
-    const int gbase = blockIdx.x * reps + rep, gstride = nblk * reps;
-    for (int it = 0; it < rg.iters[l]; ++it) {
-      const bool last = rg.close && l == rg.last && it == rg.iters[l] - 1;
-      if (it == 0) conv = false;
-      if (!(skip || (kStop && conv))) {
-        float acc[kNT];
-#pragma unroll
-        for (int q = 0; q < kNT; ++q) acc[q] = 0.f;
-        int cnt = 0;
-        const int nloop = gbase < ngroup ? (ngroup - gbase + gstride - 1) / gstride : 0;
-        icp_pixels(p, b, lv, S, recs, L, ln, lid, rep, gbase, gstride, nloop, acc, cnt);
-        float* part = b.partial + (gen & 1u) * pbuf;
-        int* part_n = b.partial_n + (gen & 1u) * nblk;
-        icp_block_sums(S, acc, cnt, L, reps, ln, rep, warp, lid, part, pst, blockIdx.x, nblk, part_n);
-        ++gen;
-        if (!grid_barrier(b.grid_bar, gen * (unsigned)nblk, b.status + 5)) {
-          timed_out = true;
-          break;
-        }
-        icp_cross_sum(S, part, pst, nblk, part_n, L, warp, lid);
-        icp_solve(p, S, L, npx, false, true);
-        ncorr_last = S.s_ncorr;
-        if (S.s_fail) {
-          skip = true;
-        } else {
-          icp_update(S, L, sTd);
-          for (int i = threadIdx.x; i < L * 12; i += blockDim.x) S.sT[i / 12][i % 12] = (float)sTd[i];
-        }
-        if (kStop) {
-          double x2 = 0.0;
-#pragma unroll
-          for (int k = 0; k < 6; ++k) x2 += S.sx[0][k] * S.sx[0][k];
-          conv = !S.s_fail && x2 < (double)p.icp_stop * (double)p.icp_stop;
-          if (blockIdx.x == 0 && threadIdx.x == 0 && b.stats) b.stats[kStatIcpIters] += 1;
-        }
-        __syncthreads();
-      }
-      if (last) {
-        // close the frame: a failed frame falls back to T_{k-1} on every lane and is counted
-        if (skip) {
-          for (int i = threadIdx.x; i < L * 12; i += blockDim.x) sTd[i] = b.pose_prev[i];
-          if (blockIdx.x == 0 && threadIdx.x == 0) b.status[1] += 1;
-          ncorr_last = 0;
-        }
-        skip = false;
-        conv = false;
-        __syncthreads();
-      }
-    }
-  }
-  if (blockIdx.x == 0 && !timed_out) {
-    for (int i = threadIdx.x; i < L * 12; i += blockDim.x) b.pose[i] = sTd[i];
-    if (threadIdx.x == 0) {
-      b.status[0] = skip ? 1 : 0;
-      b.status[2] = ncorr_last;
-      b.status[3] = conv ? 1 : 0;
-    }
-  }
-  // leave: the last block out resets the barrier counter for the next launch (every block has
-  // passed its last barrier when it counts itself out)
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(b.grid_bar + 1, 1u) == (unsigned)nblk - 1) {
-      b.grid_bar[0] = 0u;
-      b.grid_bar[1] = 0u;
-    }
-  }
+__global__ void __launch_bounds__(kIcpThreads, 1) k_icp(Params p, Buffers b, Lvl lv, int flags) {
+  pdl_enter();
+  icp_body<kStop>(p, b, lv, flags, blockIdx.x, gridDim.x);
 }
 
-static size_t icp_rec_bytes(int reps, int L) { return sizeof(float) * (size_t)reps * L * kRec * 32; }
+// segments: arg = pyramid level | iteration flags << 4 (fixed-count iterations)
+__global__ void __launch_bounds__(kIcpThreads, 1) k_icp_seg(SegTable st) {
+  pdl_enter();
+  const Seg sg = st.seg[seg_find(st, blockIdx.x)];
+  const TrajDesc& d = st.desc[sg.traj];
+  icp_body<false>(d.p, d.b, icp_level(d.p, sg.arg & 15), sg.arg >> 4, blockIdx.x - sg.block0, sg.nblk);
+}
 
+cudaError_t launch_icp_seg(const SegTable& t, int nblocks, int max_lanes, cudaStream_t s) {
+  return launch_pdl(k_icp_seg, dim3(nblocks), dim3(kIcpThreads), (size_t)icp_dyn_bytes(max_lanes), s, t);
+}
+
+// the kernels' dynamic shared memory above the default 48 KB (once per device of the process)
 cudaError_t icp_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k_icp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_icp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_icp_run<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_icp_run<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  return e;
-}
-
-int icp_reps(int L) {
-  int reps = 16 / L;
-  if (reps > kMaxReps) reps = kMaxReps;
-  return reps < 1 ? 1 : reps;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  const int bytes = icp_dyn_bytes(kMaxLanes);
+  if ((e = cudaFuncSetAttribute(k_icp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_icp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_icp_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+    return e;
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return cudaSuccess;
 }
 
 int icp_blocks(int level_pixels, int L) {
-  const int reps = icp_reps(L);
+  (void)L;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // at least 4 chunks of 32 pixels per warp: small levels get fewer blocks (fewer partials to add)
+  // one chunk of 32 pixels per warp at least: small levels get fewer blocks (fewer partials to add)
   const int nchunk = (level_pixels + 31) / 32;
-  int nblk = (nchunk + 4 * reps - 1) / (4 * reps);
+  int nblk = (nchunk + kIcpWarps - 1) / kIcpWarps;
   if (nblk > sms) nblk = sms;
   if (nblk > kMaxPartials) nblk = kMaxPartials;
   if (nblk < 1) nblk = 1;
@@ -822,51 +688,10 @@ cudaError_t launch_icp(const Params& p, const Buffers& b, int level, int flags, 
   lv.fy = p.fy / lv.s;
   lv.cx = p.cx / lv.s;
   lv.cy = p.cy / lv.s;
-  int reps = icp_reps(p.L);
-  const int threads = 32 * p.L * reps;
+  const size_t dyn = (size_t)icp_dyn_bytes(p.L);
   const cudaError_t e = p.icp_stop > 0.f
-                            ? launch_pdl(k_icp<true>, dim3(nblk), dim3(threads), icp_rec_bytes(reps, p.L), s, p, b, lv,
-                                         flags, reps)
-                            : launch_pdl(k_icp<false>, dim3(nblk), dim3(threads), icp_rec_bytes(reps, p.L), s, p, b, lv,
-                                         flags, reps);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
-}
-
-// blocks of the cooperative ICP launch: as many as are resident at once (one per SM), at most
-// kMaxPartials (the partial buffers' column bound)
-int icp_run_blocks(int L) {
-  const int reps = icp_reps(L);
-  const size_t smem = icp_rec_bytes(reps, L);
-  int dev = 0, sms = 148, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_icp_run<false>, 32 * L * reps, smem) != cudaSuccess)
-    per_sm = 1;
-  int n = sms * (per_sm < 1 ? 1 : per_sm);
-  return n > kMaxPartials ? kMaxPartials : n;
-}
-
-cudaError_t launch_icp_run(const Params& p, const Buffers& b, int first, int last, const int* iters, bool close,
-                           int nblk, cudaStream_t s) {
-  IcpRange rg;
-  rg.first = first;
-  rg.last = last;
-  for (int l = 0; l < 3; ++l) rg.iters[l] = iters[l];
-  rg.close = close ? 1 : 0;
-  const int reps = icp_reps(p.L);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nblk);
-  cfg.blockDim = dim3(32 * p.L * reps);
-  cfg.dynamicSmemBytes = icp_rec_bytes(reps, p.L);
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeCooperative;
-  at[0].val.cooperative = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  const cudaError_t e = p.icp_stop > 0.f ? cudaLaunchKernelEx(&cfg, k_icp_run<true>, p, b, rg, reps)
-                                         : cudaLaunchKernelEx(&cfg, k_icp_run<false>, p, b, rg, reps);
+                            ? launch_pdl(k_icp<true>, dim3(nblk), dim3(kIcpThreads), dyn, s, p, b, lv, flags)
+                            : launch_pdl(k_icp<false>, dim3(nblk), dim3(kIcpThreads), dyn, s, p, b, lv, flags);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

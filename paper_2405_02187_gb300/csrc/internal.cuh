@@ -65,9 +65,8 @@ struct Buffers {
   float* partial;   // ICP per-block partial sums: nblk x L x 27
   int* partial_n;   // ICP per-block correspondence counts
   unsigned* ticket; // last-block-done counter
-  unsigned* grid_bar;  // cooperative ICP: [0] barrier arrivals, [1] blocks out (both 0 between launches)
   int* status;      // [0] ICP failed in this frame, [1] frames failed since last sync, [2] last n_valid,
-                    // [3] level converged, [4] tensor-core wait timed out, [5] ICP grid barrier timed out
+                    // [3] level converged, [4] tensor-core wait timed out
   double* result;   // read-out: 12 (pose) + 12 K (dpose) + 6 K (dtwist) + 27 L (last system)
   unsigned long long* stats;  // kNStat counters (kStat* below); NULL in the allocation-free calls
   int* hit;                   // per pixel: index m of the first sample of the ray-cast hit pair, -1 = none
@@ -183,9 +182,46 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 }
 
 // ---------------------------------------------------------------------------------------------
+// Segmented launches (batches of trajectories, batch.cu): one launch runs a kernel over several
+// trajectories, each with its own parameters, buffers and grid. Segment i owns the blocks
+// [block0, block0 + nblk) of the launch; a block finds its segment by binary search and then works as
+// block (blockIdx.x - block0) of a grid of nblk blocks of its trajectory, so every trajectory sees the
+// same grid, the same work split and the same per-trajectory tickets as in a launch of its own.
+// ---------------------------------------------------------------------------------------------
+struct TrajDesc {
+  Params p;
+  Buffers b;
+  const int* kinds;  // lane seed kinds and indices (device)
+  const int* index;
+};
+struct Seg {
+  int traj;    // index into the TrajDesc table
+  int block0;  // first block of the launch that belongs to this segment
+  int nblk;    // the trajectory's grid (1-D) or its blocks along x times along y (2-D kernels)
+  int arg;     // per-segment argument: the pyramid level (and flags) or the 2-D grid's width in blocks
+};
+struct SegTable {
+  const TrajDesc* desc;
+  const Seg* seg;
+  int nseg;
+};
+__device__ __forceinline__ int seg_find(const SegTable& t, int bx) {
+  int lo = 0, hi = t.nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t.seg[mid].block0 <= bx) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------------------------
 // launches (each defined in its own translation unit)
 // ---------------------------------------------------------------------------------------------
 cudaError_t launch_prepare(const Params& p, const Buffers& b, int levels, cudaStream_t s);
+// segmented measurement stage: 0 range gate (segment grids of ceil(W H / 256) blocks), 1 bilateral
+// filter, 1 + l pyramid level l (2-D grids of 32 x 8 blocks over the output, arg = width in blocks)
+cudaError_t launch_prepare_seg(const SegTable& t, int nblocks, int stage, cudaStream_t s);
 cudaError_t launch_integrate(const Params& p, const Buffers& b, cudaStream_t s);
 // The fusion tile list (Buffers::tiles, tile_ctr) of the frame pose `pose` (device, 12 doubles); the
 // consumer of the list clears the counters.
@@ -200,8 +236,17 @@ cudaError_t launch_tsdf_hess(const Params& p, const Buffers& b, const float* dep
 cudaError_t launch_tsdf_hess64(const Params& p, const Buffers& b, const float* depth, const double* pose,
                                const double* poses, double h, double* out, int nblk, cudaStream_t s);
 int fuse_tile_count(const Params& p);
+int fuse_tiles_grid(const Params& p);  // grids of the single-trajectory fusion launches
+int integrate_grid(const Params& p);
+// segmented fusion launches (every segment's trajectory of L lanes for the update)
+cudaError_t launch_fuse_tiles_seg(const SegTable& t, int nblocks, cudaStream_t s);
+cudaError_t launch_integrate_seg(const SegTable& t, int nblocks, int L, cudaStream_t s);
 cudaError_t launch_raycast(const Params& p, const Buffers& b, const double* pose, float* depth,
                            float* vmap, float* nmap, bool ignore_imag_volume, bool set_prev, cudaStream_t s);
+// the frame chain's ray cast (march and refinement into each handle's model) of every segment; blocks of
+// tile_w x (256 / tile_w) pixels, segment grids of nblk = ceil(W / tile_w) ceil(H / (256 / tile_w))
+// blocks, arg = ceil(W / tile_w)
+cudaError_t launch_raycast_seg(const SegTable& t, int nblocks, int tile_w, cudaStream_t s);
 // the real march alone: hit[pixel] = first sample of the hit pair, -1 = none
 cudaError_t launch_march(const Params& p, const Buffers& b, const double* pose, cudaStream_t s);
 // Newton ICP iteration (icp_newton.cu): real pose, lanes unused
@@ -219,19 +264,21 @@ cudaError_t launch_depth_lanes(const Params& p, const Buffers& b, int levels, cu
 // zero the restarted lanes' TSDF planes over the tiles of the last update (fuse.cu)
 cudaError_t launch_clear_fresh(const Params& p, const Buffers& b, cudaStream_t s);
 cudaError_t launch_readout(const Params& p, const Buffers& b, cudaStream_t s);
+// segmented: mode 0 frame 0's pose lanes, mode 1 the read-out (a block per segment)
+cudaError_t launch_lanes_seg(const SegTable& t, int mode, cudaStream_t s);
+// segmented Gauss-Newton iteration: segment arg = level | flags << 4 (fixed counts, no stop tolerance)
+cudaError_t launch_icp_seg(const SegTable& t, int nblocks, int max_lanes, cudaStream_t s);
 // relocalisation loss, gradient and Hessian (hess.cu); poses: 21 x 12 truncated-bicomplex pose
 // elements (4 floats each), out: [E, g(6), H upper (21), count]
 cudaError_t launch_hess(const Params& p, const Buffers& b, const float* depth, const float* poses, double* out,
                         int nblk, cudaStream_t s);
+// the same loss, gradient and Hessian by the plain FP64 path (full bicomplex products, FP64 march and
+// decisions); poses: 21 x 12 bicomplex pose elements (4 doubles each) with the step h folded in
+cudaError_t launch_hess64(const Params& p, const Buffers& b, const float* depth, const double* poses, double h,
+                          double* out, int nblk, cudaStream_t s);
 cudaError_t launch_loss(const Params& p, const Buffers& b, const float* depth, const float* model,
                         const double* pose, double* out, int nblk, cudaStream_t s);
 int icp_blocks(int level_pixels, int L);
-// all iterations of pyramid levels first .. last (coarse to fine, iters[l] each) in one cooperative
-// launch of nblk resident blocks (icp_run_blocks); close: the last iteration closes the frame
-cudaError_t launch_icp_run(const Params& p, const Buffers& b, int first, int last, const int* iters, bool close,
-                           int nblk, cudaStream_t s);
-int icp_run_blocks(int L);
-int icp_reps(int L);
 cudaError_t icp_configure();
 
 // learned proposal / constant-velocity start (proposal.cu)

@@ -16,18 +16,23 @@
 
 namespace xslam {
 
-__global__ void k_gate(const float* __restrict__ in, float* __restrict__ out, int n, float dmin, float dmax) {
-  pdl_enter();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void gate_body(const float* __restrict__ in, float* __restrict__ out, int n, float dmin,
+                                          float dmax, int bx) {
+  int i = bx * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float d = in[i];
   out[i] = (d >= dmin && d <= dmax) ? d : 0.f;
 }
 
-__global__ void k_bilateral(const float* __restrict__ src, float* __restrict__ dst, int W, int H) {
+__global__ void k_gate(const float* __restrict__ in, float* __restrict__ out, int n, float dmin, float dmax) {
   pdl_enter();
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  gate_body(in, out, n, dmin, dmax, blockIdx.x);
+}
+
+__device__ __forceinline__ void bilateral_body(const float* __restrict__ src, float* __restrict__ dst, int W, int H,
+                                               int bx, int by) {
+  const int u = bx * blockDim.x + threadIdx.x;
+  const int v = by * blockDim.y + threadIdx.y;
   if (u >= W || v >= H) return;
   const float c = src[v * W + u];
   float out = 0.f;
@@ -54,11 +59,15 @@ __global__ void k_bilateral(const float* __restrict__ src, float* __restrict__ d
   dst[v * W + u] = out;
 }
 
-__global__ void k_pyr_down(const float* __restrict__ src, int Ws, int Hs, float* __restrict__ dst, int Wd, int Hd,
-                           float range) {
+__global__ void k_bilateral(const float* __restrict__ src, float* __restrict__ dst, int W, int H) {
   pdl_enter();
-  int u = blockIdx.x * blockDim.x + threadIdx.x;
-  int v = blockIdx.y * blockDim.y + threadIdx.y;
+  bilateral_body(src, dst, W, H, blockIdx.x, blockIdx.y);
+}
+
+__device__ __forceinline__ void pyr_down_body(const float* __restrict__ src, int Ws, int Hs, float* __restrict__ dst,
+                                              int Wd, int Hd, float range, int bx, int by) {
+  int u = bx * blockDim.x + threadIdx.x;
+  int v = by * blockDim.y + threadIdx.y;
   if (u >= Wd || v >= Hd) return;
   const int sx = 2 * u, sy = 2 * v;
   const float c = src[sy * Ws + sx];
@@ -83,6 +92,38 @@ __global__ void k_pyr_down(const float* __restrict__ src, int Ws, int Hs, float*
     out = acc / wsum;  // wsum >= 36/256 (the centre tap)
   }
   dst[v * Wd + u] = out;
+}
+
+__global__ void k_pyr_down(const float* __restrict__ src, int Ws, int Hs, float* __restrict__ dst, int Wd, int Hd,
+                           float range) {
+  pdl_enter();
+  pyr_down_body(src, Ws, Hs, dst, Wd, Hd, range, blockIdx.x, blockIdx.y);
+}
+
+// Segmented measurement stages (batches): stage 0 the range gate (1-D grids of 256-thread blocks, into
+// the filter's source or level 0), stage 1 the bilateral filter, stage 1 + l level l of the pyramid
+// (2-D grids of 32 x 8 blocks; a segment's arg is its grid's width in blocks).
+__global__ void __launch_bounds__(256) k_prepare_seg(SegTable st, int stage) {
+  pdl_enter();
+  const Seg sg = st.seg[seg_find(st, blockIdx.x)];
+  const TrajDesc& d = st.desc[sg.traj];
+  const Params& p = d.p;
+  const Buffers& b = d.b;
+  const int lb = blockIdx.x - sg.block0;
+  if (stage == 0) {
+    gate_body(b.depth_in, p.bilateral ? b.gated : b.pyr[0], p.W * p.H, p.depth_min, p.depth_max, lb);
+  } else if (stage == 1) {
+    bilateral_body(b.gated, b.pyr[0], p.W, p.H, lb % sg.arg, lb / sg.arg);
+  } else {
+    const int l = stage - 1;
+    pyr_down_body(b.pyr[l - 1], p.W >> (l - 1), p.H >> (l - 1), b.pyr[l], p.W >> l, p.H >> l, p.pyr_range,
+                  lb % sg.arg, lb / sg.arg);
+  }
+}
+
+cudaError_t launch_prepare_seg(const SegTable& t, int nblocks, int stage, cudaStream_t s) {
+  const dim3 blk = stage == 0 ? dim3(256) : dim3(32, 8);
+  return launch_pdl(k_prepare_seg, dim3(nblocks), blk, 0, s, t, stage);
 }
 
 // Im depth maps of single-pixel DEPTH lanes, one block per lane (blockIdx.x + 1). The seed pixel s carries

@@ -19,15 +19,15 @@
 
 namespace xslam {
 
-__global__ void __launch_bounds__(256) k_march(Params p, const float* __restrict__ F, const double* __restrict__ pose,
-                                               int* __restrict__ hit) {
-  pdl_enter();
+// (bx, by): this block's coordinates in its trajectory's 2-D grid
+__device__ __forceinline__ void march_body(const Params& p, const float* __restrict__ F, const double* __restrict__ pose,
+                                           int* __restrict__ hit, int bx, int by) {
   __shared__ float sT[12];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   if (tid < 12) sT[tid] = (float)pose[tid];
   __syncthreads();
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  const int u = bx * blockDim.x + threadIdx.x;
+  const int v = by * blockDim.y + threadIdx.y;
   if (u >= p.W || v >= p.H) return;
   const Ray ry = make_ray(p, sT, u, v);
   // alpha interval where 0 <= g < n - 1 on every axis (slab test), widened by one sample
@@ -68,19 +68,34 @@ __global__ void __launch_bounds__(256) k_march(Params p, const float* __restrict
   hit[(size_t)v * p.W + u] = m_hit;
 }
 
-__global__ void __launch_bounds__(256) k_refine(Params p, const float* __restrict__ F, const double* __restrict__ pose,
-                                                const int* __restrict__ hit, float* __restrict__ out_depth,
-                                                float* __restrict__ vmap, float* __restrict__ nmap, int ignore_imag,
-                                                double* __restrict__ pose_prev, unsigned long long* __restrict__ hits) {
+__global__ void __launch_bounds__(256) k_march(Params p, const float* __restrict__ F, const double* __restrict__ pose,
+                                               int* __restrict__ hit) {
   pdl_enter();
+  march_body(p, F, pose, hit, blockIdx.x, blockIdx.y);
+}
+
+// segments: nblk = blocks of the trajectory's grid, arg = its width in blocks
+__global__ void __launch_bounds__(256) k_march_seg(SegTable st) {
+  pdl_enter();
+  const Seg sg = st.seg[seg_find(st, blockIdx.x)];
+  const TrajDesc& d = st.desc[sg.traj];
+  const int lb = blockIdx.x - sg.block0;
+  march_body(d.p, d.b.F0lin, d.b.pose, d.b.hit, lb % sg.arg, lb / sg.arg);
+}
+
+__device__ __forceinline__ void refine_body(const Params& p, const float* __restrict__ F,
+                                            const double* __restrict__ pose, const int* __restrict__ hit,
+                                            float* __restrict__ out_depth, float* __restrict__ vmap,
+                                            float* __restrict__ nmap, int ignore_imag, double* __restrict__ pose_prev,
+                                            unsigned long long* __restrict__ hits, int bx, int by) {
   __shared__ float sT[kMaxLanes][12];
   for (int i = threadIdx.x + blockDim.x * threadIdx.y; i < p.L * 12; i += blockDim.x * blockDim.y) {
     sT[i / 12][i % 12] = (float)pose[i];
-    if (pose_prev && blockIdx.x == 0 && blockIdx.y == 0) pose_prev[i] = pose[i];
+    if (pose_prev && bx == 0 && by == 0) pose_prev[i] = pose[i];
   }
   __syncthreads();
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  const int u = bx * blockDim.x + threadIdx.x;
+  const int v = by * blockDim.y + threadIdx.y;
   if (u >= p.W || v >= p.H) return;
   const size_t hw = (size_t)p.W * p.H;
   const size_t pix = (size_t)v * p.W + u;
@@ -183,6 +198,33 @@ __global__ void __launch_bounds__(256) k_refine(Params p, const float* __restric
       nmap[(size_t)(3 * l + 2) * hw + pix] = (gzl - Nz * dot) / nrm;
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_refine(Params p, const float* __restrict__ F, const double* __restrict__ pose,
+                                                const int* __restrict__ hit, float* __restrict__ out_depth,
+                                                float* __restrict__ vmap, float* __restrict__ nmap, int ignore_imag,
+                                                double* __restrict__ pose_prev, unsigned long long* __restrict__ hits) {
+  pdl_enter();
+  refine_body(p, F, pose, hit, out_depth, vmap, nmap, ignore_imag, pose_prev, hits, blockIdx.x, blockIdx.y);
+}
+
+// the frame chain's refinement of every segment: the model maps of its handle, T_{k-1} := T_k
+__global__ void __launch_bounds__(256) k_refine_seg(SegTable st) {
+  pdl_enter();
+  const Seg sg = st.seg[seg_find(st, blockIdx.x)];
+  const TrajDesc& d = st.desc[sg.traj];
+  const Buffers& b = d.b;
+  const size_t hw = (size_t)d.p.W * d.p.H;
+  const int lb = blockIdx.x - sg.block0;
+  refine_body(d.p, b.F, b.pose, b.hit, b.model, b.model + hw, b.model + hw * (1 + 3 * d.p.L), 0, b.pose_prev,
+              b.stats + 1, lb % sg.arg, lb / sg.arg);
+}
+
+cudaError_t launch_raycast_seg(const SegTable& t, int nblocks, int tile_w, cudaStream_t s) {
+  const dim3 blk(tile_w, 256 / tile_w);
+  cudaError_t e = launch_pdl(k_march_seg, dim3(nblocks), blk, 0, s, t);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_refine_seg, dim3(nblocks), blk, 0, s, t);
 }
 
 cudaError_t launch_march(const Params& p, const Buffers& b, const double* pose, cudaStream_t s) {

@@ -16,6 +16,7 @@
 // shared memory, which the block drains 256 voxels at a time, so that the derivative work runs on full
 // warps whatever the mix of clamped and free voxels in a tile. Order 1 computes the 6 tangents only.
 // Per-thread sums of E, g and H in registers, then block sums, FP64 cross-block sums in the last block.
+#include "bc.cuh"
 #include "internal.cuh"
 
 namespace xslam {
@@ -303,25 +304,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_tsdf_hess(Params p, const float
 // with the step h folded into the start poses (b, c scaled by h, d by h^2): g = Im_1 E / h and
 // H = Im_12 E / h^2. The update's decisions are taken in FP64 too. This is the comparison path of the
 // truncated FP32 kernel above: same loss, same voxels, the paper's arithmetic.
-struct BC {
-  double a, b, c, d;
-};
-__device__ __forceinline__ BC bc(double a) { return {a, 0.0, 0.0, 0.0}; }
-__device__ __forceinline__ BC operator+(BC x, BC y) { return {x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; }
-__device__ __forceinline__ BC operator-(BC x, BC y) { return {x.a - y.a, x.b - y.b, x.c - y.c, x.d - y.d}; }
-__device__ __forceinline__ BC operator+(BC x, double s) { return {x.a + s, x.b, x.c, x.d}; }
-__device__ __forceinline__ BC operator*(double s, BC x) { return {s * x.a, s * x.b, s * x.c, s * x.d}; }
-__device__ __forceinline__ BC operator*(BC x, BC y) {
-  return {x.a * y.a - x.b * y.b - x.c * y.c + x.d * y.d, x.a * y.b + x.b * y.a - x.c * y.d - x.d * y.c,
-          x.a * y.c + x.c * y.a - x.b * y.d - x.d * y.b, x.a * y.d + x.d * y.a + x.b * y.c + x.c * y.b};
-}
-// 1/z: with z = z1 + z2 i2 (z1 = a + b i1, z2 = c + d i1 complex in i1), 1/z = (z1 - z2 i2) / (z1^2 + z2^2)
-__device__ __forceinline__ BC binv(BC z) {
-  const double p = z.a * z.a - z.b * z.b + z.c * z.c - z.d * z.d, q = 2.0 * (z.a * z.b + z.c * z.d);
-  const double n = p * p + q * q, r = p / n, s = -q / n;  // 1/(p + q i1) = r + s i1
-  return {z.a * r - z.b * s, z.a * s + z.b * r, -(z.c * r - z.d * s), -(z.c * s + z.d * r)};
-}
-
 __global__ void __launch_bounds__(kThreads) k_tsdf_hess64(Params p, const float* __restrict__ D,
                                                          const float* __restrict__ F, const float* __restrict__ Wt,
                                                          const double* __restrict__ poses, double inv_h,

@@ -63,6 +63,8 @@ SYMBOLS = [
     ("xslam_raycast", ctypes.c_int, [ctypes.c_void_p, _c_double_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("xslam_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_double_p, ctypes.c_int, _c_double_p,
                                   _c_double_p, _c_double_p]),
+    ("xslam_grad_plain64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_double_p, _c_double_p, _c_double_p,
+                                          _c_double_p]),
     ("xslam_grad_tsdf", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_double_p, ctypes.c_int, _c_double_p,
                                        _c_double_p, _c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
     ("xslam_grad_tsdf_plain64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_double_p, _c_double_p,
@@ -105,6 +107,10 @@ SYMBOLS = [
     ("xslam_batch_latency", ctypes.c_int, [ctypes.c_void_p, _c_float_p]),
     ("xslam_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _c_int_p,
                                             _c_float_p]),
+    ("xslam_batch_set_shapes", ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
+    ("xslam_batch_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("xslam_batch_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_int_p, _c_int_p, _c_int_p,
+                                                _c_float_p, _c_int_p]),
     ("xslam_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     # include/xslam_mlp.h: the learned pose proposal
     ("xslam_mlp_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _c_int_p, ctypes.c_int,
@@ -203,6 +209,15 @@ def _dev(t, dtype_name="float32"):
     if not t.is_contiguous() or str(t.dtype) != f"torch.{dtype_name}":
         raise TypeError(f"expected a contiguous {dtype_name} CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _sym6(packed):
+    """Symmetric 6x6 matrix from its packed upper triangle (row by row)."""
+    H = np.zeros((6, 6))
+    iu = np.triu_indices(6)
+    H[iu] = packed
+    H[(iu[1], iu[0])] = packed
+    return H
 
 
 def _seeds(seeds):
@@ -335,6 +350,16 @@ class XSlam:
             Hm[(iu[1], iu[0])] = H
             return loss.value, g, Hm
         return loss.value, g
+
+    def grad_plain64(self, query_depth, T_q):
+        """(E, g[6], H[6x6]) of the order-2 loss by the plain FP64 bicomplex path (xslam_grad_plain64)."""
+        T_q = np.ascontiguousarray(T_q, np.float64).reshape(12)
+        loss = ctypes.c_double(0)
+        g = np.zeros(6)
+        H = np.zeros(21)
+        self._check(self.lib.xslam_grad_plain64(self.h, self._depth(query_depth), _dptr(T_q), ctypes.byref(loss),
+                                                _dptr(g), _dptr(H)))
+        return loss.value, g, _sym6(H)
 
     def grad_tsdf(self, query_depth, T_q, order=2):
         """TSDF-difference relocalisation loss (E, g[6], H 6x6 or None, observed voxels updated) at T_q."""
@@ -591,10 +616,40 @@ class XSlamBatch:
         for s_ in range(steps):
             flat += [None if d is None else _dev(d).value for d in frames[s_]]
         arr = (ctypes.c_void_p * len(flat))(*flat)
-        d = ctypes.c_int(0)
-        ms = np.zeros(5, np.float32)
-        self._check(self.lib.xslam_batch_autotune(self.b, arr, int(steps), ctypes.byref(d), ms.ctypes.data_as(_c_float_p)))
-        return d.value, ms
+        choice = (ctypes.c_int * 4)()
+        ms = np.zeros(13, np.float32)
+        self._check(self.lib.xslam_batch_autotune(self.b, arr, int(steps), choice, ms.ctypes.data_as(_c_float_p)))
+        ms = ms[:int(np.count_nonzero(ms))]
+        return dict(icp_divisor=choice[0], fuse_blocks_per_sm=choice[1], ray_tile=self.TILES[choice[2]],
+                    mode=self.MODES[choice[3]]), ms
+
+    TILES = ("32x8", "16x16", "64x4")
+    MODES = ("segmented", "branches")
+
+    def set_shapes(self, choice):
+        """Launch shapes as autotune returns them (a dict)."""
+        c = (ctypes.c_int * 4)(int(choice["icp_divisor"]), int(choice["fuse_blocks_per_sm"]),
+                               self.TILES.index(choice["ray_tile"]), self.MODES.index(choice["mode"]))
+        self._check(self.lib.xslam_batch_set_shapes(self.b, c))
+
+    STAGES = ("measure", "seed", "icp", "tiles", "update", "raycast", "readout")
+
+    def profile(self, enable=True):
+        """Launch profile of the segmented step (adds an event after every launch; not for timed runs)."""
+        self._check(self.lib.xslam_batch_profile(self.b, int(bool(enable))))
+
+    def profile_read(self, cap=1024):
+        """The last step's launches: list of (stage, argument, blocks, ms); empty in branch mode."""
+        kind = np.zeros(cap, np.int32)
+        arg = np.zeros(cap, np.int32)
+        blk = np.zeros(cap, np.int32)
+        ms = np.zeros(cap, np.float32)
+        n = ctypes.c_int()
+        self._check(self.lib.xslam_batch_profile_read(self.b, cap, kind.ctypes.data_as(_c_int_p),
+                                                      arg.ctypes.data_as(_c_int_p), blk.ctypes.data_as(_c_int_p),
+                                                      ms.ctypes.data_as(_c_float_p), ctypes.byref(n)))
+        m = min(n.value, cap)
+        return [(self.STAGES[kind[q]], int(arg[q]), int(blk[q]), float(ms[q])) for q in range(m)]
 
 
 # ------------------------------------------------------------------------------------------------

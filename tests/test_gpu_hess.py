@@ -58,3 +58,21 @@ def test_newton_step_from_the_hessian(mapped):
     d1 = np.linalg.norm(T1[:, 3] - wl.poses[4][:, 3])
     E1, _ = x.grad(q, T1, order=1)
     assert E1 < E and d1 < 0.5 * d0
+
+
+@pytest.mark.parametrize("off", [0, 1])
+def test_plain64_hessian_matches_oracle_and_fp32(mapped, off):
+    """xslam_grad_plain64: the paper's bicomplex arithmetic in FP64 (full products, h = 1e-20, its own
+    FP64 march and decisions) against the oracle's bicomplex Hessian on the same volume (1e-5), and the
+    FP32 truncated path against it (2e-3)."""
+    wl, x, F, W = mapped
+    T = se3.compose(se3.se3_exp(OFFSETS[off]), wl.poses[4])
+    q = torch.tensor(wl.depth[4], device="cuda")
+    E64, g64, H64 = x.grad_plain64(q, T)
+    D = measure.range_gate(wl.depth[4].astype(np.float64), wl.depth_min, wl.depth_max)
+    Eo, go, Ho = reloc.hessian_bicomplex(F, W, T, D, wl.intr, wl.dims, wl.origin, wl.voxel, depth_min=wl.depth_min,
+                                         depth_max=wl.depth_max)
+    assert abs(E64 - Eo) <= 1e-5 * Eo
+    assert rel_err(g64, go) < 1e-5 and rel_err(H64, Ho) < 1e-5
+    E, g, H = x.grad(q, T, order=2)
+    assert rel_err(g, g64) < 1e-3 and rel_err(H, H64) < 2e-3

@@ -239,33 +239,3 @@ def test_deterministic_and_graph_equals_direct(orbit, monkeypatch):
     for ra, rb, rc in zip(a, b, c):
         for u, v, w in zip(ra[:3], rb[:3], rc[:3]):
             assert np.array_equal(u, v) and np.array_equal(u, w)
-
-
-@pytest.mark.parametrize("stop", [0.0, 1e-5])
-def test_cooperative_icp_matches_per_iteration_launches(orbit, monkeypatch, stop):
-    """The frame chain's ICP runs one launch per iteration; with XSLAM_ICP_RUN=1 it runs every
-    iteration of a range in one cooperative launch. Both add the same per-pixel terms and differ only
-    in how the FP32 block partials are grouped: poses agree to 1e-6, twist blocks to 1e-4 relative."""
-    seeds = [P.Seed(P.POSE0, 0), P.Seed(P.POSE0, 4), P.Seed(P.TRUNC), P.Seed(P.DEPTH, -1)]
-
-    def run():
-        c = xslam_cfg(orbit)
-        c.icp_stop = stop
-        x = xslam.XSlam(orbit.dims, orbit.voxel, orbit.trunc, orbit.origin, orbit.intr, c, max_lanes=len(seeds))
-        x.set_pose(orbit.poses[0])
-        out = [x.frame(_cuda(orbit.depth[k]), gpu_seeds(seeds)) for k in range(8)]
-        it = x.counters()["icp_iterations"] if stop > 0 else None
-        x.close()
-        return out, it
-
-    monkeypatch.setenv("XSLAM_ICP_RUN", "1")
-    a, ia = run()
-    monkeypatch.setenv("XSLAM_ICP_RUN", "0")
-    b, ib = run()
-    for (pa, _, ta, sa), (pb, _, tb, sb) in zip(a, b):
-        assert sa == sb == xslam.OK
-        assert np.abs(pa - pb).max() < 1e-6
-        for j in range(len(seeds)):
-            assert rel_err(ta[j], tb[j]) < 1e-4
-    if stop > 0:
-        assert ia == ib

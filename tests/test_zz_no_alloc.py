@@ -16,8 +16,7 @@ def _seed_set(n):
     from oracle import pipeline as P
     if n == 3:
         return [P.Seed(P.POSE0, 0), P.Seed(P.POSE0, 3), P.Seed(P.DEPTH, -1)]
-    # 15 lanes: the largest lane count, whose block is one replica of 16 warps (512 threads) and whose
-    # partial sums use the largest stride of the fixed array
+    # 15 lanes: the largest lane count, whose partial sums use the largest stride of the fixed array
     s = [P.Seed(P.POSE0, j) for j in range(6)] + [P.Seed(P.TRUNC), P.Seed(P.DEPTH, -1)]
     s += [P.Seed(P.POSE0, j, h=2e-20) for j in range(6)] + [P.Seed(P.TRUNC, h=3e-20)]
     assert len(s) == 15
