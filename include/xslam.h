@@ -297,6 +297,12 @@ xslam_status xslam_icp_system_noalloc(const float* depth, int level, const xslam
                                       const double* Tj, const double* T_prev, const xslam_seed* seeds, int K_lanes,
                                       const xslam_config* cfg, double* out, int* n_valid, void* cuda_stream);
 
+/* Host utility (no GPU work): out = exp(xi) T for a left twist xi = (phi, rho) (Sec. 4.1, Eq. lie,
+ * Eq. rotvector, Eq. rotation_jacobi), with the library's FP64 SE(3) exponential, the formula of the ICP
+ * pose update. xi[6], T[12] and out[12] are host arrays (3x4 row-major poses); out may alias T.
+ * Returns XSLAM_EINVAL if a pointer is NULL or xi is not finite. */
+xslam_status xslam_se3_exp_compose(const double* xi, const double* T, double* out);
+
 /* Description of the last error on this handle; with h = NULL, of the last failed call made without a
  * handle (xslam_create, xslam_icp_system_noalloc). */
 const char* xslam_last_error(xslam_t h);

@@ -16,6 +16,7 @@
 #include "handle.cuh"
 #include "mlp.cuh"
 #include "internal.cuh"
+#include "se3.cuh"
 
 using namespace xslam;
 
@@ -1133,5 +1134,24 @@ extern "C" xslam_status xslam_counters(xslam_t h, unsigned long long* out, int r
     CU(cudaMemsetAsync(h->b.stats + kStatIcpIters, 0, sizeof(unsigned long long) * 3, h->s));
     CU(cudaStreamSynchronize(h->s));
   }
+  return XSLAM_OK;
+}
+
+extern "C" xslam_status xslam_se3_exp_compose(const double* xi, const double* T, double* out) {
+  if (!xi || !T || !out) return XSLAM_EINVAL;
+  for (int i = 0; i < 6; ++i)
+    if (!std::isfinite(xi[i])) return XSLAM_EINVAL;
+  const double zero[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  SeCoef k;
+  se3_coef_lane(xi, zero, k);
+  double E[12], R[12];
+  for (int e = 0; e < 12; ++e) E[e] = se3_exp_element(xi, zero, k, false, e);
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 4; ++c) {
+      double v = E[4 * r] * T[c] + E[4 * r + 1] * T[4 + c] + E[4 * r + 2] * T[8 + c];
+      if (c == 3) v += E[4 * r + 3];
+      R[4 * r + c] = v;
+    }
+  for (int e = 0; e < 12; ++e) out[e] = R[e];
   return XSLAM_OK;
 }

@@ -1,8 +1,8 @@
 // SE(3) exponential with one tangent direction (X-SLAM Sec. 4.1, Eq. lie, rotvector, rotation_jacobi)
 // for the pose update T <- exp(x) T of ICP, evaluated one matrix element per thread. The ICP step x is
 // small, so the update is formed as exp(x) = I + delta with delta computed in FP32 (its relative
-// precision is what matters) and T <- T + delta T composed in FP64; FP64 variants are kept for
-// reference use.
+// precision is what matters) and T <- T + delta T composed in FP64. The FP64 variants also serve the
+// host (xslam_se3_exp_compose).
 //
 // exp([phi, rho]) = [R | V rho] with R = I + A [phi] + B [phi]^2 and V = I + B [phi] + C [phi]^2,
 // A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3, th^2 = phi.phi; this is the
@@ -19,7 +19,7 @@ struct Coef {
 
 // sum_{n=0}^{N} (-x)^n / (2n+1+s)! and its derivative in x by Horner's rule (s = 0: A, 1: B, 2: C)
 template <int N>
-__device__ __forceinline__ void series(double x, int s, double& v, double& dv) {
+__host__ __device__ __forceinline__ void series(double x, int s, double& v, double& dv) {
   constexpr double inv_fact[22] = {
       1.0, 1.0, 1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0, 1.0 / 5040.0, 1.0 / 40320.0,
       1.0 / 362880.0, 1.0 / 3628800.0, 1.0 / 39916800.0, 1.0 / 479001600.0, 1.0 / 6227020800.0,
@@ -35,7 +35,7 @@ __device__ __forceinline__ void series(double x, int s, double& v, double& dv) {
   }
 }
 
-__device__ __forceinline__ Coef se3_coef(double x) {
+__host__ __device__ __forceinline__ Coef se3_coef(double x) {
   Coef c;
   if (x < 1e-2) {
     // terms up to x^5: truncation below 2e-22 for x < 1e-2 (rotations under 0.1 rad, every ICP step)
@@ -64,7 +64,7 @@ struct SeCoef {
   double A, B, C, dA, dB, dC;  // dA etc.: tangents along x1 (derivative in theta^2 times d theta^2)
 };
 
-__device__ __forceinline__ void se3_coef_lane(const double* x0, const double* x1, SeCoef& out) {
+__host__ __device__ __forceinline__ void se3_coef_lane(const double* x0, const double* x1, SeCoef& out) {
   const double th2 = x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2];
   const double dth2 = 2.0 * (x0[0] * x1[0] + x0[1] * x1[1] + x0[2] * x1[2]);
   const Coef c = se3_coef(th2);
@@ -77,7 +77,7 @@ __device__ __forceinline__ void se3_coef_lane(const double* x0, const double* x1
 }
 
 // [v]_{rk}
-__device__ __forceinline__ double hat_el(const double* v, int r, int k) {
+__host__ __device__ __forceinline__ double hat_el(const double* v, int r, int k) {
   if (r == k) return 0.0;
   if (r == 0) return k == 1 ? -v[2] : v[1];
   if (r == 1) return k == 0 ? v[2] : -v[0];
@@ -85,15 +85,15 @@ __device__ __forceinline__ double hat_el(const double* v, int r, int k) {
 }
 
 // ([phi]^2)_{rk} = phi_r phi_k - th2 delta_rk and its tangent along phi1
-__device__ __forceinline__ double hat2_el(const double* v, int r, int k) {
+__host__ __device__ __forceinline__ double hat2_el(const double* v, int r, int k) {
   return v[r] * v[k] - (r == k ? v[0] * v[0] + v[1] * v[1] + v[2] * v[2] : 0.0);
 }
-__device__ __forceinline__ double hat2_tan(const double* v, const double* v1, int r, int k) {
+__host__ __device__ __forceinline__ double hat2_tan(const double* v, const double* v1, int r, int k) {
   return v1[r] * v[k] + v[r] * v1[k] - (r == k ? 2.0 * (v[0] * v1[0] + v[1] * v1[1] + v[2] * v1[2]) : 0.0);
 }
 
 // Element e = 4 r + c of E = exp(x0) (tangent = false) or of its tangent along x1 (tangent = true).
-__device__ __forceinline__ double se3_exp_element(const double* x0, const double* x1, const SeCoef& k, bool tangent,
+__host__ __device__ __forceinline__ double se3_exp_element(const double* x0, const double* x1, const SeCoef& k, bool tangent,
                                                   int e) {
   const int r = e >> 2, c = e & 3;
   if (c < 3) {

@@ -6,7 +6,8 @@ optimisers of Sec. 6's ICP comparison, "High order ICP") or by Newton's method w
 Two losses: the point-to-plane reading (xslam_grad) and the paper's TSDF difference, the sum of squared
 changes the query's surface update would make to the map (xslam_grad_tsdf). Every loss, gradient and
 Hessian comes from those calls (orders 1 and 2, computed on the GPU); this module holds only the
-host-side iteration: 6x6 solves, the SE(3) exponential of the step, and the step-size control.
+host-side iteration: 6x6 solves and the step-size control; the SE(3) exponential of a step is the
+library's (xslam_se3_exp_compose).
 """
 from __future__ import annotations
 
@@ -16,25 +17,16 @@ import math
 import numpy as np
 
 
-def _hat(w):
-    return np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
-
-
 def se3_exp(xi):
-    """exp of a left twist (phi then rho) as a 3x4 pose (Rodrigues and the left Jacobian)."""
-    xi = np.asarray(xi, np.float64)
-    phi, rho = xi[:3], xi[3:]
-    th = math.sqrt(float(phi @ phi))
-    W = _hat(phi)
-    if th < 1e-8:
-        R = np.eye(3) + W + 0.5 * W @ W
-        V = np.eye(3) + 0.5 * W + W @ W / 6.0
-    else:
-        a, b = math.sin(th) / th, (1.0 - math.cos(th)) / (th * th)
-        c = (th - math.sin(th)) / (th ** 3)
-        R = np.eye(3) + a * W + b * W @ W
-        V = np.eye(3) + b * W + c * W @ W
-    return np.concatenate([R, (V @ rho)[:, None]], 1)
+    """exp of a left twist (phi then rho) as a 3x4 pose, by the library's FP64 SE(3) exponential."""
+    from . import xslam
+    return xslam.se3_exp_compose(xi)
+
+
+def se3_step(xi, T):
+    """exp(xi) T, by the library."""
+    from . import xslam
+    return xslam.se3_exp_compose(xi, T)
 
 
 def compose(A, B):
@@ -85,13 +77,13 @@ def _nlcg(ev, depth, T, iters, tol, step0, trace):
             d, gd = -g, -float(g @ g)
         best = None
         for _ in range(16):
-            Ta = compose(se3_exp(a * d), T)
+            Ta = se3_step(a * d, T)
             Ea, ga = ev(depth, Ta, order=1)
             evals += 1
             curv = (Ea - E - gd * a) / (a * a)
             if curv > 0.0:
                 a2 = -gd / (2.0 * curv)
-                T2 = compose(se3_exp(a2 * d), T)
+                T2 = se3_step(a2 * d, T)
                 E2, g2 = ev(depth, T2, order=1)
                 evals += 1
                 if E2 <= E + 1e-4 * a2 * gd and E2 <= Ea:
@@ -151,7 +143,7 @@ def relocalise(handle, depth, T_init, method="newton", eta=1e-3, iters=30, tol=1
         if direction is not None:
             s = 1.0
             for _ in range(6):
-                T1 = compose(se3_exp(s * direction), T)
+                T1 = se3_step(s * direction, T)
                 E1, g1, H1 = ev(depth, T1, order=2)
                 evals += 1
                 if E1 <= E:
@@ -164,7 +156,7 @@ def relocalise(handle, depth, T_init, method="newton", eta=1e-3, iters=30, tol=1
         if not accepted:
             for _ in range(12):
                 step = -alpha * g
-                T1 = compose(se3_exp(step), T)
+                T1 = se3_step(step, T)
                 if method == "newton":
                     E1, g1, H1 = ev(depth, T1, order=2)
                 else:

@@ -87,6 +87,7 @@ SYMBOLS = [
                                                 ctypes.c_int, ctypes.POINTER(Config), _c_double_p, _c_int_p,
                                                 ctypes.c_void_p]),
     ("xslam_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("xslam_se3_exp_compose", ctypes.c_int, [_c_double_p, _c_double_p, _c_double_p]),
     # include/xslam_plain.h: the plain FP64 complex path
     ("xslam_plain_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_float, ctypes.c_float, _c_float_p, ctypes.POINTER(Intrinsics),
@@ -153,6 +154,19 @@ def load(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def se3_exp_compose(xi, T=None):
+    """exp(xi) T (3x4; T = identity when None) through the library's FP64 SE(3) exponential."""
+    lib = load()
+    x = np.ascontiguousarray(xi, np.float64).reshape(6)
+    Tm = np.eye(3, 4) if T is None else np.asarray(T, np.float64)
+    Tin = np.ascontiguousarray(Tm[:3, :4], np.float64).reshape(-1).copy()
+    out = np.zeros(12)
+    st = lib.xslam_se3_exp_compose(_dptr(x), _dptr(Tin), _dptr(out))
+    if st != OK:
+        raise XSlamError(st, "xslam_se3_exp_compose: NULL or non-finite argument")
+    return out.reshape(3, 4)
 
 
 def icp_system_noalloc(depth, level, intr, model, Tj, T_prev, seeds=(), cfg: Config | None = None, stream=None):

@@ -1,24 +1,36 @@
-"""Host side of relocalisation (paper_2405_02187_gb300/reloc.py) without a GPU: the SE(3) exponential
-against the matrix exponential, and the optimiser's control flow on a fake handle whose loss is a known
-quadratic in the left twist."""
+"""Host side of relocalisation (paper_2405_02187_gb300/reloc.py) without a GPU: the library's SE(3)
+exponential (xslam_se3_exp_compose, host code) against the matrix exponential, and the optimiser's control
+flow on a fake handle whose loss is a known quadratic in the left twist."""
 import numpy as np
+import pytest
 import scipy.linalg
 
-from paper_2405_02187_gb300 import reloc
+from paper_2405_02187_gb300 import reloc, xslam
 
 
 def _twist_matrix(xi):
     M = np.zeros((4, 4))
-    M[:3, :3] = reloc._hat(xi[:3])
+    w = xi[:3]
+    M[:3, :3] = [[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]]
     M[:3, 3] = xi[3:]
     return M
 
 
 def test_se3_exp_is_the_matrix_exponential():
     rng = np.random.default_rng(0)
-    for scale in (1e-9, 1e-3, 0.3, 2.0):
+    # both branches of the coefficient series (theta^2 < 1e-2, < 1/4) and the closed form
+    for scale in (1e-9, 1e-3, 0.04, 0.2, 0.3, 2.0):
         xi = rng.standard_normal(6) * scale
         assert np.allclose(reloc.se3_exp(xi), scipy.linalg.expm(_twist_matrix(xi))[:3], atol=1e-12, rtol=1e-10)
+
+
+def test_se3_exp_compose_composes_and_checks_arguments():
+    rng = np.random.default_rng(1)
+    xi, T = rng.standard_normal(6) * 0.5, reloc.se3_exp(rng.standard_normal(6))
+    want = scipy.linalg.expm(_twist_matrix(xi)) @ np.vstack([T, [0, 0, 0, 1]])
+    assert np.allclose(xslam.se3_exp_compose(xi, T), want[:3], atol=1e-12)
+    with pytest.raises(xslam.XSlamError):
+        xslam.se3_exp_compose(np.array([np.nan, 0, 0, 0, 0, 0]), T)
 
 
 class _Quadratic:
