@@ -655,12 +655,15 @@ def _second_summary(s2):
 def _learned_summary(lp):
     if not lp:
         return None
-    out = dict(train_ms=lp["train"]["train_ms"], pairs=lp["train"]["pairs"], start_error_sigma=lp["start_error_sigma"])
-    for k in ("constant_velocity", "constant_velocity_proposal", "previous_pose", "previous_pose_proposal"):
-        if k in lp:
-            r = lp[k]
-            out[k] = dict(fps=r["fps"], failures=r["failures"], trans_err_cm_mean=r["trans_err_cm_mean"],
-                          fallback_rate=r.get("fallback_rate"))
+    out = dict(train_ms=lp["train"]["train_ms"], pairs=lp["train"]["pairs"])
+    for wname, w in lp.get("walks", {}).items():
+        o = dict(start_error_sigma=w["start_error_sigma"])
+        for k in ("constant_velocity", "constant_velocity_proposal", "previous_pose", "previous_pose_proposal"):
+            if k in w:
+                r = w[k]
+                o[k] = dict(fps=r["fps"], failures=r["failures"], trans_err_cm_mean=r["trans_err_cm_mean"],
+                            fallback_rate=r.get("fallback_rate"))
+        out[wname] = o
     return out
 
 
@@ -764,7 +767,7 @@ def run_batch(args, dev, rank):
                       frac=round(moved / (ms * 1e-3) / 1e9 / peak, 4), algorithmic_gb=round(moved / 1e9, 2),
                       note="algorithmic bytes of every ICP, fusion and ray-cast launch of the run / its time"),
         autotune=dict(choice=choice, ms_per_step=[round(float(m), 3) for m in tune_ms],
-                      candidates="mode segmented, branches; ICP grid / 1, 2, 4, 8; then in segmented mode fusion "
+                      candidates="mode segmented, branches; ICP grid / 1, 2, 4, 8, 16, 32; then in segmented mode fusion "
                                  "blocks per SM default, 1, 2, 4 and ray tile 32x8, 16x16, 64x4 (one coordinate at a "
                                  "time, each with the best of the ones before)"),
         segmented_step_ms_by_stage={k: round(v, 3) for k, v in stage_ms.items()},
@@ -963,32 +966,37 @@ def run_learned(args, dev, rank):
                  tensor_frac_whole_steps=round(tfl / peak, 4), peak_tflops=peak,
                  peak_note=f"whole training steps (GEMMs, reductions, loss, Adam, gather) against the {peak_kind} "
                            "bf16 burst peak")
-    wl = synth.room_smooth(seed=31000 + rank, frames=args.learned_frames, dims=512, voxel=0.005, step_m=0.04,
-                           step_deg=3.0, jerk_every=10, device=dev)
-    starts = learn.start_errors(m, ds.scale, wl)
     seeds = [(0, j, 1e-10) for j in range(6)]
-    arms = {}
-    for name, seed_mode, use in (("constant_velocity", 1, False), ("constant_velocity_proposal", 1, True),
-                                 ("previous_pose", 0, False), ("previous_pose_proposal", 0, True)):
-        r = learn.track(wl, learn.handle_config(wl, seed_mode, 1e-5), seeds, mlp=m if use else None,
-                        scale=ds.scale, judge_level=2)
-        dt, dr = learn.pose_errors(r["poses"], wl.poses)
-        c = r["counters"]
-        row = dict(fps=round(r["fps"], 1), icp_iterations_per_frame=round(c["icp_iterations"] / (len(dt) - 1), 2),
-                   failures=r["failures"], trans_err_cm_mean=round(float(dt.mean()) * 100, 3),
-                   trans_err_cm_max=round(float(dt.max()) * 100, 3), rot_err_deg_mean=round(float(dr.mean()), 4),
-                   rot_err_deg_max=round(float(dr.max()), 4))
-        if use:
-            row.update(judged=c["judged"], accepted=c["accepted"],
-                       fallback_rate=round(1.0 - c["accepted"] / max(c["judged"], 1), 4))
-        arms[name] = row
+    walks = {}
+    # the fast walk (steps up to 4 cm and 3 deg, a fresh motion every 10 frames) and a gentle one (2 cm,
+    # 1.5 deg, every 25 frames)
+    for wname, step_m, step_deg, jerk in (("fast", 0.04, 3.0, 10), ("gentle", 0.02, 1.5, 25)):
+        wl = synth.room_smooth(seed=31000 + rank, frames=args.learned_frames, dims=512, voxel=0.005, step_m=step_m,
+                               step_deg=step_deg, jerk_every=jerk, device=dev)
+        starts = learn.start_errors(m, ds.scale, wl)
+        arms = {}
+        for name, seed_mode, use in (("constant_velocity", 1, False), ("constant_velocity_proposal", 1, True),
+                                     ("previous_pose", 0, False), ("previous_pose_proposal", 0, True)):
+            r = learn.track(wl, learn.handle_config(wl, seed_mode, 1e-5), seeds, mlp=m if use else None,
+                            scale=ds.scale, judge_level=2)
+            dt, dr = learn.pose_errors(r["poses"], wl.poses)
+            c = r["counters"]
+            row = dict(fps=round(r["fps"], 1), icp_iterations_per_frame=round(c["icp_iterations"] / (len(dt) - 1), 2),
+                       failures=r["failures"], trans_err_cm_mean=round(float(dt.mean()) * 100, 3),
+                       trans_err_cm_max=round(float(dt.max()) * 100, 3), rot_err_deg_mean=round(float(dr.mean()), 4),
+                       rot_err_deg_max=round(float(dr.max()), 4))
+            if use:
+                row.update(judged=c["judged"], accepted=c["accepted"],
+                           fallback_rate=round(1.0 - c["accepted"] / max(c["judged"], 1), 4))
+            arms[name] = row
+        walks[wname] = dict(walk=dict(step_m=step_m, step_deg=step_deg, fresh_motion_every=jerk),
+                            start_error_sigma=dict((k, round(float(v.mean()), 3)) for k, v in starts.items()), **arms)
+        del wl
     m.close()
-    return dict(workload=f"{args.learned_frames} frames of a 640x480 camera with inertia in the room (steps up to "
-                         "4 cm and 3 deg, rho = 0.9, a fresh motion every 10 frames), 512^3 x 0.5 cm, K = 6 "
-                         "(d pose / d pose0), ICP stop tolerance 1e-5, judge at the coarsest level",
-                train=train, network=f"{'-'.join(str(v) for v in learn.SIZES)} BF16, tcgen05 GEMMs",
-                start_error_sigma=dict((k, round(float(v.mean()), 3)) for k, v in starts.items()),
-                **arms)
+    return dict(workload=f"{args.learned_frames} frames of a 640x480 camera with inertia in the room (rho = 0.9; a "
+                         "fast and a gentle walk), 512^3 x 0.5 cm, K = 6 (d pose / d pose0), ICP stop tolerance "
+                         "1e-5, judge at the coarsest level",
+                train=train, network=f"{'-'.join(str(v) for v in learn.SIZES)} BF16, tcgen05 GEMMs", walks=walks)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -1041,7 +1049,7 @@ def main():
     ap.add_argument("--reloc-iters", type=int, default=30)
     ap.add_argument("--reloc-eta", type=float, default=1e-3)
     ap.add_argument("--no-learned", action="store_true", help="skip training and evaluating the learned proposal")
-    ap.add_argument("--learned-rooms", type=int, default=100, help="room walks of 16 frames for the training pairs")
+    ap.add_argument("--learned-rooms", type=int, default=110, help="room walks of 16 frames for the training pairs")
     ap.add_argument("--learned-epochs", type=int, default=30)
     ap.add_argument("--learned-frames", type=int, default=1000)
     ap.add_argument("--batch-n", type=int, default=32)

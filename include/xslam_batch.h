@@ -64,7 +64,7 @@ xslam_status xslam_batch_latency(xslam_batch_t b, float* ms);
 /* Autotuner of the step's launch shapes. A coordinate search, each coordinate tried with the best
  * choices of the coordinates before it: the mode (segmented launches or every trajectory's own chain as
  * a graph branch; only when every handle runs the plain frame chain, see xslam_batch_create); the ICP
- * grid of every trajectory and level divided by 1, 2, 4 or 8 (at least one block); then, in segmented
+ * grid of every trajectory and level divided by 1, 2, 4, 8, 16 or 32 (at least one block); then, in segmented
  * mode, the fusion grid (the default, or 1, 2 or 4 blocks per SM for every trajectory) and the ray-cast
  * tile (32 x 8, 16 x 16 or 64 x 4 pixels). The fusion tile is the 8 x 8 x 8 brick of the TSDF layout and
  * is not tuned. Each candidate runs `steps` >= 3 batch steps from frame 0 on the given frames
@@ -72,7 +72,7 @@ xslam_status xslam_batch_latency(xslam_batch_t b, float* ms);
  * 2.. with CUDA events (steps 0 and 1 build the graphs). Then the best choices are kept, every handle is
  * restored to frame 0 (empty volume, the lanes and pose recorded at xslam_batch_create), choice[4]
  * receives the ICP divisor, the fusion blocks per SM (0 = default), the tile (0 = 32 x 8, 1 = 16 x 16,
- * 2 = 64 x 4) and the mode (0 = segmented, 1 = branches), and ms_per_step[13] (NULL allowed) the
+ * 2 = 64 x 4) and the mode (0 = segmented, 1 = branches), and ms_per_step[15] (NULL allowed) the
  * candidates' milliseconds per step in the order tried, zeros after the last.
  * Errors: XSLAM_EINVAL (steps < 3, NULL frames or choice), as step. */
 xslam_status xslam_batch_autotune(xslam_batch_t b, const float* const* frames, int steps, int* choice,

@@ -4,7 +4,10 @@ previous pose, Sec. 4.1).
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Start poses of frame k, with T_1 = T_{k-1} and T_2 = T_{k-2} (T_2 = T_1 at k = 1):
-  constant velocity  T_1 T_2^-1 T_1 (the last camera motion repeated, in the camera frame);
+  constant velocity  T_1 T_2^-1 T_1 (the last camera motion repeated, in the camera frame), its rotation
+                     block R then taken through one Newton step of the polar decomposition,
+                     1.5 R - 0.5 R R^T R (the nearest rotation to second order): the extrapolation
+                     otherwise multiplies a pose's deviation from SO(3) by about 2.4 per frame;
   proposal           T_1 exp(xi), xi = scale * y the network's output (oracle/mlp.py).
 Both carry the CSFD lanes of T_1 and T_2 (xi is real: the depth frames carry no perturbation in the
 runs that use the proposal).
@@ -24,9 +27,18 @@ import numpy as np
 from . import se3
 
 
+def polar_step(T):
+    """T with its rotation block R replaced by 1.5 R - 0.5 R R^T R (plain transpose: on complex lanes
+    the step's derivative, which keeps a tangent of SO(3) at R as it is)."""
+    T = np.array(T)
+    R = T[:, :3]
+    T[:, :3] = 1.5 * R - 0.5 * R @ R.T @ R
+    return T
+
+
 def cv_seed(T1, T2):
-    """T_1 T_2^-1 T_1."""
-    return se3.compose(T1, se3.compose(se3.inverse(T2), T1))
+    """T_1 T_2^-1 T_1, its rotation taken to SO(3) by polar_step."""
+    return polar_step(se3.compose(T1, se3.compose(se3.inverse(T2), T1)))
 
 
 def proposal_seed(T1, xi):

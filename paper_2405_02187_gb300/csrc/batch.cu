@@ -37,7 +37,7 @@ __global__ void k_gather_frames(const float* const* __restrict__ src, float* con
 std::string g_batch_err;
 constexpr int kRing = 8;        // pinned source tables in flight
 constexpr int kMaxBatch = 256;  // trajectories per batch
-constexpr int kDivisors[5] = {1, 2, 4, 8, 16};
+constexpr int kTuneMax = 15;    // autotuner candidates at most: 2 modes, 6 ICP divisors, 4 fusion grids, 3 tiles
 
 }  // namespace
 
@@ -579,7 +579,8 @@ extern "C" xslam_status xslam_batch_autotune(xslam_batch_t b, const float* const
   // divisor, then (segmented mode only) the fusion grid and the ray-cast tile
   int best[4] = {1, 0, 0, b->seg_ok ? 0 : 1};  // divisor, fusion blocks per SM, tile, mode
   const int order[4] = {3, 0, 1, 2};
-  const int cands[4][4] = {{1, 2, 4, 8}, {0, 1, 2, 4}, {0, 1, 2, -1}, {0, 1, -1, -1}};
+  constexpr int kCands = 6;
+  const int cands[4][kCands] = {{1, 2, 4, 8, 16, 32}, {0, 1, 2, 4, -1, -1}, {0, 1, 2, -1, -1, -1}, {0, 1, -1, -1, -1, -1}};
   xslam_status st = XSLAM_OK;
   int k = 0;
   for (int o = 0; o < 4 && st == XSLAM_OK; ++o) {
@@ -587,7 +588,7 @@ extern "C" xslam_status xslam_batch_autotune(xslam_batch_t b, const float* const
     if (coord == 3 && !b->seg_ok) continue;        // branches only
     if ((coord == 1 || coord == 2) && best[3] != 0) continue;  // shapes of the segmented launches
     float best_ms = 0.f;
-    for (int c = 0; c < 4 && st == XSLAM_OK; ++c) {
+    for (int c = 0; c < kCands && st == XSLAM_OK; ++c) {
       const int v = cands[coord][c];
       if (v < 0) continue;
       int shape[4] = {best[0], best[1], best[2], best[3]};
@@ -611,7 +612,7 @@ extern "C" xslam_status xslam_batch_autotune(xslam_batch_t b, const float* const
   if ((st = restore_all(b)) != XSLAM_OK) return st;
   for (int q = 0; q < 4; ++q) choice[q] = best[q];
   if (ms_per_step)
-    for (int q = k; q < 13; ++q) ms_per_step[q] = 0.f;
+    for (int q = k; q < kTuneMax; ++q) ms_per_step[q] = 0.f;
   return XSLAM_OK;
 }
 

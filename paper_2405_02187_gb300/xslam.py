@@ -631,7 +631,7 @@ class XSlamBatch:
             flat += [None if d is None else _dev(d).value for d in frames[s_]]
         arr = (ctypes.c_void_p * len(flat))(*flat)
         choice = (ctypes.c_int * 4)()
-        ms = np.zeros(13, np.float32)
+        ms = np.zeros(15, np.float32)
         self._check(self.lib.xslam_batch_autotune(self.b, arr, int(steps), choice, ms.ctypes.data_as(_c_float_p)))
         ms = ms[:int(np.count_nonzero(ms))]
         return dict(icp_divisor=choice[0], fuse_blocks_per_sm=choice[1], ray_tile=self.TILES[choice[2]],

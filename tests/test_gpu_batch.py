@@ -92,10 +92,10 @@ def test_batch_autotune_restores_frame0():
     batch = xslam.XSlamBatch(bh)
     frames = [[d[k] for d in dev] for k in range(4)]
     choice, ms = batch.autotune(frames, 4)
-    assert choice["icp_divisor"] in (1, 2, 4, 8) and choice["fuse_blocks_per_sm"] in (0, 1, 2, 4)
+    assert choice["icp_divisor"] in (1, 2, 4, 8, 16, 32) and choice["fuse_blocks_per_sm"] in (0, 1, 2, 4)
     assert choice["ray_tile"] in ("32x8", "16x16", "64x4") and choice["mode"] in ("segmented", "branches")
-    # mode (2), divisor (4), then fusion (4) and tile (3) in segmented mode
-    assert len(ms) == (13 if choice["mode"] == "segmented" else 6) and np.all(ms > 0)
+    # mode (2), divisor (6), then fusion (4) and tile (3) in segmented mode
+    assert len(ms) == (15 if choice["mode"] == "segmented" else 8) and np.all(ms > 0)
     # from frame 0 again, on the chosen grids: parity with the oracle
     for k in range(4):
         batch.step([d[k] for d in dev])

@@ -50,6 +50,55 @@ def test_judge_level_reads_level0_model_at_stride():
     assert proposal.judge(D1, lin1, 1, I, I, model, 0.1) == pytest.approx(1e-4, rel=1e-9)
 
 
+def test_polar_step_takes_a_pose_to_so3_to_second_order():
+    import scipy.linalg
+    rng = np.random.default_rng(4)
+    T = se3.se3_exp(rng.normal(0, 0.7, 6))
+    E = rng.normal(0, 1e-6, (3, 3))
+    E = 0.5 * (E + E.T)  # a symmetric deviation from SO(3)
+    Tb = T.copy()
+    Tb[:, :3] = T[:, :3] @ (np.eye(3) + E)
+    P = proposal.polar_step(Tb)
+    dev = lambda R: np.abs(R.T @ R - np.eye(3)).max()  # noqa: E731
+    d0 = dev(Tb[:, :3])
+    assert d0 > 1e-7 and dev(P[:, :3]) < 2 * d0 ** 2 + 1e-15  # quadratic
+    U, _ = scipy.linalg.polar(Tb[:, :3])  # the nearest rotation
+    assert np.abs(P[:, :3] - U).max() < 2 * d0 ** 2 + 1e-15
+    np.testing.assert_array_equal(P[:, 3], Tb[:, 3])
+    # a tangent of SO(3) at R (R S, S skew) on a complex lane passes unchanged
+    S = se3.hat(rng.normal(0, 1, 3))
+    Tc = T.astype(np.complex128)
+    Tc[:, :3] += 1j * 1e-20 * (T[:, :3] @ S)
+    Pc = proposal.polar_step(Tc)
+    np.testing.assert_allclose(Pc.imag[:, :3], 1e-20 * (T[:, :3] @ S), rtol=0, atol=1e-33)
+
+
+def test_cv_seed_keeps_the_deviation_from_so3_bounded():
+    """Without the polar step, T_1 T_2^-1 T_1 multiplies a deviation from SO(3) by about 1 + sqrt(2)
+    per frame (e_k = 2 e_{k-1} + e_{k-2}); with it the deviation stays at rounding level."""
+    rng = np.random.default_rng(5)
+    xi = np.array([0.01, -0.02, 0.015, 0.02, 0.01, -0.01])
+    dev = lambda T: np.abs(T[:, :3].T @ T[:, :3] - np.eye(3)).max()  # noqa: E731
+
+    def drift(T):  # what FP32 increments leave: a deviation of 1e-9
+        E = rng.normal(0, 1e-9, (3, 3))
+        T = T.copy()
+        T[:, :3] = T[:, :3] @ (np.eye(3) + 0.5 * (E + E.T))
+        return T
+
+    for seed_fn in (proposal.cv_seed, lambda T1, T2: se3.compose(T1, se3.compose(se3.inverse(T2), T1))):
+        T2 = se3.se3_exp(rng.normal(0, 0.5, 6))
+        T1 = drift(se3.compose(T2, se3.se3_exp(xi)))
+        worst = 0.0
+        for _ in range(30):
+            T1, T2 = drift(seed_fn(T1, T2)), T1
+            worst = max(worst, dev(T1))
+        if seed_fn is proposal.cv_seed:
+            assert worst < 1e-8
+        else:
+            assert worst > 1e-3  # the plain extrapolation: 2.4^30 * 1e-9
+
+
 def test_cv_seed_repeats_camera_frame_motion():
     rng = np.random.default_rng(1)
     T0 = se3.se3_exp(rng.normal(0, 0.7, 6))
