@@ -289,7 +289,7 @@ __global__ void k_mark_unobserved_lin(Params p, float* Flin, const float* W) {
   const size_t n = vox_count(p);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % p.nx), y = (int)((i / p.nx) % p.ny), z = (int)(i / ((size_t)p.nx * p.ny));
-    if (!(W[vox_index(p, x, y, z)] > 0.f)) Flin[i] = kUnobserved;
+    if (!(W[vox_index(p, x, y, z)] > 0.f)) Flin[i] = unobserved_lin();
   }
 }
 
@@ -300,7 +300,7 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   const unsigned g = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)h->nsm * 32);
   k_fill<<<g, 256, 0, h->s>>>(h->b.F, n, kUnobserved);
   CU(cudaGetLastError());
-  k_fill<<<g, 256, 0, h->s>>>(h->b.F0lin, vox_count(h->p), kUnobserved);
+  k_fill<<<g, 256, 0, h->s>>>(h->b.F0lin, vox_count(h->p), unobserved_lin());
   CU(cudaGetLastError());
   if (Lmax > 1) CU(cudaMemsetAsync(h->b.F + n, 0, sizeof(float) * n * (Lmax - 1), h->s));
   CU(cudaMemsetAsync(h->b.Wt, 0, sizeof(float) * n, h->s));

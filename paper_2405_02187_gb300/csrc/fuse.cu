@@ -243,10 +243,14 @@ __device__ __forceinline__ void integrate_body(const Params& p, const float* __r
 #pragma unroll
     for (int l = 0; l < NL; ++l)
       *reinterpret_cast<float4*>(F + (size_t)l * n + base) = make_float4(f[l][0], f[l][1], f[l][2], f[l][3]);
-    // the march's linear copy of Re F (unchanged voxels rewrite the value they hold in both layouts)
+    // the march's linear copy of Re F (unchanged voxels rewrite the value they hold; an unobserved one
+    // its NaN there)
     const size_t li = (size_t)i0 + (size_t)p.nx * ((size_t)j + (size_t)p.ny * k);
     if (lin4 && i0 + 3 < p.nx) {
-      *reinterpret_cast<float4*>(F0lin + li) = make_float4(f[0][0], f[0][1], f[0][2], f[0][3]);
+      float o[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) o[v] = w[v] > 0.f ? f[0][v] : unobserved_lin();
+      *reinterpret_cast<float4*>(F0lin + li) = make_float4(o[0], o[1], o[2], o[3]);
     } else {
 #pragma unroll
       for (int v = 0; v < 4; ++v)

@@ -18,6 +18,17 @@ constexpr int kNT = 27;              // 21 upper-triangle entries of J J^T + 6 o
 constexpr int kResSys = 12 + 18 * (kMaxLanes - 1);       // offset of the last ICP system in `result`
 constexpr int kResLen = kResSys + kNT * kMaxLanes + 8;   // doubles in `result` (+ loss / grad scratch)
 constexpr float kUnobserved = 2.f;      // Re F of a voxel with W = 0 (observed values lie in [-1, 1])
+// the same in the march's linear copy: a quiet NaN, which every trilinear sample of its cell carries
+__host__ __device__ __forceinline__ float unobserved_lin() {
+#ifdef __CUDA_ARCH__
+  return __int_as_float(0x7fc00000);
+#else
+  const unsigned u = 0x7fc00000u;
+  float f;
+  __builtin_memcpy(&f, &u, sizeof(f));
+  return f;
+#endif
+}
 constexpr float kCellBias = 0.015625f;  // 2^-6 pixel: ICP bilinear-cell tie breaker (first iteration
                                         // evaluates u_hat on integer pixels by construction)
 
@@ -56,6 +67,7 @@ struct Buffers {
   float* F;         // L planes of vox_plane floats: lane 0 = Re F (kUnobserved where W = 0), lane j = Im F (raw)
   float* Wt;        // one plane
   float* F0lin;     // Re F again, in the linear layout x + nx (y + ny z): the ray-cast march's copy
+                    // (unobserved_lin() where W = 0)
   float* depth_in;  // H*W raw input
   float* gated;     // H*W range-gated input (bilateral filter source)
   float* pyr[3];    // range-gated level 0 and its two coarser levels

@@ -8,9 +8,9 @@
 // alpha0 = alpha_m - dalpha F_m / (F_{m+1} - F_m), V_g = r(alpha0), N_g = grad F / |grad F| from
 // central differences of the trilinear F at V_g +- one voxel per axis.
 // Samples outside the volume are invalid, so the march starts and stops at the volume's bounds
-// (widened by one sample), which visits every valid sample in the same order. An unobserved voxel
-// holds F = kUnobserved (> 1, outside the range of any observed average), so a sample's validity
-// and value come from the 8 F loads alone.
+// (widened by one sample), which visits every valid sample in the same order. In the march's linear
+// copy of Re F an unobserved voxel holds a quiet NaN, which the trilinear interpolation carries to the
+// sample: a sample's validity and value come from the 8 loads alone.
 // Two kernels: k_march (real lane only, small register footprint, many warps per SM to hide the
 // gather latency) records per pixel the index of the hit pair's first sample; k_refine re-evaluates
 // the pair and the six normal samples on every lane and writes the model maps.

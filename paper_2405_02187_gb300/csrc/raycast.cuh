@@ -48,27 +48,27 @@ __device__ __forceinline__ bool tri_real(const Params& p, const float* __restric
 }
 
 // The march's sample: validity and real trilinear value from the linear-layout copy of Re F (the
-// brick layout's index arithmetic would cost more than the march's loads, which hit L1).
+// brick layout's index arithmetic would cost more than the march's loads, which hit L1). The cell is
+// inside the volume iff floor(g) lies in [0, n - 2] on every axis (the same test as 0 <= g < n - 1 for
+// finite g; a rounding-down conversion and one unsigned compare per axis). An unobserved corner holds a
+// NaN, which every lerp below carries to the value, so validity is the value being a number.
 __device__ __forceinline__ bool march_real(const Params& p, const float* __restrict__ Flin, float gx, float gy,
                                            float gz, float& val) {
-  if (!(gx >= 0.f && gx < (float)(p.nx - 1) && gy >= 0.f && gy < (float)(p.ny - 1) && gz >= 0.f &&
-        gz < (float)(p.nz - 1)))
+  const int i = __float2int_rd(gx), j = __float2int_rd(gy), k = __float2int_rd(gz);
+  if ((unsigned)i >= (unsigned)(p.nx - 1) || (unsigned)j >= (unsigned)(p.ny - 1) || (unsigned)k >= (unsigned)(p.nz - 1))
     return false;
-  const int i = (int)gx, j = (int)gy, k = (int)gz;  // gx >= 0: truncation is floor
   const unsigned sy = (unsigned)p.nx, sz = (unsigned)p.nx * (unsigned)p.ny;
   const unsigned b = (unsigned)i + sy * (unsigned)j + sz * (unsigned)k;
   const float c000 = __ldg(Flin + b), c100 = __ldg(Flin + b + 1), c010 = __ldg(Flin + b + sy),
               c110 = __ldg(Flin + b + 1 + sy);
   const float c001 = __ldg(Flin + b + sz), c101 = __ldg(Flin + b + 1 + sz), c011 = __ldg(Flin + b + sy + sz),
               c111 = __ldg(Flin + b + 1 + sy + sz);
-  const float mx = fmaxf(fmaxf(fmaxf(c000, c100), fmaxf(c010, c110)), fmaxf(fmaxf(c001, c101), fmaxf(c011, c111)));
-  if (!(mx <= 1.f)) return false;  // an unobserved corner
   const float fx = gx - i, fy = gy - j, fz = gz - k;
   const float x00 = c000 + fx * (c100 - c000), x10 = c010 + fx * (c110 - c010);
   const float x01 = c001 + fx * (c101 - c001), x11 = c011 + fx * (c111 - c011);
   const float y0 = x00 + fy * (x10 - x00), y1 = x01 + fy * (x11 - x01);
   val = y0 + fz * (y1 - y0);
-  return true;
+  return val == val;  // false for a NaN: an unobserved corner
 }
 
 // Imaginary part of the trilinear F on lane plane Fl at the cell of t, with the sample position
