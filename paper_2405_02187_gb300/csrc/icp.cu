@@ -37,12 +37,52 @@ struct Lvl {
 // index of (r, c), r <= c, in the row-major packed upper triangle of a 6x6 matrix
 __host__ __device__ constexpr int up6(int r, int c) { return r * 6 - r * (r - 1) / 2 + (c - r); }
 
+// Double-FP32 numbers (hi + lo, |lo| <= ulp(hi) / 2: about 48 significant bits) for the tail's sums and
+// residuals. GB300's FP64 units make a dependent FP64 operation cost far more than the handful of FP32
+// operations of an error-free transformation: Knuth's two-sum, and the exact product error of an FMA.
+// The _rn intrinsics keep the compiler from contracting a product into a neighbouring sum.
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {  // |a| >= |b|, or a = 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  DF s = two_sum(x.h, y.h);
+  const DF t = two_sum(x.l, y.l);
+  s.l = __fadd_rn(s.l, t.h);
+  s = quick_two_sum(s.h, s.l);
+  s.l = __fadd_rn(s.l, t.l);
+  return quick_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ DF df_add_f(DF x, float y) {
+  DF s = two_sum(x.h, y);
+  s.l = __fadd_rn(s.l, x.l);
+  return quick_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ DF df_neg(DF x) { return {-x.h, -x.l}; }
+// x y for a float y: the high part's exact product (rounded product + FMA residual) and the low part's
+__device__ __forceinline__ DF df_mul_f(DF x, float y) {
+  const float p = __fmul_rn(x.h, y);
+  const float e = fmaf(x.l, y, fmaf(x.h, y, -p));
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float p = __fmul_rn(x.h, y.h);
+  const float e = fmaf(x.h, y.l, fmaf(x.l, y.h, fmaf(x.h, y.h, -p)));
+  return quick_two_sum(p, e);
+}
+
 // The 6x6 solve. A = L D L^T is factored in FP32 (square-root-free Cholesky) and every right-hand
-// side is solved by mixed-precision iterative refinement: x = S(b), r = b - A x in FP64 (A and b are
-// the FP64 sums), x += S(r), with S the FP32 forward/back substitution; one round brings the relative
-// error from ~cond(A) 2^-24 to ~(cond(A) 2^-24)^2. On GB300 every FP64 warp instruction occupies the
-// SM sub-partition's FP64 pipe for ~64-80 cycles whatever the number of active threads, so the FP64
-// steps of the tail run SIMT-parallel: one thread per (system, row) or per matrix element.
+// side is solved by mixed-precision iterative refinement: x = S(b), r = b - A x in double-FP32 (A and b
+// are the double-FP32 sums), x += S(r), with S the FP32 forward/back substitution; one round brings the
+// relative error from ~cond(A) 2^-24 to ~(cond(A) 2^-24)^2. The steps of the tail run SIMT-parallel: one
+// thread per (system, row) or per matrix element.
 struct Ldl32 {
   float L[15];  // strictly lower part, row-major packed: (i, k) for k < i at i(i-1)/2 + k
   float rD[6];  // 1 / D
@@ -114,11 +154,11 @@ struct IcpShared {
   IcpLane sL[kMaxLanes];     // per-lane affine maps of the camera-frame tangent
   float sb0[3];
   int s_cnt[kIcpWarps];
-  double sA[kMaxLanes * kNT];
+  float sAh[kMaxLanes * kNT], sAl[kMaxLanes * kNT];  // the summed normal equations, double-FP32
+  float sx0h[6], sx0l[6];                            // x_0 (refined), double-FP32
   double sx[kMaxLanes][6];
   Ldl32 s_ldl;
-  double s_half[2 * kNT * kMaxLanes];
-  float sAf[kNT * kMaxLanes];
+  float s_halfh[2 * kNT * kMaxLanes], s_halfl[2 * kNT * kMaxLanes];
   float sxf[kMaxLanes][6], srf[kMaxLanes][6], sdf[kMaxLanes][6];
   SeCoefF scf[kMaxLanes];
   float sxs[kMaxLanes][6];
@@ -382,11 +422,11 @@ __device__ __forceinline__ void icp_block_sums(IcpShared& S, int cnt, int L, int
   }
 }
 
-// FP64 cross-block sum of the partials of `ncol` blocks into S.sA (27 L values) and S.s_ncorr. Value v
-// is summed by two threads, one per half of its row: all float4 loads of a half (up to 20, i.e. up to
-// 160 columns) issued together, FP32 sums of 16 partials, FP64 accumulation of those sums, FP64 add of
-// the two halves. Different values sit in different lanes, so each FP64 warp instruction adds 32 values.
-// The order is fixed by the column count alone: every block that runs it gets the same bits.
+// Cross-block sum of the partials of `ncol` blocks into S.sAh / S.sAl (27 L values, double-FP32) and
+// S.s_ncorr. Value v is summed by two threads, one per half of its row: all float4 loads of a half (up
+// to 20, i.e. up to 160 columns) issued together, FP32 sums of 16 partials, double-FP32 accumulation of
+// those sums and of the two halves. The order is fixed by the column count alone: every block that runs
+// it gets the same bits.
 __device__ __forceinline__ void icp_cross_sum(IcpShared& S, const float* __restrict__ partial, int pst, int ncol,
                                               const int* __restrict__ partial_n, int L, int warp, int lid) {
   const int NV = L * kNT;
@@ -412,7 +452,7 @@ __device__ __forceinline__ void icp_cross_sum(IcpShared& S, const float* __restr
     const int v = t >> 1, half = t & 1;
     const float4* row = reinterpret_cast<const float4*>(partial + (size_t)v * pst) + half * h4;
     const int cnt = half ? n4 - h4 : h4;
-    double acc = 0.0;
+    DF acc = {0.f, 0.f};
     for (int c0 = 0; c0 < cnt; c0 += 20) {
       float4 q[20];
 #pragma unroll
@@ -422,69 +462,79 @@ __device__ __forceinline__ void icp_cross_sum(IcpShared& S, const float* __restr
         float f = 0.f;
 #pragma unroll
         for (int j = 4 * g; j < 4 * g + 4; ++j) f += (q[j].x + q[j].y) + (q[j].z + q[j].w);
-        acc += (double)f;
+        acc = df_add_f(acc, f);
       }
     }
-    S.s_half[t] = acc;
+    S.s_halfh[t] = acc.h;
+    S.s_halfl[t] = acc.l;
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < NV; v += blockDim.x) S.sA[v] = S.s_half[2 * v] + S.s_half[2 * v + 1];
+  for (int v = threadIdx.x; v < NV; v += blockDim.x) {
+    const DF a = df_add({S.s_halfh[2 * v], S.s_halfl[2 * v]}, {S.s_halfh[2 * v + 1], S.s_halfl[2 * v + 1]});
+    S.sAh[v] = a.h;
+    S.sAl[v] = a.l;
+  }
   __syncthreads();
 }
 
 // The 6x6 solve of the summed normal equations: factor the real A once, x_0 = A^-1 (-g_0) and
-// x_l = A^-1 (-g_l - A_l x_0) on every lane, each refined once with FP64 residuals. Sets S.s_fail (too
-// few correspondences, A not positive definite, or `skip`) and S.sx.
+// x_l = A^-1 (-g_l - A_l x_0) on every lane, each refined once with double-FP32 residuals. Sets S.s_fail
+// (too few correspondences, A not positive definite, or `skip`) and S.sx.
+__device__ __forceinline__ DF sA_df(const IcpShared& S, int i) { return {S.sAh[i], S.sAl[i]}; }
+
 __device__ __forceinline__ void icp_solve(const Params& p, IcpShared& S, int L, int npx, bool skip, bool update) {
-  const int NV = L * kNT;
   const int t = threadIdx.x;
-  for (int v = t; v < NV; v += blockDim.x) S.sAf[v] = (float)S.sA[v];
-  __syncthreads();
   if (t == 0) {
     int fail = skip;
     if (!fail && (float)S.s_ncorr < p.min_corr_frac * (float)npx) fail = 1;
-    if (!fail && !ldl32(S.sAf, S.s_ldl)) fail = 1;
+    if (!fail && !ldl32(S.sAh, S.s_ldl)) fail = 1;  // the high parts: the sums rounded to FP32
     if (!fail) {
       float b0[6];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) b0[i] = -S.sAf[21 + i];
+      for (int i = 0; i < 6; ++i) b0[i] = -S.sAh[21 + i];
       subst32(S.s_ldl, b0, S.sxf[0]);
     }
     S.s_fail = fail;
   }
   __syncthreads();
   const bool go = update && !S.s_fail;
-  // real lane: residual in FP64 (thread i = row), FP32 correction
+  // real lane: residual -g_0 - A x_0 in double-FP32 (thread i = row), FP32 correction
   if (go && t < 6) {
-    double r = -S.sA[21 + t];
+    DF r = df_neg(sA_df(S, 21 + t));
 #pragma unroll
-    for (int k = 0; k < 6; ++k) r = fma(-S.sA[t <= k ? up6(t, k) : up6(k, t)], (double)S.sxf[0][k], r);
-    S.srf[0][t] = (float)r;
+    for (int k = 0; k < 6; ++k) r = df_add(r, df_neg(df_mul_f(sA_df(S, t <= k ? up6(t, k) : up6(k, t)), S.sxf[0][k])));
+    S.srf[0][t] = r.h;
   }
   __syncthreads();
   if (go && t == 0) subst32(S.s_ldl, S.srf[0], S.sdf[0]);
   __syncthreads();
-  if (go && t < 6) S.sx[0][t] = (double)S.sxf[0][t] + (double)S.sdf[0][t];
+  if (go && t < 6) {
+    const DF x = two_sum(S.sxf[0][t], S.sdf[0][t]);  // exact
+    S.sx0h[t] = x.h;
+    S.sx0l[t] = x.l;
+    S.sx[0][t] = (double)x.h + (double)x.l;
+  }
   __syncthreads();
-  // imaginary lanes: right-hand sides in FP64, thread (l, i)
+  // imaginary lanes: right-hand sides -g_l - A_l x_0 in double-FP32, thread (l, i)
   const int ls = 1 + t / 6, li = t % 6;
   const bool lane_thread = go && t < 6 * (L - 1);
-  double rhs = 0.0;
+  DF rhs = {0.f, 0.f};
   if (lane_thread) {
-    const double* Al = S.sA + ls * kNT;
-    rhs = -Al[21 + li];
+    const int o = ls * kNT;
+    rhs = df_neg(sA_df(S, o + 21 + li));
 #pragma unroll
-    for (int k = 0; k < 6; ++k) rhs = fma(-Al[li <= k ? up6(li, k) : up6(k, li)], S.sx[0][k], rhs);
-    S.srf[ls][li] = (float)rhs;
+    for (int k = 0; k < 6; ++k)
+      rhs = df_add(rhs, df_neg(df_mul(sA_df(S, o + (li <= k ? up6(li, k) : up6(k, li))), DF{S.sx0h[k], S.sx0l[k]})));
+    S.srf[ls][li] = rhs.h;
   }
   __syncthreads();
   if (go && t >= 1 && t < L) subst32(S.s_ldl, S.srf[t], S.sxf[t]);
   __syncthreads();
   if (lane_thread) {
-    double r = rhs;
+    DF r = rhs;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) r = fma(-S.sA[li <= k ? up6(li, k) : up6(k, li)], (double)S.sxf[ls][k], r);
-    S.srf[ls][li] = (float)r;
+    for (int k = 0; k < 6; ++k) r = df_add(r, df_neg(df_mul_f(sA_df(S, li <= k ? up6(li, k) : up6(k, li)), S.sxf[ls][k])));
+    S.srf[ls][li] = r.h;
   }
   __syncthreads();
   if (go && t >= 1 && t < L) subst32(S.s_ldl, S.srf[t], S.sdf[t]);
@@ -596,7 +646,7 @@ __device__ __forceinline__ void icp_body(const Params& p, const Buffers& b, cons
   // ---------------- last block: FP64 cross-block sum, solve, update ----------------
   icp_cross_sum(S, b.partial, pst, gx, b.partial_n, L, warp, lid);
   if (flags & kIcpNoUpdate) {
-    for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) b.result[kResSys + i] = S.sA[i];
+    for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) b.result[kResSys + i] = (double)S.sAh[i] + (double)S.sAl[i];
     if (threadIdx.x == 0) b.status[2] = S.s_ncorr;
     return;
   }
