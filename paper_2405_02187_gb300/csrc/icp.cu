@@ -457,13 +457,15 @@ __device__ __forceinline__ void icp_cross_sum(IcpShared& S, const float* __restr
       float4 q[20];
 #pragma unroll
       for (int j = 0; j < 20; ++j) q[j] = (c0 + j < cnt) ? __ldcg(row + c0 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      float f[5];
 #pragma unroll
       for (int g = 0; g < 5; ++g) {
-        float f = 0.f;
+        f[g] = 0.f;
 #pragma unroll
-        for (int j = 4 * g; j < 4 * g + 4; ++j) f += (q[j].x + q[j].y) + (q[j].z + q[j].w);
-        acc = df_add_f(acc, f);
+        for (int j = 4 * g; j < 4 * g + 4; ++j) f[g] += (q[j].x + q[j].y) + (q[j].z + q[j].w);
       }
+      // the five group sums added as a tree
+      acc = df_add(acc, df_add_f(df_add(two_sum(f[0], f[1]), two_sum(f[2], f[3])), f[4]));
     }
     S.s_halfh[t] = acc.h;
     S.s_halfl[t] = acc.l;
@@ -481,6 +483,12 @@ __device__ __forceinline__ void icp_cross_sum(IcpShared& S, const float* __restr
 // x_l = A^-1 (-g_l - A_l x_0) on every lane, each refined once with double-FP32 residuals. Sets S.s_fail
 // (too few correspondences, A not positive definite, or `skip`) and S.sx.
 __device__ __forceinline__ DF sA_df(const IcpShared& S, int i) { return {S.sAh[i], S.sAl[i]}; }
+
+// base - (p0 + ... + p5) with the products summed as a tree (3 levels instead of a chain of 6)
+__device__ __forceinline__ DF df_sub_sum6(DF base, const DF* pr) {
+  const DF s = df_add(df_add(df_add(pr[0], pr[1]), df_add(pr[2], pr[3])), df_add(pr[4], pr[5]));
+  return df_add(base, df_neg(s));
+}
 
 __device__ __forceinline__ void icp_solve(const Params& p, IcpShared& S, int L, int npx, bool skip, bool update) {
   const int t = threadIdx.x;
@@ -500,10 +508,10 @@ __device__ __forceinline__ void icp_solve(const Params& p, IcpShared& S, int L, 
   const bool go = update && !S.s_fail;
   // real lane: residual -g_0 - A x_0 in double-FP32 (thread i = row), FP32 correction
   if (go && t < 6) {
-    DF r = df_neg(sA_df(S, 21 + t));
+    DF pr[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) r = df_add(r, df_neg(df_mul_f(sA_df(S, t <= k ? up6(t, k) : up6(k, t)), S.sxf[0][k])));
-    S.srf[0][t] = r.h;
+    for (int k = 0; k < 6; ++k) pr[k] = df_mul_f(sA_df(S, t <= k ? up6(t, k) : up6(k, t)), S.sxf[0][k]);
+    S.srf[0][t] = df_sub_sum6(df_neg(sA_df(S, 21 + t)), pr).h;
   }
   __syncthreads();
   if (go && t == 0) subst32(S.s_ldl, S.srf[0], S.sdf[0]);
@@ -521,20 +529,20 @@ __device__ __forceinline__ void icp_solve(const Params& p, IcpShared& S, int L, 
   DF rhs = {0.f, 0.f};
   if (lane_thread) {
     const int o = ls * kNT;
-    rhs = df_neg(sA_df(S, o + 21 + li));
+    DF pr[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
-      rhs = df_add(rhs, df_neg(df_mul(sA_df(S, o + (li <= k ? up6(li, k) : up6(k, li))), DF{S.sx0h[k], S.sx0l[k]})));
+    for (int k = 0; k < 6; ++k) pr[k] = df_mul(sA_df(S, o + (li <= k ? up6(li, k) : up6(k, li))), DF{S.sx0h[k], S.sx0l[k]});
+    rhs = df_sub_sum6(df_neg(sA_df(S, o + 21 + li)), pr);
     S.srf[ls][li] = rhs.h;
   }
   __syncthreads();
   if (go && t >= 1 && t < L) subst32(S.s_ldl, S.srf[t], S.sxf[t]);
   __syncthreads();
   if (lane_thread) {
-    DF r = rhs;
+    DF pr[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) r = df_add(r, df_neg(df_mul_f(sA_df(S, li <= k ? up6(li, k) : up6(k, li)), S.sxf[ls][k])));
-    S.srf[ls][li] = r.h;
+    for (int k = 0; k < 6; ++k) pr[k] = df_mul_f(sA_df(S, li <= k ? up6(li, k) : up6(k, li)), S.sxf[ls][k]);
+    S.srf[ls][li] = df_sub_sum6(rhs, pr).h;
   }
   __syncthreads();
   if (go && t >= 1 && t < L) subst32(S.s_ldl, S.srf[t], S.sdf[t]);
@@ -548,29 +556,40 @@ __device__ __forceinline__ void icp_solve(const Params& p, IcpShared& S, int L, 
 // one element per thread.
 __device__ __forceinline__ void icp_update(IcpShared& S, int L, double* pose) {
   const int t = threadIdx.x;
+  const bool elem = t < 12 * L;
+  // this thread's element (l, e = 4 r + c) reads 7 values of the old pose: loaded first, so that their
+  // latency passes while the increments are formed
+  double te = 0.0, t0c[3] = {0.0, 0.0, 0.0}, tlc[3] = {0.0, 0.0, 0.0};
+  if (elem) {
+    const int l = t / 12, e = t % 12, c = e & 3;
+    te = pose[12 * l + e];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      t0c[q] = pose[4 * q + c];
+      tlc[q] = pose[12 * l + 4 * q + c];
+    }
+  }
   if (t < 6 * L) S.sxs[t / 6][t % 6] = (float)S.sx[t / 6][t % 6];
   __syncthreads();
   if (t < L) se3_coef_lane_f(S.sxs[0], S.sxs[t], S.scf[t]);
   __syncthreads();
-  if (t < 12 * L) {
+  if (elem) {
     const int l = t / 12, e = t % 12;
     S.sdl[l][e] = se3_delta_element(S.sxs[0], S.sxs[l], S.scf[l], l > 0, e);
   }
   __syncthreads();
   double tn = 0.0;
-  if (t < 12 * L) {
+  if (elem) {
     const int l = t / 12, e = t % 12, r = e >> 2, c = e & 3;
-    const double* T0 = pose;
-    const double* Tl = pose + 12 * l;
     // lane 0: T0 + d0 T0; lane l: Tl + dl T0 + d0 Tl (translation column adds the delta's own column)
-    tn = Tl[e] + (double)S.sdl[l][4 * r] * T0[c] + (double)S.sdl[l][4 * r + 1] * T0[4 + c] +
-         (double)S.sdl[l][4 * r + 2] * T0[8 + c] + (c == 3 ? (double)S.sdl[l][4 * r + 3] : 0.0);
+    tn = te + (double)S.sdl[l][4 * r] * t0c[0] + (double)S.sdl[l][4 * r + 1] * t0c[1] +
+         (double)S.sdl[l][4 * r + 2] * t0c[2] + (c == 3 ? (double)S.sdl[l][4 * r + 3] : 0.0);
     if (l > 0)
-      tn += (double)S.sdl[0][4 * r] * Tl[c] + (double)S.sdl[0][4 * r + 1] * Tl[4 + c] +
-            (double)S.sdl[0][4 * r + 2] * Tl[8 + c];
+      tn += (double)S.sdl[0][4 * r] * tlc[0] + (double)S.sdl[0][4 * r + 1] * tlc[1] +
+            (double)S.sdl[0][4 * r + 2] * tlc[2];
   }
   __syncthreads();
-  if (t < 12 * L) pose[t] = tn;
+  if (elem) pose[t] = tn;
   __syncthreads();
 }
 
