@@ -8,8 +8,11 @@ twist of the first pose). Prints one JSON line (rank 0):
 
   value        frames/s with the depth frames resident in HBM (CUDA events on the caller's stream,
                which the library's stream is ordered against), summed over ranks;
-  e2e          frames/s through the public call with pinned host depth in and the pose + derivative
-               block out every frame (host<->device copies inside the timed region);
+  e2e          frames/s through the public calls with pinned host depth in and the pose + derivative
+               block out every frame (host<->device copies inside the timed region): frame k + 1 is
+               submitted (xslam_frame_submit) before frame k's outputs are read (xslam_frame_wait), the
+               way a camera loop runs; `synchronous` is the same through xslam_frame, one frame at a
+               time;
   roofline     the dominant kernel (largest device time per frame in a profiled pass over the same
                frames): algorithmic bytes per launch / its mean launch time, against the measured HBM
                copy bandwidth;
@@ -509,27 +512,40 @@ def run_ours(args, rank, world, local_rank):
     # ---- end to end: pinned host depth in, pose + derivative block out, every frame ----
     host = torch.empty((nf,) + tuple(wl.depth.shape[1:]), dtype=torch.float32, pin_memory=True)
     host.copy_(torch.from_numpy(wl.depth))
-    x = handle()
-    dtw_frame1 = None
-    for k in range(W):
-        pose, dpose, dtw, st = x.frame(host[k], seeds)
-        if k == 1:
-            dtw_frame1 = dtw.copy()
-    torch.cuda.synchronize()
-    barrier()
-    e0.record()
-    dtw_all = {}
-    for k in range(W, W + K):
-        pose, dpose, dtw, st = x.frame(host[k], seeds)
-        dtw_all[k] = dtw
-    e1.record()
-    torch.cuda.synchronize()
-    barrier()
-    ms_e2e = e0.elapsed_time(e1)
-    x.close()
-    ms_e2e = max_over_ranks(ms_e2e, dev)
-    e2e = dict(value=round(replica_throughput(K, world, ms_e2e), 2), unit="frames/s",
-               h2d_bytes_per_step=int(4 * wl.intr.width * wl.intr.height), d2h_bytes_per_step=int(8 * (12 + 18 * L)))
+    ms_e2e, dtw_all, dtw_frame1 = {}, {}, None
+    for mode in ("synchronous", "pipelined"):
+        x = handle()
+        for k in range(W):
+            pose, dpose, dtw, st = x.frame(host[k], seeds)
+            if k == 1:
+                dtw_frame1 = dtw.copy()
+        torch.cuda.synchronize()
+        barrier()
+        e0.record()
+        out = {}
+        if mode == "synchronous":
+            for k in range(W, W + K):
+                out[k] = x.frame(host[k], seeds)[2]
+        else:  # submit frame k, then read frame k - 1: every frame's depth in and outputs out, overlapped
+            prev = None
+            for k in range(W, W + K):
+                t = x.submit(host[k], seeds)
+                if prev is not None:
+                    out[prev[0]] = x.wait(prev[1])[2]
+                prev = (k, t)
+            out[prev[0]] = x.wait(prev[1])[2]
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms_e2e[mode] = max_over_ranks(e0.elapsed_time(e1), dev)
+        x.close()
+        if mode == "synchronous":
+            dtw_all = out
+        else:
+            assert all(np.array_equal(out[k], dtw_all[k]) for k in out), "pipelined frames differ"
+    e2e = dict(value=round(replica_throughput(K, world, ms_e2e["pipelined"]), 2), unit="frames/s",
+               h2d_bytes_per_step=int(4 * wl.intr.width * wl.intr.height), d2h_bytes_per_step=int(8 * (12 + 18 * L)),
+               synchronous=round(replica_throughput(K, world, ms_e2e["synchronous"]), 2))
 
     # ---- beside the headline: the uncomplexified FP32 run (K = 0) and the plain FP64 complex path ----
     x = xslam.XSlam(wl.dims, wl.voxel, wl.trunc, wl.origin, wl.intr, cfg, max_lanes=0)

@@ -147,8 +147,37 @@ xslam_status xslam_frame(xslam_t h, const float* depth, int depth_on_device, con
                          int K, double* pose_out, double* dpose_out, double* dtwist_out);
 
 /* Wait for the handle's work; returns XSLAM_ENOTRACK if any frame since the last xslam_sync failed
- * to track, *n_failed (may be NULL) receives how many. */
+ * to track, *n_failed (may be NULL) receives how many. Frames run through xslam_frame_submit report
+ * their failures to xslam_frame_wait instead and are not counted here. */
 xslam_status xslam_sync(xslam_t h, int* n_failed);
+
+/* Frames that may be submitted and not yet waited for (xslam_frame_submit). */
+#define XSLAM_PIPELINE 4
+
+/*
+ * Pipelined form of xslam_frame (the same Sec. 4.1 step, same arguments, same results bit for bit):
+ * enqueue the frame and return without waiting for it; *ticket receives the frame's number, which
+ * xslam_frame_wait takes to deliver its outputs. This lets a caller submit frame k + 1 before it reads
+ * frame k's pose, so the host's own work, the depth upload and the result read overlap the GPU's
+ * frames. A host depth map (pinned memory for an asynchronous copy) is uploaded on a second stream
+ * into one of two device staging buffers while the frame before runs; the caller keeps it unchanged
+ * until xslam_frame_wait(ticket) returns. A device depth map is copied on the handle's stream.
+ * Frames run in submission order, each from the one before, as xslam_frame runs them; the two calls
+ * may be mixed. Returns XSLAM_ESTATE when XSLAM_PIPELINE frames are outstanding (wait for the oldest
+ * first), and the errors of xslam_frame's argument checks, before anything is enqueued. xslam_reset
+ * finishes and drops the outstanding frames; xslam_destroy finishes them.
+ */
+xslam_status xslam_frame_submit(xslam_t h, const float* depth, int depth_on_device, const xslam_seed* seeds,
+                                int K, long long* ticket);
+
+/*
+ * Wait for submitted frame `ticket` and write its outputs (host arrays, each may be NULL; layout as in
+ * xslam_frame). Tickets are waited for in submission order: `ticket` must be the oldest outstanding
+ * one (XSLAM_EINVAL otherwise). Returns XSLAM_ENOTRACK (outputs filled) if that frame failed to
+ * track, XSLAM_ETIMEOUT if a tensor-core wait of the proposal network ran out during it.
+ */
+xslam_status xslam_frame_wait(xslam_t h, long long ticket, double* pose_out, double* dpose_out,
+                              double* dtwist_out);
 
 /*
  * Ray cast the volume (Sec. 4.1, "Ray casting"; Eq. surface_prediction) at pose lanes T (host,

@@ -67,6 +67,8 @@ extern "C" void xslam_default_config(xslam_config* c) {
   c->icp_stop = 0.f;
 }
 
+static void pipe_free(xslam_t h);  // the frame pipeline's streams, buffers and events (below)
+
 static void drop_graphs(xslam_t h) {
   if (h->g_first) cudaGraphExecDestroy(h->g_first);
   if (h->g_track) cudaGraphExecDestroy(h->g_track);
@@ -233,6 +235,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
 extern "C" xslam_status xslam_destroy(xslam_t h) {
   if (!h) return XSLAM_OK;
   if (h->s) cudaStreamSynchronize(h->s);
+  pipe_free(h);
   drop_graphs(h);
   Buffers& b = h->b;
   cudaFree(b.F); cudaFree(b.Wt); cudaFree(b.F0lin); cudaFree(b.depth_in); cudaFree(b.gated);
@@ -321,6 +324,7 @@ extern "C" xslam_status xslam_reset(xslam_t h) {
   h->p.L = 1;
   drop_graphs(h);
   CU(cudaStreamSynchronize(h->s));
+  h->t_done = h->t_next;  // frames submitted before the reset are finished and their outputs dropped
   return XSLAM_OK;
 }
 
@@ -620,18 +624,28 @@ static xslam_status run_chain(xslam_t h, bool first) {
   return XSLAM_OK;
 }
 
+// the read-out block of a finished frame (host copy of `result`): pose, dpose and dtwist of K lanes
+static void copy_outputs(const double* res, int K, double* pose_out, double* dpose_out, double* dtwist_out) {
+  if (pose_out) memcpy(pose_out, res, sizeof(double) * 12);
+  if (dpose_out) memcpy(dpose_out, res + 12, sizeof(double) * 12 * K);
+  if (dtwist_out) memcpy(dtwist_out, res + 12 + 12 * (kMaxLanes - 1), sizeof(double) * 6 * K);
+}
+
+// the lane checks of a frame call: frame 0 fixes the lanes, later frames must repeat them
+static xslam_status frame_lanes(xslam_t h, const xslam_seed* seeds, int K) {
+  if (K < 0 || K > h->max_lanes) return fail(h, XSLAM_EINVAL, "K must be in 0..max_lanes");
+  if (h->frame == 0) return xslam_set_lanes(h, seeds, K);
+  if (!same_seeds(h, seeds, K)) return fail(h, XSLAM_ESTATE, "seeds must not change after the first frame (xslam_reset first)");
+  return XSLAM_OK;
+}
+
 extern "C" xslam_status xslam_frame(xslam_t h, const float* depth, int depth_on_device, const xslam_seed* seeds, int K,
                                     double* pose_out, double* dpose_out, double* dtwist_out) {
   if (!h) return XSLAM_EINVAL;
   if (!depth) return fail(h, XSLAM_EINVAL, "depth is NULL");
-  if (K < 0 || K > h->max_lanes) return fail(h, XSLAM_EINVAL, "K must be in 0..max_lanes");
-  if (h->frame == 0) {
-    xslam_status st = xslam_set_lanes(h, seeds, K);
-    if (st != XSLAM_OK) return st;
-  } else if (!same_seeds(h, seeds, K)) {
-    return fail(h, XSLAM_ESTATE, "seeds must not change after the first frame (xslam_reset first)");
-  }
-  xslam_status st = enter(h);
+  xslam_status st = frame_lanes(h, seeds, K);
+  if (st != XSLAM_OK) return st;
+  if ((st = enter(h)) != XSLAM_OK) return st;
   if (st != XSLAM_OK) return st;
   if ((st = copy_depth(h, depth, depth_on_device)) != XSLAM_OK) return st;
   if ((st = run_chain(h, h->frame == 0)) != XSLAM_OK) return st;
@@ -647,9 +661,7 @@ extern "C" xslam_status xslam_frame(xslam_t h, const float* depth, int depth_on_
     CU(cudaStreamSynchronize(h->s));
     return fail(h, XSLAM_ETIMEOUT, "a tensor-core wait of the proposal network ran out");
   }
-  if (pose_out) memcpy(pose_out, h->h_result, sizeof(double) * 12);
-  if (dpose_out) memcpy(dpose_out, h->h_result + 12, sizeof(double) * 12 * h->K);
-  if (dtwist_out) memcpy(dtwist_out, h->h_result + 12 + 12 * (kMaxLanes - 1), sizeof(double) * 6 * h->K);
+  copy_outputs(h->h_result, h->K, pose_out, dpose_out, dtwist_out);
   if (h->h_status[1] > 0) {
     CU(cudaMemsetAsync(h->b.status + 1, 0, sizeof(int), h->s));
     CU(cudaStreamSynchronize(h->s));
@@ -669,6 +681,109 @@ extern "C" xslam_status xslam_sync(xslam_t h, int* n_failed) {
   if (h->h_status[4]) return fail(h, XSLAM_ETIMEOUT, "a tensor-core wait of the proposal network ran out");
   if (h->h_status[1] > 0) {
     h->err = "ICP failed to track on some frames";
+    return XSLAM_ENOTRACK;
+  }
+  return XSLAM_OK;
+}
+
+// ---- pipelined frames ----------------------------------------------------------------------------
+static void pipe_free(xslam_t h) {
+  if (h->cs) {
+    cudaStreamSynchronize(h->cs);
+    cudaStreamDestroy(h->cs);
+    h->cs = nullptr;
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (h->stage[i]) cudaFree(h->stage[i]);
+    if (h->ev_h2d[i]) cudaEventDestroy(h->ev_h2d[i]);
+    if (h->ev_used[i]) cudaEventDestroy(h->ev_used[i]);
+    h->stage[i] = nullptr;
+    h->ev_h2d[i] = h->ev_used[i] = nullptr;
+  }
+  for (int i = 0; i < XSLAM_PIPELINE; ++i) {
+    if (h->ev_res[i]) cudaEventDestroy(h->ev_res[i]);
+    h->ev_res[i] = nullptr;
+  }
+  if (h->h_ring) cudaFreeHost(h->h_ring);
+  if (h->h_sring) cudaFreeHost(h->h_sring);
+  h->h_ring = nullptr;
+  h->h_sring = nullptr;
+}
+
+// the copy stream, staging buffers, events and pinned output slots, made by the first submit
+static xslam_status pipe_alloc(xslam_t h) {
+  if (h->h_ring) return XSLAM_OK;
+  const size_t hw = (size_t)h->p.W * h->p.H;
+  bool ok = cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < 2; ++i) {
+    ok = ok && cudaMalloc(&h->stage[i], sizeof(float) * hw) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&h->ev_h2d[i], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&h->ev_used[i], cudaEventDisableTiming) == cudaSuccess;
+  }
+  for (int i = 0; i < XSLAM_PIPELINE; ++i)
+    ok = ok && cudaEventCreateWithFlags(&h->ev_res[i], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaMallocHost(&h->h_sring, sizeof(int) * 8 * XSLAM_PIPELINE) == cudaSuccess;
+  ok = ok && cudaMallocHost(&h->h_ring, sizeof(double) * kResSys * XSLAM_PIPELINE) == cudaSuccess;
+  if (!ok) {
+    pipe_free(h);
+    return fail(h, XSLAM_ENOMEM, "allocation of the frame pipeline failed");
+  }
+  return XSLAM_OK;
+}
+
+extern "C" xslam_status xslam_frame_submit(xslam_t h, const float* depth, int depth_on_device, const xslam_seed* seeds,
+                                           int K, long long* ticket) {
+  if (!h) return XSLAM_EINVAL;
+  if (!depth || !ticket) return fail(h, XSLAM_EINVAL, "depth or ticket is NULL");
+  if (h->t_next - h->t_done >= XSLAM_PIPELINE)
+    return fail(h, XSLAM_ESTATE, "XSLAM_PIPELINE frames are outstanding: wait for the oldest first");
+  xslam_status st = frame_lanes(h, seeds, K);
+  if (st != XSLAM_OK) return st;
+  if ((st = pipe_alloc(h)) != XSLAM_OK) return st;
+  if ((st = enter(h)) != XSLAM_OK) return st;
+  const size_t bytes = sizeof(float) * h->p.W * h->p.H;
+  if (depth_on_device) {
+    CU(cudaMemcpyAsync(h->b.depth_in, depth, bytes, cudaMemcpyDeviceToDevice, h->s));
+  } else {
+    // upload on the copy stream while the frames before run; the frame's stream takes it from there
+    const int i = h->stage_next;
+    h->stage_next ^= 1;
+    CU(cudaStreamWaitEvent(h->cs, h->ev_used[i], 0));  // the frame two back has consumed this buffer
+    CU(cudaMemcpyAsync(h->stage[i], depth, bytes, cudaMemcpyHostToDevice, h->cs));
+    CU(cudaEventRecord(h->ev_h2d[i], h->cs));
+    CU(cudaStreamWaitEvent(h->s, h->ev_h2d[i], 0));
+    CU(cudaMemcpyAsync(h->b.depth_in, h->stage[i], bytes, cudaMemcpyDeviceToDevice, h->s));
+    CU(cudaEventRecord(h->ev_used[i], h->s));
+  }
+  if ((st = run_chain(h, h->frame == 0)) != XSLAM_OK) return st;
+  h->frame += 1;
+  // the frame's read-out block and status words to its slot; the failure and timeout words restart
+  // at 0 for the next frame, so each slot reports its own frame
+  const int slot = (int)(h->t_next % XSLAM_PIPELINE);
+  CU(cudaMemcpyAsync(h->h_ring + (size_t)slot * kResSys, h->b.result, sizeof(double) * kResSys,
+                     cudaMemcpyDeviceToHost, h->s));
+  CU(cudaMemcpyAsync(h->h_sring + 8 * slot, h->b.status, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->s));
+  CU(cudaMemsetAsync(h->b.status + 1, 0, sizeof(int), h->s));
+  CU(cudaMemsetAsync(h->b.status + 4, 0, sizeof(int), h->s));
+  CU(cudaEventRecord(h->ev_res[slot], h->s));
+  h->ring_K[slot] = h->K;
+  *ticket = h->t_next++;
+  return leave(h);
+}
+
+extern "C" xslam_status xslam_frame_wait(xslam_t h, long long ticket, double* pose_out, double* dpose_out,
+                                         double* dtwist_out) {
+  if (!h) return XSLAM_EINVAL;
+  if (h->t_done >= h->t_next || ticket != h->t_done)
+    return fail(h, XSLAM_EINVAL, "ticket is not the oldest outstanding frame");
+  const int slot = (int)(ticket % XSLAM_PIPELINE);
+  CU(cudaEventSynchronize(h->ev_res[slot]));
+  h->t_done += 1;
+  const int* stat = h->h_sring + 8 * slot;
+  if (stat[4]) return fail(h, XSLAM_ETIMEOUT, "a tensor-core wait of the proposal network ran out");
+  copy_outputs(h->h_ring + (size_t)slot * kResSys, h->ring_K[slot], pose_out, dpose_out, dtwist_out);
+  if (stat[1] > 0) {
+    h->err = "ICP failed to track (too few correspondences or singular normal equations)";
     return XSLAM_ENOTRACK;
   }
   return XSLAM_OK;

@@ -29,6 +29,16 @@ struct xslam_s {
   float* model_q = nullptr;    // scratch model maps of xslam_grad (7 lanes)
   double* h_result = nullptr;  // pinned host staging
   int* h_status = nullptr;
+  // pipelined frames (xslam_frame_submit / xslam_frame_wait), allocated by the first submit
+  cudaStream_t cs = nullptr;                  // copy stream of host depth maps
+  float* stage[2] = {};                       // device staging buffers of host depth maps, used in turn
+  cudaEvent_t ev_h2d[2] = {}, ev_used[2] = {};  // staging buffer filled / consumed by its frame
+  int stage_next = 0;
+  double* h_ring = nullptr;                   // pinned outputs: XSLAM_PIPELINE slots of kResSys doubles
+  int* h_sring = nullptr;                     // pinned status words: XSLAM_PIPELINE slots of 8
+  cudaEvent_t ev_res[XSLAM_PIPELINE] = {};    // a slot's outputs are on the host
+  int ring_K[XSLAM_PIPELINE] = {};            // lane count of each slot's frame
+  long long t_next = 0, t_done = 0;           // next ticket handed out, oldest not waited for
   // constant-velocity start and learned proposal (proposal.cu); the network is the caller's
   xslam::PropBuffers q = {};
   struct xslam_mlp_s* mlp = nullptr;

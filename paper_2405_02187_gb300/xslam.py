@@ -13,6 +13,7 @@ import numpy as np
 
 POSE0, POSE, TRUNC, DEPTH, POSE_TRACKED = 0, 1, 2, 3, 4
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTRACK, ESTATE = range(7)
+PIPELINE = 4  # XSLAM_PIPELINE: frames submitted and not yet waited for
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTRACK", 6: "ESTATE"}
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libxslam.so")
 
@@ -60,6 +61,9 @@ SYMBOLS = [
     ("xslam_frame", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Seed), ctypes.c_int,
                                    _c_double_p, _c_double_p, _c_double_p]),
     ("xslam_sync", ctypes.c_int, [ctypes.c_void_p, _c_int_p]),
+    ("xslam_frame_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Seed),
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
+    ("xslam_frame_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, _c_double_p, _c_double_p, _c_double_p]),
     ("xslam_raycast", ctypes.c_int, [ctypes.c_void_p, _c_double_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("xslam_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_double_p, ctypes.c_int, _c_double_p,
                                   _c_double_p, _c_double_p]),
@@ -302,6 +306,7 @@ class XSlam:
     def reset(self):
         self._check(self.lib.xslam_reset(self.h))
         self.K = 0
+        self._inflight = {}
 
     def set_pose(self, T):
         T = np.ascontiguousarray(T, np.float64).reshape(12)
@@ -334,6 +339,43 @@ class XSlam:
         st = self.lib.xslam_frame(self.h, ptr, on_dev, sd, K, _dptr(pose), _dptr(dpose), _dptr(dtw))
         self._check(st, (OK, ENOTRACK))
         self.K = K
+        return pose.reshape(3, 4), dpose[:12 * K].reshape(K, 3, 4), dtw[:6 * K].reshape(K, 6), st
+
+    def submit(self, depth, seeds=()):
+        """Enqueue one frame without waiting (xslam_frame_submit); returns its ticket for wait(). A host
+        depth map (ideally a pinned tensor) is kept referenced until its frame is waited for."""
+        K = len(seeds)
+        sd = _seeds(seeds)
+        n = depth.size if isinstance(depth, np.ndarray) else depth.numel()
+        if n != self.W * self.H:
+            raise ValueError(f"depth has {n} values, expected {self.H} x {self.W}")
+        if isinstance(depth, np.ndarray):
+            depth = np.ascontiguousarray(depth, np.float32)
+            ptr, on_dev = ctypes.c_void_p(depth.ctypes.data), 0
+        elif not depth.is_cuda:
+            assert depth.is_contiguous() and str(depth.dtype) == "torch.float32"
+            ptr, on_dev = ctypes.c_void_p(depth.data_ptr()), 0
+        else:
+            ptr, on_dev = _dev(depth), 1
+        t = ctypes.c_longlong(0)
+        self._check(self.lib.xslam_frame_submit(self.h, ptr, on_dev, sd, K, ctypes.byref(t)))
+        self.K = K
+        if not hasattr(self, "_inflight"):
+            self._inflight = {}
+        self._inflight[t.value] = (depth, K)
+        return t.value
+
+    def wait(self, ticket):
+        """Outputs of a submitted frame (xslam_frame_wait; tickets in submission order): (pose (3,4),
+        dpose (K,3,4), dtwist (K,6), status)."""
+        _, K = self._inflight.get(ticket, (None, self.K))
+        pose = np.zeros(12)
+        dpose = np.zeros(max(1, 12 * K))
+        dtw = np.zeros(max(1, 6 * K))
+        st = self.lib.xslam_frame_wait(self.h, int(ticket), _dptr(pose), _dptr(dpose), _dptr(dtw))
+        if st in (OK, ENOTRACK, ETIMEOUT):
+            self._inflight.pop(ticket, None)
+        self._check(st, (OK, ENOTRACK))
         return pose.reshape(3, 4), dpose[:12 * K].reshape(K, 3, 4), dtw[:6 * K].reshape(K, 6), st
 
     def sync(self):

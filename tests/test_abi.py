@@ -43,6 +43,11 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, name)
 
 
+def test_pipeline_depth_matches_header():
+    src = open(os.path.join(ROOT, "include", "xslam.h")).read()
+    assert int(re.search(r"#define XSLAM_PIPELINE (\d+)", src).group(1)) == xslam.PIPELINE
+
+
 def test_default_config(lib):
     c = xslam.default_config()
     assert c.icp_levels == 3 and list(c.icp_iters)[:3] == [10, 5, 4]
@@ -93,6 +98,8 @@ def test_null_handle_calls(lib):
     assert lib.xslam_destroy(None) == xslam.OK
     assert lib.xslam_frame(None, None, 0, None, 0, None, None, None) == xslam.EINVAL
     assert lib.xslam_sync(None, None) == xslam.EINVAL
+    assert lib.xslam_frame_submit(None, None, 0, None, 0, None) == xslam.EINVAL
+    assert lib.xslam_frame_wait(None, 0, None, None, None) == xslam.EINVAL
 
 
 @pytest.mark.parametrize("kw,msg", [
