@@ -67,7 +67,9 @@ extern "C" void xslam_default_config(xslam_config* c) {
   c->icp_stop = 0.f;
 }
 
-static void pipe_free(xslam_t h);  // the frame pipeline's streams, buffers and events (below)
+// the frame pipeline's copy stream, staging buffers, events and pinned output slots (below)
+static void pipe_free(xslam_t h);
+static xslam_status pipe_alloc(xslam_t h);
 
 static void drop_graphs(xslam_t h) {
   if (h->g_first) cudaGraphExecDestroy(h->g_first);
@@ -215,6 +217,7 @@ extern "C" xslam_status xslam_create(xslam_t* out, int nx, int ny, int nz, float
   if (max_lanes >= 6) ok &= cudaMalloc(&h->model_q, sizeof(float) * hw * (1 + 6 * 7)) == cudaSuccess;
   ok &= cudaMallocHost(&h->h_result, sizeof(double) * kResLen) == cudaSuccess;
   ok &= cudaMallocHost(&h->h_status, sizeof(int) * 8) == cudaSuccess;
+  ok = ok && pipe_alloc(h) == XSLAM_OK;
   if (!ok) return cleanup(XSLAM_ENOMEM, "device or pinned allocation failed");
   *out = h;
   xslam_status st = xslam_reset(h);
@@ -710,9 +713,8 @@ static void pipe_free(xslam_t h) {
   h->h_sring = nullptr;
 }
 
-// the copy stream, staging buffers, events and pinned output slots, made by the first submit
+// the copy stream, staging buffers, events and pinned output slots of xslam_frame_submit (at create)
 static xslam_status pipe_alloc(xslam_t h) {
-  if (h->h_ring) return XSLAM_OK;
   const size_t hw = (size_t)h->p.W * h->p.H;
   bool ok = cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking) == cudaSuccess;
   for (int i = 0; i < 2; ++i) {
@@ -739,7 +741,6 @@ extern "C" xslam_status xslam_frame_submit(xslam_t h, const float* depth, int de
     return fail(h, XSLAM_ESTATE, "XSLAM_PIPELINE frames are outstanding: wait for the oldest first");
   xslam_status st = frame_lanes(h, seeds, K);
   if (st != XSLAM_OK) return st;
-  if ((st = pipe_alloc(h)) != XSLAM_OK) return st;
   if ((st = enter(h)) != XSLAM_OK) return st;
   const size_t bytes = sizeof(float) * h->p.W * h->p.H;
   if (depth_on_device) {
