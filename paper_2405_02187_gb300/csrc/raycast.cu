@@ -11,13 +11,15 @@
 // (widened by one sample), which visits every valid sample in the same order. In the march's linear
 // copy of Re F an unobserved voxel holds a quiet NaN, which the trilinear interpolation carries to the
 // sample: a sample's validity and value come from the 8 loads alone.
-// Two kernels: k_march (real lane only, small register footprint, many warps per SM to hide the
-// gather latency) records per pixel the index of the hit pair's first sample; k_refine re-evaluates
-// the pair and the six normal samples on every lane and writes the model maps.
+// Two kernels: k_march (real lane only; each thread keeps the corner loads of 4 consecutive samples in
+// flight to hide the gather latency) records per pixel the index of the hit pair's first sample; k_refine
+// re-evaluates the pair and the six normal samples on every lane and writes the model maps.
 #include "internal.cuh"
 #include "raycast.cuh"
 
 namespace xslam {
+
+constexpr int kMarchU = 4;  // samples of a ray whose corner loads are in flight together
 
 // (bx, by): this block's coordinates in its trajectory's 2-D grid
 __device__ __forceinline__ void march_body(const Params& p, const float* __restrict__ F, const double* __restrict__ pose,
@@ -48,22 +50,39 @@ __device__ __forceinline__ void march_body(const Params& p, const float* __restr
   }
   const int m_lo = max(p.m0, (int)floorf(lo / p.ray_step) - 1);
   const int m_hi = min(p.m1, (int)ceilf(hi / p.ray_step) + 1);
+  // kMarchU samples per trip: all their corner loads are issued before the first is tested (the march
+  // is bound by the latency of those loads); the samples are then taken in order, as one at a time
   int m_hit = -1;
   bool prev_valid = false, prev_pos = false;
-  for (int m = m_lo; m <= m_hi; ++m) {
-    const float al = m * p.ray_step;
-    float val = 0.f;
-    const bool ok = march_real(p, F, ry.g0x + al * ry.gdx, ry.g0y + al * ry.gdy, ry.g0z + al * ry.gdz, val);
-    if (prev_valid && ok) {
-      const bool pos = val > 0.f;
-      if (prev_pos && !pos) {
-        m_hit = m - 1;
-        break;
-      }
-      if (!prev_pos && pos) break;
+  for (int m0 = m_lo; m0 <= m_hi; m0 += kMarchU) {
+    MarchSample sm[kMarchU];
+#pragma unroll
+    for (int q = 0; q < kMarchU; ++q) {
+      const float al = (m0 + q) * p.ray_step;
+      march_load(p, F, ry.g0x + al * ry.gdx, ry.g0y + al * ry.gdy, ry.g0z + al * ry.gdz, m0 + q <= m_hi, sm[q]);
     }
-    prev_valid = ok;
-    prev_pos = ok && val > 0.f;
+    bool stop = false;
+#pragma unroll
+    for (int q = 0; q < kMarchU; ++q) {
+      if (stop || m0 + q > m_hi) continue;
+      float val;
+      const bool ok = march_value(sm[q], val);
+      if (prev_valid && ok) {
+        const bool pos = val > 0.f;
+        if (prev_pos && !pos) {  // the hit pair: samples m - 1 and m
+          m_hit = m0 + q - 1;
+          stop = true;
+          continue;
+        }
+        if (!prev_pos && pos) {  // from behind a surface into free space: no hit
+          stop = true;
+          continue;
+        }
+      }
+      prev_valid = ok;
+      prev_pos = ok && val > 0.f;
+    }
+    if (stop) break;
   }
   hit[(size_t)v * p.W + u] = m_hit;
 }

@@ -48,27 +48,45 @@ __device__ __forceinline__ bool tri_real(const Params& p, const float* __restric
 }
 
 // The march's sample: validity and real trilinear value from the linear-layout copy of Re F (the
-// brick layout's index arithmetic would cost more than the march's loads, which hit L1). The cell is
-// inside the volume iff floor(g) lies in [0, n - 2] on every axis (the same test as 0 <= g < n - 1 for
-// finite g; a rounding-down conversion and one unsigned compare per axis). An unobserved corner holds a
-// NaN, which every lerp below carries to the value, so validity is the value being a number.
-__device__ __forceinline__ bool march_real(const Params& p, const float* __restrict__ Flin, float gx, float gy,
-                                           float gz, float& val) {
+// brick layout's index arithmetic would cost more than the march's loads, which hit L1), in two parts so
+// that several samples of a ray have their corner loads in flight at once. The cell is inside the volume
+// iff floor(g) lies in [0, n - 2] on every axis (the same test as 0 <= g < n - 1 for finite g; a
+// rounding-down conversion and one unsigned compare per axis). march_load issues the 8 corner loads
+// without a branch: a sample outside the volume (or past the ray's last one, live = false) reads cell 0
+// and is marked out. An unobserved corner holds a NaN, which every lerp of march_value carries to the
+// value, so validity is the sample being in and its value a number.
+struct MarchSample {
+  float c[8];  // corners c[dx + 2 dy + 4 dz]
+  float fx, fy, fz;
+  bool in;
+};
+
+__device__ __forceinline__ void march_load(const Params& p, const float* __restrict__ Flin, float gx, float gy, float gz,
+                                           bool live, MarchSample& s) {
   const int i = __float2int_rd(gx), j = __float2int_rd(gy), k = __float2int_rd(gz);
-  if ((unsigned)i >= (unsigned)(p.nx - 1) || (unsigned)j >= (unsigned)(p.ny - 1) || (unsigned)k >= (unsigned)(p.nz - 1))
-    return false;
+  s.in = live && (unsigned)i < (unsigned)(p.nx - 1) && (unsigned)j < (unsigned)(p.ny - 1) &&
+         (unsigned)k < (unsigned)(p.nz - 1);
   const unsigned sy = (unsigned)p.nx, sz = (unsigned)p.nx * (unsigned)p.ny;
-  const unsigned b = (unsigned)i + sy * (unsigned)j + sz * (unsigned)k;
-  const float c000 = __ldg(Flin + b), c100 = __ldg(Flin + b + 1), c010 = __ldg(Flin + b + sy),
-              c110 = __ldg(Flin + b + 1 + sy);
-  const float c001 = __ldg(Flin + b + sz), c101 = __ldg(Flin + b + 1 + sz), c011 = __ldg(Flin + b + sy + sz),
-              c111 = __ldg(Flin + b + 1 + sy + sz);
-  const float fx = gx - i, fy = gy - j, fz = gz - k;
-  const float x00 = c000 + fx * (c100 - c000), x10 = c010 + fx * (c110 - c010);
-  const float x01 = c001 + fx * (c101 - c001), x11 = c011 + fx * (c111 - c011);
-  const float y0 = x00 + fy * (x10 - x00), y1 = x01 + fy * (x11 - x01);
-  val = y0 + fz * (y1 - y0);
-  return val == val;  // false for a NaN: an unobserved corner
+  const unsigned b = s.in ? (unsigned)i + sy * (unsigned)j + sz * (unsigned)k : 0u;
+  s.fx = gx - i;
+  s.fy = gy - j;
+  s.fz = gz - k;
+  s.c[0] = __ldg(Flin + b);
+  s.c[1] = __ldg(Flin + b + 1);
+  s.c[2] = __ldg(Flin + b + sy);
+  s.c[3] = __ldg(Flin + b + 1 + sy);
+  s.c[4] = __ldg(Flin + b + sz);
+  s.c[5] = __ldg(Flin + b + 1 + sz);
+  s.c[6] = __ldg(Flin + b + sy + sz);
+  s.c[7] = __ldg(Flin + b + 1 + sy + sz);
+}
+
+__device__ __forceinline__ bool march_value(const MarchSample& s, float& val) {
+  const float x00 = s.c[0] + s.fx * (s.c[1] - s.c[0]), x10 = s.c[2] + s.fx * (s.c[3] - s.c[2]);
+  const float x01 = s.c[4] + s.fx * (s.c[5] - s.c[4]), x11 = s.c[6] + s.fx * (s.c[7] - s.c[6]);
+  const float y0 = x00 + s.fy * (x10 - x00), y1 = x01 + s.fy * (x11 - x01);
+  val = y0 + s.fz * (y1 - y0);
+  return s.in && val == val;  // false outside, or for a NaN: an unobserved corner
 }
 
 // Imaginary part of the trilinear F on lane plane Fl at the cell of t, with the sample position
