@@ -227,6 +227,21 @@ __device__ __forceinline__ float warp_transpose_sum(float* v, int lid) {
   return v[0];
 }
 
+// Lane groups of a level: where the level has fewer chunks than the grid has warps (the coarse levels),
+// a chunk's imaginary lanes are split over G warps, each of which forms the chunk's real correspondence
+// itself, so that a chunk's chain of dependent lane loads is about 1/G as long. Group 0 also adds the real
+// sums and the correspondence count. G = 3 from 4 lanes up (two imaginary lanes a group at K = 6), 2 for
+// 3 lanes, 1 for fewer or where G warps a chunk do not fit the grid; then no group is left without a lane.
+__host__ __device__ __forceinline__ int icp_groups(int nchunk, int nwarps, int L) {
+  int G = L >= 4 ? 3 : (L == 3 ? 2 : 1);
+  while (G > 1 && nchunk * G > nwarps) --G;
+  if (G > 1) {
+    const int per = (L - 1 + G - 1) / G;
+    G = (L - 1 + per - 1) / per;
+  }
+  return G;
+}
+
 // The level's chunks c0, c0 + cstride, ... of 32 pixels for this warp (lane `lid` = pixel). For each
 // pixel: the real part (V = D K_l^-1 u, the measured normal for the gate, p' = T V, the projection
 // u_hat = pi(K_l P^-1 p'), the bilinear model vertex q and normal n at u_hat with their slopes in the
@@ -234,10 +249,13 @@ __device__ __forceinline__ float warp_transpose_sum(float* v, int lid) {
 // J from the lane's affine map, its depth perturbation and its own model taps. Each lane's 27 terms
 // (J J^T upper triangle, J r; the tangent lanes J J_l^T + J_l J^T and J r_l + J_l r) are summed over
 // the warp at once (warp_transpose_sum) and added to this warp's sums wacc[lane][27] in shared memory;
-// cnt counts the correspondences.
+// cnt counts the correspondences. The warp is lane group grp of G (icp_groups).
 __device__ __forceinline__ void icp_chunks(const Params& p, const Buffers& b, const Lvl& lv, IcpShared& S, int L,
                                            int warp, int lid, int c0, int cstride, int nchunk, int& cnt,
-                                           float* __restrict__ wacc) {
+                                           float* __restrict__ wacc, int grp, int G) {
+  const int per = (L - 1 + G - 1) / G;  // imaginary lanes of a group
+  const int l_lo = 1 + grp * per, l_hi = min(L, l_lo + per);
+  const bool real_sums = grp == 0;
   const float* D = lv.s == 1 ? b.pyr[0] : (lv.s == 2 ? b.pyr[1] : b.pyr[2]);
   const unsigned hw0 = (unsigned)p.W * (unsigned)p.H;
   const float* mdep = b.model;
@@ -317,7 +335,7 @@ __device__ __forceinline__ void icp_chunks(const Params& p, const Buffers& b, co
     const float nl2 = nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2];
     ok = ok && fabsf(nw[0] * nn[0] + nw[1] * nn[1] + nw[2] * nn[2]) >= p.cos_normal_gate * sqrtf(nl2);
     if (!__any_sync(0xffffffffu, ok)) continue;
-    cnt += ok ? 1 : 0;
+    if (real_sums) cnt += ok ? 1 : 0;
     // a pixel without a correspondence adds zeros: its J and r are zero and its lanes stay finite
     const float m = ok ? 1.f : 0.f;
     const float res = m * (df[0] * nn[0] + df[1] * nn[1] + df[2] * nn[2]);
@@ -335,16 +353,16 @@ __device__ __forceinline__ void icp_chunks(const Params& p, const Buffers& b, co
 #pragma unroll
       for (int r = 27; r < 32; ++r) cv[r] = 0.f;
     }
-    {
+    if (real_sums) {
       const float sum = warp_transpose_sum(cv, lid);
       if (lid < kNT) wacc[lid] += sum;
     }
-    if (L < 2) continue;
+    if (l_lo >= l_hi) continue;
     // what the lanes share: the model pose's P^T T ray for DEPTH lanes, T ray likewise
     const float id0 = ok ? 1.f / d0 : 0.f;
     const float Cray[3] = {(pc[0] - S.sb0[0]) * id0, (pc[1] - S.sb0[1]) * id0, (pc[2] - S.sb0[2]) * id0};
     const float Tray[3] = {(pp[0] - T[3]) * id0, (pp[1] - T[7]) * id0, (pp[2] - T[11]) * id0};
-    for (int l = 1; l < L; ++l) {
+    for (int l = l_lo; l < l_hi; ++l) {
       const float* Tl = S.sT[l];
       const IcpLane& LA = S.sL[l];
       float dDl = p.dD[l];
@@ -645,9 +663,10 @@ __device__ __forceinline__ void icp_body(const Params& p, const Buffers& b, cons
   int cnt = 0;
   const int npx = lv.W * lv.H;
   const int nchunk = (npx + 31) >> 5;
-  if (!s_skip)
-    icp_chunks(p, b, lv, S, L, warp, lid, bx * kIcpWarps + warp, gx * kIcpWarps, nchunk, cnt,
-               icp_wacc + warp * L * kNT);
+  const int G = icp_groups(nchunk, gx * kIcpWarps, L);
+  const int gw = bx * kIcpWarps + warp, nslot = (gx * kIcpWarps) / G;  // chunk slots of G warps each
+  if (!s_skip && gw < nslot * G)
+    icp_chunks(p, b, lv, S, L, warp, lid, gw / G, nslot, nchunk, cnt, icp_wacc + warp * L * kNT, gw % G, G);
 
   const int pst = icp_pstride(gx);
   icp_block_sums(S, cnt, L, warp, lid, icp_wacc, b.partial, pst, bx, gx, b.partial_n);
@@ -734,13 +753,14 @@ cudaError_t icp_configure() {
 }
 
 int icp_blocks(int level_pixels, int L) {
-  (void)L;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // one chunk of 32 pixels per warp at least: small levels get fewer blocks (fewer partials to add)
+  // one chunk of 32 pixels per warp (per lane group) at least: small levels get fewer blocks (fewer
+  // partials to add)
   const int nchunk = (level_pixels + 31) / 32;
-  int nblk = (nchunk + kIcpWarps - 1) / kIcpWarps;
+  const int G = icp_groups(nchunk, sms * kIcpWarps, L);
+  int nblk = (nchunk * G + kIcpWarps - 1) / kIcpWarps;
   if (nblk > sms) nblk = sms;
   if (nblk > kMaxPartials) nblk = kMaxPartials;
   if (nblk < 1) nblk = 1;
