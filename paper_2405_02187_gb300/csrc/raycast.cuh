@@ -53,7 +53,7 @@ __device__ __forceinline__ bool tri_real(const Params& p, const float* __restric
 // iff floor(g) lies in [0, n - 2] on every axis (the same test as 0 <= g < n - 1 for finite g; a
 // rounding-down conversion and one unsigned compare per axis). march_load issues the 8 corner loads
 // without a branch: a sample outside the volume (or past the ray's last one, live = false) reads cell 0
-// and is marked out. An unobserved corner holds a NaN, which every lerp of march_value carries to the
+// (inside the volume: every axis has at least 2 voxels) and is marked out. An unobserved corner holds a NaN, which every lerp of march_value carries to the
 // value, so validity is the sample being in and its value a number.
 struct MarchSample {
   float c[8];  // corners c[dx + 2 dy + 4 dz]
