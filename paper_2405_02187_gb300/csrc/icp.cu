@@ -8,16 +8,16 @@
 // solved and T_{j+1} = exp(x) T_j.
 //
 // GB300 mapping: one launch per Gauss-Newton iteration, blocks of 16 warps, at most one block per SM.
-// A warp takes one chunk of 32 consecutive pixels of the level at a time (a pixel per thread) and
-// computes its real part once, then every lane's tangent in turn from the lane's affine map of the
-// camera-frame point (formed once per launch from the pose lanes) and the lane's own model taps. The 27
-// terms of each lane are summed over the warp right away by a transpose reduction (thread t ends with
-// value t), so a thread holds no accumulators across chunks and warps never wait for each other; the
-// warps' sums go to shared memory, the block's to value-major partials. The last block to finish
-// (ticket counter, no grid-wide wait) adds the partials in FP64, factors the real 6x6 matrix (FP32
-// square-root-free Cholesky with one FP64-residual refinement of every right-hand side), solves the
-// K + 1 right-hand sides (x_0 from the real part, x_j = A^-1 (-g_j - A_j x_0) for each lane) and
-// composes exp(x) T_j on every lane in FP64.
+// A warp takes one chunk of 32 consecutive pixels of the level at a time (a pixel per thread; at a
+// coarse level a chunk's lanes may be split over up to 3 warps, icp_groups), computes its real part,
+// then every lane's tangent in turn from the lane's affine map of the camera-frame point and its own
+// model taps. The 27 terms of each lane are summed over the warp right away by a transpose reduction
+// (thread t ends with value t), so a thread holds no accumulators across chunks and warps never wait
+// for each other; the warps' sums go to shared memory, the block's to value-major partials. The last
+// block to finish (ticket counter, no grid-wide wait) adds the partials in double-FP32, factors the
+// real 6x6 matrix (FP32 square-root-free Cholesky, one refinement of every right-hand side with
+// double-FP32 residuals), solves the K + 1 right-hand sides (x_0 from the real part, x_j = A^-1 (-g_j -
+// A_j x_0) for each lane) and composes exp(x) T_j on every lane (FP32 increment, FP64 composition).
 #include "internal.cuh"
 #include "se3.cuh"
 
