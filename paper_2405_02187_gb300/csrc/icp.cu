@@ -681,7 +681,7 @@ __device__ __forceinline__ void icp_body(const Params& p, const Buffers& b, cons
   __threadfence();
   if (threadIdx.x == 0) *b.ticket = 0u;  // ready for the next launch
 
-  // ---------------- last block: FP64 cross-block sum, solve, update ----------------
+  // ---------------- last block: double-FP32 cross-block sum, solve, update ----------------
   icp_cross_sum(S, b.partial, pst, gx, b.partial_n, L, warp, lid);
   if (flags & kIcpNoUpdate) {
     for (int i = threadIdx.x; i < L * kNT; i += blockDim.x) b.result[kResSys + i] = (double)S.sAh[i] + (double)S.sAl[i];
