@@ -588,9 +588,9 @@ def run_ours(args, rank, world, local_rank):
                      speedup_of_value=round(value / (Kp * world / (ms_plain / 1000.0)), 2),
                      grad_rel_err_fp32_lanes_vs_plain=err, grad_err_frame=last)
 
-    batched = None if args.no_batch else run_batch(args, dev, rank)
-    second = None if args.no_second_order else run_second_order(args, dev, rank)
-    learned = None if args.no_learned else run_learned(args, dev, rank)
+    batched = None if args.no_batch else run_section("batched", run_batch, args, dev, rank)
+    second = None if args.no_second_order else run_section("second_order", run_second_order, args, dev, rank)
+    learned = None if args.no_learned else run_section("learned_proposal", run_learned, args, dev, rank)
 
     # ---- CPU oracle on the host cores (rank 0, N = 1): frame 1 of the same sequence ----
     cpu = None
@@ -645,17 +645,28 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line))
 
 
+def run_section(name, fn, *a):
+    """One of the line's companion sections (no collectives inside): an exception in it is reported in
+    the line as {"error": ...} with its traceback on stderr, and the headline is still printed."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001 - any failure of a companion section
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{name}: {type(e).__name__}: {e}"[:300]}
+
+
 def _batched_summary(b):
-    if not b:
-        return None
+    if not b or "error" in b:
+        return b or None
     return dict(value=b["value"], unit=b["unit"], frames=b["frames"], speedup_vs_sequential=b["speedup_vs_sequential"],
                 latency_ms_median=b["latency_ms_per_frame"]["median"], roofline_frac=b["roofline"]["frac"],
                 tracking_failures=b["tracking_failures"])
 
 
 def _second_summary(s2):
-    if not s2:
-        return None
+    if not s2 or "error" in s2:
+        return s2 or None
     h = s2["hessian"]
     t = s2["tsdf_loss"]
     return dict(newton_recall=s2["newton_eta"].get("recall_1cm_1deg"), newton_median_cm=s2["newton_eta"]["median_cm"],
@@ -669,8 +680,8 @@ def _second_summary(s2):
 
 
 def _learned_summary(lp):
-    if not lp:
-        return None
+    if not lp or "error" in lp:
+        return lp or None
     out = dict(train_ms=lp["train"]["train_ms"], pairs=lp["train"]["pairs"])
     for wname, w in lp.get("walks", {}).items():
         o = dict(start_error_sigma=w["start_error_sigma"])

@@ -1,7 +1,7 @@
 """Host-side measurement logic of bench.py without a GPU: the algorithmic bytes per launch of each
 frame stage against their closed forms at the 640x480, K = 6 workload, the ray cast's distinct voxel
-reads against a brute-force count, and the rule that an ncu traffic record counts only while the kernel
-source it was taken on is unchanged."""
+reads against a brute-force count, the rule that an ncu traffic record counts only while the kernel
+source it was taken on is unchanged, and the line's handling of a failing companion section."""
 import hashlib
 import json
 import os
@@ -125,3 +125,18 @@ def test_committed_traffic_records_name_their_kernel_sources():
         stage = key.split(":")[1]
         assert stage in bench.KERNEL_SRC
         assert len(e["src_sha256_16"]) == 16 and e["dram_bytes_per_launch"] > 0
+
+
+def test_a_failing_companion_section_leaves_the_headline():
+    # a companion section (batched, second order, learned proposal) that raises is reported in the line
+    # as an error object; the line's summaries pass it through instead of failing on its missing keys
+    def boom(*_):
+        raise RuntimeError("no memory")
+
+    r = bench.run_section("batched", boom, None, None, 0)
+    assert r == {"error": "batched: RuntimeError: no memory"}
+    assert bench._batched_summary(r) == r
+    assert bench._second_summary({"error": "e"}) == {"error": "e"}
+    assert bench._learned_summary({"error": "e"}) == {"error": "e"}
+    assert bench._batched_summary(None) is None and bench._learned_summary(None) is None
+    assert bench.run_section("batched", lambda *a: {"value": 1.0}) == {"value": 1.0}
