@@ -34,7 +34,7 @@ typedef struct xslam_s* xslam_t;
 typedef enum {
   XSLAM_OK = 0,
   XSLAM_EINVAL = 1,   /* bad argument or unsupported option                         */
-  XSLAM_ENOMEM = 2,   /* device or host allocation failed (in xslam_create only)    */
+  XSLAM_ENOMEM = 2,   /* device or host allocation failed (create, set_proposal)    */
   XSLAM_ECUDA = 3,    /* a CUDA runtime call failed; see xslam_last_error           */
   XSLAM_ETIMEOUT = 4, /* a device-side wait exceeded its budget                     */
   XSLAM_ENOTRACK = 5, /* soft: ICP failed; the frame was fused at the previous pose */
@@ -111,7 +111,9 @@ void xslam_default_config(xslam_config* cfg);
  * origin_m (voxel centres at origin + (i + 0.5) voxel, linear index x + nx (y + ny z)), truncation
  * distance trunc_m (mu), intrinsics K, options cfg (NULL = defaults), room for up to max_lanes
  * imaginary lanes (0..15), ordered after the CUDA stream cuda_stream (a cudaStream_t; NULL = the
- * legacy default stream). Allocates all device memory the later calls use; no other call allocates.
+ * legacy default stream). Allocates all device memory the later calls use (the frame pipeline
+ * included); no other call allocates, except xslam_set_proposal (include/xslam_mlp.h), which
+ * allocates the attached network's inference buffers.
  * The volume starts unobserved (F = 1, W = 0) and the first frame's pose is the identity until
  * xslam_set_pose. Errors: XSLAM_EINVAL (sizes, intrinsics, lanes, config), XSLAM_ENOMEM, XSLAM_ECUDA.
  */
