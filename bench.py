@@ -626,8 +626,8 @@ def run_ours(args, rank, world, local_rank):
                 ms_per_step=round(ms / K, 4), higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32", data="synthetic", **companions,
                 config=dict(wl_desc(wl, L), parallelism=f"replicas x{world}" if world > 1 else "single GPU",
-                            l2="inputs larger than L2: the TSDF state alone is "
-                               f"{np.prod(wl.dims) * 4 * (L + 1) / 1e6:.0f} MB",
+                            l2="inputs larger than L2: the TSDF state (F lanes and W) alone is "
+                               f"{np.prod(wl.dims) * 4 * (L + 2) / 1e6:.0f} MB",
                             tracking_failures=int(n_fail)),
                 roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(round(launches_per_frame * K)),
                 clocks=clk, stage_ms_per_frame=stage_ms, roofline_stages=roofline_stages,
